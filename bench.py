@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Throughput of the fused hybrid LB/FD step on GB300.
+
+Workload (default): the precision form of the method, 2D D2Q9 on 1024 x 1024
+sites, FP32 state (populations stored as deviations from w_i n0), walls at
+y = 0 and 1023 (bounce-back, T_w = 0.5), Tc = 1, T0 = 1.1, b = 1,
+kappa = -0.025, c = 0.02, Gamma = 0.05, xi = 1e-3, tau = 1, phi i.i.d. uniform
+in [-0.05, 0.05] (synthetic, seeded).  One benchmark step is one time step of
+the method (one lf_step(ctx, 1) call = one fused kernel launch).  The L2 cache
+(129 MB; the state is 2 x 44 MiB) is flushed by writing a 256 MiB buffer
+before every timed step, and each step is timed alone with CUDA events on the
+library's stream, so that every step reads its inputs from HBM.
+
+Metric: MLUPS = 1e-6 x sites x steps / s (million lattice-site updates per
+second), whole job over all ranks.  --impl reference times the FP64 CPU oracle
+on the host cores instead (the only reference this method has).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_SITE = {("fp32", 2): 88, ("fp64", 2): 176, ("fp32", 3): 168, ("fp64", 3): 336}
+METRIC = "coupled LB+FD MLUPS"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ranks():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000):
+    """The FP64 CPU oracle as it stands on a bounded sample: steps of an
+    nx x ny lattice with the workload's physics, for about `seconds`."""
+    from oracle import oracle as O
+
+    cfg = O.make_cfg(nx=nx, ny=ny, xi=xi)
+    st = O.init(cfg)
+    st = O.run(st, 1)   # warm: compile/load, first touch
+    steps, t0 = 0, time.perf_counter()
+    chunk = 1
+    while time.perf_counter() - t0 < seconds and steps < max_steps:
+        st = O.run(st, chunk)
+        steps += chunk
+        el = time.perf_counter() - t0
+        if el < seconds / 4:
+            chunk *= 2
+    el = time.perf_counter() - t0
+    return 1e-6 * nx * ny * steps / el, steps, el, O.threads()
+
+
+def run_reference(args):
+    rank, world, _ = ranks()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+
+    nx = ny = 256
+    cfg = O.make_cfg(nx=nx, ny=ny, xi=1e-3)
+    st = O.init(cfg)
+    for _ in range(args.warmup):
+        st = O.run(st, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = O.run(st, 1)
+    el = time.perf_counter() - t0
+    value = 1e-6 * nx * ny * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "prec1024: 2D D2Q9 lamellar quench between cold walls, sampled as 256x256 per step",
+                   "sites_per_step": nx * ny, "grid": [nx, ny], "xi": 1e-3, "tau": 1.0},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
+                         "sample": f"{args.steps} FP64 oracle steps of a 256x256 lattice (same physics as the "
+                                   f"1024x1024 workload), OpenMP over rows"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_for(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        j = json.load(fh)
+    ent = j.get(kernel_key)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1102_3094_gb300 import lf
+
+    rank, world, local = ranks()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    nx = ny = args.size
+    prec = args.precision
+    sim = lf.Lattice(nx=nx, ny=ny, precision=prec, xi=args.xi, seed=1 + rank, stream=stream, device=dev)
+    N = nx * ny
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            sim.step(1)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = Clocks(local)
+    with clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                starts[k].record(stream)
+                sim.step(1)
+                ends[k].record(stream)
+        barrier()
+    times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(times_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_s = float(t.item())
+    d = sim.diag()
+    value = 1e-6 * N * args.steps * world / total_s
+    ms = 1e3 * total_s / args.steps
+    bps = BYTES_PER_SITE[(prec, 2)]
+    peak, peak_kind = peaks()
+    launches_per_step = 1 + (lf.lf_nsub(args.xi, 2) - 1 if args.xi not in (0.0, math.inf) else 0)
+    kernel_ms = statistics.mean(times_ms) / launches_per_step
+    achieved = bps * N / (kernel_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_for(f"k_step2d_{prec}_{nx}"), "peak_kind": peak_kind,
+            "algorithmic_bytes_per_site": bps, "kernel": "k_step2d (fused phi-chain + LB + FD)",
+            "kernel_ms_mean": kernel_ms, "kernel_ms_median": statistics.median(times_ms) / launches_per_step}
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        tdt = torch.float32 if prec == "fp32" else torch.float64
+        pop_h = torch.empty((9, ny, nx), dtype=tdt, pin_memory=True)
+        phi_h = torch.empty((ny, nx), dtype=tdt, pin_memory=True)
+        T_h = torch.empty((ny, nx), dtype=tdt, pin_memory=True)
+        out_h = torch.empty((ny, nx), dtype=tdt, pin_memory=True)
+        es = pop_h.element_size()
+        lf.lf_fields(sim.ctx, lf.FIELDS["pop"], pop_h.data_ptr(), pop_h.numel() * es, False)
+        lf.lf_fields(sim.ctx, lf.FIELDS["phi"], phi_h.data_ptr(), phi_h.numel() * es, False)
+        lf.lf_fields(sim.ctx, lf.FIELDS["T"], T_h.data_ptr(), T_h.numel() * es, False)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            lf.lf_fields_set(sim.ctx, lf.FIELDS["pop"], pop_h.data_ptr(), pop_h.numel() * es, False)
+            lf.lf_fields_set(sim.ctx, lf.FIELDS["phi"], phi_h.data_ptr(), phi_h.numel() * es, False)
+            lf.lf_fields_set(sim.ctx, lf.FIELDS["T"], T_h.data_ptr(), T_h.numel() * es, False)
+            lf.lf_step(sim.ctx, 1)
+            lf.lf_fields(sim.ctx, lf.FIELDS["phi"], out_h.data_ptr(), out_h.numel() * es, False)
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": 1e-6 * N * args.e2e_steps * world / el, "unit": "MLUPS",
+               "h2d_bytes_per_step": (9 + 2) * N * es, "d2h_bytes_per_step": N * es,
+               "steps": args.e2e_steps,
+               "what": "per step: lf_fields_set of f, phi, T from pinned host, lf_step(1), lf_fields of phi to "
+                       "pinned host"}
+
+    cpu = None
+    if rank == 0 and args.cpu_seconds > 0:
+        rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"{steps} FP64 oracle steps of a 256x256 lattice with the workload's physics "
+                         f"({el:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": f"prec1024: 2D D2Q9 lamellar quench between cold walls, {nx}x{ny}, "
+                                   f"{prec.upper()} state (deviation populations), xi={args.xi}, tau=1",
+                       "sites": N, "l2": "flushed (256 MiB write) before every timed step; each step timed "
+                                         "alone with CUDA events on the library stream",
+                       "parallelism": f"replicas x{world} (one independent lattice per GPU)"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * launches_per_step,
+            "clocks": clk.summary(),
+            "diag_after": {"mass": d["mass"], "mach": d["mach"], "rc": d["rc"]},
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--xi", type=float, default=1e-3)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * lf.h -- C ABI of the GB300 library for the hybrid lattice-Boltzmann /
+ * finite-difference time step of Gonnella, Lamura & Tiribocchi, "Thermal and
+ * hydrodynamic effects in the ordering of lamellar fluids" (arXiv:1102.3094).
+ *
+ * One call of lf_step advances, per lattice site and per step (Sec. 2):
+ *   a    = (T - Tc)/Tc                                       (Eq. aterm)
+ *   mu   = a phi + b phi^3 - kappa nabla^2 phi + c nabla^4 phi (Eq. chem)
+ *   P_ab = phi-dependent pressure tensor of the free energy    (Eq. fren, P_ab)
+ *   F_b  = -d_a P_ab                                           (Eq. ff)
+ *   n, n u = sum f_i, sum f_i e_i + F/2                        (Eq. moment)
+ *   f_i(r + e_i, t+1) = f_i - (f_i - f_i^eq)/tau + F_i         (Eqs. evoleqn,
+ *                                                               latticeforceterm)
+ *   phi(t+1) = phi - d_a(phi u_a) + Gamma nabla^2 mu           (Eq. massdiff)
+ *   T(t+1)   = T + xi nabla^2 T                                (Sec. 2, after
+ *                                                               Eq. massdiff)
+ * on a D2Q9 (d = 2) or D3Q19 (d = 3) lattice with dx = dt = c = 1, c_s^2 = 1/3.
+ * Walls (Sec. 2, boundary paragraph) sit half a spacing outside the first and
+ * last layer along the last axis (y in 2D, z in 3D); the other axes are
+ * periodic.  At the walls: halfway bounce-back for the populations; even
+ * reflection of phi, nabla^2 phi, nabla^4 phi, mu and a (neutral wetting and
+ * exact conservation of phi); no flux of phi through the wall; T held at T_w.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (LF_OK) or a negative LF_E* code; nothing exits, aborts or
+ *     throws across this boundary.  lf_strerror maps a code to a message.
+ *   - "Device" pointers are CUDA device (or managed) addresses of the current
+ *     device, e.g. a torch tensor's data_ptr(); "host" pointers are ordinary
+ *     (pageable or pinned) CPU memory.
+ *   - Field layout is row-major [nz][ny][nx] (x fastest), nz = 1 in 2D;
+ *     populations are [Q][nz][ny][nx] in the order lf_lattice reports.
+ *   - The context owns its device state; no pointer into it escapes.  Caller
+ *     buffers are only read or written during the call that receives them.
+ *   - Work is enqueued on params.stream (a cudaStream_t; 0 = legacy default
+ *     stream).  lf_step returns without waiting; lf_fields, lf_fields_set,
+ *     lf_diag, lf_save and lf_load wait for the stream, with a time limit
+ *     (LF_ETIMEOUT).
+ */
+#ifndef LF_H
+#define LF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define LF_OK          0
+#define LF_EINVAL     -1  /* bad argument (sizes, pointers, enum values)           */
+#define LF_EUNSTABLE  -2  /* parameters outside the explicit schemes' stability    */
+#define LF_ENOMEM     -3  /* device or host allocation failed / workspace too small */
+#define LF_ECUDA      -4  /* a CUDA runtime call or kernel launch failed            */
+#define LF_ENONFINITE -5  /* a NaN or Inf appeared in phi, T or the density         */
+#define LF_ETIMEOUT   -6  /* a bounded wait for the GPU ran out                     */
+#define LF_EIO        -7  /* checkpoint file could not be written / read / matched  */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define LF_FP64 0         /* all state and arithmetic in double                     */
+#define LF_FP32 1         /* state and arithmetic in float; populations stored as
+                             deviations f_i - w_i n0; diagnostics sums in double   */
+
+#define LF_TWALL_LAYERS  0 /* T = T_w held on the first and last layer (default)    */
+#define LF_TWALL_HALFWAY 1 /* every layer evolves; ghost T = 2 T_w - T at the wall  */
+
+#define LF_FIELD_PHI 0    /* order parameter phi                       [N]          */
+#define LF_FIELD_T   1    /* temperature T                             [N]          */
+#define LF_FIELD_RHO 2    /* density n = sum f_i                       [N]          */
+#define LF_FIELD_UX  3    /* velocity u (Eq. moment, with F/2)         [N]          */
+#define LF_FIELD_UY  4
+#define LF_FIELD_UZ  5
+#define LF_FIELD_POP 6    /* populations f_i (full, not deviations)    [Q][N]       */
+#define LF_FIELD_MU  7    /* chemical potential mu (Eq. chem)          [N]          */
+#define LF_FIELD_FX  8    /* force density F (Eq. ff)                  [N]          */
+#define LF_FIELD_FY  9
+#define LF_FIELD_FZ  10
+
+/* ---- configuration ----------------------------------------------------- */
+typedef struct {
+    int     d;            /* 2 or 3                                               */
+    int     pad_;
+    int64_t nx, ny, nz;   /* lattice sizes; nz must be 1 when d = 2               */
+} lf_grid;
+
+typedef struct {
+    int    walls;         /* 1: walls normal to the last axis; 0: fully periodic  */
+    int    t_wall_mode;   /* LF_TWALL_LAYERS or LF_TWALL_HALFWAY                  */
+    double T_w;           /* wall temperature                                     */
+} lf_walls;
+
+typedef struct {
+    double   b, kappa, c; /* free-energy coefficients, Eq. fren (b, c > 0)        */
+    double   Gamma;       /* mobility, Eq. massdiff                               */
+    double   Tc;          /* critical temperature, Eq. aterm (> 0)                */
+    double   T0;          /* initial temperature away from the walls              */
+    double   xi;          /* thermal conductivity; +INFINITY = instant quench     */
+    double   tau;         /* BGK relaxation time (> 1/2)                          */
+    double   n0;          /* initial (reference) density                          */
+    double   phi_amp;     /* initial phi i.i.d. uniform in [-phi_amp, phi_amp)    */
+    uint64_t seed;        /* SplitMix64 seed of the initial phi                   */
+    int      precision;   /* LF_FP64 or LF_FP32                                   */
+    int      hydro;       /* 1: LB coupled; 0: Eq. massdiff without convection    */
+    int      ideal_mode;  /* must be 0: ideal pressure n c_s^2 kept by the LB     */
+    int      pad_;
+    void*    stream;      /* cudaStream_t to enqueue on (borrowed, not owned)     */
+    void*    workspace;   /* optional caller device buffer for all state          */
+    size_t   workspace_bytes; /* its size; see lf_workspace_bytes                 */
+} lf_params;
+
+typedef struct {
+    int64_t step;         /* steps taken since lf_create / the loaded checkpoint  */
+    double  mass;         /* sum n                        (FP64 reduction)        */
+    double  phi_sum;      /* sum phi                                              */
+    double  mom[3];       /* sum n u                                              */
+    double  umax;         /* max |u|                                              */
+    double  mach;         /* umax / c_s (Sec. 2: must stay < 0.1)                 */
+    double  free_energy;  /* phi part of Eq. fren on the lattice                  */
+    double  grad2[3];     /* sum (d_x phi)^2, (d_y phi)^2, (d_z phi)^2 (central)  */
+    double  orient_s;     /* (d <(d_perp phi)^2>/<|grad phi|^2> - 1)/(d - 1)      */
+    double  k_peak;       /* first moment of S(k) over shells above S_peak / 2    */
+    double  s_peak;       /* largest shell average of S(k)                        */
+    int     nonfinite;    /* 1 if a NaN/Inf was seen since creation               */
+    int     pad_;
+} lf_diag_t;
+
+typedef struct lf_ctx lf_ctx;
+
+/* ---- lattice ----------------------------------------------------------- */
+/* Velocity set of the library: fills e[Q*3] (integer components, z = 0 in 2D)
+ * and w[Q] when non-NULL and returns Q (9 for d = 2, 19 for d = 3), or
+ * LF_EINVAL.  Populations in LF_FIELD_POP follow this order.  Sec. 2, text
+ * around Eqs. evoleqn and latticeforceterm (moduli 0, c, sqrt(2) c; weights
+ * 4/9, 1/9, 1/36 in 2D; 1/3, 1/18, 1/36 for D3Q19). */
+int lf_lattice(int d, int* e, double* w);
+
+/* Number of explicit temperature sub-steps per step for this xi and d: the
+ * smallest n with xi/n <= 0.8/(2d) (1 for xi = 0 or +INFINITY). */
+int lf_nsub(double xi, int d);
+
+/* Bytes of device memory one context needs for its state (both ping-pong
+ * copies of f, phi, T, the aux fields and the reduction scratch). */
+int lf_workspace_bytes(const lf_grid* grid, const lf_walls* walls,
+                       const lf_params* params, size_t* bytes);
+
+/* ---- life cycle -------------------------------------------------------- */
+/* Validates the arguments (LF_EINVAL), the stability of the explicit schemes
+ * (LF_EUNSTABLE: tau <= 1/2 with hydro, or Gamma lam (a + kappa lam + c lam^2)
+ * >= 2 for some lattice eigenvalue lam at the largest a in the run), places
+ * the state in params->workspace (if given; LF_ENOMEM if too small) or in its
+ * own device allocation, and enqueues the initial state: phi from SplitMix64,
+ * T = T0 (T_w on the wall layers; T_w everywhere for xi = +INFINITY),
+ * f_i = w_i n0 (u = 0).  *out receives the context (NULL on failure). */
+int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* params,
+              lf_ctx** out);
+
+/* Enqueues nsteps time steps on the context's stream and returns without
+ * waiting.  Returns LF_ENONFINITE if an earlier, completed step saw a NaN/Inf,
+ * LF_ECUDA if a launch failed (including errors of earlier async work). */
+int lf_step(lf_ctx* ctx, int64_t nsteps);
+
+/* Copies one field of the state at the current step into dst.  `bytes`
+ * selects the element type: N*8 (or Q*N*8 for LF_FIELD_POP) gives double,
+ * N*4 (Q*N*4) gives float; anything else is LF_EINVAL.  dst_on_device says
+ * whether dst is a device or a host pointer.  Derived fields (RHO, U*, MU,
+ * F*) are computed from the current state by the same device code the step
+ * uses.  Waits for completion. */
+int lf_fields(lf_ctx* ctx, int which, void* dst, size_t bytes, int dst_on_device);
+
+/* Overwrites PHI, T or POP (full f_i) of the current state from src, with the
+ * same size/type rule as lf_fields.  Used for tests, restarts and fault
+ * injection.  Waits for completion. */
+int lf_fields_set(lf_ctx* ctx, int which, const void* src, size_t bytes, int src_on_device);
+
+/* Diagnostics of the current state (FP64 reductions on the GPU, S(k) by an
+ * FP64 FFT on the GPU).  Waits, bounded.  Returns LF_ENONFINITE (and fills
+ * out) when a NaN/Inf is present. */
+int lf_diag(lf_ctx* ctx, lf_diag_t* out);
+
+/* Per-layer orientation s(h) along the wall normal, h = 0 .. L-1, into the
+ * host array out[L] (L = ny in 2D, nz in 3D). */
+int lf_diag_layers(lf_ctx* ctx, double* out, int64_t L);
+
+/* Shell-averaged structure factor S_b, b = 0 .. nb-1, into host out[nb]
+ * (nb = min lattice size / 2 + 1; S_0 = 0). */
+int lf_structure_factor(lf_ctx* ctx, double* out, int64_t nb);
+
+/* Checkpoint: writes / reads grid, walls, params (except pointers), step and
+ * the full state in the context's precision.  lf_load requires a context
+ * created with the same grid, walls and precision (LF_EIO otherwise). */
+int lf_save(lf_ctx* ctx, const char* path);
+int lf_load(lf_ctx* ctx, const char* path);
+
+/* Current step counter. */
+int64_t lf_step_count(const lf_ctx* ctx);
+
+/* Frees the context's own allocations (not a caller workspace).  NULL is a no-op. */
+void lf_destroy(lf_ctx* ctx);
+
+const char* lf_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_H */

@@ -488,3 +488,11 @@ void or_run(const or_cfg* g, int64_t nsteps, double* f, double* phi, double* T)
     }
     free(f2); free(p2); free(t2);
 }
+
+/* Number of OpenMP threads the oracle's parallel loops use. */
+#ifdef _OPENMP
+#include <omp.h>
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+int or_threads(void) { return 1; }
+#endif

@@ -68,6 +68,8 @@ def _load():
             lib.or_feq.argtypes = [C.c_int, C.c_double, dp, dp]
             lib.or_guo.argtypes = [C.c_int, C.c_double, dp, dp, dp]
             lib.or_collide_site.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+            lib.or_threads.argtypes = []
+            lib.or_threads.restype = C.c_int
             for fn in ("or_init", "or_step", "or_run", "or_aux", "or_feq", "or_guo",
                        "or_collide_site", "or_splitmix64"):
                 getattr(lib, fn).restype = None
@@ -114,6 +116,11 @@ def velocity_set(d: int):
     w = np.zeros(19, np.float64)
     q = lib.or_velocity_set(d, e.reshape(-1), w)
     return e[:q].copy(), w[:q].copy()
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops run on."""
+    return int(_load().or_threads())
 
 
 def splitmix64(seed: int, count: int) -> np.ndarray:

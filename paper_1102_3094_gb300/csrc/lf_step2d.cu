@@ -1,0 +1,347 @@
+// lf_step2d.cu -- one fused pass per time step of the hybrid LB/FD method of
+// arXiv:1102.3094, Sec. 2, on the D2Q9 lattice.
+//
+// A CTA owns a TX x TY tile of sites.  From HBM it reads phi with a halo of 4,
+// T with a halo of 2 and the populations of its tile plus a one-site ring; it
+// writes phi(t+1), T(t+1) of the tile and pushes the post-collision
+// populations to their destinations.  Everything in between lives in shared
+// memory, each stage on a region one site smaller than the one before:
+//
+//   r=4  phi, r=2 T                       (loaded; halo mapped by the walls)
+//   r=3  psi = nabla^2 phi                 (5-point)
+//   r=2  lam = nabla^2 psi = nabla^4 phi;  P_ab (pressure tensor, Sec. 2)
+//   r=1  mu (Eq. chem);  F_b = -d_a P_ab   (Eq. ff, central differences)
+//   r=1  n, u = (sum f e + F/2)/n (Eq. moment); g = phi u;
+//        interior sites: BGK + Guo collision (Eqs. evoleqn, latticeforceterm)
+//        and push streaming with halfway bounce-back at the walls
+//   r=0  phi += -div(g) + Gamma nabla^2 mu (Eq. massdiff); T += dxi nabla^2 T
+//
+// Halo sites are read through the boundary map: x wraps; along y the lattice
+// is either periodic or reflected evenly about the planes half a spacing
+// outside rows 0 and ny-1 (the walls).  Every derived field at a halo site is
+// then computed from the reflected state, which is the wall rule itself.  The
+// one odd quantity, the wall-normal flux g_y, is reflected with a sign flip
+// in the last stage.  Populations are stored as deviations f_i - w_i n0.
+#include "lf_internal.cuh"
+
+namespace lf {
+
+namespace {
+
+__device__ __forceinline__ int wrap_any(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Row index of an unwrapped y along an axis that is either periodic or
+// bounded by two mirror planes (period 2n reflection).
+__device__ __forceinline__ int map_axis(int v, int n, int walls)
+{
+    if (!walls) return wrap_any(v, n);
+    int m = wrap_any(v, 2 * n);
+    return m < n ? m : 2 * n - 1 - m;
+}
+
+template <typename R, int TX, int TY>
+struct Tile {
+    static constexpr int W4 = TX + 8, H4 = TY + 8;
+    static constexpr int W3 = TX + 6, H3 = TY + 6;
+    static constexpr int W2 = TX + 4, H2 = TY + 4;
+    static constexpr int W1 = TX + 2, H1 = TY + 2;
+    static constexpr int PHI = 0;
+    static constexpr int T = PHI + W4 * H4;
+    static constexpr int PSI = T + W2 * H2;
+    static constexpr int LAM = PSI + W3 * H3;
+    static constexpr int P = LAM + W2 * H2;       // Pxx, Pyy, Pxy
+    static constexpr int F = P + 3 * W2 * H2;     // Fx, Fy
+    static constexpr int MU = F + 2 * W1 * H1;
+    static constexpr int G = P;                   // gx, gy reuse the P area
+    static constexpr int TOTAL = MU + W1 * H1;
+    static constexpr size_t BYTES = sizeof(R) * TOTAL;
+    static_assert(2 * W1 * H1 <= 3 * W2 * H2, "g must fit in the P area");
+};
+
+template <typename R, int TX, int TY, int NT, bool AUX>
+__global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
+{
+    using L = D2Q9;
+    using TL = Tile<R, TX, TY>;
+    constexpr int W4 = TL::W4, H4 = TL::H4, W3 = TL::W3, H3 = TL::H3;
+    constexpr int W2 = TL::W2, H2 = TL::H2, W1 = TL::W1, H1 = TL::H1;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    R* sphi = sm + TL::PHI;
+    R* sT = sm + TL::T;
+    R* spsi = sm + TL::PSI;
+    R* slam = sm + TL::LAM;
+    R* sPxx = sm + TL::P;
+    R* sPyy = sPxx + W2 * H2;
+    R* sPxy = sPyy + W2 * H2;
+    R* sFx = sm + TL::F;
+    R* sFy = sFx + W1 * H1;
+    R* smu = sm + TL::MU;
+    R* sgx = sm + TL::G;
+    R* sgy = sgx + W1 * H1;
+
+    const int nx = g.nx, ny = g.ny, pitch = g.pitch, walls = g.walls;
+    const int64_t plane = g.plane;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const R half = R(0.5);
+    bool bad = false;
+
+    // ---- stage 1: phi (r = 4) and T (r = 2) -----------------------------
+    for (int k = threadIdx.x; k < W4 * H4; k += NT) {
+        const int ly = k / W4, lx = k - ly * W4;
+        const int gx = wrap_any(x0 - 4 + lx, nx), gy = map_axis(y0 - 4 + ly, ny, walls);
+        sphi[k] = io.phi_in[(int64_t)gy * pitch + gx];
+    }
+    for (int k = threadIdx.x; k < W2 * H2; k += NT) {
+        const int ly = k / W2, lx = k - ly * W2;
+        const int gx = wrap_any(x0 - 2 + lx, nx), gy = map_axis(y0 - 2 + ly, ny, walls);
+        sT[k] = io.T_in[(int64_t)gy * pitch + gx];
+    }
+    __syncthreads();
+
+    // ---- stage 2: psi = nabla^2 phi (r = 3) ------------------------------
+    for (int k = threadIdx.x; k < W3 * H3; k += NT) {
+        const int ly = k / W3, lx = k - ly * W3;
+        const int c = (ly + 1) * W4 + lx + 1;
+        spsi[k] = sphi[c - 1] + sphi[c + 1] + sphi[c - W4] + sphi[c + W4] - R(4) * sphi[c];
+    }
+    __syncthreads();
+
+    // ---- stage 3: lam = nabla^4 phi and P_ab (r = 2) ---------------------
+    for (int k = threadIdx.x; k < W2 * H2; k += NT) {
+        const int ly = k / W2, lx = k - ly * W2;
+        const int cp = (ly + 2) * W4 + lx + 2;
+        const int cs = (ly + 1) * W3 + lx + 1;
+        const R ph = sphi[cp], psi = spsi[cs];
+        const R lam = spsi[cs - 1] + spsi[cs + 1] + spsi[cs - W3] + spsi[cs + W3] - R(4) * psi;
+        slam[k] = lam;
+        if (AUX || p.hydro) {
+            const R av = (sT[k] - p.Tc) / p.Tc;
+            const R dpx = half * (sphi[cp + 1] - sphi[cp - 1]);
+            const R dpy = half * (sphi[cp + W4] - sphi[cp - W4]);
+            const R dsx = half * (spsi[cs + 1] - spsi[cs - 1]);
+            const R dsy = half * (spsi[cs + W3] - spsi[cs - W3]);
+            const R ph2 = ph * ph;
+            const R iso = av * ph2 * half + R(0.75) * p.b * ph2 * ph2
+                        - p.kappa * (ph * psi + half * (dpx * dpx + dpy * dpy))
+                        + p.c * (ph * lam + half * psi * psi + dpx * dsx + dpy * dsy);
+            sPxx[k] = iso + p.kappa * dpx * dpx - R(2) * p.c * dpx * dsx;
+            sPyy[k] = iso + p.kappa * dpy * dpy - R(2) * p.c * dpy * dsy;
+            sPxy[k] = p.kappa * dpx * dpy - p.c * (dpx * dsy + dpy * dsx);
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 4: mu and F (r = 1) --------------------------------------
+    for (int k = threadIdx.x; k < W1 * H1; k += NT) {
+        const int ly = k / W1, lx = k - ly * W1;
+        const int c2 = (ly + 1) * W2 + lx + 1;
+        const int cs = (ly + 2) * W3 + lx + 2;
+        const int cp = (ly + 3) * W4 + lx + 3;
+        const R ph = sphi[cp];
+        const R av = (sT[c2] - p.Tc) / p.Tc;
+        smu[k] = av * ph + p.b * ph * ph * ph - p.kappa * spsi[cs] + p.c * slam[c2];
+        if (AUX || p.hydro) {
+            sFx[k] = -(half * (sPxx[c2 + 1] - sPxx[c2 - 1]) + half * (sPxy[c2 + W2] - sPxy[c2 - W2]));
+            sFy[k] = -(half * (sPxy[c2 + 1] - sPxy[c2 - 1]) + half * (sPyy[c2 + W2] - sPyy[c2 - W2]));
+        } else {
+            sFx[k] = R(0);
+            sFy[k] = R(0);
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 5: moments, flux g = phi u (r = 1, no corners); interior
+    //      sites collide and push --------------------------------------------
+    for (int k = threadIdx.x; k < W1 * H1; k += NT) {
+        const int ly = k / W1, lx = k - ly * W1;
+        const bool edge_x = (lx == 0 || lx == W1 - 1), edge_y = (ly == 0 || ly == H1 - 1);
+        if (edge_x && edge_y) continue;
+        const int ux = x0 - 1 + lx, uy = y0 - 1 + ly;        // unwrapped position
+        if (walls && (uy < 0 || uy >= ny)) continue;         // ghost row: see stage 6
+        const bool inner = !edge_x && !edge_y;
+        const bool real = inner && ux < nx && uy < ny;
+        if (!p.hydro && !(AUX && real)) {
+            sgx[k] = R(0);
+            sgy[k] = R(0);
+            continue;
+        }
+        const int gx = wrap_any(ux, nx), gy = walls ? uy : wrap_any(uy, ny);
+        const int64_t site = (int64_t)gy * pitch + gx;
+        R df[L::Q];
+        R dn = R(0), jx = R(0), jy = R(0);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            df[i] = io.f_in[i * plane + site];
+            dn += df[i];
+            jx += R(L::ex(i)) * df[i];
+            jy += R(L::ey(i)) * df[i];
+        }
+        const R n = p.n0 + dn;
+        const R Fx = sFx[k], Fy = sFy[k];
+        const R inv_n = R(1) / n;
+        const R vx = p.hydro ? (jx + half * Fx) * inv_n : R(0);
+        const R vy = p.hydro ? (jy + half * Fy) * inv_n : R(0);
+        const R ph = sphi[(ly + 3) * W4 + lx + 3];
+        sgx[k] = ph * vx;
+        sgy[k] = ph * vy;
+        if (!real) continue;
+        bad |= !isfinite(n);
+        if (AUX) {
+            io.rho[site] = n;
+            io.u[0][site] = vx;
+            io.u[1][site] = vy;
+            continue;
+        }
+        if (!p.hydro) continue;
+        // Eq. evoleqn with the Qian equilibrium and Guo's term, in deviation
+        // form: df* = df - (df - dfeq)/tau + F_i,  dfeq = feq - w n0.
+        const R uu = vx * vx + vy * vy;
+        const R uF = vx * Fx + vy * Fy;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const R wi = R(L::w(i));
+            const R eu = R(L::ex(i)) * vx + R(L::ey(i)) * vy;
+            const R eF = R(L::ex(i)) * Fx + R(L::ey(i)) * Fy;
+            const R dfeq = wi * (dn + n * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
+            const R Fi = p.guo * wi * (R(3) * (eF - uF) + R(9) * eu * eF);
+            const R post = df[i] - (df[i] - dfeq) * p.inv_tau + Fi;
+            int tx = ux + L::ex(i);
+            int ty = uy + L::ey(i);
+            if (walls && (ty < 0 || ty >= ny)) {
+                io.f_out[L::opp(i) * plane + site] = post;       // halfway bounce-back
+            } else {
+                tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
+                ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
+                io.f_out[i * plane + (int64_t)ty * pitch + tx] = post;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 6: phi and T updates (r = 0) ------------------------------
+    for (int k = threadIdx.x; k < TX * TY; k += NT) {
+        const int ly = k / TX, lx = k - ly * TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        const int64_t site = (int64_t)gy * pitch + gx;
+        const int c1 = (ly + 1) * W1 + lx + 1;
+        if (AUX) {
+            io.mu[site] = smu[c1];
+            io.F[0][site] = sFx[c1];
+            io.F[1][site] = sFy[c1];
+            continue;
+        }
+        const int cp = (ly + 4) * W4 + lx + 4;
+        const int c2 = (ly + 2) * W2 + lx + 2;
+        const R lapmu = smu[c1 - 1] + smu[c1 + 1] + smu[c1 - W1] + smu[c1 + W1] - R(4) * smu[c1];
+        R div = R(0);
+        if (p.hydro) {
+            R gyu = sgy[c1 + W1], gyd = sgy[c1 - W1];
+            if (walls) {                                     // no flux through the walls
+                if (gy == 0) gyd = -sgy[c1];
+                if (gy == ny - 1) gyu = -sgy[c1];
+            }
+            div = half * (sgx[c1 + 1] - sgx[c1 - 1]) + half * (gyu - gyd);
+        }
+        const R phn = sphi[cp] - div + p.Gamma * lapmu;
+        const R Tc0 = sT[c2];
+        R Tn = Tc0;
+        if (p.t_update) {
+            if (walls && g.t_mode == LF_TWALL_LAYERS && (gy == 0 || gy == ny - 1)) {
+                Tn = p.T_w;
+            } else {
+                R tu = sT[c2 + W2], td = sT[c2 - W2];
+                if (walls && g.t_mode == LF_TWALL_HALFWAY) {
+                    if (gy == 0) td = R(2) * p.T_w - Tc0;
+                    if (gy == ny - 1) tu = R(2) * p.T_w - Tc0;
+                }
+                Tn = Tc0 + p.dxi * (sT[c2 - 1] + sT[c2 + 1] + tu + td - R(4) * Tc0);
+            }
+        }
+        bad |= !isfinite(phn) || !isfinite(Tn);
+        io.phi_out[site] = phn;
+        io.T_out[site] = Tn;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+        *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
+template <typename R, int TX, int TY, int NT, bool AUX>
+cudaError_t launch_cfg(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
+{
+    constexpr size_t bytes = Tile<R, TX, TY>::BYTES;
+    auto kern = k_step2d<R, TX, TY, NT, AUX>;
+    static bool attr_set = false;   // per instantiation; harmless to repeat
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+    kern<<<grid, NT, bytes, s>>>(g, p, io);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Extra temperature sub-steps (xi/nsub each) when nsub > 1.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_tsub2d(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __restrict__ Tout)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int nx = g.nx, ny = g.ny, pitch = g.pitch;
+    const int64_t site = (int64_t)y * pitch + x;
+    const R t0 = Tin[site];
+    if (g.walls && g.t_mode == LF_TWALL_LAYERS && (y == 0 || y == ny - 1)) {
+        Tout[site] = p.T_w;
+        return;
+    }
+    const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+    R td, tu;
+    if (g.walls) {
+        td = y == 0 ? R(2) * p.T_w - t0 : Tin[site - pitch];
+        tu = y == ny - 1 ? R(2) * p.T_w - t0 : Tin[site + pitch];
+    } else {
+        td = Tin[(int64_t)(y == 0 ? ny - 1 : y - 1) * pitch + x];
+        tu = Tin[(int64_t)(y == ny - 1 ? 0 : y + 1) * pitch + x];
+    }
+    Tout[site] = t0 + p.dxi * (Tin[(int64_t)y * pitch + xl] + Tin[(int64_t)y * pitch + xr] + tu + td - R(4) * t0);
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
+{
+    if constexpr (sizeof(R) == 4) {
+        return aux ? launch_cfg<R, 64, 16, 256, true>(g, p, io, s)
+                   : launch_cfg<R, 64, 16, 256, false>(g, p, io, s);
+    } else {
+        return aux ? launch_cfg<R, 32, 16, 256, true>(g, p, io, s)
+                   : launch_cfg<R, 32, 16, 256, false>(g, p, io, s);
+    }
+}
+
+template <typename R>
+cudaError_t launch_tsub(const Geom& g, const Phys<R>& p, const R* Tin, R* Tout, cudaStream_t s)
+{
+    if (g.d != 2) return cudaErrorInvalidValue;
+    dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
+    k_tsub2d<R><<<grd, blk, 0, s>>>(g, p, Tin, Tout);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step2d<float>(const Geom&, const Phys<float>&, const StepIO<float>&, bool, cudaStream_t);
+template cudaError_t launch_step2d<double>(const Geom&, const Phys<double>&, const StepIO<double>&, bool, cudaStream_t);
+template cudaError_t launch_tsub<float>(const Geom&, const Phys<float>&, const float*, float*, cudaStream_t);
+template cudaError_t launch_tsub<double>(const Geom&, const Phys<double>&, const double*, double*, cudaStream_t);
+
+}  // namespace lf

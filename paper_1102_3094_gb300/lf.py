@@ -1,0 +1,278 @@
+"""Thin Python binding of the C ABI in include/lf.h (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``liblf.so``.  Device buffers are torch tensors (``data_ptr()``) and the stream
+is a torch CUDA stream; torch is used for nothing else.  Importing this module
+does not load the library; the first call does, and raises if it is missing
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblf.so")
+
+LF_OK, LF_EINVAL, LF_EUNSTABLE, LF_ENOMEM, LF_ECUDA, LF_ENONFINITE, LF_ETIMEOUT, LF_EIO = 0, -1, -2, -3, -4, -5, -6, -7
+LF_FP64, LF_FP32 = 0, 1
+LF_TWALL_LAYERS, LF_TWALL_HALFWAY = 0, 1
+FIELDS = {"phi": 0, "T": 1, "rho": 2, "ux": 3, "uy": 4, "uz": 5, "pop": 6, "mu": 7, "Fx": 8, "Fy": 9, "Fz": 10}
+
+
+class LFError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class lf_grid(C.Structure):
+    _fields_ = [("d", C.c_int), ("pad_", C.c_int), ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64)]
+
+
+class lf_walls(C.Structure):
+    _fields_ = [("walls", C.c_int), ("t_wall_mode", C.c_int), ("T_w", C.c_double)]
+
+
+class lf_params(C.Structure):
+    _fields_ = [("b", C.c_double), ("kappa", C.c_double), ("c", C.c_double), ("Gamma", C.c_double),
+                ("Tc", C.c_double), ("T0", C.c_double), ("xi", C.c_double), ("tau", C.c_double),
+                ("n0", C.c_double), ("phi_amp", C.c_double), ("seed", C.c_uint64),
+                ("precision", C.c_int), ("hydro", C.c_int), ("ideal_mode", C.c_int), ("pad_", C.c_int),
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class lf_diag_t(C.Structure):
+    _fields_ = [("step", C.c_int64), ("mass", C.c_double), ("phi_sum", C.c_double), ("mom", C.c_double * 3),
+                ("umax", C.c_double), ("mach", C.c_double), ("free_energy", C.c_double),
+                ("grad2", C.c_double * 3), ("orient_s", C.c_double), ("k_peak", C.c_double),
+                ("s_peak", C.c_double), ("nonfinite", C.c_int), ("pad_", C.c_int)]
+
+    def as_dict(self):
+        return {"step": self.step, "mass": self.mass, "phi_sum": self.phi_sum, "mom": list(self.mom),
+                "umax": self.umax, "mach": self.mach, "free_energy": self.free_energy,
+                "grad2": list(self.grad2), "orient_s": self.orient_s, "k_peak": self.k_peak,
+                "s_peak": self.s_peak, "nonfinite": self.nonfinite}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded liblf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it first (__graft_entry__.build()); "
+                                   "there is no CPU fallback")
+            L = C.CDLL(LIB_PATH)
+            vp, sz, i64 = C.c_void_p, C.c_size_t, C.c_int64
+            L.lf_lattice.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.lf_nsub.argtypes = [C.c_double, C.c_int]
+            L.lf_workspace_bytes.argtypes = [C.POINTER(lf_grid), C.POINTER(lf_walls), C.POINTER(lf_params),
+                                             C.POINTER(sz)]
+            L.lf_create.argtypes = [C.POINTER(lf_grid), C.POINTER(lf_walls), C.POINTER(lf_params), C.POINTER(vp)]
+            L.lf_step.argtypes = [vp, i64]
+            L.lf_fields.argtypes = [vp, C.c_int, vp, sz, C.c_int]
+            L.lf_fields_set.argtypes = [vp, C.c_int, vp, sz, C.c_int]
+            L.lf_diag.argtypes = [vp, C.POINTER(lf_diag_t)]
+            L.lf_diag_layers.argtypes = [vp, C.POINTER(C.c_double), i64]
+            L.lf_structure_factor.argtypes = [vp, C.POINTER(C.c_double), i64]
+            L.lf_save.argtypes = [vp, C.c_char_p]
+            L.lf_load.argtypes = [vp, C.c_char_p]
+            L.lf_step_count.argtypes = [vp]
+            L.lf_step_count.restype = i64
+            L.lf_destroy.argtypes = [vp]
+            L.lf_destroy.restype = None
+            L.lf_strerror.argtypes = [C.c_int]
+            L.lf_strerror.restype = C.c_char_p
+            for fn in ("lf_lattice", "lf_nsub", "lf_workspace_bytes", "lf_create", "lf_step", "lf_fields",
+                       "lf_fields_set", "lf_diag", "lf_diag_layers", "lf_structure_factor", "lf_save", "lf_load"):
+                getattr(L, fn).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().lf_strerror(code).decode()
+
+
+def _ok(rc: int, where: str) -> int:
+    if rc < 0:
+        raise LFError(rc, where)
+    return rc
+
+
+# ------------------------------------------------------------------ calls
+def lf_lattice(d: int):
+    e = (C.c_int * 57)()
+    w = (C.c_double * 19)()
+    q = _ok(lib().lf_lattice(d, e, w), "lf_lattice")
+    return np.array(e[: 3 * q], dtype=np.int32).reshape(q, 3), np.array(w[:q])
+
+
+def lf_nsub(xi: float, d: int) -> int:
+    return _ok(lib().lf_nsub(xi, d), "lf_nsub")
+
+
+def lf_workspace_bytes(grid, walls, params) -> int:
+    n = C.c_size_t()
+    _ok(lib().lf_workspace_bytes(C.byref(grid), C.byref(walls), C.byref(params), C.byref(n)), "lf_workspace_bytes")
+    return n.value
+
+
+def lf_create(grid, walls, params) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _ok(lib().lf_create(C.byref(grid), C.byref(walls), C.byref(params), C.byref(ctx)), "lf_create")
+    return ctx
+
+
+def lf_step(ctx, nsteps: int) -> None:
+    _ok(lib().lf_step(ctx, nsteps), "lf_step")
+
+
+def lf_fields(ctx, which: int, dst_ptr: int, nbytes: int, dst_on_device: bool) -> None:
+    _ok(lib().lf_fields(ctx, which, C.c_void_p(dst_ptr), nbytes, int(dst_on_device)), "lf_fields")
+
+
+def lf_fields_set(ctx, which: int, src_ptr: int, nbytes: int, src_on_device: bool) -> None:
+    _ok(lib().lf_fields_set(ctx, which, C.c_void_p(src_ptr), nbytes, int(src_on_device)), "lf_fields_set")
+
+
+def lf_diag(ctx) -> lf_diag_t:
+    out = lf_diag_t()
+    rc = lib().lf_diag(ctx, C.byref(out))
+    if rc < 0 and rc != LF_ENONFINITE:
+        raise LFError(rc, "lf_diag")
+    return out, rc
+
+
+def lf_diag_layers(ctx, L: int) -> np.ndarray:
+    out = np.zeros(L)
+    _ok(lib().lf_diag_layers(ctx, out.ctypes.data_as(C.POINTER(C.c_double)), L), "lf_diag_layers")
+    return out
+
+
+def lf_structure_factor(ctx, nb: int) -> np.ndarray:
+    out = np.zeros(nb)
+    _ok(lib().lf_structure_factor(ctx, out.ctypes.data_as(C.POINTER(C.c_double)), nb), "lf_structure_factor")
+    return out
+
+
+def lf_save(ctx, path: str) -> None:
+    _ok(lib().lf_save(ctx, path.encode()), "lf_save")
+
+
+def lf_load(ctx, path: str) -> None:
+    _ok(lib().lf_load(ctx, path.encode()), "lf_load")
+
+
+def lf_step_count(ctx) -> int:
+    return lib().lf_step_count(ctx)
+
+
+def lf_destroy(ctx) -> None:
+    lib().lf_destroy(ctx)
+
+
+# ------------------------------------------------------- convenience wrapper
+class Lattice:
+    """One simulation context.  Wraps the C calls above; holds the workspace
+    tensor (device memory from torch) and the stream the library enqueues on."""
+
+    def __init__(self, d=2, nx=64, ny=64, nz=1, walls=1, t_wall_mode=0, T_w=0.5, b=1.0, kappa=-0.025,
+                 c=0.02, Gamma=0.05, Tc=1.0, T0=1.1, xi=0.01, tau=1.0, n0=1.0, phi_amp=0.05, seed=1,
+                 precision="fp64", hydro=1, stream=None, device=None, use_torch_workspace=True):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda:0")
+        if d == 2:
+            nz = 1
+        self.grid = lf_grid(d=d, nx=nx, ny=ny, nz=nz)
+        self.walls = lf_walls(walls=walls, t_wall_mode=t_wall_mode, T_w=T_w)
+        self.prec = LF_FP64 if precision in ("fp64", LF_FP64) else LF_FP32
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.params = lf_params(b=b, kappa=kappa, c=c, Gamma=Gamma, Tc=Tc, T0=T0, xi=xi, tau=tau, n0=n0,
+                                phi_amp=phi_amp, seed=seed, precision=self.prec, hydro=hydro, ideal_mode=0,
+                                stream=self.stream.cuda_stream, workspace=None, workspace_bytes=0)
+        self.ws = None
+        if use_torch_workspace:
+            nbytes = lf_workspace_bytes(self.grid, self.walls, self.params)
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.ws.data_ptr()
+            off = (-base) % 256
+            self.params.workspace = base + off
+            self.params.workspace_bytes = nbytes
+        self.ctx = lf_create(self.grid, self.walls, self.params)
+        self.Q = 9 if d == 2 else 19
+        self.shape = (ny, nx) if d == 2 else (nz, ny, nx)
+        self.N = int(np.prod(self.shape))
+
+    # -- state access -------------------------------------------------------
+    def _dtype(self, dtype):
+        return np.float64 if dtype in (None, "fp64", np.float64) else np.float32
+
+    def get(self, name: str, dtype=None, device=False):
+        """Field as a numpy array (host) or a torch tensor (device=True)."""
+        which = FIELDS[name]
+        shp = ((self.Q,) + self.shape) if name == "pop" else self.shape
+        npdt = self._dtype(dtype)
+        if device:
+            tdt = self.torch.float64 if npdt == np.float64 else self.torch.float32
+            out = self.torch.empty(shp, dtype=tdt, device=self.device)
+            lf_fields(self.ctx, which, out.data_ptr(), out.numel() * out.element_size(), True)
+            return out
+        out = np.empty(shp, dtype=npdt)
+        lf_fields(self.ctx, which, out.ctypes.data, out.nbytes, False)
+        return out
+
+    def set(self, name: str, value):
+        which = FIELDS[name]
+        if hasattr(value, "data_ptr"):
+            v = value.contiguous()
+            lf_fields_set(self.ctx, which, v.data_ptr(), v.numel() * v.element_size(), True)
+        else:
+            v = np.ascontiguousarray(value)
+            lf_fields_set(self.ctx, which, v.ctypes.data, v.nbytes, False)
+
+    def step(self, n: int = 1):
+        lf_step(self.ctx, n)
+
+    def diag(self):
+        d, rc = lf_diag(self.ctx)
+        out = d.as_dict()
+        out["rc"] = rc
+        return out
+
+    def layers(self):
+        return lf_diag_layers(self.ctx, self.shape[0])
+
+    def structure_factor(self):
+        return lf_structure_factor(self.ctx, min(self.shape) // 2 + 1)
+
+    def save(self, path):
+        lf_save(self.ctx, path)
+
+    def load(self, path):
+        lf_load(self.ctx, path)
+
+    @property
+    def step_count(self):
+        return lf_step_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+function include/*.h declares, and its pure host logic (lattice tables, the
+temperature sub-step rule, argument and stability validation) agrees with the
+oracle and the documented rules."""
+import ctypes as C
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1102_3094_gb300 import _build, lf
+    _build.build()
+    return lf
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(lf\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function(L):
+    names = _declared_functions()
+    assert len(names) >= 15
+    lib = C.CDLL(L.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_lattice_matches_oracle_set(L, d):
+    e, w = L.lf_lattice(d)
+    eo, wo = O.velocity_set(d)
+    got = {tuple(v): x for v, x in zip(e.tolist(), w)}
+    want = {tuple(v): x for v, x in zip(eo.tolist(), wo)}
+    assert got.keys() == want.keys()
+    for k in got:
+        assert got[k] == pytest.approx(want[k], abs=1e-16)
+
+
+def test_nsub_rule_matches_oracle(L):
+    for d in (2, 3):
+        for xi in [0.0, 1e-4, 1e-3, 0.01, 0.1, 0.13, 0.2, 0.2000001, 0.25, 0.5, 1.0, 3.7, 100.0, math.inf]:
+            assert L.lf_nsub(xi, d) == O.nsub_for(xi, d), (xi, d)
+
+
+def _args(L, **kw):
+    g = L.lf_grid(d=2, nx=64, ny=64, nz=1)
+    w = L.lf_walls(walls=1, t_wall_mode=0, T_w=0.5)
+    p = L.lf_params(b=1.0, kappa=-0.025, c=0.02, Gamma=0.05, Tc=1.0, T0=1.1, xi=0.01, tau=1.0, n0=1.0,
+                    phi_amp=0.05, seed=1, precision=0, hydro=1, ideal_mode=0)
+    for k, v in kw.items():
+        for s in (g, w, p):
+            if hasattr(s, k):
+                setattr(s, k, v)
+    return g, w, p
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(tau=0.5), -2), (dict(tau=0.3), -2), (dict(Gamma=5.0), -2),
+    (dict(d=4), -1), (dict(nx=0), -1), (dict(nz=2), -1), (dict(precision=7), -1),
+    (dict(ideal_mode=1), -1), (dict(Tc=0.0), -1), (dict(xi=-1.0), -1), (dict(xi=float("nan")), -1),
+    (dict(ny=1), -1), (dict(walls=2), -1), (dict(t_wall_mode=3), -1), (dict(b=float("inf")), -1),
+])
+def test_validation_codes(L, kw, code):
+    g, w, p = _args(L, **kw)
+    n = C.c_size_t()
+    rc = L.lib().lf_workspace_bytes(C.byref(g), C.byref(w), C.byref(p), C.byref(n))
+    assert rc == code
+    ctx = C.c_void_p()
+    assert L.lib().lf_create(C.byref(g), C.byref(w), C.byref(p), C.byref(ctx)) == code
+    assert not ctx.value
+
+
+def test_workspace_bytes_scale(L):
+    g, w, p = _args(L)
+    b64 = L.lf_workspace_bytes(g, w, p)
+    p.precision = 1
+    b32 = L.lf_workspace_bytes(g, w, p)
+    # two copies of 9 populations + phi + T, plus 8 aux planes, in the state precision
+    assert b64 > 2 * 11 * 64 * 64 * 8 and b32 < b64
+
+
+def test_strerror_covers_codes(L):
+    for c in range(0, -8, -1):
+        assert L.strerror(c) != "unknown error"

@@ -1,0 +1,71 @@
+"""GPU diagnostics (FP64 reductions, orientation, S(k) by the GPU FFT) against
+the oracle's plain definitions on the same state, and the 2000-step run of the
+64 x 64 case compared with the oracle at the reporting times (structure-factor
+peak position and height within 2%, orientation within 0.02 absolute)."""
+import numpy as np
+import pytest
+
+from oracle import diag as D
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1102_3094_gb300 import lf  # noqa: E402
+
+from test_gpu_step import make_pair, to_oracle_f  # noqa: E402
+
+
+def _oracle_diag(st, cfg):
+    ax = O.aux(st)
+    s = D.sums(ax, st.phi)
+    s["orient"], s["layers"] = D.orientation(st.phi, bool(cfg.walls))
+    kb, Sb, kp, sp = D.structure_factor(st.phi)
+    s["Sb"], s["k_peak"], s["s_peak"] = Sb, kp, sp
+    s["fe"] = D.free_energy(st.phi, st.T, bool(cfg.walls), cfg.b, cfg.kappa, cfg.c, cfg.Tc)
+    return s
+
+
+@pytest.mark.parametrize("case", [dict(nx=64, ny=64, xi=0.01), dict(nx=48, ny=32, walls=0, xi=0.01),
+                                  dict(nx=96, ny=30, xi=0.1), dict(nx=60, ny=36, xi=0.01)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_diag_matches_oracle_definitions(case, prec):
+    sim, cfg, st = make_pair(case, prec, seed=5)
+    ref = _oracle_diag(st, cfg)
+    d = sim.diag()
+    assert d["rc"] == 0
+    rt = 1e-12 if prec == "fp64" else 2e-6   # FP32: the aux fields are FP32
+    assert d["mass"] == pytest.approx(ref["mass"], rel=1e-13 if prec == "fp64" else 1e-6)
+    assert d["phi_sum"] == pytest.approx(ref["phi_sum"], rel=1e-11, abs=1e-11)
+    for a in range(2):
+        assert abs(d["mom"][a] - ref["mom"][a]) < rt * 1e2 * max(1.0, abs(ref["mom"][a]))
+    assert d["umax"] == pytest.approx(ref["umax"], rel=rt * 10)
+    assert d["orient_s"] == pytest.approx(ref["orient"], rel=1e-11, abs=1e-12)
+    assert d["free_energy"] == pytest.approx(ref["fe"], rel=1e-11)
+    assert d["k_peak"] == pytest.approx(ref["k_peak"], rel=1e-10)
+    assert d["s_peak"] == pytest.approx(ref["s_peak"], rel=1e-10)
+    np.testing.assert_allclose(sim.structure_factor(), ref["Sb"], rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(sim.layers(), ref["layers"], rtol=1e-11, atol=1e-12)
+    sim.close()
+
+
+def test_small64_run_statistics_match_oracle():
+    """64 x 64 FP64, 2000 steps, reports every 200 steps."""
+    sim = lf.Lattice(nx=64, ny=64, precision="fp64", xi=0.01)
+    cfg = O.make_cfg(nx=64, ny=64, xi=0.01)
+    st = O.init(cfg)
+    for k in range(10):
+        sim.step(200)
+        st = O.run(st, 200)
+        d = sim.diag()
+        kb, Sb, kp, sp = D.structure_factor(st.phi)
+        s_ref = D.orientation(st.phi, True)[0]
+        assert d["rc"] == 0
+        assert abs(d["k_peak"] / kp - 1) < 0.02, (k, d["k_peak"], kp)
+        assert abs(d["s_peak"] / sp - 1) < 0.02, (k, d["s_peak"], sp)
+        assert abs(d["orient_s"] - s_ref) < 0.02, (k, d["orient_s"], s_ref)
+        assert d["mach"] < 0.1
+    sim.close()

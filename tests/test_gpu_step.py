@@ -1,0 +1,194 @@
+"""GPU parity of the fused step kernels against the FP64 oracle, through the
+C ABI.  Tolerances (max-norm relative error per field, on f (full, not the
+deviations), phi, T, mu, F): 1e-12 in FP64, 2e-6 in FP32, from an identical
+state, one step."""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import diag as D
+from oracle import oracle as O
+from paper_1102_3094_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1102_3094_gb300 import lf  # noqa: E402
+
+TOL = {"fp64": 1e-12, "fp32": 2e-6}
+
+
+def relerr(got, want):
+    s = np.abs(want).max()
+    return np.abs(got - want).max() / (s if s > 0 else 1.0)
+
+
+def perm_to_oracle(d):
+    """index in the oracle's order for each library population."""
+    e, _ = lf.lf_lattice(d)
+    eo, _ = O.velocity_set(d)
+    return [int(np.where((eo == v).all(1))[0][0]) for v in e]
+
+
+def to_oracle_f(f_lib, d):
+    out = np.empty_like(f_lib)
+    for i, j in enumerate(perm_to_oracle(d)):
+        out[j] = f_lib[i]
+    return out
+
+
+def make_pair(case, prec, seed=11):
+    """A GPU lattice and an oracle config with the same parameters, the GPU set
+    to a random state; returns (sim, cfg, oracle_state_read_back)."""
+    kw = dict(synth.BASE)
+    kw.update(case)
+    d = kw.get("d", 2)
+    sim = lf.Lattice(precision=prec, **{k: v for k, v in kw.items() if k not in ("d",)}, d=d)
+    cfg = O.make_cfg(d=d, nx=kw["nx"], ny=kw["ny"], nz=kw.get("nz", 1), walls=kw["walls"],
+                     t_wall_mode=kw["t_wall_mode"], hydro=kw["hydro"], b=kw["b"], kappa=kw["kappa"],
+                     c=kw["c"], Gamma=kw["Gamma"], Tc=kw["Tc"], T0=kw["T0"], T_w=kw["T_w"], xi=kw["xi"],
+                     tau=kw["tau"], n0=kw["n0"], phi_amp=kw["phi_amp"], seed=kw.get("seed", 1))
+    dt = np.float64 if prec == "fp64" else np.float32
+    phi, T, r = synth.random_state(sim.shape, sim.Q, seed, dtype=dt)
+    _, w = lf.lf_lattice(d)
+    f = (w.reshape((-1,) + (1,) * len(sim.shape)) * (1 + r)).astype(dt)
+    if kw["walls"] and kw["t_wall_mode"] == 0:
+        T[0] = kw["T_w"]
+        T[-1] = kw["T_w"]
+    sim.set("phi", phi)
+    sim.set("T", T)
+    sim.set("pop", f)
+    st = O.State(cfg, to_oracle_f(sim.get("pop"), d), sim.get("phi"), sim.get("T"))
+    return sim, cfg, st
+
+
+CASES = [
+    dict(nx=64, ny=64, xi=0.01),                                  # whole tiles
+    dict(nx=70, ny=37, xi=0.01),                                  # ragged in x and y
+    dict(nx=5, ny=3, xi=0.01),                                    # smaller than one tile and the halo
+    dict(nx=48, ny=20, walls=0, xi=0.01),                         # fully periodic
+    dict(nx=33, ny=17, t_wall_mode=1, xi=0.5),                    # halfway T ghost, 3 T sub-steps
+    dict(nx=40, ny=24, hydro=0, xi=0.1),                          # no hydrodynamics
+    dict(nx=130, ny=70, tau=0.6, xi=1e-3),                        # several tiles, low viscosity
+    dict(nx=36, ny=30, xi=math.inf, tau=3.0),                     # instantaneous quench
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny")) + str(c))
+def test_aux_and_step_parity(case, prec):
+    sim, cfg, st = make_pair(case, prec)
+    tol = TOL[prec]
+    d = 2
+    ax = O.aux(st)
+    checks = {"mu": (sim.get("mu"), ax["mu"]), "Fx": (sim.get("Fx"), ax["F"][0]),
+              "Fy": (sim.get("Fy"), ax["F"][1]), "rho": (sim.get("rho"), ax["n"]),
+              "ux": (sim.get("ux"), ax["u"][0]), "uy": (sim.get("uy"), ax["u"][1])}
+    for k, (g, w) in checks.items():
+        if np.abs(w).max() == 0:
+            assert np.abs(g).max() == 0, k
+            continue
+        assert relerr(g, w) < tol, (k, relerr(g, w))
+    sim.step(1)
+    ref = O.step(st)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), d), ref.f)):
+        assert relerr(got, want) < tol, (name, relerr(got, want))
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_init_matches_generator(prec):
+    sim = lf.Lattice(nx=70, ny=37, precision=prec, seed=123)
+    cfg = O.make_cfg(nx=70, ny=37, seed=123)
+    st = O.init(cfg)
+    if prec == "fp64":
+        np.testing.assert_array_equal(sim.get("phi"), st.phi)
+        np.testing.assert_array_equal(sim.get("T"), st.T)
+    else:
+        np.testing.assert_array_equal(sim.get("phi", "fp32"), st.phi.astype(np.float32))
+        np.testing.assert_array_equal(sim.get("T", "fp32"), st.T.astype(np.float32))
+    np.testing.assert_allclose(to_oracle_f(sim.get("pop"), 2), st.f, rtol=0, atol=0)
+    sim.close()
+
+
+def test_multistep_fp64_small64():
+    """200 coupled steps of the 64 x 64 case from the seeded initial state."""
+    sim = lf.Lattice(nx=64, ny=64, precision="fp64")
+    st = O.init(O.make_cfg(nx=64, ny=64))
+    sim.step(200)
+    ref = O.run(st, 200)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), 2), ref.f)):
+        assert relerr(got, want) < 1e-10, (name, relerr(got, want))
+    sim.close()
+
+
+def test_full_size_one_step_fp32():
+    """The 1024 x 1024 FP32 workload, in the launch configuration the benchmark
+    times: one step from the seeded state, every site against the oracle."""
+    kw = synth.WORKLOADS["prec1024"]
+    sim = lf.Lattice(nx=1024, ny=1024, precision="fp32", xi=kw["xi"])
+    cfg = O.make_cfg(nx=1024, ny=1024, xi=kw["xi"])
+    sim.step(3)            # leave the trivial initial populations
+    st = O.State(cfg, to_oracle_f(sim.get("pop"), 2), sim.get("phi"), sim.get("T"))
+    sim.step(1)
+    ref = O.step(st)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), 2), ref.f)):
+        assert relerr(got, want) < 2e-6, (name, relerr(got, want))
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_resume_bit_identical(prec):
+    a = lf.Lattice(nx=70, ny=37, precision=prec)
+    a.step(10)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "ck.bin")
+        a.save(path)
+        a.step(15)
+        b = lf.Lattice(nx=70, ny=37, precision=prec, seed=99)
+        b.load(path)
+        assert b.step_count == 10
+        b.step(15)
+    dt = "fp64" if prec == "fp64" else "fp32"
+    for name in ("phi", "T", "pop"):
+        np.testing.assert_array_equal(a.get(name, dt), b.get(name, dt))
+    assert a.step_count == b.step_count == 25
+    a.close()
+    b.close()
+
+
+def test_nonfinite_is_reported():
+    sim = lf.Lattice(nx=40, ny=24, precision="fp32")
+    phi = sim.get("phi", "fp32")
+    phi[5, 7] = np.nan
+    sim.set("phi", phi)
+    sim.step(1)
+    torch.cuda.synchronize()
+    with pytest.raises(lf.LFError) as ei:
+        sim.step(1)
+    assert ei.value.code == lf.LF_ENONFINITE
+    assert sim.diag()["rc"] == lf.LF_ENONFINITE
+    sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_conservation_2000_steps(prec):
+    sim = lf.Lattice(nx=64, ny=64, precision=prec)
+    d0 = sim.diag()
+    sim.step(2000)
+    d1 = sim.diag()
+    assert d1["rc"] == 0
+    tol_m = 1e-12 if prec == "fp64" else 1e-6
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < tol_m
+    assert abs(d1["phi_sum"] - d0["phi_sum"]) < (1e-11 if prec == "fp64" else 2e-3)
+    assert d1["mach"] < 0.1
+    sim.close()
