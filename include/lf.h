@@ -191,6 +191,18 @@ int lf_structure_factor(lf_ctx* ctx, double* out, int64_t nb);
 int lf_save(lf_ctx* ctx, const char* path);
 int lf_load(lf_ctx* ctx, const char* path);
 
+/* Kernel variant of the step.  Both compute the same step (parity-tested
+ * against the oracle); they differ in how work is mapped to the GPU:
+ *   LF_VARIANT_MARCH (default): one thread per column, a CTA marches down a
+ *     segment of `param` rows (0 = chosen from the lattice size), inputs
+ *     prefetched with cp.async;
+ *   LF_VARIANT_TILE: one CTA per 2D tile, each stage of the step on the whole
+ *     tile in shared memory (`param` ignored).
+ * Returns LF_EINVAL for an unknown variant or a negative param. */
+#define LF_VARIANT_MARCH 0
+#define LF_VARIANT_TILE  1
+int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
+
 /* Current step counter. */
 int64_t lf_step_count(const lf_ctx* ctx);
 

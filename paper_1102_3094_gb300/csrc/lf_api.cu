@@ -62,6 +62,11 @@ int validate(const lf_grid* grid, const lf_walls* walls, const lf_params* p)
     if (walls->walls != 0 && walls->walls != 1) return LF_EINVAL;
     if (walls->t_wall_mode != LF_TWALL_LAYERS && walls->t_wall_mode != LF_TWALL_HALFWAY) return LF_EINVAL;
     if (walls->walls && wall_len(grid) < 2) return LF_EINVAL;
+    {   // kernels index populations with 32-bit offsets: Q * padded sites < 2^31
+        const int64_t pitch = (grid->nx + 31) / 32 * 32;
+        const int64_t Q = grid->d == 2 ? 9 : 19;
+        if (Q * pitch * grid->ny * grid->nz >= ((int64_t)1 << 31)) return LF_EINVAL;
+    }
     if (p->precision != LF_FP64 && p->precision != LF_FP32) return LF_EINVAL;
     if (p->hydro != 0 && p->hydro != 1) return LF_EINVAL;
     if (p->ideal_mode != 0) return LF_EINVAL;
@@ -116,6 +121,7 @@ Phys<R> phys_of(const lf_ctx* c)
     Phys<R> ph;
     ph.b = (R)p.b; ph.kappa = (R)p.kappa; ph.c = (R)p.c; ph.Gamma = (R)p.Gamma; ph.Tc = (R)p.Tc;
     ph.T_w = (R)c->walls.T_w;
+    ph.inv_Tc = (R)(1.0 / p.Tc);
     ph.t_update = !(std::isinf(p.xi) || p.xi == 0.0);
     ph.dxi = ph.t_update ? (R)(p.xi / c->nsub) : R(0);
     ph.inv_tau = (R)(1.0 / p.tau);
@@ -337,6 +343,8 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
     c->g.plane = plane;
     c->g.walls = walls->walls;
     c->g.t_mode = walls->t_wall_mode;
+    c->g.variant = LF_VARIANT_MARCH;
+    c->g.tune = 0;
 
     if (params->workspace) {
         if (params->workspace_bytes < L.total || ((uintptr_t)params->workspace % kAlign) != 0) {
@@ -519,6 +527,14 @@ int lf_structure_factor(lf_ctx* c, double* out, int64_t nb)
 }
 
 int64_t lf_step_count(const lf_ctx* c) { return c ? c->step : -1; }
+
+int lf_set_kernel_variant(lf_ctx* c, int variant, int param)
+{
+    if (!c || (variant != LF_VARIANT_MARCH && variant != LF_VARIANT_TILE) || param < 0) return LF_EINVAL;
+    c->g.variant = variant;
+    c->g.tune = param;
+    return LF_OK;
+}
 
 // ---- checkpoints ----------------------------------------------------------
 namespace {

@@ -26,6 +26,7 @@ constexpr int kBlocks = 152 * 8;   // partial sums: a few waves on 152 SMs
 constexpr int kThreads = 256;
 constexpr int kMaxRadix = 32;
 constexpr int kMaxStages = 40;
+constexpr int kShellSmemBins = 4096;   // shell histogram kept in shared memory up to this many bins
 
 struct Scratch {
     double* part;    // kBlocks * DQ_N
@@ -211,23 +212,28 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// e^{-2 pi i num / den}
-__device__ __forceinline__ double2 twiddle(int64_t num, int64_t den)
-{
-    double s, c;
-    sincospi(-2.0 * (double)(num % den) / (double)den, &s, &c);
-    return make_double2(c, s);
-}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// multiply by -i
+__device__ __forceinline__ double2 cmul_mi(double2 a) { return make_double2(a.y, -a.x); }
 
 // C lines of length n per CTA; line l starts at (l / inner) * outer_stride +
-// (l % inner) * inner_stride and has element stride `es`.
+// (l % inner) * inner_stride and has element stride `es`.  Shared memory:
+// the twiddle table tw[j] = e^{-2 pi i j / n}, j < n, then the C lines.
 __global__ void k_fft_lines(double2* data, FftPlan plan, int64_t es, int64_t nlines, int64_t inner,
                             int64_t inner_stride, int64_t outer_stride, int C)
 {
-    extern __shared__ double2 buf[];
+    extern __shared__ double2 smem_fft[];
     const int n = plan.n;
+    double2* tw = smem_fft;
+    double2* buf = smem_fft + n;
     const int64_t l0 = (int64_t)blockIdx.x * C;
     const int nl = (int)((nlines - l0) < C ? (nlines - l0) : C);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * (double)j / (double)n, &sn, &cs);
+        tw[j] = make_double2(cs, sn);
+    }
     // digit-reversed load
     for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
         int c, j;
@@ -249,20 +255,36 @@ __global__ void k_fft_lines(double2* data, FftPlan plan, int64_t es, int64_t nli
     for (int st = 0; st < plan.nst; ++st) {
         const int r = plan.radix[st];
         const int nb = n / r;
+        const int stride = n / (m * r);          // tw index step of W_{m r}
         for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) {
             const int c = t / nb, bi = t - c * nb;
             const int grp = bi / m, k = bi - grp * m;
-            const int base = c * n + grp * m * r + k;
-            double2 y[kMaxRadix];
-            for (int s = 0; s < r; ++s) y[s] = cmul(buf[base + s * m], twiddle((int64_t)k * s, (int64_t)m * r));
-            for (int q = 0; q < r; ++q) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int s = 0; s < r; ++s) {
-                    const double2 w = twiddle((int64_t)q * s, r);
-                    acc.x += y[s].x * w.x - y[s].y * w.y;
-                    acc.y += y[s].x * w.y + y[s].y * w.x;
+            double2* b = buf + c * n + grp * m * r + k;
+            if (r == 2) {
+                const double2 y0 = b[0], y1 = cmul(b[m], tw[k * stride]);
+                b[0] = cadd(y0, y1);
+                b[m] = csub(y0, y1);
+            } else if (r == 4) {
+                const double2 y0 = b[0];
+                const double2 y1 = cmul(b[m], tw[k * stride]);
+                const double2 y2 = cmul(b[2 * m], tw[2 * k * stride]);
+                const double2 y3 = cmul(b[3 * m], tw[3 * k * stride]);
+                const double2 a0 = cadd(y0, y2), a1 = csub(y0, y2);
+                const double2 b0 = cadd(y1, y3), b1 = cmul_mi(csub(y1, y3));
+                b[0] = cadd(a0, b0);
+                b[m] = cadd(a1, b1);
+                b[2 * m] = csub(a0, b0);
+                b[3 * m] = csub(a1, b1);
+            } else {
+                double2 y[kMaxRadix];
+                y[0] = b[0];
+                for (int s2 = 1; s2 < r; ++s2) y[s2] = cmul(b[s2 * m], tw[k * s2 * stride]);
+                const int wr = n / r;            // tw index step of W_r
+                for (int q = 0; q < r; ++q) {
+                    double2 acc = y[0];
+                    for (int s2 = 1; s2 < r; ++s2) acc = cadd(acc, cmul(y[s2], tw[((q * s2) % r) * wr]));
+                    b[q * m] = acc;
                 }
-                buf[base + q * m] = acc;
             }
         }
         __syncthreads();
@@ -298,6 +320,13 @@ __device__ __forceinline__ double kfreq2(int64_t i, int64_t n, int64_t lmin)
 
 __global__ void k_shells(Geom g, const double2* __restrict__ X, int64_t lmin, int64_t B, double* bins)
 {
+    extern __shared__ double hist[];            // 2 (B + 1) doubles when B <= kShellSmemBins
+    const bool local = B <= kShellSmemBins;
+    if (local) {
+        for (int i = threadIdx.x; i < 2 * (B + 1); i += blockDim.x) hist[i] = 0.0;
+        __syncthreads();
+    }
+    double* h = local ? hist : bins;
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         if (k == 0) continue;
@@ -308,8 +337,13 @@ __global__ void k_shells(Geom g, const double2* __restrict__ X, int64_t lmin, in
         const int64_t b = (int64_t)floor(sqrt(r2) + 0.5);
         if (b < 1 || b > B) continue;
         const double2 v = X[k];
-        atomicAdd(&bins[2 * b], (v.x * v.x + v.y * v.y) / (double)N);
-        atomicAdd(&bins[2 * b + 1], 1.0);
+        atomicAdd(&h[2 * b], (v.x * v.x + v.y * v.y) / (double)N);
+        atomicAdd(&h[2 * b + 1], 1.0);
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * (B + 1); i += blockDim.x)
+            if (hist[i] != 0.0) atomicAdd(&bins[i], hist[i]);
     }
 }
 
@@ -337,7 +371,7 @@ bool enqueue_sk(const DiagInput& in, const Scratch& sc, cudaStream_t s, cudaErro
     const int sizes[3] = {g.nx, g.ny, g.nz};
     FftPlan plans[3];
     for (int a = 0; a < g.d; ++a) {
-        if (!make_plan(sizes[a], &plans[a]) || sizes[a] > 8192) return false;
+        if (!make_plan(sizes[a], &plans[a]) || sizes[a] > 4096) return false;   // line + twiddles fit in smem
     }
     *err = cudaSuccess;
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
@@ -352,7 +386,7 @@ bool enqueue_sk(const DiagInput& in, const Scratch& sc, cudaStream_t s, cudaErro
         if (a == 0) { nlines = N / n; inner = 1; inner_stride = 0; outer_stride = n; es = 1; }
         else if (a == 1) { nlines = N / n; inner = g.nx; inner_stride = 1; outer_stride = (int64_t)g.nx * g.ny; es = g.nx; }
         else { nlines = N / n; inner = (int64_t)g.nx * g.ny; inner_stride = 1; outer_stride = 0; es = (int64_t)g.nx * g.ny; }
-        const size_t smem = sizeof(double2) * (size_t)C * n;
+        const size_t smem = sizeof(double2) * (size_t)(C + 1) * n;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) { *err = e; return true; }
@@ -361,7 +395,12 @@ bool enqueue_sk(const DiagInput& in, const Scratch& sc, cudaStream_t s, cudaErro
         k_fft_lines<<<blocks, kThreads, smem, s>>>(sc.fft, plans[a], es, nlines, inner, inner_stride, outer_stride, C);
     }
     cudaMemsetAsync(sc.bins, 0, sizeof(double) * 2 * (B + 1), s);
-    k_shells<<<grid_n(N), kThreads, 0, s>>>(g, sc.fft, lmin, B, sc.bins);
+    const size_t hs = B <= kShellSmemBins ? sizeof(double) * 2 * (B + 1) : 0;
+    if (hs > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_shells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs);
+        if (e != cudaSuccess) { *err = e; return true; }
+    }
+    k_shells<<<grid_n(N), kThreads, hs, s>>>(g, sc.fft, lmin, B, sc.bins);
     *err = cudaGetLastError();
     return true;
 }

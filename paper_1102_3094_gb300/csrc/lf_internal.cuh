@@ -61,12 +61,15 @@ struct Geom {
     int64_t plane;   // pitch * ny * nz elements
     int walls;
     int t_mode;
+    int variant;     // LF_VARIANT_MARCH or LF_VARIANT_TILE
+    int tune;        // march: rows per segment (0 = automatic)
 };
 
 // Physical parameters in the precision of the arithmetic.
 template <typename R>
 struct Phys {
     R b, kappa, c, Gamma, Tc, T_w;
+    R inv_Tc;     // 1 / Tc
     R dxi;        // xi / nsub: explicit Euler step of the temperature
     R inv_tau;    // 1 / tau
     R guo;        // 1 - 1/(2 tau)

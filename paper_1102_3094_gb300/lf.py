@@ -86,6 +86,8 @@ def lib():
             L.lf_structure_factor.argtypes = [vp, C.POINTER(C.c_double), i64]
             L.lf_save.argtypes = [vp, C.c_char_p]
             L.lf_load.argtypes = [vp, C.c_char_p]
+            L.lf_set_kernel_variant.argtypes = [vp, C.c_int, C.c_int]
+            L.lf_set_kernel_variant.restype = C.c_int
             L.lf_step_count.argtypes = [vp]
             L.lf_step_count.restype = i64
             L.lf_destroy.argtypes = [vp]
@@ -173,6 +175,13 @@ def lf_load(ctx, path: str) -> None:
     _ok(lib().lf_load(ctx, path.encode()), "lf_load")
 
 
+LF_VARIANT_MARCH, LF_VARIANT_TILE = 0, 1
+
+
+def lf_set_kernel_variant(ctx, variant: int, param: int = 0) -> None:
+    _ok(lib().lf_set_kernel_variant(ctx, variant, param), "lf_set_kernel_variant")
+
+
 def lf_step_count(ctx) -> int:
     return lib().lf_step_count(ctx)
 
@@ -243,6 +252,9 @@ class Lattice:
 
     def step(self, n: int = 1):
         lf_step(self.ctx, n)
+
+    def set_variant(self, variant: str = "march", param: int = 0):
+        lf_set_kernel_variant(self.ctx, LF_VARIANT_MARCH if variant == "march" else LF_VARIANT_TILE, param)
 
     def diag(self):
         d, rc = lf_diag(self.ctx)

@@ -43,13 +43,17 @@ def to_oracle_f(f_lib, d):
     return out
 
 
-def make_pair(case, prec, seed=11):
+VARIANTS = {"march": ("march", 0), "march-h5": ("march", 5), "tile": ("tile", 0)}
+
+
+def make_pair(case, prec, seed=11, variant="march"):
     """A GPU lattice and an oracle config with the same parameters, the GPU set
     to a random state; returns (sim, cfg, oracle_state_read_back)."""
     kw = dict(synth.BASE)
     kw.update(case)
     d = kw.get("d", 2)
     sim = lf.Lattice(precision=prec, **{k: v for k, v in kw.items() if k not in ("d",)}, d=d)
+    sim.set_variant(*VARIANTS[variant])
     cfg = O.make_cfg(d=d, nx=kw["nx"], ny=kw["ny"], nz=kw.get("nz", 1), walls=kw["walls"],
                      t_wall_mode=kw["t_wall_mode"], hydro=kw["hydro"], b=kw["b"], kappa=kw["kappa"],
                      c=kw["c"], Gamma=kw["Gamma"], Tc=kw["Tc"], T0=kw["T0"], T_w=kw["T_w"], xi=kw["xi"],
@@ -80,10 +84,11 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny")) + str(c))
-def test_aux_and_step_parity(case, prec):
-    sim, cfg, st = make_pair(case, prec)
+def test_aux_and_step_parity(case, prec, variant):
+    sim, cfg, st = make_pair(case, prec, variant=variant)
     tol = TOL[prec]
     d = 2
     ax = O.aux(st)
