@@ -104,12 +104,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000):
+def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000, d=2, nz=1, tau=1.0):
     """The FP64 CPU oracle as it stands on a bounded sample: steps of an
-    nx x ny lattice with the workload's physics, for about `seconds`."""
+    nx x ny (x nz) lattice with the workload's physics, for about `seconds`."""
     from oracle import oracle as O
 
-    cfg = O.make_cfg(nx=nx, ny=ny, xi=xi)
+    cfg = O.make_cfg(d=d, nx=nx, ny=ny, nz=nz, xi=xi, tau=tau)
     st = O.init(cfg)
     st = O.run(st, 1)   # warm: compile/load, first touch
     steps, t0 = 0, time.perf_counter()
@@ -121,7 +121,7 @@ def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000):
         if el < seconds / 4:
             chunk *= 2
     el = time.perf_counter() - t0
-    return 1e-6 * nx * ny * steps / el, steps, el, O.threads()
+    return 1e-6 * nx * ny * nz * steps / el, steps, el, O.threads()
 
 
 def run_reference(args):
@@ -172,6 +172,82 @@ def traffic_for(kernel_key: str):
     return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
+def run_ensemble(args):
+    """96 independent runs (mixed sizes, xi, tau): batched (one graph-replayed
+    persistent launch per step) against the same runs stepped one after
+    another by lf_step; identical results, compared at the end."""
+    import numpy as np
+    import torch
+
+    from paper_1102_3094_gb300 import lf, synth
+
+    rank, world, local = ranks()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    members = synth.ensemble_members()
+    sites = sum(m["nx"] * m["ny"] for m in members)
+    with torch.cuda.stream(stream):
+        ens = lf.Ensemble(members, stream=stream)
+        t0 = time.time()
+        ens.tune(reps=5)
+        tune_s = time.time() - t0
+        singles = [lf.Lattice(precision="fp32", stream=stream, **m) for m in members]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ens.step(args.warmup)
+        for s_ in singles:
+            s_.step(args.warmup)
+        torch.cuda.synchronize(dev)
+        clk = Clocks(local)
+        with clk:
+            time.sleep(0.5)
+            tb = time.time()
+            ev[0].record(stream)
+            ens.step(args.steps)
+            ev[1].record(stream)
+            ev[2].record(stream)
+            for s_ in singles:
+                s_.step(args.steps)
+            ev[3].record(stream)
+            torch.cuda.synchronize(dev)
+            te = time.time()
+        clk.window(tb, te + 0.15)
+        t_batch = ev[0].elapsed_time(ev[1]) / 1e3
+        t_seq = ev[2].elapsed_time(ev[3]) / 1e3
+        identical, nonfinite = True, 0
+        for r in range(len(members)):
+            a = ens.run(r).get("phi", "fp32")
+            b = singles[r].get("phi", "fp32")
+            identical &= bool(np.array_equal(a, b, equal_nan=True))
+            nonfinite += int(not np.isfinite(a).all())
+    value = 1e-6 * sites * args.steps / t_batch
+    peak, peak_kind = peaks()
+    achieved = 88 * sites * args.steps / t_batch / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ens96: 96 independent 2D runs, 24 each of 128^2, 256^2, 384^2, 512^2, xi "
+                               "log-uniform in [1e-4, 1], tau in {0.6, 1, 3}, one persistent launch per step "
+                               "replayed from a CUDA graph, tuned segment heights",
+                   "sites_per_step": sites, "l2": "inputs (1 GB of state) larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_site": 88,
+                     "kernel": "k_ens_march2d (+ k_ens_tsub2d for runs with xi/nsub sub-steps)"},
+        "batched_vs_sequential": {"t_batched_s": t_batch, "t_sequential_s": t_seq, "speedup": t_seq / t_batch,
+                                  "bit_identical_phi": identical, "tune_s": tune_s,
+                                  "runs_nonfinite": nonfinite,
+                                  "note": "runs with tau = 0.6 and fast quenches (xi above ~0.05) diverge for the "
+                                          "method itself at these parameters (the CPU oracle diverges the same way)"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    ens.close()
+    for s_ in singles:
+        s_.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -186,11 +262,17 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    nx = ny = args.size
     prec = args.precision
-    sim = lf.Lattice(nx=nx, ny=ny, precision=prec, xi=args.xi, seed=1 + rank, stream=stream, device=dev)
+    if args.workload == "cube384":
+        d, nx, ny, nz = 3, args.size3, args.size3, args.size3
+        tau = 0.6
+    else:
+        d, nx, ny, nz = 2, args.size, args.size, 1
+        tau = 1.0
+    sim = lf.Lattice(d=d, nx=nx, ny=ny, nz=nz, precision=prec, xi=args.xi, tau=tau, seed=1 + rank, stream=stream,
+                     device=dev)
     sim.set_variant(args.variant, args.tune)
-    N = nx * ny
+    N = nx * ny * nz
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -225,28 +307,30 @@ def run_ours(args):
         t = torch.tensor([total_s], device=dev, dtype=torch.float64)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         total_s = float(t.item())
-    d = sim.diag()
+    dg = sim.diag()
     value = 1e-6 * N * args.steps * world / total_s
     ms = 1e3 * total_s / args.steps
-    bps = BYTES_PER_SITE[(prec, 2)]
+    bps = BYTES_PER_SITE[(prec, d)]
     peak, peak_kind = peaks()
-    launches_per_step = 1 + (lf.lf_nsub(args.xi, 2) - 1 if args.xi not in (0.0, math.inf) else 0)
+    launches_per_step = 1 + (lf.lf_nsub(args.xi, d) - 1 if args.xi not in (0.0, math.inf) else 0)
     kernel_ms = statistics.mean(times_ms) / launches_per_step
     achieved = bps * N / (kernel_ms * 1e-3) / 1e9
+    kname = "k_march3d" if d == 3 else ("k_march2d" if args.variant == "march" else "k_step2d")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_for(f"{'k_march2d' if args.variant == 'march' else 'k_step2d'}_{prec}_{nx}"), "peak_kind": peak_kind,
+            "traffic": traffic_for(f"{kname}_{prec}_{nx}"), "peak_kind": peak_kind,
             "algorithmic_bytes_per_site": bps,
-            "kernel": f"{'k_march2d' if args.variant == 'march' else 'k_step2d'} (fused phi-chain + LB + FD)",
+            "kernel": kname + " (fused phi-chain + LB + FD)",
             "kernel_ms_mean": kernel_ms, "kernel_ms_median": statistics.median(times_ms) / launches_per_step}
 
     # ---- end to end through the C ABI with host buffers ---------------------
     e2e = None
     if args.e2e_steps > 0:
         tdt = torch.float32 if prec == "fp32" else torch.float64
-        pop_h = torch.empty((9, ny, nx), dtype=tdt, pin_memory=True)
-        phi_h = torch.empty((ny, nx), dtype=tdt, pin_memory=True)
-        T_h = torch.empty((ny, nx), dtype=tdt, pin_memory=True)
-        out_h = torch.empty((ny, nx), dtype=tdt, pin_memory=True)
+        shp = sim.shape
+        pop_h = torch.empty((sim.Q,) + shp, dtype=tdt, pin_memory=True)
+        phi_h = torch.empty(shp, dtype=tdt, pin_memory=True)
+        T_h = torch.empty(shp, dtype=tdt, pin_memory=True)
+        out_h = torch.empty(shp, dtype=tdt, pin_memory=True)
         es = pop_h.element_size()
         lf.lf_fields(sim.ctx, lf.FIELDS["pop"], pop_h.data_ptr(), pop_h.numel() * es, False)
         lf.lf_fields(sim.ctx, lf.FIELDS["phi"], phi_h.data_ptr(), phi_h.numel() * es, False)
@@ -265,24 +349,31 @@ def run_ours(args):
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
             el = float(t.item())
         e2e = {"value": 1e-6 * N * args.e2e_steps * world / el, "unit": "MLUPS",
-               "h2d_bytes_per_step": (9 + 2) * N * es, "d2h_bytes_per_step": N * es,
+               "h2d_bytes_per_step": (sim.Q + 2) * N * es, "d2h_bytes_per_step": N * es,
                "steps": args.e2e_steps,
                "what": "per step: lf_fields_set of f, phi, T from pinned host, lf_step(1), lf_fields of phi to "
                        "pinned host"}
 
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
-        rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds)
+        if d == 3:
+            rate, steps, el, cores = oracle_rate(64, 64, args.xi, seconds=args.cpu_seconds, d=3, nz=64, tau=tau)
+            smp = "64x64x64"
+        else:
+            rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds)
+            smp = "256x256"
         cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{steps} FP64 oracle steps of a 256x256 lattice with the workload's physics "
+               "sample": f"{steps} FP64 oracle steps of a {smp} lattice with the workload's physics "
                          f"({el:.1f} s)"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": f"prec1024: 2D D2Q9 lamellar quench between cold walls, {nx}x{ny}, "
-                                   f"{prec.upper()} state (deviation populations), xi={args.xi}, tau=1",
+            "config": {"workload": (f"prec1024: 2D D2Q9 lamellar quench between cold walls, {nx}x{ny}, "
+                                    if d == 2 else
+                                    f"cube384: 3D D3Q19 lamellar quench between cold walls (z), {nx}x{ny}x{nz}, ")
+                                   + f"{prec.upper()} state (deviation populations), xi={args.xi}, tau={tau}",
                        "sites": N, "l2": "flushed (256 MiB write) before every timed step; each step timed "
                                          "alone with CUDA events on the library stream",
                        "parallelism": f"replicas x{world} (one independent lattice per GPU)"},
@@ -291,7 +382,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk.summary(),
-            "diag_after": {"mass": d["mass"], "mach": d["mach"], "rc": d["rc"]},
+            "diag_after": {"mass": dg["mass"], "mach": dg["mach"], "rc": dg["rc"]},
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -306,7 +397,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--workload", choices=["prec1024", "cube384", "ens96"], default="prec1024")
+    ap.add_argument("--size", type=int, default=1024, help="2D lattice side (prec1024)")
+    ap.add_argument("--size3", type=int, default=384, help="3D lattice side (cube384)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--xi", type=float, default=1e-3)
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -319,6 +412,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ens96":
+        return run_ensemble(args)
     return run_ours(args)
 
 

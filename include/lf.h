@@ -164,7 +164,8 @@ int lf_step(lf_ctx* ctx, int64_t nsteps);
  * N*4 (Q*N*4) gives float; anything else is LF_EINVAL.  dst_on_device says
  * whether dst is a device or a host pointer.  Derived fields (RHO, U*, MU,
  * F*) are computed from the current state by the same device code the step
- * uses.  Waits for completion. */
+ * uses.  Waits for completion.  Copies whatever the state holds: a NaN/Inf
+ * is reported by lf_step and lf_diag, not here. */
 int lf_fields(lf_ctx* ctx, int which, void* dst, size_t bytes, int dst_on_device);
 
 /* Overwrites PHI, T or POP (full f_i) of the current state from src, with the

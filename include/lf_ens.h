@@ -1,0 +1,62 @@
+/*
+ * lf_ens.h -- batched ensembles of independent 2D runs of the hybrid
+ * LB/FD step of arXiv:1102.3094 (Sec. 2) in one launch per time step.
+ *
+ * The paper itself runs one lattice at a time; an ensemble advances many
+ * independent lattices of uneven sizes and parameters (xi, tau, seed, ...)
+ * together.  Each run is an ordinary lf_ctx (so lf_fields, lf_fields_set,
+ * lf_diag, lf_save and lf_load work on it) whose steps are taken by the
+ * ensemble: one persistent kernel per time step walks a work list of
+ * (run, strip, segment) items, and the steps are replayed from a CUDA graph.
+ * Results are bit-identical to stepping every run alone with lf_step (the
+ * per-site arithmetic is the same code).
+ *
+ * Restrictions: every run is two-dimensional (d = 2) and LF_FP32.
+ * Conventions (return codes, layouts, ownership) are those of lf.h.
+ */
+#ifndef LF_ENS_H
+#define LF_ENS_H
+
+#include "lf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lf_ens lf_ens;
+
+/* Creates nruns contexts, run r from grids[r], walls[r], params[r] (the
+ * stream, workspace and workspace_bytes fields of params are ignored), all in
+ * one device arena, enqueued on `stream` (a cudaStream_t; 0 = a private
+ * stream the ensemble creates).  LF_EINVAL if a run is not d = 2 / LF_FP32
+ * or fails lf_create's checks (then nothing is allocated). */
+int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const lf_params* params,
+                  void* stream, lf_ens** out);
+
+/* Autotuner: for every distinct lattice size in the ensemble, times the
+ * step kernel with candidate segment heights on a scratch copy of one run
+ * (reps timed steps each, CUDA events) and keeps the fastest.  The runs'
+ * states are not touched.  Rebuilds the work list and the graphs. */
+int lf_ens_tune(lf_ens* e, int reps);
+
+/* Segment height the work list uses for run r (after tuning, or automatic). */
+int lf_ens_rows(const lf_ens* e, int run);
+
+/* Enqueues nsteps steps of every run on the ensemble's stream (graph
+ * replays) and returns without waiting. */
+int lf_ens_step(lf_ens* e, int64_t nsteps);
+
+/* Borrowed context of run r (valid until lf_ens_destroy).  lf_step on it
+ * returns LF_EINVAL: only the ensemble advances its runs. */
+int lf_ens_run(lf_ens* e, int run, lf_ctx** ctx);
+
+/* Waits (bounded) for the ensemble's stream. */
+int lf_ens_sync(lf_ens* e);
+
+void lf_ens_destroy(lf_ens* e);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_ENS_H */

@@ -12,36 +12,11 @@
 #include <cstring>
 #include <new>
 
+#include "lf_ctx.cuh"
 #include "lf_diag.cuh"
 #include "lf_internal.cuh"
 
 using namespace lf;
-
-struct lf_ctx {
-    lf_grid grid;
-    lf_walls walls;
-    lf_params params;
-    Geom g;
-    int Q, nsub, prec;
-    size_t esz;
-    int64_t N;            // sites
-    cudaStream_t stream;
-    unsigned char* base;  // device block
-    size_t bytes;
-    bool own;
-    void* f[2];
-    void* phi[2];
-    void* T[2];
-    int fcur, pcur, tcur;
-    void* aux;            // 8 planes: mu, Fx, Fy, Fz, rho, ux, uy, uz
-    void* stage;          // N doubles
-    void* scratch;        // diagnostics reduction scratch
-    size_t scratch_bytes;
-    int* flag_dev;
-    volatile int* flag_host;
-    int64_t step;
-    bool aux_valid;
-};
 
 namespace {
 
@@ -55,7 +30,7 @@ int wall_len(const lf_grid* g) { return g->d == 2 ? (int)g->ny : (int)g->nz; }
 int validate(const lf_grid* grid, const lf_walls* walls, const lf_params* p)
 {
     if (!grid || !walls || !p) return LF_EINVAL;
-    if (grid->d != 2) return LF_EINVAL;   // D3Q19 path not built yet
+    if (grid->d != 2 && grid->d != 3) return LF_EINVAL;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return LF_EINVAL;
     if (grid->d == 2 && grid->nz != 1) return LF_EINVAL;
     if (grid->nx > (1 << 24) || grid->ny > (1 << 24) || grid->nz > (1 << 24)) return LF_EINVAL;
@@ -407,7 +382,7 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
 
 int lf_step(lf_ctx* c, int64_t nsteps)
 {
-    if (!c || nsteps < 0) return LF_EINVAL;
+    if (!c || nsteps < 0 || c->ens_member) return LF_EINVAL;
     int rc = pending_status(c);
     if (rc != LF_OK) return rc;
     return c->prec == LF_FP64 ? do_steps<double>(c, nsteps) : do_steps<float>(c, nsteps);
@@ -432,7 +407,7 @@ int lf_fields(lf_ctx* c, int which, void* dst, size_t bytes, int dst_on_device)
                                 : pack_dispatch<float>(c, field_plane(c, which, q), d, add, dst_on_device, dbl);
     }
     if (rc == LF_OK) rc = wait_stream(c->stream);
-    if (rc == LF_OK) rc = pending_status(c);
+    if (rc == LF_OK) rc = check(cudaGetLastError());
     return rc;
 }
 

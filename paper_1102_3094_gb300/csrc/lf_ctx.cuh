@@ -1,0 +1,33 @@
+// lf_ctx.cuh -- the context behind the opaque lf_ctx handle of lf.h, shared
+// by the single-lattice API (lf_api.cu) and the ensemble (lf_ens.cu).
+#pragma once
+
+#include "lf_internal.cuh"
+
+struct lf_ctx {
+    lf_grid grid;
+    lf_walls walls;
+    lf_params params;
+    lf::Geom g;
+    int Q, nsub, prec;
+    size_t esz;
+    int64_t N;            // sites
+    cudaStream_t stream;
+    unsigned char* base;  // device block
+    size_t bytes;
+    bool own;
+    void* f[2];
+    void* phi[2];
+    void* T[2];
+    int fcur, pcur, tcur;
+    void* aux;            // 8 planes: mu, Fx, Fy, Fz, rho, ux, uy, uz
+    void* stage;          // N doubles
+    void* scratch;        // diagnostics reduction scratch
+    size_t scratch_bytes;
+    int* flag_dev;
+    volatile int* flag_host;
+    int64_t step;
+    bool aux_valid;
+    bool ens_member;      // stepped by an ensemble; lf_step on it is refused
+};
+

@@ -1,0 +1,439 @@
+// lf_ens.cu -- batched ensembles of independent 2D FP32 runs (include/lf_ens.h).
+//
+// Every run is an ordinary context placed in one shared device arena.  A time
+// step of the whole ensemble is one launch of a persistent kernel that walks
+// a work list of (run, strip, segment) items -- each item is exactly the
+// row-marching step of lf_march2d.cuh -- followed, when some runs need extra
+// temperature sub-steps, by one launch per sub-step over the tiles of those
+// runs.  Every run returns to its starting buffers after two steps (f and phi
+// flip once per step, T flips nsub times), so two steps are captured in one
+// CUDA graph and replayed; single-step graphs handle odd counts.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "lf_ctx.cuh"
+#include "lf_ens.h"
+#include "lf_march2d.cuh"
+
+using namespace lf;
+
+namespace {
+
+constexpr int kNT = 128, kD = 3;
+using MarchCfg = march::March<float, kNT, kD>;
+
+struct EnsRun {
+    Geom g;
+    Phys<float> p;
+    StepIO<float> io;
+};
+
+struct EnsItem {
+    int run, strip, seg, H;
+};
+
+struct EnsT {
+    Geom g;
+    Phys<float> p;
+    const float* Tin;
+    float* Tout;
+};
+
+struct EnsTItem {
+    int run, bx, by;
+};
+
+__global__ void __launch_bounds__(kNT) k_ens_march2d(const EnsRun* __restrict__ runs,
+                                                    const EnsItem* __restrict__ items, int nitems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const EnsItem w = items[it];
+        const EnsRun r = runs[w.run];
+        march::march2d_segment<float, kNT, kD>(r.g, r.p, r.io, w.strip, w.seg, w.H, smem_raw);
+        __syncthreads();   // the next item reuses the shared rings
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ens_tsub2d(const EnsT* __restrict__ runs, const EnsTItem* __restrict__ items,
+                                                   int nitems)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const EnsTItem w = items[it];
+        const EnsT r = runs[w.run];
+        const int x = w.bx * 32 + (threadIdx.x & 31), y = w.by * 8 + (threadIdx.x >> 5);
+        if (x < r.g.nx && y < r.g.ny) march::tsub2d_site(r.g, r.p, r.Tin, r.Tout, x, y);
+    }
+}
+
+Phys<float> phys_f(const lf_ctx* c)
+{
+    const lf_params& p = c->params;
+    Phys<float> ph;
+    ph.b = (float)p.b; ph.kappa = (float)p.kappa; ph.c = (float)p.c; ph.Gamma = (float)p.Gamma; ph.Tc = (float)p.Tc;
+    ph.T_w = (float)c->walls.T_w;
+    ph.inv_Tc = (float)(1.0 / p.Tc);
+    ph.t_update = !(std::isinf(p.xi) || p.xi == 0.0);
+    ph.dxi = ph.t_update ? (float)(p.xi / c->nsub) : 0.f;
+    ph.inv_tau = (float)(1.0 / p.tau);
+    ph.guo = (float)(1.0 - 1.0 / (2.0 * p.tau));
+    ph.n0 = (float)p.n0;
+    ph.hydro = p.hydro;
+    return ph;
+}
+
+struct Cursor {
+    int f, p, t;
+};
+
+}  // namespace
+
+struct lf_ens {
+    int nruns;
+    std::vector<lf_ctx*> runs;
+    std::vector<int> rows;          // segment height per run
+    cudaStream_t stream;
+    bool own_stream;
+    unsigned char* arena;
+    unsigned char* tables;          // device copies of the descriptor tables and work lists
+    cudaGraphExec_t gA, gB, gAB;
+    int parity;                     // 0: the next step is step A of the cycle, 1: step B
+    std::vector<Cursor> base;       // buffer cursors at the start of step A
+    int march_blocks;
+};
+
+namespace {
+
+void free_graphs(lf_ens* e)
+{
+    if (e->gA) cudaGraphExecDestroy(e->gA);
+    if (e->gB) cudaGraphExecDestroy(e->gB);
+    if (e->gAB) cudaGraphExecDestroy(e->gAB);
+    e->gA = e->gB = e->gAB = nullptr;
+    if (e->tables) cudaFree(e->tables);
+    e->tables = nullptr;
+}
+
+// Device layout of one half-cycle (step A or B): run table, T tables.
+struct Half {
+    EnsRun* runs;
+    std::vector<EnsT*> ts;          // per extra sub-step s = 1 .. max_nsub - 1
+};
+
+int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsItem* items, int nitems,
+            const std::vector<EnsTItem*>& titems, const std::vector<int>& ntitems, cudaGraphExec_t* out)
+{
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LF_ECUDA;
+    for (int h : halves) {
+        k_ens_march2d<<<e->march_blocks, kNT, MarchCfg::BYTES, e->stream>>>(H[h].runs, items, nitems);
+        for (size_t s = 0; s < H[h].ts.size(); ++s) {
+            if (ntitems[s] == 0) continue;
+            const int blocks = std::min(ntitems[s], 152 * 8);
+            k_ens_tsub2d<<<blocks, 256, 0, e->stream>>>(H[h].ts[s], titems[s], ntitems[s]);
+        }
+    }
+    cudaError_t err = cudaStreamEndCapture(e->stream, &graph);
+    if (err != cudaSuccess) return LF_ECUDA;
+    err = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return err == cudaSuccess ? LF_OK : LF_ECUDA;
+}
+
+// (Re)builds the descriptor tables, the work lists and the three graphs from
+// the runs' current buffer cursors.
+int build(lf_ens* e)
+{
+    free_graphs(e);
+    const int R = e->nruns;
+    int max_nsub = 1;
+    for (lf_ctx* c : e->runs)
+        if (phys_f(c).t_update) max_nsub = std::max(max_nsub, c->nsub);
+
+    // host tables for both halves
+    e->base.resize(R);
+    std::vector<EnsRun> hr[2];
+    std::vector<std::vector<EnsT>> ht[2];
+    for (int h = 0; h < 2; ++h) {
+        hr[h].resize(R);
+        ht[h].assign(max_nsub - 1, std::vector<EnsT>(R));
+    }
+    for (int r = 0; r < R; ++r) {
+        lf_ctx* c = e->runs[r];
+        Cursor cur{c->fcur, c->pcur, c->tcur};
+        e->base[r] = cur;
+        const Phys<float> ph = phys_f(c);
+        for (int h = 0; h < 2; ++h) {
+            EnsRun& d = hr[h][r];
+            std::memset(&d, 0, sizeof(d));
+            d.g = c->g;
+            d.p = ph;
+            d.io.f_in = (const float*)c->f[cur.f];
+            d.io.f_out = (float*)c->f[cur.f ^ 1];
+            d.io.phi_in = (const float*)c->phi[cur.p];
+            d.io.phi_out = (float*)c->phi[cur.p ^ 1];
+            d.io.T_in = (const float*)c->T[cur.t];
+            d.io.T_out = (float*)c->T[cur.t ^ 1];
+            d.io.flag = c->flag_dev;
+            if (c->params.hydro) cur.f ^= 1;
+            cur.p ^= 1;
+            cur.t ^= 1;
+            for (int s = 1; s < max_nsub; ++s) {
+                EnsT& t = ht[h][s - 1][r];
+                t.g = c->g;
+                t.p = ph;
+                t.Tin = (const float*)c->T[cur.t];
+                t.Tout = (float*)c->T[cur.t ^ 1];
+                if (ph.t_update && s < c->nsub) cur.t ^= 1;
+            }
+        }
+    }
+    // work lists: march items sorted by cost, T tiles per sub-step
+    std::vector<EnsItem> items;
+    for (int r = 0; r < R; ++r) {
+        const lf_ctx* c = e->runs[r];
+        const int H = e->rows[r];
+        const int strips = (c->g.nx + MarchCfg::U - 1) / MarchCfg::U, segs = (c->g.ny + H - 1) / H;
+        for (int sg = 0; sg < segs; ++sg)
+            for (int st = 0; st < strips; ++st) items.push_back({r, st, sg, H});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const EnsItem& a, const EnsItem& b) { return a.H > b.H; });
+    std::vector<std::vector<EnsTItem>> titems(max_nsub > 1 ? max_nsub - 1 : 0);
+    for (int s = 1; s < max_nsub; ++s)
+        for (int r = 0; r < R; ++r) {
+            const lf_ctx* c = e->runs[r];
+            if (!phys_f(c).t_update || s >= c->nsub) continue;
+            for (int by = 0; by < (c->g.ny + 7) / 8; ++by)
+                for (int bx = 0; bx < (c->g.nx + 31) / 32; ++bx) titems[s - 1].push_back({r, bx, by});
+        }
+    // one device block for everything
+    auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
+    size_t bytes = 2 * a256(sizeof(EnsRun) * R) + a256(sizeof(EnsItem) * items.size());
+    for (int s = 1; s < max_nsub; ++s) bytes += 2 * a256(sizeof(EnsT) * R) + a256(sizeof(EnsTItem) * titems[s - 1].size());
+    if (cudaMalloc((void**)&e->tables, bytes) != cudaSuccess) { cudaGetLastError(); return LF_ENOMEM; }
+    unsigned char* p = e->tables;
+    Half halves[2];
+    std::vector<std::pair<void*, std::pair<const void*, size_t>>> copies;
+    for (int h = 0; h < 2; ++h) {
+        halves[h].runs = (EnsRun*)p;
+        copies.push_back({p, {hr[h].data(), sizeof(EnsRun) * R}});
+        p += a256(sizeof(EnsRun) * R);
+    }
+    EnsItem* d_items = (EnsItem*)p;
+    copies.push_back({p, {items.data(), sizeof(EnsItem) * items.size()}});
+    p += a256(sizeof(EnsItem) * items.size());
+    std::vector<EnsTItem*> d_titems;
+    std::vector<int> ntitems;
+    for (int s = 1; s < max_nsub; ++s) {
+        for (int h = 0; h < 2; ++h) {
+            halves[h].ts.push_back((EnsT*)p);
+            copies.push_back({p, {ht[h][s - 1].data(), sizeof(EnsT) * R}});
+            p += a256(sizeof(EnsT) * R);
+        }
+        d_titems.push_back((EnsTItem*)p);
+        ntitems.push_back((int)titems[s - 1].size());
+        copies.push_back({p, {titems[s - 1].data(), sizeof(EnsTItem) * titems[s - 1].size()}});
+        p += a256(sizeof(EnsTItem) * titems[s - 1].size());
+    }
+    for (auto& cp : copies)
+        if (cp.second.second && cudaMemcpyAsync(cp.first, cp.second.first, cp.second.second, cudaMemcpyHostToDevice,
+                                                e->stream) != cudaSuccess)
+            return LF_ECUDA;
+    int rc = wait_stream(e->stream);   // host vectors go out of scope
+    if (rc != LF_OK) return rc;
+
+    if (cudaFuncSetAttribute(k_ens_march2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg::BYTES) !=
+        cudaSuccess)
+        return LF_ECUDA;
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_march2d, kNT, MarchCfg::BYTES);
+    e->march_blocks = std::max(1, std::min((int)items.size(), std::max(1, per_sm) * std::max(1, sms)));
+
+    const int nitems = (int)items.size();
+    if ((rc = capture(e, {0}, halves, d_items, nitems, d_titems, ntitems, &e->gA)) != LF_OK) return rc;
+    if ((rc = capture(e, {1}, halves, d_items, nitems, d_titems, ntitems, &e->gB)) != LF_OK) return rc;
+    if ((rc = capture(e, {0, 1}, halves, d_items, nitems, d_titems, ntitems, &e->gAB)) != LF_OK) return rc;
+    e->parity = 0;
+    return LF_OK;
+}
+
+void advance_cursors(lf_ens* e, int64_t n)
+{
+    for (lf_ctx* c : e->runs) {
+        const bool tu = phys_f(c).t_update;
+        const int tflips = tu ? c->nsub : 1;
+        if ((n & 1) != 0) {
+            if (c->params.hydro) c->fcur ^= 1;
+            c->pcur ^= 1;
+            if (tflips & 1) c->tcur ^= 1;
+        }
+        c->step += n;
+        c->aux_valid = false;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const lf_params* params, void* stream,
+                  lf_ens** out)
+{
+    if (!out || nruns < 1 || !grids || !walls || !params) return LF_EINVAL;
+    *out = nullptr;
+    std::vector<size_t> ws(nruns);
+    size_t total = 0;
+    for (int r = 0; r < nruns; ++r) {
+        if (grids[r].d != 2 || params[r].precision != LF_FP32) return LF_EINVAL;
+        lf_params p = params[r];
+        p.workspace = nullptr;
+        p.workspace_bytes = 0;
+        int rc = lf_workspace_bytes(&grids[r], &walls[r], &p, &ws[r]);
+        if (rc != LF_OK) return rc;
+        total += (ws[r] + 255) / 256 * 256;
+    }
+    lf_ens* e = new (std::nothrow) lf_ens();
+    if (!e) return LF_ENOMEM;
+    e->nruns = nruns;
+    e->stream = (cudaStream_t)stream;
+    if (!e->stream) {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete e;
+            return LF_ECUDA;
+        }
+        e->own_stream = true;
+    }
+    if (cudaMalloc((void**)&e->arena, total) != cudaSuccess) {
+        cudaGetLastError();
+        if (e->own_stream) cudaStreamDestroy(e->stream);
+        delete e;
+        return LF_ENOMEM;
+    }
+    size_t off = 0;
+    int rc = LF_OK;
+    for (int r = 0; r < nruns && rc == LF_OK; ++r) {
+        lf_params p = params[r];
+        p.stream = e->stream;
+        p.workspace = e->arena + off;
+        p.workspace_bytes = ws[r];
+        off += (ws[r] + 255) / 256 * 256;
+        lf_ctx* c = nullptr;
+        rc = lf_create(&grids[r], &walls[r], &p, &c);
+        if (rc == LF_OK) {
+            c->ens_member = true;
+            e->runs.push_back(c);
+            e->rows.push_back(march::march_rows_for(c->g.nx, c->g.ny, MarchCfg::U, 0));
+        }
+    }
+    if (rc == LF_OK) rc = build(e);
+    if (rc != LF_OK) {
+        lf_ens_destroy(e);
+        return rc;
+    }
+    *out = e;
+    return LF_OK;
+}
+
+int lf_ens_tune(lf_ens* e, int reps)
+{
+    if (!e || reps < 1) return LF_EINVAL;
+    int rc = wait_stream(e->stream);
+    if (rc != LF_OK) return rc;
+    std::map<std::pair<int, int>, int> best;   // (nx, ny) -> rows
+    for (int r = 0; r < e->nruns; ++r) {
+        lf_ctx* c = e->runs[r];
+        const auto key = std::make_pair(c->g.nx, c->g.ny);
+        if (best.count(key)) continue;
+        lf_params p = c->params;
+        p.workspace = nullptr;
+        p.workspace_bytes = 0;
+        p.stream = e->stream;
+        lf_ctx* tmp = nullptr;
+        if ((rc = lf_create(&c->grid, &c->walls, &p, &tmp)) != LF_OK) return rc;
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        float best_ms = 1e30f;
+        int best_h = e->rows[r];
+        const int cand[] = {8, 12, 16, 20, 24, 32, 48, 64, 96, 128};
+        for (int h : cand) {
+            if (h > c->g.ny && h != cand[0]) continue;
+            lf_set_kernel_variant(tmp, LF_VARIANT_MARCH, h);
+            lf_step(tmp, 2);
+            cudaEventRecord(t0, e->stream);
+            lf_step(tmp, reps);
+            cudaEventRecord(t1, e->stream);
+            if ((rc = wait_stream(e->stream)) != LF_OK) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (ms < best_ms) { best_ms = ms; best_h = h < c->g.ny ? h : c->g.ny; }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        lf_destroy(tmp);
+        if (rc != LF_OK) return rc;
+        best[key] = best_h;
+    }
+    for (int r = 0; r < e->nruns; ++r) e->rows[r] = best[std::make_pair(e->runs[r]->g.nx, e->runs[r]->g.ny)];
+    return build(e);
+}
+
+int lf_ens_rows(const lf_ens* e, int run)
+{
+    if (!e || run < 0 || run >= e->nruns) return LF_EINVAL;
+    return e->rows[run];
+}
+
+int lf_ens_step(lf_ens* e, int64_t nsteps)
+{
+    if (!e || nsteps < 0) return LF_EINVAL;
+    if (cudaGetLastError() != cudaSuccess) return LF_ECUDA;
+    int64_t n = nsteps;
+    while (n > 0) {
+        cudaGraphExec_t g;
+        int64_t k;
+        if (e->parity == 1) { g = e->gB; k = 1; }
+        else if (n >= 2) { g = e->gAB; k = 2; }
+        else { g = e->gA; k = 1; }
+        if (cudaGraphLaunch(g, e->stream) != cudaSuccess) return LF_ECUDA;
+        e->parity = (int)((e->parity + k) & 1);
+        n -= k;
+    }
+    advance_cursors(e, nsteps);
+    return LF_OK;
+}
+
+int lf_ens_run(lf_ens* e, int run, lf_ctx** ctx)
+{
+    if (!e || !ctx || run < 0 || run >= e->nruns) return LF_EINVAL;
+    *ctx = e->runs[run];
+    return LF_OK;
+}
+
+int lf_ens_sync(lf_ens* e)
+{
+    if (!e) return LF_EINVAL;
+    return wait_stream(e->stream);
+}
+
+void lf_ens_destroy(lf_ens* e)
+{
+    if (!e) return;
+    if (e->stream) wait_stream(e->stream);
+    free_graphs(e);
+    for (lf_ctx* c : e->runs) lf_destroy(c);
+    if (e->arena) cudaFree(e->arena);
+    if (e->own_stream) cudaStreamDestroy(e->stream);
+    cudaGetLastError();
+    delete e;
+}
+
+}  // extern "C"

@@ -288,3 +288,128 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- ensembles
+def _ens_lib():
+    L = lib()
+    if not getattr(L, "_ens_ready", False):
+        vp = C.c_void_p
+        L.lf_ens_create.argtypes = [C.c_int, C.POINTER(lf_grid), C.POINTER(lf_walls), C.POINTER(lf_params), vp,
+                                    C.POINTER(vp)]
+        L.lf_ens_tune.argtypes = [vp, C.c_int]
+        L.lf_ens_rows.argtypes = [vp, C.c_int]
+        L.lf_ens_step.argtypes = [vp, C.c_int64]
+        L.lf_ens_run.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        L.lf_ens_sync.argtypes = [vp]
+        L.lf_ens_destroy.argtypes = [vp]
+        L.lf_ens_destroy.restype = None
+        for fn in ("lf_ens_create", "lf_ens_tune", "lf_ens_rows", "lf_ens_step", "lf_ens_run", "lf_ens_sync"):
+            getattr(L, fn).restype = C.c_int
+        L._ens_ready = True
+    return L
+
+
+def lf_ens_create(grids, walls, params, stream_ptr=0):
+    n = len(grids)
+    G = (lf_grid * n)(*grids)
+    W = (lf_walls * n)(*walls)
+    P = (lf_params * n)(*params)
+    ens = C.c_void_p()
+    _ok(_ens_lib().lf_ens_create(n, G, W, P, C.c_void_p(stream_ptr), C.byref(ens)), "lf_ens_create")
+    return ens
+
+
+def lf_ens_tune(ens, reps: int = 5) -> None:
+    _ok(_ens_lib().lf_ens_tune(ens, reps), "lf_ens_tune")
+
+
+def lf_ens_rows(ens, run: int) -> int:
+    return _ok(_ens_lib().lf_ens_rows(ens, run), "lf_ens_rows")
+
+
+def lf_ens_step(ens, nsteps: int) -> None:
+    _ok(_ens_lib().lf_ens_step(ens, nsteps), "lf_ens_step")
+
+
+def lf_ens_run(ens, run: int):
+    ctx = C.c_void_p()
+    _ok(_ens_lib().lf_ens_run(ens, run, C.byref(ctx)), "lf_ens_run")
+    return ctx
+
+
+def lf_ens_sync(ens) -> None:
+    _ok(_ens_lib().lf_ens_sync(ens), "lf_ens_sync")
+
+
+def lf_ens_destroy(ens) -> None:
+    _ens_lib().lf_ens_destroy(ens)
+
+
+class _RunView(Lattice):
+    """Field access to one run of an ensemble (no ownership)."""
+
+    def __init__(self, ens, ctx, shape):  # noqa: D401 - no super().__init__: the context exists
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda:0")
+        self.ctx = ctx
+        self.Q = 9
+        self.shape = shape
+        self.N = int(np.prod(shape))
+        self._ens = ens
+
+    def close(self):
+        self.ctx = None
+
+    def step(self, n: int = 1):
+        raise RuntimeError("runs of an ensemble are advanced by Ensemble.step")
+
+
+class Ensemble:
+    """Independent 2D FP32 runs advanced together (include/lf_ens.h)."""
+
+    def __init__(self, members, stream=None, **common):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        grids, walls, params, self.shapes = [], [], [], []
+        for m in members:
+            kw = dict(common)
+            kw.update(m)
+            grids.append(lf_grid(d=2, nx=kw["nx"], ny=kw["ny"], nz=1))
+            walls.append(lf_walls(walls=kw.get("walls", 1), t_wall_mode=kw.get("t_wall_mode", 0),
+                                  T_w=kw.get("T_w", 0.5)))
+            params.append(lf_params(b=kw.get("b", 1.0), kappa=kw.get("kappa", -0.025), c=kw.get("c", 0.02),
+                                    Gamma=kw.get("Gamma", 0.05), Tc=kw.get("Tc", 1.0), T0=kw.get("T0", 1.1),
+                                    xi=kw.get("xi", 0.01), tau=kw.get("tau", 1.0), n0=kw.get("n0", 1.0),
+                                    phi_amp=kw.get("phi_amp", 0.05), seed=kw.get("seed", 1), precision=LF_FP32,
+                                    hydro=kw.get("hydro", 1), ideal_mode=0))
+            self.shapes.append((kw["ny"], kw["nx"]))
+        self.ens = lf_ens_create(grids, walls, params, self.stream.cuda_stream)
+        self.n = len(members)
+
+    def step(self, n: int = 1):
+        lf_ens_step(self.ens, n)
+
+    def tune(self, reps: int = 5):
+        lf_ens_tune(self.ens, reps)
+
+    def rows(self, run: int) -> int:
+        return lf_ens_rows(self.ens, run)
+
+    def run(self, r: int) -> Lattice:
+        return _RunView(self.ens, lf_ens_run(self.ens, r), self.shapes[r])
+
+    def sync(self):
+        lf_ens_sync(self.ens)
+
+    def close(self):
+        if getattr(self, "ens", None) is not None and self.ens.value:
+            lf_ens_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

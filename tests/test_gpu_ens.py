@@ -1,0 +1,71 @@
+"""Batched ensembles (include/lf_ens.h): every run of an ensemble, advanced
+by the graph-replayed persistent launch, must equal the same run advanced
+alone by lf_step, bit for bit (the per-site arithmetic is shared code)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1102_3094_gb300 import lf  # noqa: E402
+
+MEMBERS = [
+    dict(nx=64, ny=64, xi=0.01, tau=1.0, seed=11),
+    dict(nx=96, ny=80, xi=0.5, tau=0.6, seed=12),            # 3 temperature sub-steps
+    dict(nx=130, ny=70, xi=1e-3, tau=3.0, seed=13),
+    dict(nx=40, ny=24, xi=math.inf, tau=1.0, seed=14),       # instantaneous quench
+    dict(nx=33, ny=17, xi=0.2, tau=0.8, seed=15, walls=0),   # periodic
+    dict(nx=128, ny=128, xi=1.0, tau=1.0, seed=16, t_wall_mode=1),   # 5 sub-steps, halfway T
+]
+
+
+def _alone(m, steps):
+    kw = {k: v for k, v in m.items()}
+    sim = lf.Lattice(precision="fp32", **kw)
+    sim.step(steps)
+    return sim
+
+
+def _compare(ens, steps):
+    for r, m in enumerate(MEMBERS):
+        ref = _alone(m, steps)
+        run = ens.run(r)
+        for name in ("phi", "T", "pop"):
+            np.testing.assert_array_equal(run.get(name, "fp32"), ref.get(name, "fp32"), err_msg=f"run {r} {name}")
+        assert run.step_count == ref.step_count == steps
+        ref.close()
+
+
+def test_ensemble_equals_single_runs():
+    ens = lf.Ensemble(MEMBERS)
+    ens.step(7)          # odd: single-step graphs and the two-step graph
+    ens.step(10)
+    _compare(ens, 17)
+    d = ens.run(1).diag()
+    assert d["rc"] == 0 and d["mach"] < 0.1
+    ens.close()
+
+
+def test_ensemble_after_tuning():
+    ens = lf.Ensemble(MEMBERS)
+    ens.step(3)
+    ens.tune(reps=3)
+    rows = [ens.rows(r) for r in range(len(MEMBERS))]
+    assert all(r >= 1 for r in rows)
+    ens.step(6)
+    _compare(ens, 9)
+    ens.close()
+
+
+def test_ensemble_run_refuses_lf_step():
+    ens = lf.Ensemble(MEMBERS[:2])
+    ctx = lf.lf_ens_run(ens.ens, 0)
+    with pytest.raises(lf.LFError) as ei:
+        lf.lf_step(ctx, 1)
+    assert ei.value.code == lf.LF_EINVAL
+    ens.close()

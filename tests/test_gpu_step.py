@@ -108,6 +108,52 @@ def test_aux_and_step_parity(case, prec, variant):
     sim.close()
 
 
+CASES3 = [
+    dict(d=3, nx=12, ny=10, nz=9, xi=0.01),                        # walls along z, one tile
+    dict(d=3, nx=40, ny=12, nz=20, xi=0.01),                       # several tiles, ragged in x and y
+    dict(d=3, nx=9, ny=7, nz=6, walls=0, xi=0.01),                 # fully periodic, smaller than the halo
+    dict(d=3, nx=14, ny=11, nz=8, t_wall_mode=1, xi=0.4),          # halfway T ghost, 3 sub-steps
+    dict(d=3, nx=10, ny=9, nz=7, hydro=0, xi=0.1),                 # no hydrodynamics
+    dict(d=3, nx=36, ny=17, nz=5, tau=0.6, xi=1e-3),               # thin in z
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
+def test_aux_and_step_parity_3d(case, prec):
+    sim, cfg, st = make_pair(case, prec)
+    tol = TOL[prec]
+    ax = O.aux(st)
+    checks = {"mu": (sim.get("mu"), ax["mu"]), "rho": (sim.get("rho"), ax["n"])}
+    for a, name in enumerate(("x", "y", "z")):
+        checks["F" + name] = (sim.get("F" + name), ax["F"][a])
+        checks["u" + name] = (sim.get("u" + name), ax["u"][a])
+    for k, (g, w) in checks.items():
+        if np.abs(w).max() == 0:
+            assert np.abs(g).max() == 0, k
+            continue
+        assert relerr(g, w) < tol, (k, relerr(g, w))
+    sim.step(1)
+    ref = O.step(st)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), 3), ref.f)):
+        assert relerr(got, want) < tol, (name, relerr(got, want))
+    sim.close()
+
+
+def test_multistep_3d_fp64():
+    sim = lf.Lattice(d=3, nx=20, ny=16, nz=18, precision="fp64", xi=0.01)
+    st = O.init(O.make_cfg(d=3, nx=20, ny=16, nz=18, xi=0.01))
+    sim.step(50)
+    ref = O.run(st, 50)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), 3), ref.f)):
+        assert relerr(got, want) < 1e-10, (name, relerr(got, want))
+    d = sim.diag()
+    assert d["rc"] == 0 and abs(d["mass"] - 20 * 16 * 18) < 1e-9
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_init_matches_generator(prec):
     sim = lf.Lattice(nx=70, ny=37, precision=prec, seed=123)
