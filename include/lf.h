@@ -186,6 +186,35 @@ int lf_diag_layers(lf_ctx* ctx, double* out, int64_t L);
  * (nb = min lattice size / 2 + 1; S_0 = 0). */
 int lf_structure_factor(lf_ctx* ctx, double* out, int64_t nb);
 
+/* Diagnostics sums without any allocation.  The paper has no counterpart:
+ * this serves callers that cannot allocate device memory at the point of the
+ * call -- inside CUDA graph capture, in a loop that must not stall on
+ * cudaMalloc's implicit device synchronisation, or in a host framework that
+ * owns all device memory.  It computes what lf_diag and lf_diag_layers
+ * report, from fields the caller holds on the device:
+ *   phi, T:   [nz][ny][nx] (unpadded, nz = 1 in 2D) of double (LF_FP64) or
+ *             float (LF_FP32);
+ *   moments:  [4][nz][ny][nx] of the same type: n, ux, uy, uz (uz zero in 2D),
+ *             e.g. from lf_fields(LF_FIELD_RHO / UX / UY / UZ);
+ *   out:      device array of 10 + L doubles (L = ny in 2D, nz in 3D):
+ *             out[0..9] = sum n, sum phi, sum n ux, sum n uy, sum n uz,
+ *             sum (d_x phi)^2, sum (d_y phi)^2, sum (d_z phi)^2, free energy
+ *             (phi part), max |u|^2; out[10 + h] = orientation s of layer h.
+ * Work is enqueued on `stream` (cudaStream_t) and the call returns without
+ * waiting; nothing is allocated and no CUDA allocation routine is called.
+ * Scratch: a fixed device array of 162,816 bytes in this library (1216 x 10
+ * partial sums and 2 x 4096 layer sums), present on every GPU that loads
+ * the library until the process exits; L above 4096, or 2^31 or more sites,
+ * is rejected with LF_EINVAL.  The first call on a device resolves that
+ * array's device address (cudaGetSymbolAddress); make it before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (different streams, or devices in one context) race and corrupt each
+ * other's partial sums -- serialise them.  No state carries over between
+ * calls (every partial read is written by the same call). */
+int lf_diag_sums_noalloc(int d, int64_t nx, int64_t ny, int64_t nz, int walls, int precision,
+                         const void* phi, const void* T, const void* moments, double b, double kappa,
+                         double c, double Tc, double* out, void* stream);
+
 /* Checkpoint: writes / reads grid, walls, params (except pointers), step and
  * the full state in the context's precision.  lf_load requires a context
  * created with the same grid, walls and precision (LF_EIO otherwise). */

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lf_diag.cuh"
@@ -508,3 +509,103 @@ int run_sk_shells(const DiagInput& in, double* out_host, int64_t nb, cudaStream_
 }
 
 }  // namespace lf
+
+// ===========================================================================
+// Diagnostics without allocation (lf_diag_sums_noalloc in include/lf.h).
+//
+// For callers that cannot allocate device memory on the way: a reduction
+// started while a CUDA graph is being captured, a real-time loop that must
+// not stall on cudaMalloc's implicit synchronisation, or a host framework
+// that owns every byte of device memory.  Same kernels as lf_diag's sums and
+// layer sums; their scratch (per-CTA partial sums and per-layer sums) lives in
+// the file-scope array below instead of a context's workspace.  Every GPU that
+// loads this library holds the array (kNoAllocScratchBytes) until exit.
+// ===========================================================================
+namespace lf {
+namespace {
+
+constexpr int kNoAllocMaxLayers = 4096;
+constexpr size_t kNoAllocPartDoubles = (size_t)kBlocks * DQ_N;
+constexpr size_t kNoAllocScratchDoubles = kNoAllocPartDoubles + 2 * (size_t)kNoAllocMaxLayers;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+// s(h) = (d sum(d_perp phi)^2 / sum |grad phi|^2 - 1) / (d - 1), per layer.
+__global__ void k_layers_to_s(const double* __restrict__ sums, int L, int d, double* __restrict__ s)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= L) return;
+    const double a = sums[2 * h], b = sums[2 * h + 1];
+    s[h] = b > 0 ? (d * a / b - 1.0) / (d - 1) : 0.0;
+}
+
+// Device address of the scratch array on the current device, resolved once
+// per device (the first call on a device does it; see the header).
+int noalloc_scratch(double** out)
+{
+    static std::mutex mu;
+    static double* addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LF_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return LF_ECUDA;
+        }
+        addr[dev] = (double*)p;
+    }
+    *out = addr[dev];
+    return LF_OK;
+}
+
+}  // namespace
+}  // namespace lf
+
+extern "C" int lf_diag_sums_noalloc(int d, int64_t nx, int64_t ny, int64_t nz, int walls, int precision,
+                                    const void* phi, const void* T, const void* moments, double b, double kappa,
+                                    double c, double Tc, double* out, void* stream)
+{
+    using namespace lf;
+    if (d != 2 && d != 3) return LF_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1 || (d == 2 && nz != 1)) return LF_EINVAL;
+    if (precision != LF_FP64 && precision != LF_FP32) return LF_EINVAL;
+    if (!phi || !T || !moments || !out) return LF_EINVAL;
+    if (!(Tc > 0)) return LF_EINVAL;
+    const int64_t L = d == 2 ? ny : nz;
+    if (L > kNoAllocMaxLayers) return LF_EINVAL;              // the layer sums would not fit
+    if (nx * ny * nz >= ((int64_t)1 << 31)) return LF_EINVAL;
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != LF_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    Geom g{};
+    g.d = d;
+    g.nx = (int)nx; g.ny = (int)ny; g.nz = (int)nz;
+    g.pitch = (int)nx;                                     // caller fields are unpadded
+    g.plane = nx * ny * nz;
+    g.walls = walls ? 1 : 0;
+    // The sums kernel reads n, ux, uy, uz as planes 4..7 of a context's aux
+    // block; the caller's moments block holds exactly those four planes, so
+    // it is addressed through a base four planes before it (only planes 4..7
+    // are ever read).
+    const size_t es = precision == LF_FP64 ? 8 : 4;
+    const uintptr_t aux_addr = (uintptr_t)moments - 4 * (uintptr_t)g.plane * es;
+    const void* aux = (const void*)aux_addr;
+    const int64_t N = nx * ny * nz;
+    const unsigned nblk = grid_n(N);
+    double* part = scratch;
+    double* lay = scratch + kNoAllocPartDoubles;
+    if (precision == LF_FP64)
+        k_diag_partial<double><<<nblk, kThreads, 0, s>>>(g, (const double*)phi, (const double*)T,
+                                                         (const double*)aux, b, kappa, c, Tc, part);
+    else
+        k_diag_partial<float><<<nblk, kThreads, 0, s>>>(g, (const float*)phi, (const float*)T,
+                                                        (const float*)aux, b, kappa, c, Tc, part);
+    k_diag_final<<<1, kThreads, 0, s>>>(part, (int)nblk, out);
+    if (precision == LF_FP64) k_layers<double><<<(unsigned)L, kThreads, 0, s>>>(g, (const double*)phi, lay);
+    else k_layers<float><<<(unsigned)L, kThreads, 0, s>>>(g, (const float*)phi, lay);
+    k_layers_to_s<<<(unsigned)((L + 127) / 128), 128, 0, s>>>(lay, (int)L, d, out + DQ_N);
+    return cudaGetLastError() == cudaSuccess ? LF_OK : LF_ECUDA;
+}

@@ -290,6 +290,22 @@ class Lattice:
             pass
 
 
+# ----------------------------------------------- diagnostics, no allocation
+def lf_diag_sums_noalloc(d, nx, ny, nz, walls, precision, phi_ptr, T_ptr, moments_ptr, b, kappa, c, Tc,
+                         out_ptr, stream_ptr) -> int:
+    """Return code of lf_diag_sums_noalloc (enqueued; no allocation)."""
+    L = lib()
+    if not getattr(L, "_noalloc_ready", False):
+        L.lf_diag_sums_noalloc.argtypes = [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+        L.lf_diag_sums_noalloc.restype = C.c_int
+        L._noalloc_ready = True
+    return L.lf_diag_sums_noalloc(d, nx, ny, nz, walls, precision, C.c_void_p(phi_ptr), C.c_void_p(T_ptr),
+                                  C.c_void_p(moments_ptr), b, kappa, c, Tc, C.c_void_p(out_ptr),
+                                  C.c_void_p(stream_ptr))
+
+
 # ------------------------------------------------------------- ensembles
 def _ens_lib():
     L = lib()
