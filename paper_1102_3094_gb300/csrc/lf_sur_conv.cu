@@ -1,0 +1,247 @@
+// lf_sur_conv.cu -- 3x3 convolution of NHWC BF16 activations on the 5th-gen
+// tensor cores (tcgen05.mma, FP32 accumulator in tensor memory).
+//
+// Implicit GEMM: a CTA computes a tile of 128 consecutive pixels of one image
+// row (M = 128) times all COUT output channels (N), accumulating over the 9
+// taps x CIN input channels (K = 9 CIN, in steps of 16).  Activations live in
+// a padded layout [B][NY + 2][NX + 2][C] whose one-pixel halo holds the
+// boundary rule of the lattice (x periodic: the halo columns copy the opposite
+// edge; y walls: the halo rows are zero), so the A operand of every tap is a
+// plain shifted window of 128 pixels.  All 9 weight taps stay in shared
+// memory; A tiles are double-buffered; one thread issues the MMAs and commits
+// them to an mbarrier per buffer; the epilogue reads TMEM with tcgen05.ld.
+#include <cuda_bf16.h>
+
+#include "lf_internal.cuh"
+#include "lf_sur.h"
+#include "lf_tc.cuh"
+
+namespace lf {
+namespace sur {
+
+struct ConvArgs {
+    const __nv_bfloat16* in;     // padded NHWC, CIN channels
+    const __nv_bfloat16* w;      // [9][COUT][CIN], tap t = 3 (dy + 1) + (dx + 1)
+    const float* bias;           // [COUT] or null
+    const __nv_bfloat16* resid;  // padded NHWC COUT, added after the activation, or null
+    const __nv_bfloat16* mask;   // padded NHWC COUT: out2 = out * (mask > 0), or null
+    __nv_bfloat16* out;          // padded NHWC COUT, or null
+    __nv_bfloat16* out2;         // padded NHWC COUT (masked copy of out), or null
+    __nv_bfloat16* zout;         // padded NHWC COUT: pre-activation value, or null
+    const float* x4;             // [B][NY][NX][4]: y4 = x4 + (acc + bias)[0..3], or null
+    float* y4;
+    int relu;
+    int B, NY, NX;
+    int* err;
+};
+
+template <int CIN, int COUT>
+struct ConvSmem {
+    static constexpr int A_BYTES = 128 * CIN * 2;
+    static constexpr int B_TAP = COUT * CIN * 2;
+    static constexpr int B_OFF = 0;
+    static constexpr int A_OFF = 9 * B_TAP;
+    static constexpr int BAR_OFF = A_OFF + 2 * A_BYTES;
+    static constexpr int BYTES = BAR_OFF + 64;
+    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+};
+
+__device__ __forceinline__ int64_t pix_off(int b, int y, int x, int NY, int NX)
+{
+    return ((int64_t)b * (NY + 2) + (y + 1)) * (NX + 2) + (x + 1);   // padded pixel index
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
+{
+    using S = ConvSmem<CIN, COUT>;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT >= 16 && COUT <= 256, "MMA shape");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sB = smem + S::B_OFF;
+    unsigned char* sA = smem + S::A_OFF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int NY = a.NY, NX = a.NX;
+    const int tiles_per_row = NX / 128;
+    const int ntiles = a.B * NY * tiles_per_row;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+    constexpr uint32_t SBO = (CIN / 8) * 128;
+
+    if (warp == 0) tc::tmem_alloc(tslot, S::TMEM_COLS);
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::fence_mbar_init();
+    }
+    // all 9 weight taps into shared memory (K-major core-matrix layout)
+    for (int q = tid; q < 9 * COUT * (CIN / 8); q += 128) {
+        const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
+        const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
+        tc::cp_async16(sB + t * S::B_TAP + tc::kmajor_offset(n, 8 * j, CIN), a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
+    }
+    tc::cp_async_commit_wait_all();
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    uint32_t ph0 = 0, ph1 = 0;
+    bool ok = true;
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int xt = tile % tiles_per_row;
+        const int row = tile / tiles_per_row;
+        const int y = row % NY, b = row / NY;
+        const int x0 = xt * 128;
+        for (int t = 0; t < 9; ++t) {
+            const int buf = t & 1;
+            if (t >= 2) {   // the MMAs that read this buffer two taps ago are done
+                const bool w = tc::mbar_wait(&bar[buf], buf ? ph1 : ph0);
+                if (buf) ph1 ^= 1; else ph0 ^= 1;
+                if (__syncthreads_or(!w)) { ok = false; break; }
+            }
+            const int dy = t / 3 - 1, dx = t % 3 - 1;
+            const __nv_bfloat16* src = a.in + pix_off(b, y + dy, x0 + dx, NY, NX) * CIN;
+            unsigned char* dA = sA + buf * S::A_BYTES;
+            for (int q = tid; q < 128 * (CIN / 8); q += 128) {
+                const int p = q / (CIN / 8), j = q - p * (CIN / 8);
+                tc::cp_async16(dA + tc::kmajor_offset(p, 8 * j, CIN), src + (int64_t)p * CIN + 8 * j);
+            }
+            tc::cp_async_commit_wait_all();
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t abase = tc::smem_u32(dA), bbase = tc::smem_u32(sB + t * S::B_TAP);
+#pragma unroll
+                for (int s = 0; s < CIN / 16; ++s)
+                    tc::mma_bf16(tmem, tc::smem_desc(abase + 256 * s, 128, SBO), tc::smem_desc(bbase + 256 * s, 128, SBO),
+                                 idesc, (t > 0 || s > 0) ? 1u : 0u);
+                tc::mma_commit(&bar[buf]);
+            }
+        }
+        if (!ok) break;
+        // all MMAs of the tile: tap 7 committed to bar[1], tap 8 to bar[0]
+        bool w = tc::mbar_wait(&bar[1], ph1);
+        ph1 ^= 1;
+        w = w && tc::mbar_wait(&bar[0], ph0);
+        ph0 ^= 1;
+        if (__syncthreads_or(!w)) { ok = false; break; }
+        tc::fence_after_sync();
+
+        // ---- epilogue: thread = pixel (TMEM lane) ---------------------------
+        const int x = x0 + tid;
+        const int64_t po = pix_off(b, y, x, NY, NX);
+        const bool halo_hi = (x == 0), halo_lo = (x == NX - 1);   // copies into columns NX + 1 / 0
+        const int64_t po_h = halo_hi ? pix_off(b, y, NX, NY, NX) : pix_off(b, y, -1, NY, NX);
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (a.bias)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += a.bias[c0 + i];
+            if (a.y4 && c0 == 0) {
+                const int64_t q = (((int64_t)b * NY + y) * NX + x) * 4;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a.y4[q + i] = a.x4[q + i] + v[i];
+            }
+            __align__(16) __nv_bfloat16 hz[16], ho[16], hm[16];
+            if (a.zout)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hz[i] = __float2bfloat16_rn(v[i]);
+            if (a.relu)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+            if (a.resid) {
+                const __nv_bfloat16* r = a.resid + po * COUT + c0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += __bfloat162float(r[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) ho[i] = __float2bfloat16_rn(v[i]);
+            if (a.mask) {
+                const __nv_bfloat16* m = a.mask + po * COUT + c0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hm[i] = __bfloat162float(m[i]) > 0.f ? ho[i] : __float2bfloat16_rn(0.f);
+            }
+            auto store = [&](__nv_bfloat16* base, const __nv_bfloat16* h) {
+                if (!base) return;
+                const uint4* hv = reinterpret_cast<const uint4*>(h);
+                uint4* d = reinterpret_cast<uint4*>(base + po * COUT + c0);
+                d[0] = hv[0];
+                d[1] = hv[1];
+                if (halo_hi || halo_lo) {
+                    uint4* dh = reinterpret_cast<uint4*>(base + po_h * COUT + c0);
+                    dh[0] = hv[0];
+                    dh[1] = hv[1];
+                }
+            };
+            store(a.zout, hz);
+            store(a.out, ho);
+            if (a.mask) store(a.out2, hm);
+        }
+        tc::fence_before_sync();
+        __syncthreads();   // TMEM read out before the next tile's first MMA overwrites it
+    }
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
+{
+    using S = ConvSmem<CIN, COUT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = a.B * a.NY * (a.NX / 128);
+    int blocks = ntiles < 2 * 152 ? ntiles : 2 * 152;
+    k_conv3x3<CIN, COUT><<<blocks, 128, S::BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3x3(int cin, int cout, const ConvArgs& a, cudaStream_t s)
+{
+    if (cin == 16 && cout == 64) return launch_conv<16, 64>(a, s);
+    if (cin == 64 && cout == 64) return launch_conv<64, 64>(a, s);
+    if (cin == 64 && cout == 16) return launch_conv<64, 16>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sur
+}  // namespace lf
+
+extern "C" int lf_sur_conv3x3(int B, int NY, int NX, int cin, int cout, const void* in, const void* w,
+                              const float* bias, int relu, const void* resid, const void* mask, void* out,
+                              void* out2, void* zout, const float* x4, float* y4, int* err, void* stream)
+{
+    using namespace lf;
+    if (B < 1 || NY < 1 || NX < 128 || NX % 128 != 0 || !in || !w || !err) return LF_EINVAL;
+    if (!((cin == 16 && cout == 64) || (cin == 64 && cout == 64) || (cin == 64 && cout == 16))) return LF_EINVAL;
+    if ((mask && !out2) || (!out && !zout && !y4) || (y4 && !x4)) return LF_EINVAL;
+    if (((uintptr_t)in | (uintptr_t)w | (uintptr_t)out | (uintptr_t)out2 | (uintptr_t)zout | (uintptr_t)resid |
+         (uintptr_t)mask) & 15)
+        return LF_EINVAL;                                           // 16-byte vector accesses
+    sur::ConvArgs a{};
+    a.in = (const __nv_bfloat16*)in;
+    a.w = (const __nv_bfloat16*)w;
+    a.bias = bias;
+    a.resid = (const __nv_bfloat16*)resid;
+    a.mask = (const __nv_bfloat16*)mask;
+    a.out = (__nv_bfloat16*)out;
+    a.out2 = (__nv_bfloat16*)out2;
+    a.zout = (__nv_bfloat16*)zout;
+    a.x4 = x4;
+    a.y4 = y4;
+    a.relu = relu;
+    a.B = B; a.NY = NY; a.NX = NX;
+    a.err = err;
+    return sur::conv3x3(cin, cout, a, (cudaStream_t)stream) == cudaSuccess ? LF_OK : LF_ECUDA;
+}

@@ -429,3 +429,37 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- surrogate
+def _sur_lib():
+    L = lib()
+    if not getattr(L, "_sur_ready", False):
+        vp = C.c_void_p
+        L.lf_sur_conv3x3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int, vp, vp,
+                                     vp, vp, vp, vp, vp, vp, vp]
+        L.lf_sur_conv3x3.restype = C.c_int
+        L._sur_ready = True
+    return L
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def lf_sur_conv3x3(B, NY, NX, cin, cout, inp, w, bias=None, relu=0, resid=None, mask=None, out=None, out2=None,
+                   zout=None, x4=None, y4=None, err=None, stream=None):
+    """One tensor-core 3x3 convolution (see include/lf_sur.h); torch tensors in."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _ok(_sur_lib().lf_sur_conv3x3(B, NY, NX, cin, cout, _p(inp), _p(w), _p(bias), relu, _p(resid), _p(mask),
+                                  _p(out), _p(out2), _p(zout), _p(x4), _p(y4), _p(err), C.c_void_p(s.cuda_stream)),
+        "lf_sur_conv3x3")
+
+
+def pad_nhwc(h):
+    """[B, NY, NX, C] torch tensor -> padded [B, NY + 2, NX + 2, C] (periodic x, zero y)."""
+    import torch
+    h = torch.cat([h[:, :, -1:], h, h[:, :, :1]], dim=2)
+    z = torch.zeros_like(h[:, :1])
+    return torch.cat([z, h, z], dim=1).contiguous()
