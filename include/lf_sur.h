@@ -30,6 +30,68 @@
 extern "C" {
 #endif
 
+typedef struct lf_sur lf_sur;
+
+/* Per-channel normalisation of (phi, T, ux, uy): network input and target are
+ * (field - offset) / scale. */
+typedef struct {
+    double scale[4];
+    double offset[4];
+} lf_sur_norm;
+
+typedef struct {
+    int    windows_done;      /* windows completed (surrogate and plain)              */
+    int    surrogate_windows; /* surrogate windows whose prediction was kept          */
+    int    shadow_checks;     /* surrogate windows judged by a plain shadow window    */
+    int    fallbacks;         /* judged windows replaced by the plain result          */
+    double max_phi_l2_err;    /* largest ||phi_sur - phi_plain|| / ||phi_plain||     */
+    double max_sk_err;        /* largest relative error of S(k) peak position/height  */
+    double last_err;          /* error of the last judged window                      */
+    double t_surrogate_s;     /* device time in surrogate predictions                 */
+    double t_shadow_s;        /* device time in shadow windows and comparisons        */
+    double t_plain_s;         /* device time in plain windows                         */
+} lf_sur_report;
+
+/* ---- network ------------------------------------------------------------- */
+
+/* Creates the network for NY x NX lattices (NX a multiple of 128) and batches
+ * of up to max_batch states, weights drawn (He-uniform, last layer x 0.1)
+ * from SplitMix64(seed), Adam state zero.  Allocates its device memory once. */
+int lf_sur_create(int NY, int NX, int max_batch, uint64_t seed, const lf_sur_norm* norm, void* stream,
+                  lf_sur** out);
+
+/* Number of FP32 parameters (per layer: weights [9][cout][cin], then bias [cout]). */
+size_t lf_sur_param_count(void);
+
+/* Master (FP32) parameters to / from host memory, layer by layer in the
+ * order of lf_sur_param_count; set also refreshes the BF16 copies. */
+int lf_sur_get_params(lf_sur* s, float* host);
+int lf_sur_set_params(lf_sur* s, const float* host);
+
+/* Loss of a batch: x, y raw states [B][4][NY][NX] FP32 on the device (y the
+ * target K steps later); loss = mean over B NY NX 4 of (net(x) - y)^2 in
+ * normalised units.  With grads_host non-NULL also the gradient of the loss
+ * with respect to every parameter (same order as the parameters).  Waits. */
+int lf_sur_grads(lf_sur* s, const float* x, const float* y, int B, double* loss, float* grads_host);
+
+/* One training step: loss, gradients (tensor cores), Adam (lr, 0.9, 0.999). */
+int lf_sur_train_step(lf_sur* s, const float* x, const float* y, int B, float lr, double* loss);
+
+/* y = net(x) in raw units, [B][4][NY][NX] FP32 device arrays; enqueued. */
+int lf_sur_predict(lf_sur* s, const float* x, float* y, int B);
+
+/* Runs nwindows windows of K steps on ctx (2D, LF_FP32, hydrodynamics on,
+ * NY x NX): even windows by the surrogate, odd windows by lf_step.  Every
+ * shadow_every-th surrogate window is also advanced by the plain method from
+ * the same state; if max(phi relative L2 error, relative error of the S(k)
+ * peak position or height) exceeds threshold, the plain result replaces the
+ * prediction.  Kept predictions set phi and T and rebuild the populations as
+ * the equilibrium at n0 and the predicted velocity.  Waits; fills *rep. */
+int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shadow_every, double threshold,
+               lf_sur_report* rep);
+
+void lf_sur_destroy(lf_sur* s);
+
 /* ---- building blocks (used by the trainer; exposed for verification) ---- */
 
 /* One 3x3 convolution on the tensor cores, (cin, cout) in {(16, 64), (64, 64),
@@ -43,6 +105,15 @@ extern "C" {
 int lf_sur_conv3x3(int B, int NY, int NX, int cin, int cout, const void* in, const void* w,
                    const float* bias, int relu, const void* resid, const void* mask, void* out,
                    void* out2, void* zout, const float* x4, float* y4, int* err, void* stream);
+
+/* Weight gradient of one such convolution: dW[t][o][i] = sum over pixels p of
+ * h[p + off_t][i] g[p][o] (FP32 [9][cout][cin]), h in the padded NHWC layout
+ * with cin channels, g with cout channels (halo of g unused).  `part` is FP32
+ * device scratch of at least lf_sur_wgrad_scratch_floats(cin, cout) floats
+ * for the per-CTA partial sums (tensor cores), reduced in a second kernel. */
+int lf_sur_conv3x3_wgrad(int B, int NY, int NX, int cin, int cout, const void* h, const void* g,
+                         float* part, size_t part_floats, float* dW, int* err, void* stream);
+size_t lf_sur_wgrad_scratch_floats(int cin, int cout);
 
 #ifdef __cplusplus
 }

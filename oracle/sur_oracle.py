@@ -36,31 +36,39 @@ def conv3x3(h: torch.Tensor, W: torch.Tensor, bias=None) -> torch.Tensor:
     return out
 
 
-def forward(x16: torch.Tensor, Ws, bs):
+def _store_bf16(a: torch.Tensor) -> torch.Tensor:
+    """Value stored in BF16, gradient passed through unchanged."""
+    return a + (a.to(torch.bfloat16).to(a.dtype) - a).detach()
+
+
+def forward(x16: torch.Tensor, Ws, bs, x4=None, bf16_acts=False):
     """The network on normalised input x16 [B, NY, NX, 16] (channels 4.. zero);
-    returns (y [B, NY, NX, 4], intermediates)."""
+    y = x4 + conv(h5)[..., :4] with x4 the unrounded input (x16[..., :4] when
+    omitted).  With bf16_acts the activations are stored in BF16 between
+    layers, as the documented network does.  Returns (y, h list, z list)."""
+    st = _store_bf16 if bf16_acts else (lambda a: a)
     z1 = conv3x3(x16, Ws[0], bs[0])
-    h = torch.relu(z1)
+    h = st(torch.relu(z1))
     hs, zs = [h], [z1]
     for l in range(1, 5):
         z = conv3x3(h, Ws[l], bs[l])
-        h = h + torch.relu(z)
+        h = st(h + torch.relu(z))
         hs.append(h)
         zs.append(z)
     z6 = conv3x3(h, Ws[5], bs[5])
-    y = x16[..., :4] + z6[..., :4]
+    y = (x16[..., :4] if x4 is None else x4) + z6[..., :4]
     return y, hs, zs
 
 
-def loss_and_grads(x16, y_target, Ws, bs):
+def loss_and_grads(x16, y_target, Ws, bs, x4=None, bf16_acts=False):
     """MSE over all outputs and its gradients with respect to every weight and
     bias (autograd through the definitions above)."""
     Wt = [W.clone().requires_grad_(True) for W in Ws]
     bt = [b.clone().requires_grad_(True) for b in bs]
-    y, _, _ = forward(x16, Wt, bt)
+    y, _, _ = forward(x16, Wt, bt, x4=x4, bf16_acts=bf16_acts)
     loss = ((y - y_target) ** 2).mean()
     loss.backward()
-    return float(loss), [W.grad for W in Wt], [b.grad for b in bt]
+    return float(loss.detach()), [W.grad for W in Wt], [b.grad for b in bt]
 
 
 def bf16_round(a) -> np.ndarray:

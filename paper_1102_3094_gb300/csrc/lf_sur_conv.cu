@@ -215,6 +215,213 @@ cudaError_t conv3x3(int cin, int cout, const ConvArgs& a, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3x3 convolution on the tensor cores:
+//   dW[t][o][i] = sum_p h[p + off_t][i] g[p][o]
+// as a GEMM D[(t, i)][o] = sum_p A[(t, i)][p] B[o][p] with M = 128 rows =
+// 128 / CIN taps x CIN channels, N = COUT, K = pixels.  A CTA takes one m-tile
+// of taps and a chunk of image rows; for every 64-pixel segment it stages the
+// three needed input rows and the gradient rows with cp.async, transposes them
+// into K-major tiles in shared memory, and issues four K = 16 MMAs.  Partial
+// D tiles (FP32) go to part[chunk][mtile][128][COUT]; k_wgrad_reduce sums them.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+struct WgSmem {
+    static constexpr int SH = 3 * 66 * CIN * 2;     // input rows y-1, y, y+1, pixels x0-1 .. x0+64
+    static constexpr int SG = 64 * COUT * 2;        // gradient pixels x0 .. x0+63
+    static constexpr int AT = 128 * 64 * 2;         // A tile (K-major, K = 64)
+    static constexpr int BT = COUT * 64 * 2;        // B tile
+    static constexpr int SH_OFF = 0, SG_OFF = SH, A_OFF = SH + SG, B_OFF = A_OFF + AT, BAR_OFF = B_OFF + BT;
+    static constexpr int BYTES = BAR_OFF + 64;
+    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+    static constexpr int TAPS = 128 / CIN;
+    static constexpr int MT = (9 + TAPS - 1) / TAPS;
+};
+
+struct WgArgs {
+    const __nv_bfloat16* h;      // padded NHWC CIN
+    const __nv_bfloat16* g;      // padded NHWC COUT
+    float* part;                 // [nchunks][MT][128][COUT]
+    int B, NY, NX;
+    int rows_per_chunk;
+    int* err;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) k_conv_wgrad(WgArgs a)
+{
+    using S = WgSmem<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(smem + S::SH_OFF);
+    __nv_bfloat16* sg = reinterpret_cast<__nv_bfloat16*>(smem + S::SG_OFF);
+    unsigned char* sA = smem + S::A_OFF;
+    unsigned char* sB = smem + S::B_OFF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int NY = a.NY, NX = a.NX;
+    const int chunk = blockIdx.x, mt = blockIdx.y;
+    const int t_base = mt * S::TAPS;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+
+    if (warp == 0) tc::tmem_alloc(tslot, S::TMEM_COLS);
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    uint32_t ph = 0;
+    bool ok = true, issued = false;
+
+    const int row0 = chunk * a.rows_per_chunk;
+    const int nrows = a.B * NY;
+    const int row1 = min(row0 + a.rows_per_chunk, nrows);
+    const int segs = NX / 64;
+    int kstep = 0;
+    for (int row = row0; row < row1 && ok; ++row) {
+        const int y = row % NY, b = row / NY;
+        for (int sgi = 0; sgi < segs; ++sgi) {
+            const int x0 = sgi * 64;
+            // stage three input rows (pixels x0-1 .. x0+64) and 64 gradient pixels
+            for (int q = tid; q < 3 * 66 * (CIN / 8); q += 128) {
+                const int r = q / (66 * (CIN / 8)), rem = q - r * (66 * (CIN / 8));
+                const int px = rem / (CIN / 8), j = rem - px * (CIN / 8);
+                const __nv_bfloat16* src = a.h + pix_off(b, y + r - 1, x0 - 1 + px, NY, NX) * CIN + 8 * j;
+                tc::cp_async16(sh + ((r * 66 + px) * CIN + 8 * j), src);
+            }
+            for (int q = tid; q < 64 * (COUT / 8); q += 128) {
+                const int px = q / (COUT / 8), j = q - px * (COUT / 8);
+                tc::cp_async16(sg + (px * COUT + 8 * j), a.g + pix_off(b, y, x0 + px, NY, NX) * COUT + 8 * j);
+            }
+            tc::cp_async_commit_wait_all();
+            if (issued) {                      // previous MMAs have finished reading A and B
+                const bool w = tc::mbar_wait(&bar[0], ph);
+                ph ^= 1;
+                if (__syncthreads_or(!w)) { ok = false; break; }
+            } else {
+                __syncthreads();
+            }
+            // A[(t, i)][p] = h[p + off_t][i]: one 16-byte core row (8 pixels) per item
+            for (int q = tid; q < 128 * 8; q += 128) {
+                const int m = q >> 3, j = q & 7;
+                const int t = t_base + m / CIN, i = m % CIN;
+                __align__(16) __nv_bfloat16 v[8];
+                if (t < 9) {
+                    const int dy = t / 3 - 1, dx = t % 3 - 1;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = sh[((dy + 1) * 66 + (8 * j + k + dx + 1)) * CIN + i];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) v[k] = __float2bfloat16_rn(0.f);
+                }
+                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 8 * j, 64)) = *reinterpret_cast<const uint4*>(v);
+            }
+            // B[o][p] = g[p][o]
+            for (int q = tid; q < COUT * 8; q += 128) {
+                const int o = q >> 3, j = q & 7;
+                __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = sg[(8 * j + k) * COUT + o];
+                *reinterpret_cast<uint4*>(sB + tc::kmajor_offset(o, 8 * j, 64)) = *reinterpret_cast<const uint4*>(v);
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t ab = tc::smem_u32(sA), bb = tc::smem_u32(sB);
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    tc::mma_bf16(tmem, tc::smem_desc(ab + 256 * s, 128, 1024), tc::smem_desc(bb + 256 * s, 128, 1024),
+                                 idesc, (kstep > 0 || s > 0) ? 1u : 0u);
+                tc::mma_commit(&bar[0]);
+            }
+            issued = true;
+            ++kstep;
+        }
+    }
+    if (ok && issued) {
+        const bool w = tc::mbar_wait(&bar[0], ph);
+        if (__syncthreads_or(!w)) ok = false;
+    }
+    if (ok) {
+        tc::fence_after_sync();
+        float* dst = a.part + (((int64_t)chunk * S::MT + mt) * 128 + tid) * COUT;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            if (issued) tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            else
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dst[c0 + i] = v[i];
+        }
+    }
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+// dW[t][o][i] = sum over chunks of part[chunk][t / TAPS][(t % TAPS) CIN + i][o]
+template <int CIN, int COUT>
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nchunks, float* __restrict__ dW)
+{
+    using S = WgSmem<CIN, COUT>;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 9 * COUT * CIN) return;
+    const int t = idx / (COUT * CIN), rem = idx - t * COUT * CIN;
+    const int o = rem / CIN, i = rem - o * CIN;
+    const int mt = t / S::TAPS, m = (t % S::TAPS) * CIN + i;
+    float acc = 0.f;
+    for (int c = 0; c < nchunks; ++c) acc += part[(((int64_t)c * S::MT + mt) * 128 + m) * COUT + o];
+    dW[idx] = acc;
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
+                         size_t part_floats, float* dW, int* err, cudaStream_t s)
+{
+    using S = WgSmem<CIN, COUT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nrows = B * NY;
+    int nchunks = (2 * 152 + S::MT - 1) / S::MT;                // about two CTAs per SM
+    if (nchunks > nrows) nchunks = nrows;
+    int rpc = (nrows + nchunks - 1) / nchunks;
+    nchunks = (nrows + rpc - 1) / rpc;
+    if ((size_t)nchunks * S::MT * 128 * COUT > part_floats) return cudaErrorInvalidValue;
+    WgArgs a{h, g, part, B, NY, NX, rpc, err};
+    k_conv_wgrad<CIN, COUT><<<dim3(nchunks, S::MT), 128, S::BYTES, s>>>(a);
+    const int n = 9 * COUT * CIN;
+    k_wgrad_reduce<CIN, COUT><<<(n + 255) / 256, 256, 0, s>>>(part, nchunks, dW);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3x3_wgrad(int cin, int cout, const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX,
+                          float* part, size_t part_floats, float* dW, int* err, cudaStream_t s)
+{
+    if (cin == 16 && cout == 64) return launch_wgrad<16, 64>(h, g, B, NY, NX, part, part_floats, dW, err, s);
+    if (cin == 64 && cout == 64) return launch_wgrad<64, 64>(h, g, B, NY, NX, part, part_floats, dW, err, s);
+    if (cin == 64 && cout == 16) return launch_wgrad<64, 16>(h, g, B, NY, NX, part, part_floats, dW, err, s);
+    return cudaErrorInvalidValue;
+}
+
+// scratch floats the weight-gradient partials need for a (cin, cout) layer
+size_t wgrad_part_floats(int cin, int cout)
+{
+    const int MT = (9 + 128 / cin - 1) / (128 / cin);
+    const int nchunks = (2 * 152 + MT - 1) / MT;
+    return (size_t)nchunks * MT * 128 * cout;
+}
+
 }  // namespace sur
 }  // namespace lf
 
@@ -245,3 +452,17 @@ extern "C" int lf_sur_conv3x3(int B, int NY, int NX, int cin, int cout, const vo
     a.err = err;
     return sur::conv3x3(cin, cout, a, (cudaStream_t)stream) == cudaSuccess ? LF_OK : LF_ECUDA;
 }
+
+extern "C" int lf_sur_conv3x3_wgrad(int B, int NY, int NX, int cin, int cout, const void* h, const void* g,
+                                    float* part, size_t part_floats, float* dW, int* err, void* stream)
+{
+    using namespace lf;
+    if (B < 1 || NY < 1 || NX < 128 || NX % 128 != 0 || !h || !g || !part || !dW || !err) return LF_EINVAL;
+    if (!((cin == 16 && cout == 64) || (cin == 64 && cout == 64) || (cin == 64 && cout == 16))) return LF_EINVAL;
+    if (((uintptr_t)h | (uintptr_t)g) & 15) return LF_EINVAL;
+    if (part_floats < sur::wgrad_part_floats(cin, cout)) return LF_EINVAL;
+    return sur::conv3x3_wgrad(cin, cout, (const __nv_bfloat16*)h, (const __nv_bfloat16*)g, B, NY, NX, part,
+                              part_floats, dW, err, (cudaStream_t)stream) == cudaSuccess ? LF_OK : LF_ECUDA;
+}
+
+extern "C" size_t lf_sur_wgrad_scratch_floats(int cin, int cout) { return lf::sur::wgrad_part_floats(cin, cout); }

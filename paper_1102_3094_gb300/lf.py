@@ -463,3 +463,121 @@ def pad_nhwc(h):
     h = torch.cat([h[:, :, -1:], h, h[:, :, :1]], dim=2)
     z = torch.zeros_like(h[:, :1])
     return torch.cat([z, h, z], dim=1).contiguous()
+
+
+class lf_sur_norm(C.Structure):
+    _fields_ = [("scale", C.c_double * 4), ("offset", C.c_double * 4)]
+
+
+class lf_sur_report(C.Structure):
+    _fields_ = [("windows_done", C.c_int), ("surrogate_windows", C.c_int), ("shadow_checks", C.c_int),
+                ("fallbacks", C.c_int), ("max_phi_l2_err", C.c_double), ("max_sk_err", C.c_double),
+                ("last_err", C.c_double), ("t_surrogate_s", C.c_double), ("t_shadow_s", C.c_double),
+                ("t_plain_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _sur2_lib():
+    L = _sur_lib()
+    if not getattr(L, "_sur2_ready", False):
+        vp = C.c_void_p
+        L.lf_sur_conv3x3_wgrad.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_size_t, vp,
+                                           vp, vp]
+        L.lf_sur_wgrad_scratch_floats.argtypes = [C.c_int, C.c_int]
+        L.lf_sur_wgrad_scratch_floats.restype = C.c_size_t
+        L.lf_sur_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(lf_sur_norm), vp, C.POINTER(vp)]
+        L.lf_sur_param_count.argtypes = []
+        L.lf_sur_param_count.restype = C.c_size_t
+        L.lf_sur_get_params.argtypes = [vp, vp]
+        L.lf_sur_set_params.argtypes = [vp, vp]
+        L.lf_sur_grads.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_double), vp]
+        L.lf_sur_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.POINTER(C.c_double)]
+        L.lf_sur_predict.argtypes = [vp, vp, vp, C.c_int]
+        L.lf_sur_run.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(lf_sur_report)]
+        L.lf_sur_destroy.argtypes = [vp]
+        L.lf_sur_destroy.restype = None
+        for fn in ("lf_sur_conv3x3_wgrad", "lf_sur_create", "lf_sur_get_params", "lf_sur_set_params",
+                   "lf_sur_grads", "lf_sur_train_step", "lf_sur_predict", "lf_sur_run"):
+            getattr(L, fn).restype = C.c_int
+        L._sur2_ready = True
+    return L
+
+
+def lf_sur_conv3x3_wgrad(B, NY, NX, cin, cout, h, g, dW, err, stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    n = _sur2_lib().lf_sur_wgrad_scratch_floats(cin, cout)
+    part = torch.empty(n, dtype=torch.float32, device=h.device)
+    _ok(_sur2_lib().lf_sur_conv3x3_wgrad(B, NY, NX, cin, cout, _p(h), _p(g), _p(part), n, _p(dW), _p(err),
+                                         C.c_void_p(s.cuda_stream)), "lf_sur_conv3x3_wgrad")
+    return part
+
+
+class Surrogate:
+    """The learned surrogate of include/lf_sur.h (marshalling only)."""
+
+    def __init__(self, NY, NX, max_batch, scale, offset, seed=7, stream=None):
+        import torch
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nm = lf_sur_norm()
+        for c in range(4):
+            nm.scale[c] = float(scale[c])
+            nm.offset[c] = float(offset[c])
+        self.h = C.c_void_p()
+        _ok(_sur2_lib().lf_sur_create(NY, NX, max_batch, seed, C.byref(nm), C.c_void_p(self.stream.cuda_stream),
+                                      C.byref(self.h)), "lf_sur_create")
+        self.NY, self.NX = NY, NX
+
+    @staticmethod
+    def param_count():
+        return int(_sur2_lib().lf_sur_param_count())
+
+    def get_params(self):
+        out = np.empty(self.param_count(), dtype=np.float32)
+        _ok(_sur2_lib().lf_sur_get_params(self.h, out.ctypes.data), "lf_sur_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _ok(_sur2_lib().lf_sur_set_params(self.h, p.ctypes.data), "lf_sur_set_params")
+
+    def grads(self, x, y):
+        loss = C.c_double()
+        g = np.empty(self.param_count(), dtype=np.float32)
+        _ok(_sur2_lib().lf_sur_grads(self.h, _p(x), _p(y), x.shape[0], C.byref(loss), g.ctypes.data), "lf_sur_grads")
+        return loss.value, g
+
+    def loss(self, x, y):
+        loss = C.c_double()
+        _ok(_sur2_lib().lf_sur_grads(self.h, _p(x), _p(y), x.shape[0], C.byref(loss), None), "lf_sur_grads")
+        return loss.value
+
+    def train_step(self, x, y, lr):
+        loss = C.c_double()
+        _ok(_sur2_lib().lf_sur_train_step(self.h, _p(x), _p(y), x.shape[0], lr, C.byref(loss)), "lf_sur_train_step")
+        return loss.value
+
+    def predict(self, x):
+        y = self.torch.empty_like(x)
+        _ok(_sur2_lib().lf_sur_predict(self.h, _p(x), _p(y), x.shape[0]), "lf_sur_predict")
+        return y
+
+    def run(self, lattice, K, nwindows, shadow_every, threshold):
+        rep = lf_sur_report()
+        _ok(_sur2_lib().lf_sur_run(self.h, lattice.ctx, K, nwindows, shadow_every, threshold, C.byref(rep)),
+            "lf_sur_run")
+        return rep.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _sur2_lib().lf_sur_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
