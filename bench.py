@@ -248,6 +248,106 @@ def run_ensemble(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned surrogate at 256 x 256: trajectories of the plain solver (an
+    ensemble, xi log-uniform in [1e-4, 1]) -> (state, state K steps later)
+    pairs; training on the tensor-core kernels; then the same number of steps
+    of a fresh run done plain-only and interleaved (surrogate windows judged by
+    plain shadow windows), time-to-solution and S(k) error compared."""
+    import numpy as np
+    import torch
+
+    from paper_1102_3094_gb300 import lf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    NY = NX = 256
+    K = 50
+    rng = np.random.default_rng(2011)
+    nruns, nwin, warm = args.sur_runs, args.sur_windows, 400
+    members = [dict(nx=NX, ny=NY, xi=float(10 ** rng.uniform(-4, 0)), tau=1.0, seed=500 + i) for i in range(nruns)]
+    with torch.cuda.stream(stream):
+        t0 = time.time()
+        ens = lf.Ensemble(members, stream=stream)
+        ens.step(warm)
+        xs, ys = [], []
+
+        def snap():
+            return [torch.stack([ens.run(r).get(n, "fp32", device=True) for n in ("phi", "T", "ux", "uy")])
+                    for r in range(nruns)]
+        prev = snap()
+        for w in range(nwin):
+            ens.step(K)
+            cur = snap()
+            for r in range(nruns):
+                if torch.isfinite(prev[r]).all() and torch.isfinite(cur[r]).all():
+                    xs.append(prev[r])
+                    ys.append(cur[r])
+            prev = cur
+        X, Y = torch.stack(xs), torch.stack(ys)
+        ens.close()
+        t_data = time.time() - t0
+        flat = X.permute(1, 0, 2, 3).reshape(4, -1)
+        scale = flat.std(dim=1).clamp_min(1e-4).cpu().numpy()
+        offset = flat.mean(dim=1).cpu().numpy()
+        B = 8
+        sur = lf.Surrogate(NY, NX, B, scale=scale, offset=offset, seed=7, stream=stream)
+        npairs = X.shape[0]
+        perm = torch.randperm(npairs, generator=torch.Generator().manual_seed(0))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        losses = []
+        ev[0].record(stream)
+        for it in range(args.sur_iters):
+            idx = perm[(it * B) % max(1, npairs - B):][:B].to(dev)
+            l = sur.train_step(X[idx].contiguous(), Y[idx].contiguous(), args.sur_lr)
+            if it % 50 == 0 or it == args.sur_iters - 1:
+                losses.append((it, l))
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_train = ev[0].elapsed_time(ev[1]) / 1e3
+        # evaluation run: fresh state, same physics, xi in the middle of the range
+        ev_kw = dict(nx=NX, ny=NY, precision="fp32", xi=1e-2, tau=1.0, seed=9001, stream=stream, device=dev)
+        plain = lf.Lattice(**ev_kw)
+        hyb = lf.Lattice(**ev_kw)
+        plain.step(warm)
+        hyb.step(warm)
+        torch.cuda.synchronize(dev)
+        nsteps = args.sur_eval_windows * K
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        plain.step(nsteps)
+        e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_plain = e[0].elapsed_time(e[1]) / 1e3
+        t1 = time.time()
+        rep = sur.run(hyb, K, args.sur_eval_windows, args.sur_shadow_every, 0.02)
+        t_hyb = time.time() - t1
+        dp, dh = plain.diag(), hyb.diag()
+        pp, ph = plain.get("phi", "fp32"), hyb.get("phi", "fp32")
+        l2 = float(np.linalg.norm(ph - pp) / np.linalg.norm(pp))
+    sk_err = max(abs(dh["k_peak"] / dp["k_peak"] - 1), abs(dh["s_peak"] / dp["s_peak"] - 1))
+    sites = NX * NY
+    line = {
+        "metric": METRIC + " (surrogate-interleaved time to solution)", "value": 1e-6 * sites * nsteps / t_hyb,
+        "unit": "MLUPS", "n_gpus": 1, "steps": nsteps, "warmup": warm, "ms_per_step": 1e3 * t_hyb / nsteps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+        "config": {"workload": "sur256: 256x256 lamellar quench, 6-layer 64-channel residual CNN advancing "
+                               f"(phi, T, ux, uy) by K={K} steps, trained on {npairs} pairs from {nruns} solver "
+                               "trajectories (xi log-uniform in [1e-4, 1]); evaluation at xi = 1e-2",
+                   "train_iters": args.sur_iters, "batch": B, "lr": args.sur_lr,
+                   "shadow_every": args.sur_shadow_every, "threshold": 0.02},
+        "surrogate": {"t_data_s": t_data, "t_train_s": t_train, "losses": losses, "report": rep,
+                      "t_plain_only_s": t_plain, "t_interleaved_wall_s": t_hyb,
+                      "speedup_vs_plain": t_plain / t_hyb, "final_phi_rel_l2_vs_plain": l2,
+                      "final_sk_peak_err_vs_plain": sk_err},
+    }
+    print(json.dumps(line), flush=True)
+    for o in (plain, hyb, sur):
+        o.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -397,7 +497,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["prec1024", "cube384", "ens96"], default="prec1024")
+    ap.add_argument("--workload", choices=["prec1024", "cube384", "ens96", "sur256"], default="prec1024")
+    ap.add_argument("--sur-runs", type=int, default=16)
+    ap.add_argument("--sur-windows", type=int, default=20)
+    ap.add_argument("--sur-iters", type=int, default=600)
+    ap.add_argument("--sur-lr", type=float, default=1e-3)
+    ap.add_argument("--sur-eval-windows", type=int, default=40)
+    ap.add_argument("--sur-shadow-every", type=int, default=4)
     ap.add_argument("--size", type=int, default=1024, help="2D lattice side (prec1024)")
     ap.add_argument("--size3", type=int, default=384, help="3D lattice side (cube384)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
@@ -414,6 +520,8 @@ def main():
         return run_reference(args)
     if args.workload == "ens96":
         return run_ensemble(args)
+    if args.workload == "sur256":
+        return run_surrogate(args)
     return run_ours(args)
 
 
