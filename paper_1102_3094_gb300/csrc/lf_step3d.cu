@@ -30,6 +30,11 @@ __device__ __forceinline__ int wrap_any3(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+template <typename R>
+__device__ __forceinline__ R recip3(R x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ float recip3<float>(float x) { return __frcp_rn(x); }
+
 __device__ __forceinline__ int map_axis3(int v, int n, int walls)
 {
     if (!walls) return wrap_any3(v, n);
@@ -65,11 +70,13 @@ struct Plane3 {
     static constexpr int GXY = MU + 4 * A1;           // gx, gy: 2 planes each
     static constexpr int GZ = GXY + 4 * A1;           // gz: 3 planes
     static constexpr int TOTAL = GZ + 3 * A1;
-    static constexpr size_t BYTES = sizeof(R) * TOTAL;
+    // wrapped storage column / row of every position of the r = 4 region
+    static constexpr size_t MAPS = sizeof(R) * TOTAL;
+    static constexpr size_t BYTES = MAPS + sizeof(int) * (W4 + H4);
 };
 
 template <typename R, int TX, int TY, int NT, bool AUX>
-__global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io, int Hz)
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1) k_march3d(Geom g, Phys<R> p, StepIO<R> io, int Hz)
 {
     using L = D3Q19;
     using P3 = Plane3<R, TX, TY>;
@@ -85,6 +92,8 @@ __global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io,
     R* smu = sm + P3::MU;     // [plane mod 4][A1]
     R* sgxy = sm + P3::GXY;   // [comp 0..1][parity][A1]
     R* sgz = sm + P3::GZ;     // [plane mod 3][A1]
+    int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);   // x0 - 4 + lx -> storage column
+    int* rowmap = colmap + W4;                                   // y0 - 4 + ly -> storage row
 
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
     const int64_t plane = g.plane;                   // one population field
@@ -94,6 +103,12 @@ __global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io,
     const int kbeg = z0 - 4, kend = z1 + 3;
     const R half = R(0.5);
     bool bad = false;
+
+    for (int q = threadIdx.x; q < W4 + P3::H4; q += NT) {
+        if (q < W4) colmap[q] = wrap_any3(x0 - 4 + q, nx);
+        else rowmap[q - W4] = wrap_any3(y0 - 4 + (q - W4), ny);
+    }
+    __syncthreads();
 
     // plane ring slots are counted from kbeg
     auto ring = [&](int z, int n) { return (z - kbeg) % n; };
@@ -105,8 +120,7 @@ __global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io,
             R* dT = sT + ring(z, P3::NT_) * A2;
             for (int q = threadIdx.x; q < A4; q += NT) {
                 const int ly = q / W4, lx = q - ly * W4;
-                const int gx = wrap_any3(x0 - 4 + lx, nx), gy = wrap_any3(y0 - 4 + ly, ny);
-                const int64_t off = gz * zs + (int64_t)gy * pitch + gx;
+                const int64_t off = gz * zs + (int64_t)rowmap[ly] * pitch + colmap[lx];
                 cp_async3<sizeof(R)>(&dphi[q], io.phi_in + off);
                 if (lx >= 2 && lx < W4 - 2 && ly >= 2 && ly < P3::H4 - 2)
                     cp_async3<sizeof(R)>(&dT[(ly - 2) * W2 + lx - 2], io.T_in + off);
@@ -237,7 +251,7 @@ __global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io,
                                    + half * (sPz[(1 * 3 + pz0) * A2 + c2 + W2] - sPz[(1 * 3 + pz0) * A2 + c2 - W2])
                                    + half * (sPz[(2 * 3 + pzu) * A2 + c2] - sPz[(2 * 3 + pzd) * A2 + c2]));
                     const int ux = x0 - 1 + lx, uy = y0 - 1 + ly;
-                    const int gx = wrap_any3(ux, nx), gy = wrap_any3(uy, ny);
+                    const int gx = colmap[lx + 3], gy = rowmap[ly + 3];
                     const int64_t site = gzp * zs + (int64_t)gy * pitch + gx;
                     R df[L::Q];
                     R dn = 0, jx = 0, jy = 0, jz = 0;
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io,
                         jz += R(L::ez(i)) * df[i];
                     }
                     const R n = p.n0 + dn;
-                    const R inv_n = R(1) / n;
+                    const R inv_n = recip3(n);
                     const bool hyd = p.hydro != 0;
                     const R vx = hyd ? (jx + half * Fx) * inv_n : R(0);
                     const R vy = hyd ? (jy + half * Fy) * inv_n : R(0);
@@ -267,28 +281,41 @@ __global__ void __launch_bounds__(NT) k_march3d(Geom g, Phys<R> p, StepIO<R> io,
                             io.u[0][site] = vx; io.u[1][site] = vy; io.u[2][site] = vz;
                             io.F[0][site] = Fx; io.F[1][site] = Fy; io.F[2][site] = Fz;
                         } else if (hyd) {
-                            const R uu = vx * vx + vy * vy + vz * vz;
-                            const R uF = vx * Fx + vy * Fy + vz * Fz;
-                            const int gxp = gx + 1 == nx ? 0 : gx + 1, gxm = gx == 0 ? nx - 1 : gx - 1;
-                            const int gyp = gy + 1 == ny ? 0 : gy + 1, gym = gy == 0 ? ny - 1 : gy - 1;
+                            // Eq. evoleqn with the Qian equilibrium and Guo's term, written per
+                            // opposite pair (i, i'): f*_i = (1 - w) df_i + w_i (sym +- anti)
+                            const R omega = p.inv_tau, keep = R(1) - p.inv_tau;
+                            const R on = omega * n;
+                            const R C0 = omega * dn - R(1.5) * on * (vx * vx + vy * vy + vz * vz)
+                                       - R(3) * p.guo * (vx * Fx + vy * Fy + vz * Fz);
+                            const R a3 = R(3) * on, a45 = R(4.5) * on, g3 = R(3) * p.guo, g9 = R(9) * p.guo;
+                            const int gxp = colmap[lx + 4], gxm = colmap[lx + 2];
+                            const int gyp = rowmap[ly + 4], gym = rowmap[ly + 2];
                             const int gzu = gzp + 1 == nz ? 0 : gzp + 1, gzd = gzp == 0 ? nz - 1 : gzp - 1;
+                            const bool wall_lo = walls && gzp == 0, wall_hi = walls && gzp == nz - 1;
+                            R* out = io.f_out;
+                            out[site] = keep * df[0] + R(L::w(0)) * C0;
+                            auto dest = [&](int ex, int ey, int ez) -> int64_t {
+                                const int tx = ex > 0 ? gxp : (ex < 0 ? gxm : gx);
+                                const int ty = ey > 0 ? gyp : (ey < 0 ? gym : gy);
+                                const int tz = ez > 0 ? gzu : (ez < 0 ? gzd : gzp);
+                                return tz * zs + (int64_t)ty * pitch + tx;
+                            };
 #pragma unroll
-                            for (int i = 0; i < L::Q; ++i) {
+                            for (int i = 1; i < L::Q; i += 2) {           // (i, i + 1) are opposite
                                 const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+                                const R sv = R(ex) * vx + R(ey) * vy + R(ez) * vz;
+                                const R ev = R(ex) * Fx + R(ey) * Fy + R(ez) * Fz;
+                                const R sym = C0 + sv * (a45 * sv + g9 * ev);
+                                const R anti = a3 * sv + g3 * ev;
                                 const R wi = R(L::w(i));
-                                const R eu = R(ex) * vx + R(ey) * vy + R(ez) * vz;
-                                const R eF = R(ex) * Fx + R(ey) * Fy + R(ez) * Fz;
-                                const R dfeq = wi * (dn + n * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu));
-                                const R Fi = p.guo * wi * (R(3) * (eF - uF) + R(9) * eu * eF);
-                                const R post = df[i] - (df[i] - dfeq) * p.inv_tau + Fi;
-                                if (walls && ((ez < 0 && gzp == 0) || (ez > 0 && gzp == nz - 1))) {
-                                    io.f_out[L::opp(i) * plane + site] = post;   // halfway bounce-back
-                                } else {
-                                    const int tx = ex > 0 ? gxp : (ex < 0 ? gxm : gx);
-                                    const int ty = ey > 0 ? gyp : (ey < 0 ? gym : gy);
-                                    const int tz = ez > 0 ? gzu : (ez < 0 ? gzd : gzp);
-                                    io.f_out[i * plane + tz * zs + (int64_t)ty * pitch + tx] = post;
-                                }
+                                const R pi = keep * df[i] + wi * (sym + anti);
+                                const R pj = keep * df[i + 1] + wi * (sym - anti);
+                                const bool bb_i = (ez > 0 && wall_hi) || (ez < 0 && wall_lo);
+                                const bool bb_j = (ez < 0 && wall_hi) || (ez > 0 && wall_lo);
+                                if (bb_i) out[(i + 1) * plane + site] = pi;   // halfway bounce-back
+                                else out[i * plane + dest(ex, ey, ez)] = pi;
+                                if (bb_j) out[i * plane + site] = pj;
+                                else out[(i + 1) * plane + dest(-ex, -ey, -ez)] = pj;
                             }
                         }
                     }
@@ -357,8 +384,8 @@ cudaError_t launch_cfg3(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cu
     }
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int Hz = g.tune > 0 ? g.tune : g.nz;
-    if (g.tune <= 0) {   // enough CTAs for about three per SM, segments of at least 16 planes
-        const int want = (3 * 152 + tiles - 1) / tiles;
+    if (g.tune <= 0) {   // about eight waves of three CTAs per SM, segments of at least 16 planes
+        const int want = (8 * 3 * 152 + tiles - 1) / tiles;
         Hz = (g.nz + want - 1) / want;
         if (Hz < 16) Hz = 16;
     }
