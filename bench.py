@@ -415,7 +415,7 @@ def run_ours(args):
     launches_per_step = 1 + (lf.lf_nsub(args.xi, d) - 1 if args.xi not in (0.0, math.inf) else 0)
     kernel_ms = statistics.mean(times_ms) / launches_per_step
     achieved = bps * N / (kernel_ms * 1e-3) / 1e9
-    kname = "k_march3d" if d == 3 else ("k_march2d" if args.variant == "march" else "k_step2d")
+    kname = "k_march3d" if d == 3 else {"march": "k_march2d", "march2": "k_march2d_x2", "tile": "k_step2d"}[args.variant]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_for(f"{kname}_{prec}_{nx}"), "peak_kind": peak_kind,
             "algorithmic_bytes_per_site": bps,
@@ -510,7 +510,7 @@ def main():
     ap.add_argument("--xi", type=float, default=1e-3)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--variant", choices=["march", "tile"], default="march",
+    ap.add_argument("--variant", choices=["march", "tile", "march2"], default="march",
                     help="step kernel variant (both compute the same step)")
     ap.add_argument("--tune", type=int, default=0, help="march: rows per CTA segment (0 = automatic)")
     args = ap.parse_args()

@@ -224,13 +224,18 @@ int lf_load(lf_ctx* ctx, const char* path);
 /* Kernel variant of the step.  Both compute the same step (parity-tested
  * against the oracle); they differ in how work is mapped to the GPU:
  *   LF_VARIANT_MARCH (default): one thread per column, a CTA marches down a
- *     segment of `param` rows (0 = chosen from the lattice size), inputs
- *     prefetched with cp.async;
+ *     segment of (param & 0xFFFF) rows (0 = chosen from the lattice size),
+ *     inputs prefetched with cp.async; (param >> 16) == 1 selects CTAs of 64
+ *     threads (56 columns) instead of 128 (120 columns);
  *   LF_VARIANT_TILE: one CTA per 2D tile, each stage of the step on the whole
- *     tile in shared memory (`param` ignored).
+ *     tile in shared memory (`param` ignored);
+ *   LF_VARIANT_MARCH2 (FP32; FP64 contexts use LF_VARIANT_MARCH): the march
+ *     with two segments per CTA carried in the two lanes of packed FP32x2
+ *     arithmetic (param: rows per segment as for LF_VARIANT_MARCH).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
-#define LF_VARIANT_MARCH 0
-#define LF_VARIANT_TILE  1
+#define LF_VARIANT_MARCH  0
+#define LF_VARIANT_TILE   1
+#define LF_VARIANT_MARCH2 2
 int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
 
 /* Current step counter. */

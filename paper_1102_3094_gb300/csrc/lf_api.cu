@@ -505,7 +505,9 @@ int64_t lf_step_count(const lf_ctx* c) { return c ? c->step : -1; }
 
 int lf_set_kernel_variant(lf_ctx* c, int variant, int param)
 {
-    if (!c || (variant != LF_VARIANT_MARCH && variant != LF_VARIANT_TILE) || param < 0) return LF_EINVAL;
+    if (!c || (variant != LF_VARIANT_MARCH && variant != LF_VARIANT_TILE && variant != LF_VARIANT_MARCH2) ||
+        param < 0)
+        return LF_EINVAL;
     c->g.variant = variant;
     c->g.tune = param;
     return LF_OK;

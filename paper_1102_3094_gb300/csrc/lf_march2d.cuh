@@ -129,7 +129,7 @@ __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p,
     R pxyB = 0, pxyC = 0, pyyB = 0, pyyC = 0;
     R muB = 0, muC = 0, muD = 0;
     R gyB = 0, gyC = 0;
-    bool bad = false;
+    R probe = 0;              // sum of the outputs: NaN / Inf anywhere make it non-finite
 
     // ring positions: sk = (k - kbeg) mod SIN, m3 = (k - kbeg) mod 3
     int s_issue = 0;                                 // slot of the next phi / T row to fetch
@@ -155,6 +155,7 @@ __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p,
     for (int j = kbeg - D; j < kbeg; ++j) issue(j);
 
     int sk = 0, m3 = 0;
+#pragma unroll 2
     for (int k = kbeg; k <= kend; ++k) {
         cp_wait<D - 1>();
         __syncthreads();
@@ -186,7 +187,7 @@ __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p,
                     Tn = T1 + p.dxi * (sT[s1 * NT + t - 1] + sT[s1 * NT + t + 1] + tu + td - R(4) * T1);
                 }
             }
-            bad |= !isfinite(Tn);
+            probe += Tn;
             io.T_out[r1 * pitch + gx] = Tn;
         }
 
@@ -241,7 +242,7 @@ __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p,
                 gxv = phi3 * vx;
                 gyA = phi3 * vy;
                 if (own && r3 >= y0 && r3 < y1) {
-                    bad |= !isfinite(n);
+                    probe += n;
                     // Eq. evoleqn with the Qian equilibrium and Guo's term, written
                     // per opposite pair (i, i'): f*_i = (1 - w) df_i + w_i (sym +- anti)
                     const R on = omega * n;
@@ -289,7 +290,7 @@ __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p,
                 div = half * (sgx[qg + 1] - sgx[qg - 1]) + half * (gu - gd);
             }
             const R phn = phi4 - div + p.Gamma * lapmu;
-            bad |= !isfinite(phn);
+            probe += phn;
             io.phi_out[r4 * pitch + gx] = phn;
         }
 
@@ -304,7 +305,7 @@ __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p,
         m3 = (m3 == 2) ? 0 : m3 + 1;
     }
     cp_wait<0>();
-    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+    if (__any_sync(0xffffffffu, !isfinite(probe)) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
 
@@ -344,6 +345,19 @@ inline int march_rows_for(int nx, int ny, int U, int param)
     if (h < 12) h = 12;
     if (h > ny) h = ny;
     return h;
+}
+
+// Rows per segment for the two-segment kernel: the smallest H >= 8 whose CTAs
+// (strips x segment pairs) all fit in one wave of `slots` resident CTAs.
+inline int march2_rows_for(int nx, int ny, int U, int param, int slots)
+{
+    if (param > 0) return param < ny ? param : ny;
+    const int strips = (nx + U - 1) / U;
+    for (int h = 8; h < ny; ++h) {
+        const int pairs = ((ny + h - 1) / h + 1) / 2;
+        if ((int64_t)strips * pairs <= slots) return h;
+    }
+    return ny;
 }
 
 }  // namespace march

@@ -24,6 +24,7 @@
 // in the last stage.  Populations are stored as deviations f_i - w_i n0.
 #include "lf_internal.cuh"
 #include "lf_march2d.cuh"
+#include "lf_march2d_x2.cuh"
 
 namespace lf {
 
@@ -281,18 +282,52 @@ __global__ void __launch_bounds__(NT) k_march2d(Geom g, Phys<R> p, StepIO<R> io,
     march::march2d_segment<R, NT, D>(g, p, io, blockIdx.x, blockIdx.y, H, smem_raw);
 }
 
+// Two segments per CTA in the lanes of float2 (packed FP32x2 arithmetic).
+template <int NT, int D, bool HYDRO>
+__global__ void __launch_bounds__(NT, 3) k_march2d_x2(Geom g, Phys<float> p, StepIO<float> io, int H)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    march::march2d_pair<NT, D, HYDRO>(g, p, io, blockIdx.x, blockIdx.y, H, smem_raw);
+}
+
+template <int NT, int D, bool HYDRO>
+cudaError_t launch_march_x2(const Geom& g, const Phys<float>& p, const StepIO<float>& io, cudaStream_t s)
+{
+    using M = march::March2<NT, D>;
+    auto kern = k_march2d_x2<NT, D, HYDRO>;
+    static int slots = 0;   // resident CTAs on the whole device
+    if (slots == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, M::BYTES)) != cudaSuccess) return e;
+        slots = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, slots);
+    const int nseg = (g.ny + H - 1) / H;
+    dim3 grid((g.nx + M::U - 1) / M::U, (nseg + 1) / 2);
+    kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
+    return cudaGetLastError();
+}
+
 template <typename R, int NT, int D>
 cudaError_t launch_march(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
     using M = march::March<R, NT, D>;
     auto kern = k_march2d<R, NT, D>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static int slots = 0;   // resident CTAs on the whole device
+    if (slots == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::BYTES);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, M::BYTES)) != cudaSuccess) return e;
+        slots = sms * (per_sm > 0 ? per_sm : 1);
     }
-    const int H = march::march_rows_for(g.nx, g.ny, M::U, g.tune);
+    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, slots);
     dim3 grid((g.nx + M::U - 1) / M::U, (g.ny + H - 1) / H);
     kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
     return cudaGetLastError();
@@ -331,7 +366,12 @@ __global__ void k_tsub2d(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __rest
 template <typename R>
 cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
-    if (!aux && g.variant == LF_VARIANT_MARCH) return launch_march<R, 128, 3>(g, p, io, s);
+    if constexpr (sizeof(R) == 4) {
+        if (!aux && g.variant == LF_VARIANT_MARCH2)
+            return p.hydro ? launch_march_x2<128, 3, true>(g, p, io, s) : launch_march_x2<128, 3, false>(g, p, io, s);
+    }
+    if (!aux && (g.variant == LF_VARIANT_MARCH || g.variant == LF_VARIANT_MARCH2))
+        return (g.tune >> 16) == 1 ? launch_march<R, 64, 3>(g, p, io, s) : launch_march<R, 128, 3>(g, p, io, s);
     if constexpr (sizeof(R) == 4) {
         return aux ? launch_cfg<R, 64, 16, 256, true>(g, p, io, s)
                    : launch_cfg<R, 64, 16, 256, false>(g, p, io, s);
