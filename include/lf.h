@@ -223,15 +223,17 @@ int lf_load(lf_ctx* ctx, const char* path);
 
 /* Kernel variant of the step.  Both compute the same step (parity-tested
  * against the oracle); they differ in how work is mapped to the GPU:
- *   LF_VARIANT_MARCH (default): one thread per column, a CTA marches down a
- *     segment of (param & 0xFFFF) rows (0 = chosen from the lattice size),
- *     inputs prefetched with cp.async; (param >> 16) == 1 selects CTAs of 64
- *     threads (56 columns) instead of 128 (120 columns);
+ *   LF_VARIANT_MARCH (default for FP64 and 3D): one thread per column, a CTA
+ *     marches down a segment of (param & 0xFFFF) rows (0 = chosen from the
+ *     lattice size), inputs prefetched with cp.async; (param >> 16) == 1
+ *     selects CTAs of 64 threads (56 columns) instead of 128 (120 columns);
  *   LF_VARIANT_TILE: one CTA per 2D tile, each stage of the step on the whole
  *     tile in shared memory (`param` ignored);
- *   LF_VARIANT_MARCH2 (FP32; FP64 contexts use LF_VARIANT_MARCH): the march
- *     with two segments per CTA carried in the two lanes of packed FP32x2
- *     arithmetic (param: rows per segment as for LF_VARIANT_MARCH).
+ *   LF_VARIANT_MARCH2 (default for 2D FP32; FP64 contexts run LF_VARIANT_MARCH
+ *     instead): a CTA owns two vertically adjacent segments of a strip that
+ *     march away from their common row, carried in the two lanes of packed
+ *     FP32x2 arithmetic; param = rows per segment (0 = chosen from the lattice
+ *     size and the SM count).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
 #define LF_VARIANT_MARCH  0
 #define LF_VARIANT_TILE   1

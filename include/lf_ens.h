@@ -7,11 +7,12 @@
  * together.  Each run is an ordinary lf_ctx (so lf_fields, lf_fields_set,
  * lf_diag, lf_save and lf_load work on it) whose steps are taken by the
  * ensemble: one persistent kernel per time step walks a work list of
- * (run, strip, segment) items, and the steps are replayed from a CUDA graph.
- * Results are bit-identical to stepping every run alone with lf_step (the
- * per-site arithmetic is the same code).
+ * (run, strip, segment pair) items, and the steps are replayed from a CUDA
+ * graph.  Results are bit-identical to stepping every run alone with lf_step
+ * under LF_VARIANT_MARCH2 with param = lf_ens_rows(e, r) (the per-site
+ * arithmetic is the same code and the rows are split the same way).
  *
- * Restrictions: every run is two-dimensional (d = 2) and LF_FP32.
+ * Restrictions: every run is two-dimensional (d = 2), LF_FP32, ny >= 2.
  * Conventions (return codes, layouts, ownership) are those of lf.h.
  */
 #ifndef LF_ENS_H
@@ -28,8 +29,8 @@ typedef struct lf_ens lf_ens;
 /* Creates nruns contexts, run r from grids[r], walls[r], params[r] (the
  * stream, workspace and workspace_bytes fields of params are ignored), all in
  * one device arena, enqueued on `stream` (a cudaStream_t; 0 = a private
- * stream the ensemble creates).  LF_EINVAL if a run is not d = 2 / LF_FP32
- * or fails lf_create's checks (then nothing is allocated). */
+ * stream the ensemble creates).  LF_EINVAL if a run is not d = 2 / LF_FP32 /
+ * ny >= 2 or fails lf_create's checks (then nothing is allocated). */
 int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const lf_params* params,
                   void* stream, lf_ens** out);
 
@@ -39,7 +40,8 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
  * states are not touched.  Rebuilds the work list and the graphs. */
 int lf_ens_tune(lf_ens* e, int reps);
 
-/* Segment height the work list uses for run r (after tuning, or automatic). */
+/* Rows per segment the work list uses for run r (after tuning, or the
+ * default min(16, ny / 2)). */
 int lf_ens_rows(const lf_ens* e, int run);
 
 /* Enqueues nsteps steps of every run on the ensemble's stream (graph

@@ -318,7 +318,7 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
     c->g.plane = plane;
     c->g.walls = walls->walls;
     c->g.t_mode = walls->t_wall_mode;
-    c->g.variant = LF_VARIANT_MARCH;
+    c->g.variant = (grid->d == 2 && params->precision == LF_FP32) ? LF_VARIANT_MARCH2 : LF_VARIANT_MARCH;
     c->g.tune = 0;
 
     if (params->workspace) {

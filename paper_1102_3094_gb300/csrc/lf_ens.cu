@@ -2,8 +2,9 @@
 //
 // Every run is an ordinary context placed in one shared device arena.  A time
 // step of the whole ensemble is one launch of a persistent kernel that walks
-// a work list of (run, strip, segment) items -- each item is exactly the
-// row-marching step of lf_march2d.cuh -- followed, when some runs need extra
+// a work list of (run, strip, pair) items -- each item is exactly the
+// two-lane row-marching step of lf_march2d_x2.cuh (two segments of a strip
+// marching away from their common row) -- followed, when some runs need extra
 // temperature sub-steps, by one launch per sub-step over the tiles of those
 // runs.  Every run returns to its starting buffers after two steps (f and phi
 // flip once per step, T flips nsub times), so two steps are captured in one
@@ -19,14 +20,14 @@
 
 #include "lf_ctx.cuh"
 #include "lf_ens.h"
-#include "lf_march2d.cuh"
+#include "lf_march2d_x2.cuh"
 
 using namespace lf;
 
 namespace {
 
 constexpr int kNT = 128, kD = 3;
-using MarchCfg = march::March<float, kNT, kD>;
+using MarchCfg = march::March2<kNT, kD>;
 
 struct EnsRun {
     Geom g;
@@ -35,7 +36,7 @@ struct EnsRun {
 };
 
 struct EnsItem {
-    int run, strip, seg, H;
+    int run, strip, pair, npairs;
 };
 
 struct EnsT {
@@ -49,16 +50,28 @@ struct EnsTItem {
     int run, bx, by;
 };
 
-__global__ void __launch_bounds__(kNT) k_ens_march2d(const EnsRun* __restrict__ runs,
-                                                    const EnsItem* __restrict__ items, int nitems)
+__global__ void __launch_bounds__(kNT, 3) k_ens_march2d(const EnsRun* __restrict__ runs,
+                                                       const EnsItem* __restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const EnsItem w = items[it];
         const EnsRun r = runs[w.run];
-        march::march2d_segment<float, kNT, kD>(r.g, r.p, r.io, w.strip, w.seg, w.H, smem_raw);
+        if (r.p.hydro)
+            march::march2d_pair<kNT, kD, true>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
+        else
+            march::march2d_pair<kNT, kD, false>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
         __syncthreads();   // the next item reuses the shared rings
     }
+}
+
+// Pairs of segments of a run with H rows per segment (as the single-run
+// launcher counts them, so a run stepped alone with the same H matches).
+int pairs_for(int ny, int H)
+{
+    int np = (ny + 2 * H - 1) / (2 * H);
+    if (np > ny / 2) np = ny / 2;
+    return np < 1 ? 1 : np;
 }
 
 __global__ void __launch_bounds__(256) k_ens_tsub2d(const EnsT* __restrict__ runs, const EnsTItem* __restrict__ items,
@@ -97,7 +110,7 @@ struct Cursor {
 struct lf_ens {
     int nruns;
     std::vector<lf_ctx*> runs;
-    std::vector<int> rows;          // segment height per run
+    std::vector<int> rows;          // rows per segment (lane) per run
     cudaStream_t stream;
     bool own_stream;
     unsigned char* arena;
@@ -194,16 +207,21 @@ int build(lf_ens* e)
             }
         }
     }
-    // work lists: march items sorted by cost, T tiles per sub-step
+    // work lists: march items sorted by cost (longest lane first), T tiles per sub-step
     std::vector<EnsItem> items;
     for (int r = 0; r < R; ++r) {
         const lf_ctx* c = e->runs[r];
-        const int H = e->rows[r];
-        const int strips = (c->g.nx + MarchCfg::U - 1) / MarchCfg::U, segs = (c->g.ny + H - 1) / H;
-        for (int sg = 0; sg < segs; ++sg)
-            for (int st = 0; st < strips; ++st) items.push_back({r, st, sg, H});
+        const int np = pairs_for(c->g.ny, e->rows[r]);
+        const int strips = (c->g.nx + MarchCfg::U - 1) / MarchCfg::U;
+        for (int pr = 0; pr < np; ++pr)
+            for (int st = 0; st < strips; ++st) items.push_back({r, st, pr, np});
     }
-    std::stable_sort(items.begin(), items.end(), [](const EnsItem& a, const EnsItem& b) { return a.H > b.H; });
+    auto lane = [&](const EnsItem& w) {
+        const int ny = e->runs[w.run]->g.ny;
+        return (ny + 2 * w.npairs - 1) / (2 * w.npairs);
+    };
+    std::stable_sort(items.begin(), items.end(),
+                     [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
     std::vector<std::vector<EnsTItem>> titems(max_nsub > 1 ? max_nsub - 1 : 0);
     for (int s = 1; s < max_nsub; ++s)
         for (int r = 0; r < R; ++r) {
@@ -292,7 +310,7 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
     std::vector<size_t> ws(nruns);
     size_t total = 0;
     for (int r = 0; r < nruns; ++r) {
-        if (grids[r].d != 2 || params[r].precision != LF_FP32) return LF_EINVAL;
+        if (grids[r].d != 2 || params[r].precision != LF_FP32 || grids[r].ny < 2) return LF_EINVAL;
         lf_params p = params[r];
         p.workspace = nullptr;
         p.workspace_bytes = 0;
@@ -330,7 +348,7 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
         if (rc == LF_OK) {
             c->ens_member = true;
             e->runs.push_back(c);
-            e->rows.push_back(march::march_rows_for(c->g.nx, c->g.ny, MarchCfg::U, 0));
+            e->rows.push_back(c->g.ny / 2 < 16 ? (c->g.ny / 2 > 0 ? c->g.ny / 2 : 1) : 16);
         }
     }
     if (rc == LF_OK) rc = build(e);
@@ -365,8 +383,8 @@ int lf_ens_tune(lf_ens* e, int reps)
         int best_h = e->rows[r];
         const int cand[] = {8, 12, 16, 20, 24, 32, 48, 64, 96, 128};
         for (int h : cand) {
-            if (h > c->g.ny && h != cand[0]) continue;
-            lf_set_kernel_variant(tmp, LF_VARIANT_MARCH, h);
+            if (2 * h > c->g.ny && h != cand[0]) continue;
+            lf_set_kernel_variant(tmp, LF_VARIANT_MARCH2, h);
             lf_step(tmp, 2);
             cudaEventRecord(t0, e->stream);
             lf_step(tmp, reps);
@@ -374,7 +392,7 @@ int lf_ens_tune(lf_ens* e, int reps)
             if ((rc = wait_stream(e->stream)) != LF_OK) break;
             float ms = 0;
             cudaEventElapsedTime(&ms, t0, t1);
-            if (ms < best_ms) { best_ms = ms; best_h = h < c->g.ny ? h : c->g.ny; }
+            if (ms < best_ms) { best_ms = ms; best_h = h; }
         }
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);

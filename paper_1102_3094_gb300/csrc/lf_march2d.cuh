@@ -347,17 +347,27 @@ inline int march_rows_for(int nx, int ny, int U, int param)
     return h;
 }
 
-// Rows per segment for the two-segment kernel: the smallest H >= 8 whose CTAs
-// (strips x segment pairs) all fit in one wave of `slots` resident CTAs.
-inline int march2_rows_for(int nx, int ny, int U, int param, int slots)
+// Rows per lane for the two-segment kernel.  Co-resident CTAs share an SM's
+// issue rate, so the step takes about (CTAs per SM, rounded up) x (rows per
+// lane + 4 pipeline iterations); the smallest such cost wins among heights
+// that still give every SM about two CTAs (8 warps) when the lattice allows.
+inline int march2_rows_for(int nx, int ny, int U, int param, int sms)
 {
     if (param > 0) return param < ny ? param : ny;
     const int strips = (nx + U - 1) / U;
-    for (int h = 8; h < ny; ++h) {
-        const int pairs = ((ny + h - 1) / h + 1) / 2;
-        if ((int64_t)strips * pairs <= slots) return h;
+    int best = 8;
+    int64_t best_cost = -1;
+    for (int h = 8; h <= ny && h <= 512; ++h) {
+        int pairs = (ny + 2 * h - 1) / (2 * h);
+        if (pairs > ny / 2) pairs = ny / 2;
+        if (pairs < 1) break;
+        const int64_t ctas = (int64_t)strips * pairs;
+        if (10 * ctas < 18 * (int64_t)sms && h > 8) break;     // fewer than ~2 CTAs per SM
+        const int lane = (ny + 2 * pairs - 1) / (2 * pairs);
+        const int64_t cost = ((ctas + sms - 1) / sms) * (lane + 4);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = h; }
     }
-    return ny;
+    return best;
 }
 
 }  // namespace march

@@ -283,32 +283,32 @@ __global__ void __launch_bounds__(NT) k_march2d(Geom g, Phys<R> p, StepIO<R> io,
 }
 
 // Two segments per CTA in the lanes of float2 (packed FP32x2 arithmetic).
-template <int NT, int D, bool HYDRO>
-__global__ void __launch_bounds__(NT, 3) k_march2d_x2(Geom g, Phys<float> p, StepIO<float> io, int H)
+template <int NT, int D, bool HYDRO, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_march2d_x2(Geom g, Phys<float> p, StepIO<float> io, int npairs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    march::march2d_pair<NT, D, HYDRO>(g, p, io, blockIdx.x, blockIdx.y, H, smem_raw);
+    march::march2d_pair<NT, D, HYDRO>(g, p, io, blockIdx.x, blockIdx.y, npairs, smem_raw);
 }
 
-template <int NT, int D, bool HYDRO>
+template <int NT, int D, bool HYDRO, int MINB>
 cudaError_t launch_march_x2(const Geom& g, const Phys<float>& p, const StepIO<float>& io, cudaStream_t s)
 {
     using M = march::March2<NT, D>;
-    auto kern = k_march2d_x2<NT, D, HYDRO>;
-    static int slots = 0;   // resident CTAs on the whole device
-    if (slots == 0) {
+    auto kern = k_march2d_x2<NT, D, HYDRO, MINB>;
+    static int sms = 0;
+    if (sms == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::BYTES);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
+        int dev = 0, n = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, M::BYTES)) != cudaSuccess) return e;
-        slots = sms * (per_sm > 0 ? per_sm : 1);
+        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        sms = n > 0 ? n : 1;
     }
-    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, slots);
-    const int nseg = (g.ny + H - 1) / H;
-    dim3 grid((g.nx + M::U - 1) / M::U, (nseg + 1) / 2);
-    kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
+    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
+    int npairs = (g.ny + 2 * H - 1) / (2 * H);
+    if (npairs > g.ny / 2) npairs = g.ny / 2;       // every lane keeps at least one row
+    dim3 grid((g.nx + M::U - 1) / M::U, npairs);
+    kern<<<grid, NT, M::BYTES, s>>>(g, p, io, npairs);
     return cudaGetLastError();
 }
 
@@ -317,17 +317,16 @@ cudaError_t launch_march(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
 {
     using M = march::March<R, NT, D>;
     auto kern = k_march2d<R, NT, D>;
-    static int slots = 0;   // resident CTAs on the whole device
-    if (slots == 0) {
+    static int sms = 0;
+    if (sms == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::BYTES);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
+        int dev = 0, n = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, M::BYTES)) != cudaSuccess) return e;
-        slots = sms * (per_sm > 0 ? per_sm : 1);
+        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        sms = n > 0 ? n : 1;
     }
-    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, slots);
+    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
     dim3 grid((g.nx + M::U - 1) / M::U, (g.ny + H - 1) / H);
     kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
     return cudaGetLastError();
@@ -367,8 +366,10 @@ template <typename R>
 cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
     if constexpr (sizeof(R) == 4) {
-        if (!aux && g.variant == LF_VARIANT_MARCH2)
-            return p.hydro ? launch_march_x2<128, 3, true>(g, p, io, s) : launch_march_x2<128, 3, false>(g, p, io, s);
+        if (!aux && g.variant == LF_VARIANT_MARCH2 && g.ny >= 2)
+        {
+            return p.hydro ? launch_march_x2<128, 3, true, 3>(g, p, io, s) : launch_march_x2<128, 3, false, 3>(g, p, io, s);
+        }
     }
     if (!aux && (g.variant == LF_VARIANT_MARCH || g.variant == LF_VARIANT_MARCH2))
         return (g.tune >> 16) == 1 ? launch_march<R, 64, 3>(g, p, io, s) : launch_march<R, 128, 3>(g, p, io, s);

@@ -1,6 +1,7 @@
 """Batched ensembles (include/lf_ens.h): every run of an ensemble, advanced
 by the graph-replayed persistent launch, must equal the same run advanced
-alone by lf_step, bit for bit (the per-site arithmetic is shared code)."""
+alone by lf_step with the same kernel and row split, bit for bit (the per-site
+arithmetic is shared code)."""
 import math
 
 import numpy as np
@@ -24,16 +25,23 @@ MEMBERS = [
 ]
 
 
-def _alone(m, steps):
+def _alone(m, phases):
+    """The run advanced alone: phases = [(steps, rows per segment), ...]."""
     kw = {k: v for k, v in m.items()}
     sim = lf.Lattice(precision="fp32", **kw)
-    sim.step(steps)
+    for steps, rows in phases:
+        sim.set_variant("march2", rows)
+        sim.step(steps)
     return sim
 
 
-def _compare(ens, steps):
+def _compare(ens, steps, before=None):
+    """before: (steps, rows per run) taken before the current row split."""
     for r, m in enumerate(MEMBERS):
-        ref = _alone(m, steps)
+        phases = [(steps, ens.rows(r))]
+        if before is not None:
+            phases = [(before[0], before[1][r]), (steps - before[0], ens.rows(r))]
+        ref = _alone(m, phases)
         run = ens.run(r)
         for name in ("phi", "T", "pop"):
             np.testing.assert_array_equal(run.get(name, "fp32"), ref.get(name, "fp32"), err_msg=f"run {r} {name}")
@@ -54,11 +62,12 @@ def test_ensemble_equals_single_runs():
 def test_ensemble_after_tuning():
     ens = lf.Ensemble(MEMBERS)
     ens.step(3)
+    rows0 = [ens.rows(r) for r in range(len(MEMBERS))]
     ens.tune(reps=3)
     rows = [ens.rows(r) for r in range(len(MEMBERS))]
     assert all(r >= 1 for r in rows)
     ens.step(6)
-    _compare(ens, 9)
+    _compare(ens, 9, before=(3, rows0))
     ens.close()
 
 
