@@ -167,8 +167,9 @@ def traffic_for(kernel_key: str):
     ent = j.get(kernel_key)
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    srcs = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
+    data = b"".join(open(os.path.join(ROOT, s_), "rb").read() for s_ in srcs)
+    h = hashlib.sha256(data).hexdigest()[:16]
     return ent["dram_bytes_per_launch"] if h == ent.get("source_sha256_16") else None
 
 
