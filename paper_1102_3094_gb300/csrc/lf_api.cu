@@ -196,43 +196,80 @@ double pop_weight(const lf_ctx* c, int q)
     return (c->g.d == 2 ? D2Q9::w(q) : D3Q19::w(q)) * c->params.n0;
 }
 
-template <typename R, typename D>
-int pack_one(lf_ctx* c, const void* src, void* dst, double add, int dst_on_device)
+// Address under which kernels of this device reach a host buffer: pinned or
+// registered host memory is mapped into the device's address space, so the
+// conversion kernels read or write it directly (no staging copy); null for
+// pageable memory.
+const void* mapped_host(const void* p)
 {
-    D* target = dst_on_device ? (D*)dst : (D*)c->stage;
-    if (launch_pack<R, D>(c->g, (const R*)src, target, add, c->stream) != cudaSuccess) return LF_ECUDA;
-    if (!dst_on_device) {
-        if (cudaMemcpyAsync(dst, c->stage, (size_t)c->N * sizeof(D), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Planes [0, nplanes) of a field out (pack) or in (unpack).  Device buffers
+// and host buffers mapped into the device's address space take one kernel
+// for all planes; pageable host memory goes plane by plane through the stage
+// with stream-ordered copies.  The caller waits once at the end.
+template <typename R, typename D>
+int pack_planes(lf_ctx* c, const void* src, void* dst, int nplanes, const PlaneAdd& add, int dst_on_device)
+{
+    void* target = dst_on_device ? dst : const_cast<void*>(mapped_host(dst));
+    if (target) return launch_pack<R, D>(c->g, (const R*)src, (D*)target, nplanes, add, c->stream) == cudaSuccess
+                           ? LF_OK : LF_ECUDA;
+    for (int q = 0; q < nplanes; ++q) {
+        PlaneAdd one{};
+        one.v[0] = add.v[q];
+        const R* s = (const R*)src + (size_t)q * c->g.plane;
+        if (launch_pack<R, D>(c->g, s, (D*)c->stage, 1, one, c->stream) != cudaSuccess) return LF_ECUDA;
+        if (cudaMemcpyAsync((D*)dst + (size_t)q * c->N, c->stage, (size_t)c->N * sizeof(D), cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess)
             return LF_ECUDA;
-        return wait_stream(c->stream);
     }
     return LF_OK;
 }
 
 template <typename R, typename D>
-int unpack_one(lf_ctx* c, const void* src, void* dst, double sub, int src_on_device)
+int unpack_planes(lf_ctx* c, const void* src, void* dst, int nplanes, const PlaneAdd& sub, int src_on_device)
 {
-    const D* from = (const D*)src;
-    if (!src_on_device) {
-        if (cudaMemcpyAsync(c->stage, src, (size_t)c->N * sizeof(D), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    const void* from = src_on_device ? src : mapped_host(src);
+    if (from) return launch_unpack<R, D>(c->g, (const D*)from, (R*)dst, nplanes, sub, c->stream) == cudaSuccess
+                         ? LF_OK : LF_ECUDA;
+    for (int q = 0; q < nplanes; ++q) {
+        PlaneAdd one{};
+        one.v[0] = sub.v[q];
+        if (cudaMemcpyAsync(c->stage, (const D*)src + (size_t)q * c->N, (size_t)c->N * sizeof(D),
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
             return LF_ECUDA;
-        from = (const D*)c->stage;
+        if (launch_unpack<R, D>(c->g, (const D*)c->stage, (R*)dst + (size_t)q * c->g.plane, 1, one, c->stream) !=
+            cudaSuccess)
+            return LF_ECUDA;
     }
-    if (launch_unpack<R, D>(c->g, from, (R*)dst, sub, c->stream) != cudaSuccess) return LF_ECUDA;
-    if (!src_on_device) return wait_stream(c->stream);   // the stage is reused
     return LF_OK;
 }
 
 template <typename R>
-int pack_dispatch(lf_ctx* c, const void* src, void* dst, double add, int on_dev, bool dbl)
+int pack_dispatch(lf_ctx* c, const void* src, void* dst, int np, const PlaneAdd& add, int on_dev, bool dbl)
 {
-    return dbl ? pack_one<R, double>(c, src, dst, add, on_dev) : pack_one<R, float>(c, src, dst, add, on_dev);
+    return dbl ? pack_planes<R, double>(c, src, dst, np, add, on_dev) : pack_planes<R, float>(c, src, dst, np, add, on_dev);
 }
 
 template <typename R>
-int unpack_dispatch(lf_ctx* c, const void* src, void* dst, double sub, int on_dev, bool dbl)
+int unpack_dispatch(lf_ctx* c, const void* src, void* dst, int np, const PlaneAdd& sub, int on_dev, bool dbl)
 {
-    return dbl ? unpack_one<R, double>(c, src, dst, sub, on_dev) : unpack_one<R, float>(c, src, dst, sub, on_dev);
+    return dbl ? unpack_planes<R, double>(c, src, dst, np, sub, on_dev)
+               : unpack_planes<R, float>(c, src, dst, np, sub, on_dev);
+}
+
+PlaneAdd plane_offsets(const lf_ctx* c, int which)
+{
+    PlaneAdd a{};
+    if (which == LF_FIELD_POP)
+        for (int q = 0; q < c->Q; ++q) a.v[q] = pop_weight(c, q);
+    return a;
 }
 
 int elem_from_bytes(const lf_ctx* c, int which, size_t bytes, bool* dbl)
@@ -399,13 +436,10 @@ int lf_fields(lf_ctx* c, int which, void* dst, size_t bytes, int dst_on_device)
         if (rc != LF_OK) return rc;
     }
     const int nplanes = which == LF_FIELD_POP ? c->Q : 1;
-    const size_t es = dbl ? 8 : 4;
-    for (int q = 0; q < nplanes && rc == LF_OK; ++q) {
-        const double add = which == LF_FIELD_POP ? pop_weight(c, q) : 0.0;
-        void* d = (unsigned char*)dst + (size_t)q * c->N * es;
-        rc = c->prec == LF_FP64 ? pack_dispatch<double>(c, field_plane(c, which, q), d, add, dst_on_device, dbl)
-                                : pack_dispatch<float>(c, field_plane(c, which, q), d, add, dst_on_device, dbl);
-    }
+    const PlaneAdd add = plane_offsets(c, which);
+    const void* src = field_plane(c, which, 0);
+    rc = c->prec == LF_FP64 ? pack_dispatch<double>(c, src, dst, nplanes, add, dst_on_device, dbl)
+                            : pack_dispatch<float>(c, src, dst, nplanes, add, dst_on_device, dbl);
     if (rc == LF_OK) rc = wait_stream(c->stream);
     if (rc == LF_OK) rc = check(cudaGetLastError());
     return rc;
@@ -419,14 +453,10 @@ int lf_fields_set(lf_ctx* c, int which, const void* src, size_t bytes, int src_o
     int rc = elem_from_bytes(c, which, bytes, &dbl);
     if (rc != LF_OK) return rc;
     const int nplanes = which == LF_FIELD_POP ? c->Q : 1;
-    const size_t es = dbl ? 8 : 4;
-    for (int q = 0; q < nplanes && rc == LF_OK; ++q) {
-        const double sub = which == LF_FIELD_POP ? pop_weight(c, q) : 0.0;
-        const void* s = (const unsigned char*)src + (size_t)q * c->N * es;
-        void* d = const_cast<void*>(field_plane(c, which, q));
-        rc = c->prec == LF_FP64 ? unpack_dispatch<double>(c, s, d, sub, src_on_device, dbl)
-                                : unpack_dispatch<float>(c, s, d, sub, src_on_device, dbl);
-    }
+    const PlaneAdd sub = plane_offsets(c, which);
+    void* dst = const_cast<void*>(field_plane(c, which, 0));
+    rc = c->prec == LF_FP64 ? unpack_dispatch<double>(c, src, dst, nplanes, sub, src_on_device, dbl)
+                            : unpack_dispatch<float>(c, src, dst, nplanes, sub, src_on_device, dbl);
     c->aux_valid = false;
     if (rc == LF_OK) rc = wait_stream(c->stream);
     if (rc == LF_OK) rc = check(cudaGetLastError());
@@ -531,12 +561,13 @@ namespace {
 int raw_copy(lf_ctx* c, const void* plane_dev, void* host, bool to_host)
 {
     int rc;
+    const PlaneAdd zero{};
     if (to_host) {
-        rc = c->prec == LF_FP64 ? pack_one<double, double>(c, plane_dev, host, 0.0, 0)
-                                : pack_one<float, float>(c, plane_dev, host, 0.0, 0);
+        rc = c->prec == LF_FP64 ? pack_planes<double, double>(c, plane_dev, host, 1, zero, 0)
+                                : pack_planes<float, float>(c, plane_dev, host, 1, zero, 0);
     } else {
-        rc = c->prec == LF_FP64 ? unpack_one<double, double>(c, host, const_cast<void*>(plane_dev), 0.0, 0)
-                                : unpack_one<float, float>(c, host, const_cast<void*>(plane_dev), 0.0, 0);
+        rc = c->prec == LF_FP64 ? unpack_planes<double, double>(c, host, const_cast<void*>(plane_dev), 1, zero, 0)
+                                : unpack_planes<float, float>(c, host, const_cast<void*>(plane_dev), 1, zero, 0);
     }
     return rc;
 }
@@ -560,6 +591,7 @@ int lf_save(lf_ctx* c, const char* path)
     for (int q = 0; q < c->Q && rc == LF_OK; ++q) rc = raw_copy(c, field_plane(c, LF_FIELD_POP, q), buf + nf * q, true);
     if (rc == LF_OK) rc = raw_copy(c, field_plane(c, LF_FIELD_PHI, 0), buf + nf * c->Q, true);
     if (rc == LF_OK) rc = raw_copy(c, field_plane(c, LF_FIELD_T, 0), buf + nf * (c->Q + 1), true);
+    if (rc == LF_OK) rc = wait_stream(c->stream);
     if (rc == LF_OK) {
         FILE* fp = std::fopen(path, "wb");
         if (!fp) rc = LF_EIO;
@@ -595,6 +627,7 @@ int lf_load(lf_ctx* c, const char* path)
     for (int q = 0; q < c->Q && rc == LF_OK; ++q) rc = raw_copy(c, field_plane(c, LF_FIELD_POP, q), buf + nf * q, false);
     if (rc == LF_OK) rc = raw_copy(c, field_plane(c, LF_FIELD_PHI, 0), buf + nf * c->Q, false);
     if (rc == LF_OK) rc = raw_copy(c, field_plane(c, LF_FIELD_T, 0), buf + nf * (c->Q + 1), false);
+    if (rc == LF_OK) rc = wait_stream(c->stream);
     if (rc == LF_OK) {
         c->step = h.step;
         c->aux_valid = false;

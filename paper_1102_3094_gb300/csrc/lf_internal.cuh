@@ -105,12 +105,17 @@ cudaError_t launch_tsub(const Geom& g, const Phys<R>& p, const R* Tin, R* Tout, 
 template <typename R>
 cudaError_t launch_init(const Geom& g, uint64_t seed, double amp, double T0, double T_w,
                         int quench, R* phi, R* T, cudaStream_t s);
-// dst[k] = (D)(src[site k] + add), k over the unpadded lattice (x fastest).
+// Per-plane offsets of a layout conversion (population weights w_q n0).
+struct PlaneAdd {
+    double v[19];
+};
+// Planes q < nplanes: dst[q N + k] = (D)(src[q plane + site k] + add[q]), k
+// over the unpadded lattice (x fastest), N = nx ny nz.
 template <typename R, typename D>
-cudaError_t launch_pack(const Geom& g, const R* src, D* dst, double add, cudaStream_t s);
-// dst[site k] = (R)(src[k] - sub).
+cudaError_t launch_pack(const Geom& g, const R* src, D* dst, int nplanes, const PlaneAdd& add, cudaStream_t s);
+// dst[q plane + site k] = (R)(src[q N + k] - sub[q]).
 template <typename R, typename D>
-cudaError_t launch_unpack(const Geom& g, const D* src, R* dst, double sub, cudaStream_t s);
+cudaError_t launch_unpack(const Geom& g, const D* src, R* dst, int nplanes, const PlaneAdd& sub, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Bounded wait: polls an event recorded on `s` so that a GPU that stops
@@ -133,7 +138,10 @@ inline int wait_stream(cudaStream_t s)
         if (q != cudaErrorNotReady) { rc = LF_ECUDA; break; }
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > lim) { rc = LF_ETIMEOUT; break; }
-        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+        // poll without sleeping for the first 2 ms (a sleep of a few us
+        // overshoots by tens of us, which dominates short waits), then back off
+        if (el < 0.002) continue;
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.05 ? 20 : 200));
     }
     cudaEventDestroy(ev);
     return rc;

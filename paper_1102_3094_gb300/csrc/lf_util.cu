@@ -45,28 +45,109 @@ __global__ void k_init(Geom g, uint64_t seed, double amp, double T0, double T_w,
     }
 }
 
-template <typename R, typename D>
-__global__ void k_pack(Geom g, const R* __restrict__ src, D* __restrict__ dst, double add)
+// Layout conversion between the padded state ([rows][pitch], deviations for
+// the populations) and a packed caller array ([rows][nx]).  Work comes in
+// chunks of 1024 elements of one row, four consecutive elements per thread;
+// when every row of both arrays starts on a 16-byte boundary the four move
+// as one vector access (fewer requests when the caller array is host memory
+// reached through the device mapping), else as four scalar accesses issued
+// before any store.
+constexpr int kChunk = 1024;
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = double4_16a;
+};
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, int x, int nx, bool vec, T v[4])
 {
-    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = k / g.nx;
-        const int x = (int)(k - row * g.nx);
-        dst[k] = (D)((double)src[row * g.pitch + x] + add);
+    if (vec && x + 3 < nx) {
+        const typename Vec4<T>::type w = *reinterpret_cast<const typename Vec4<T>::type*>(p + x);
+        v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = x + u < nx ? p[x + u] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* p, int x, int nx, bool vec, const T v[4])
+{
+    if (vec && x + 3 < nx) {
+        typename Vec4<T>::type w;
+        w.x = v[0]; w.y = v[1]; w.z = v[2]; w.w = v[3];
+        *reinterpret_cast<typename Vec4<T>::type*>(p + x) = w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (x + u < nx) p[x + u] = v[u];
     }
 }
 
 template <typename R, typename D>
-__global__ void k_unpack(Geom g, const D* __restrict__ src, R* __restrict__ dst, double sub)
+__global__ void __launch_bounds__(256) k_pack(Geom g, const R* __restrict__ src, D* __restrict__ dst, int nplanes,
+                                              PlaneAdd add, int vec)
+{
+    const int nx = g.nx;
+    const int xch = (nx + kChunk - 1) / kChunk;
+    const int64_t rows = (int64_t)g.ny * g.nz, per_plane = rows * xch;
+    const int64_t N = rows * nx;
+    for (int64_t c = blockIdx.x; c < per_plane * nplanes; c += gridDim.x) {
+        const int q = (int)(c / per_plane);
+        const int64_t cr = c - q * per_plane;
+        const int64_t row = cr / xch;
+        const int x = (int)(cr - row * xch) * kChunk + 4 * threadIdx.x;
+        if (x >= nx) continue;
+        R v[4];
+        D o[4];
+        load4(src + q * g.plane + row * g.pitch, x, nx, vec != 0, v);
+        const double a = add.v[q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = (D)((double)v[u] + a);
+        store4(dst + q * N + row * nx, x, nx, vec != 0, o);
+    }
+}
+
+template <typename R, typename D>
+__global__ void __launch_bounds__(256) k_unpack(Geom g, const D* __restrict__ src, R* __restrict__ dst, int nplanes,
+                                                PlaneAdd sub, int vec)
+{
+    const int nx = g.nx;
+    const int xch = (nx + kChunk - 1) / kChunk;
+    const int64_t rows = (int64_t)g.ny * g.nz, per_plane = rows * xch;
+    const int64_t N = rows * nx;
+    for (int64_t c = blockIdx.x; c < per_plane * nplanes; c += gridDim.x) {
+        const int q = (int)(c / per_plane);
+        const int64_t cr = c - q * per_plane;
+        const int64_t row = cr / xch;
+        const int x = (int)(cr - row * xch) * kChunk + 4 * threadIdx.x;
+        if (x >= nx) continue;
+        D v[4];
+        R o[4];
+        load4(src + q * N + row * nx, x, nx, vec != 0, v);
+        const double b = sub.v[q];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = (R)((double)v[u] - b);
+        store4(dst + q * g.plane + row * g.pitch, x, nx, vec != 0, o);
+    }
+}
+
+// Vector accesses need every row and plane start of both arrays 16-byte
+// aligned (a: the padded state in R, b: the packed array in D).
+template <typename R, typename D>
+int vec_ok(const Geom& g, const void* a, const void* b)
 {
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = k / g.nx;
-        const int x = (int)(k - row * g.nx);
-        dst[row * g.pitch + x] = (R)((double)src[k] - sub);
-    }
+    const bool rows = ((size_t)g.nx * sizeof(D)) % 16 == 0 && ((size_t)g.pitch * sizeof(R)) % 16 == 0 &&
+                      ((size_t)N * sizeof(D)) % 16 == 0 && ((size_t)g.plane * sizeof(R)) % 16 == 0;
+    return rows && ((uintptr_t)a % 16 == 0) && ((uintptr_t)b % 16 == 0);
 }
 
 inline unsigned grid_for(const Geom& g)
@@ -75,6 +156,13 @@ inline unsigned grid_for(const Geom& g)
     int64_t b = (N + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
     return (unsigned)(b < 1 ? 1 : b);
+}
+
+inline unsigned grid_chunks(const Geom& g, int nplanes)
+{
+    const int64_t n = (int64_t)nplanes * g.ny * g.nz * ((g.nx + kChunk - 1) / kChunk);
+    const int64_t cap = 152 * 8;
+    return (unsigned)(n < 1 ? 1 : (n > cap ? cap : n));
 }
 
 }  // namespace
@@ -88,28 +176,28 @@ cudaError_t launch_init(const Geom& g, uint64_t seed, double amp, double T0, dou
 }
 
 template <typename R, typename D>
-cudaError_t launch_pack(const Geom& g, const R* src, D* dst, double add, cudaStream_t s)
+cudaError_t launch_pack(const Geom& g, const R* src, D* dst, int nplanes, const PlaneAdd& add, cudaStream_t s)
 {
-    k_pack<R, D><<<grid_for(g), 256, 0, s>>>(g, src, dst, add);
+    k_pack<R, D><<<grid_chunks(g, nplanes), 256, 0, s>>>(g, src, dst, nplanes, add, vec_ok<R, D>(g, src, dst));
     return cudaGetLastError();
 }
 
 template <typename R, typename D>
-cudaError_t launch_unpack(const Geom& g, const D* src, R* dst, double sub, cudaStream_t s)
+cudaError_t launch_unpack(const Geom& g, const D* src, R* dst, int nplanes, const PlaneAdd& sub, cudaStream_t s)
 {
-    k_unpack<R, D><<<grid_for(g), 256, 0, s>>>(g, src, dst, sub);
+    k_unpack<R, D><<<grid_chunks(g, nplanes), 256, 0, s>>>(g, src, dst, nplanes, sub, vec_ok<R, D>(g, dst, src));
     return cudaGetLastError();
 }
 
 template cudaError_t launch_init<float>(const Geom&, uint64_t, double, double, double, int, float*, float*, cudaStream_t);
 template cudaError_t launch_init<double>(const Geom&, uint64_t, double, double, double, int, double*, double*, cudaStream_t);
-template cudaError_t launch_pack<float, float>(const Geom&, const float*, float*, double, cudaStream_t);
-template cudaError_t launch_pack<float, double>(const Geom&, const float*, double*, double, cudaStream_t);
-template cudaError_t launch_pack<double, float>(const Geom&, const double*, float*, double, cudaStream_t);
-template cudaError_t launch_pack<double, double>(const Geom&, const double*, double*, double, cudaStream_t);
-template cudaError_t launch_unpack<float, float>(const Geom&, const float*, float*, double, cudaStream_t);
-template cudaError_t launch_unpack<float, double>(const Geom&, const double*, float*, double, cudaStream_t);
-template cudaError_t launch_unpack<double, float>(const Geom&, const float*, double*, double, cudaStream_t);
-template cudaError_t launch_unpack<double, double>(const Geom&, const double*, double*, double, cudaStream_t);
+template cudaError_t launch_pack<float, float>(const Geom&, const float*, float*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_pack<float, double>(const Geom&, const float*, double*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_pack<double, float>(const Geom&, const double*, float*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_pack<double, double>(const Geom&, const double*, double*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_unpack<float, float>(const Geom&, const float*, float*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_unpack<float, double>(const Geom&, const double*, float*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_unpack<double, float>(const Geom&, const float*, double*, int, const PlaneAdd&, cudaStream_t);
+template cudaError_t launch_unpack<double, double>(const Geom&, const double*, double*, int, const PlaneAdd&, cudaStream_t);
 
 }  // namespace lf
