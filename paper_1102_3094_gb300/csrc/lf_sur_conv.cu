@@ -1,15 +1,23 @@
 // lf_sur_conv.cu -- 3x3 convolution of NHWC BF16 activations on the 5th-gen
 // tensor cores (tcgen05.mma, FP32 accumulator in tensor memory).
 //
-// Implicit GEMM: a CTA computes a tile of 128 consecutive pixels of one image
-// row (M = 128) times all COUT output channels (N), accumulating over the 9
-// taps x CIN input channels (K = 9 CIN, in steps of 16).  Activations live in
-// a padded layout [B][NY + 2][NX + 2][C] whose one-pixel halo holds the
-// boundary rule of the lattice (x periodic: the halo columns copy the opposite
-// edge; y walls: the halo rows are zero), so the A operand of every tap is a
-// plain shifted window of 128 pixels.  All 9 weight taps stay in shared
-// memory; A tiles are double-buffered; one thread issues the MMAs and commits
-// them to an mbarrier per buffer; the epilogue reads TMEM with tcgen05.ld.
+// Implicit GEMM: an output tile is 128 consecutive pixels of one image row
+// (M = 128) times all COUT output channels (N), accumulated over the 9 taps x
+// CIN input channels (K = 9 CIN, in steps of 16).  Activations live in a
+// padded layout [B][NY + 2][NX + 2][C] whose one-pixel halo holds the
+// boundary rule of the lattice (x periodic: the halo columns copy the
+// opposite edge; y walls: the halo rows are zero).
+//
+// A persistent CTA owns a 128-pixel column block and a run of image rows and
+// marches down them.  Input rows (130 pixels with the halo) sit in a 5-slot
+// shared-memory ring in a pixel-major core-matrix layout ([k core][pixel][8
+// channels], 16 bytes per pixel and core): the 8 pixels of a core matrix are
+// contiguous, so the A operand of tap (dy, dx) is the ring row of dy with its
+// descriptor start moved by dx pixels -- all 9 taps read the same three rows,
+// which are loaded once.  The rows two ahead are prefetched with cp.async.
+// The 9 weight taps stay in shared memory (K-major).  One thread issues the
+// MMAs of row y into one of two TMEM accumulators while all four warps run
+// the epilogue of row y - 1 from the other.
 #include <cuda_bf16.h>
 
 #include "lf_internal.cuh"
@@ -37,13 +45,17 @@ struct ConvArgs {
 
 template <int CIN, int COUT>
 struct ConvSmem {
-    static constexpr int A_BYTES = 128 * CIN * 2;
+    static constexpr int RP = 130;                   // ring row: pixels x0 - 1 .. x0 + 128
+    static constexpr int KC = CIN / 8;               // 16-byte channel groups (k cores)
+    static constexpr int LBO_A = RP * 16;            // next k core of the A operand
+    static constexpr int ROW_BYTES = KC * LBO_A;
+    static constexpr int NSLOT = 5;                  // rows y - 1 .. y + 3
     static constexpr int B_TAP = COUT * CIN * 2;
     static constexpr int B_OFF = 0;
-    static constexpr int A_OFF = 9 * B_TAP;
-    static constexpr int BAR_OFF = A_OFF + 2 * A_BYTES;
+    static constexpr int R_OFF = 9 * B_TAP;
+    static constexpr int BAR_OFF = R_OFF + NSLOT * ROW_BYTES;
     static constexpr int BYTES = BAR_OFF + 64;
-    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+    static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;   // two accumulators
 };
 
 __device__ __forceinline__ int64_t pix_off(int b, int y, int x, int NY, int NX)
@@ -52,21 +64,22 @@ __device__ __forceinline__ int64_t pix_off(int b, int y, int x, int NY, int NX)
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
+__global__ void __launch_bounds__(128, 1) k_conv3x3(ConvArgs a, int rows_per_item)
 {
     using S = ConvSmem<CIN, COUT>;
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT >= 16 && COUT <= 256, "MMA shape");
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT >= 16 && COUT <= 128, "MMA shape");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem + S::B_OFF;
-    unsigned char* sA = smem + S::A_OFF;
+    unsigned char* sR = smem + S::R_OFF;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int NY = a.NY, NX = a.NX;
-    const int tiles_per_row = NX / 128;
-    const int ntiles = a.B * NY * tiles_per_row;
+    const int ncb = NX / 128;
+    const int nch = (NY + rows_per_item - 1) / rows_per_item;
+    const int nitems = a.B * ncb * nch;
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
-    constexpr uint32_t SBO = (CIN / 8) * 128;
+    constexpr uint32_t SBO_B = (CIN / 8) * 128;
 
     if (warp == 0) tc::tmem_alloc(tslot, S::TMEM_COLS);
     if (tid == 0) {
@@ -86,51 +99,39 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    uint32_t ph0 = 0, ph1 = 0;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t ph[2] = {0u, 0u};
     bool ok = true;
 
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int xt = tile % tiles_per_row;
-        const int row = tile / tiles_per_row;
-        const int y = row % NY, b = row / NY;
-        const int x0 = xt * 128;
-        for (int t = 0; t < 9; ++t) {
-            const int buf = t & 1;
-            if (t >= 2) {   // the MMAs that read this buffer two taps ago are done
-                const bool w = tc::mbar_wait(&bar[buf], buf ? ph1 : ph0);
-                if (buf) ph1 ^= 1; else ph0 ^= 1;
-                if (__syncthreads_or(!w)) { ok = false; break; }
-            }
-            const int dy = t / 3 - 1, dx = t % 3 - 1;
-            const __nv_bfloat16* src = a.in + pix_off(b, y + dy, x0 + dx, NY, NX) * CIN;
-            unsigned char* dA = sA + buf * S::A_BYTES;
-            for (int q = tid; q < 128 * (CIN / 8); q += 128) {
-                const int p = q / (CIN / 8), j = q - p * (CIN / 8);
-                tc::cp_async16(dA + tc::kmajor_offset(p, 8 * j, CIN), src + (int64_t)p * CIN + 8 * j);
-            }
-            tc::cp_async_commit_wait_all();
-            tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t abase = tc::smem_u32(dA), bbase = tc::smem_u32(sB + t * S::B_TAP);
-#pragma unroll
-                for (int s = 0; s < CIN / 16; ++s)
-                    tc::mma_bf16(tmem, tc::smem_desc(abase + 256 * s, 128, SBO), tc::smem_desc(bbase + 256 * s, 128, SBO),
-                                 idesc, (t > 0 || s > 0) ? 1u : 0u);
-                tc::mma_commit(&bar[buf]);
-            }
+    // padded row pr (image row pr - 1) of image b, pixels x0 - 1 .. x0 + 128,
+    // into ring slot pr mod 5; one 16-byte channel group per copy
+    auto load_row = [&](int b, int pr, int x0) {
+        unsigned char* dst = sR + (pr % S::NSLOT) * S::ROW_BYTES;
+        const __nv_bfloat16* src = a.in + (((int64_t)b * (NY + 2) + pr) * (NX + 2) + x0) * CIN;
+        for (int q = tid; q < S::RP * S::KC; q += 128) {
+            const int px = q / S::KC, j = q - px * S::KC;
+            tc::cp_async16(dst + j * S::LBO_A + px * 16, src + (int64_t)px * CIN + 8 * j);
         }
-        if (!ok) break;
-        // all MMAs of the tile: tap 7 committed to bar[1], tap 8 to bar[0]
-        bool w = tc::mbar_wait(&bar[1], ph1);
-        ph1 ^= 1;
-        w = w && tc::mbar_wait(&bar[0], ph0);
-        ph0 ^= 1;
-        if (__syncthreads_or(!w)) { ok = false; break; }
-        tc::fence_after_sync();
+    };
+    auto commit = [] { asm volatile("cp.async.commit_group;\n" ::: "memory"); };
 
-        // ---- epilogue: thread = pixel (TMEM lane) ---------------------------
+    // MMAs of output row y: taps (dy, dx) read padded rows y + dy + 1 at pixel shift dx
+    auto issue_row = [&](int y, uint32_t dcol) {
+        const uint32_t ring = tc::smem_u32(sR), bbase = tc::smem_u32(sB);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int dy = t / 3 - 1, dx = t % 3 - 1;
+            const uint32_t abase = ring + (uint32_t)(((y + dy + 1) % S::NSLOT) * S::ROW_BYTES + (dx + 1) * 16);
+#pragma unroll
+            for (int s = 0; s < CIN / 16; ++s)
+                tc::mma_bf16(tmem + dcol, tc::smem_desc(abase + 2 * s * S::LBO_A, S::LBO_A, 128),
+                             tc::smem_desc(bbase + t * S::B_TAP + 256 * s, 128, SBO_B), idesc,
+                             (t > 0 || s > 0) ? 1u : 0u);
+        }
+    };
+
+    // epilogue of output row y (TMEM accumulator at column dcol): thread = pixel
+    auto epilogue = [&](int b, int y, int x0, uint32_t dcol) {
         const int x = x0 + tid;
         const int64_t po = pix_off(b, y, x, NY, NX);
         const bool halo_hi = (x == 0), halo_lo = (x == NX - 1);   // copies into columns NX + 1 / 0
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
 #pragma unroll
         for (int c0 = 0; c0 < COUT; c0 += 16) {
             float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc::tmem_ld16(tmem + lane_base + dcol + (uint32_t)c0, v);
             if (a.bias)
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] += a.bias[c0 + i];
@@ -155,14 +156,20 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
             if (a.resid) {
-                const __nv_bfloat16* r = a.resid + po * COUT + c0;
+                __align__(16) __nv_bfloat16 r[16];
+                const uint4* rs = reinterpret_cast<const uint4*>(a.resid + po * COUT + c0);
+                reinterpret_cast<uint4*>(r)[0] = rs[0];
+                reinterpret_cast<uint4*>(r)[1] = rs[1];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] += __bfloat162float(r[i]);
             }
 #pragma unroll
             for (int i = 0; i < 16; ++i) ho[i] = __float2bfloat16_rn(v[i]);
             if (a.mask) {
-                const __nv_bfloat16* m = a.mask + po * COUT + c0;
+                __align__(16) __nv_bfloat16 m[16];
+                const uint4* ms = reinterpret_cast<const uint4*>(a.mask + po * COUT + c0);
+                reinterpret_cast<uint4*>(m)[0] = ms[0];
+                reinterpret_cast<uint4*>(m)[1] = ms[1];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) hm[i] = __bfloat162float(m[i]) > 0.f ? ho[i] : __float2bfloat16_rn(0.f);
             }
@@ -182,9 +189,59 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
             store(a.out, ho);
             if (a.mask) store(a.out2, hm);
         }
+    };
+
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        const int ch = item % nch, rest = item / nch;
+        const int cb = rest % ncb, b = rest / ncb;
+        const int x0 = cb * 128;
+        const int ya = ch * rows_per_item, yb = min(ya + rows_per_item, NY);
+        // prologue: padded rows ya .. ya + 2 (image rows ya - 1 .. ya + 1), then ya + 3
+        load_row(b, ya, x0);
+        load_row(b, ya + 1, x0);
+        load_row(b, ya + 2, x0);
+        commit();
+        if (ya + 3 <= yb + 1) load_row(b, ya + 3, x0);
+        commit();
+        for (int y = ya; y < yb; ++y) {
+            const uint32_t dcur = (uint32_t)((y & 1) * COUT), dprev = (uint32_t)(((y - 1) & 1) * COUT);
+            // padded rows y .. y + 2 have landed; the epilogue of row y - 2 has
+            // read accumulator y & 1
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (tid == 0) {
+                issue_row(y, dcur);
+                tc::mma_commit(&bar[y & 1]);
+            }
+            if (y > ya) {   // MMAs of row y - 1 done: its ring slot and accumulator are free to use
+                const bool w = tc::mbar_wait(&bar[(y - 1) & 1], ph[(y - 1) & 1]);
+                ph[(y - 1) & 1] ^= 1;
+                if (__syncthreads_or(!w)) { ok = false; break; }
+                tc::fence_after_sync();
+            }
+            // prefetch padded row y + 4 into the slot of padded row y - 1
+            if (y + 4 <= yb + 1) load_row(b, y + 4, x0);
+            commit();
+            if (y > ya) epilogue(b, y - 1, x0, dprev);
+        }
+        if (!ok) break;
+        {   // last row of the item
+            const int y = yb - 1;
+            const bool w = tc::mbar_wait(&bar[y & 1], ph[y & 1]);
+            ph[y & 1] ^= 1;
+            if (__syncthreads_or(!w)) { ok = false; break; }
+            tc::fence_after_sync();
+            epilogue(b, y, x0, (uint32_t)((y & 1) * COUT));
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         tc::fence_before_sync();
-        __syncthreads();   // TMEM read out before the next tile's first MMA overwrites it
+        __syncthreads();   // accumulators read and ring idle before the next item
+        tc::fence_after_sync();
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (!ok && tid == 0) atomicExch(a.err, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -201,9 +258,15 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int ntiles = a.B * a.NY * (a.NX / 128);
-    int blocks = ntiles < 2 * 152 ? ntiles : 2 * 152;
-    k_conv3x3<CIN, COUT><<<blocks, 128, S::BYTES, s>>>(a);
+    // rows per item: at least ~4 rows (prologue of 4 loaded rows) and about
+    // two items per SM over the whole launch
+    const int cols = a.B * (a.NX / 128);
+    int rpi = (int)(((int64_t)cols * a.NY + 2 * 152 - 1) / (2 * 152));
+    if (rpi < 4) rpi = 4;
+    if (rpi > a.NY) rpi = a.NY;
+    const int nitems = cols * ((a.NY + rpi - 1) / rpi);
+    const int blocks = nitems < 152 ? nitems : 152;
+    k_conv3x3<CIN, COUT><<<blocks, 128, S::BYTES, s>>>(a, rpi);
     return cudaGetLastError();
 }
 

@@ -21,10 +21,14 @@ def _rand(shape, scale, g):
     return (scale * torch.randn(shape, generator=g, dtype=torch.float32)).to(BF)
 
 
-@pytest.mark.parametrize("cin,cout,relu,use_resid", [(16, 64, 1, False), (64, 64, 1, True), (64, 16, 0, False)])
-def test_conv3x3_forward(cin, cout, relu, use_resid):
+@pytest.mark.parametrize("cin,cout,relu,use_resid,shape", [
+    (16, 64, 1, False, (2, 5, 256)), (64, 64, 1, True, (2, 5, 256)), (64, 16, 0, False, (2, 5, 256)),
+    (64, 64, 1, True, (3, 121, 256)),     # more row runs than SMs: CTAs march over several
+    (16, 64, 1, False, (1, 1, 128)),      # one row: prologue and drain only
+])
+def test_conv3x3_forward(cin, cout, relu, use_resid, shape):
     g = torch.Generator().manual_seed(cin * 100 + cout)
-    B, NY, NX = 2, 5, 256
+    B, NY, NX = shape
     h = _rand((B, NY, NX, cin), 1.0, g)
     W = _rand((9, cout, cin), 0.1, g)
     bias = (0.1 * torch.randn(cout, generator=g)).float()
