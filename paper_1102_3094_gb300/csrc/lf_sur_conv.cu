@@ -281,166 +281,202 @@ cudaError_t conv3x3(int cin, int cout, const ConvArgs& a, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // Weight gradient of a 3x3 convolution on the tensor cores:
 //   dW[t][o][i] = sum_p h[p + off_t][i] g[p][o]
-// as a GEMM D[(t, i)][o] = sum_p A[(t, i)][p] B[o][p] with M = 128 rows =
-// 128 / CIN taps x CIN channels, N = COUT, K = pixels.  A CTA takes one m-tile
-// of taps and a chunk of image rows; for every 64-pixel segment it stages the
-// three needed input rows and the gradient rows with cp.async, transposes them
-// into K-major tiles in shared memory, and issues four K = 16 MMAs.  Partial
-// D tiles (FP32) go to part[chunk][mtile][128][COUT]; k_wgrad_reduce sums them.
+// For each tap a GEMM D_t = A B^T with K = pixels, M = 64 (the 64-channel
+// side: i for CIN = 64, else o) and N = the other side.  Both operands are
+// read MN-major straight from rows staged in the pixel-major core-matrix
+// layout of the forward kernel ([channel group][pixel][8 channels]): a core
+// matrix is 8 consecutive pixels (K) of 8 channels (MN), so the tap shift dx
+// is a 16-byte move of the descriptor start and nothing is transposed.  A
+// work item is a run of row tiles (128 pixels of one image row) for one
+// group of taps; it accumulates all of its rows in TMEM (one M = 64
+// accumulator per tap) and writes one FP32 partial, summed by
+// k_wgrad_reduce.  For 64 -> 64 the taps are split in three groups by dy
+// (TMEM holds 3 x 64 columns); otherwise one group holds all nine.
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT>
-struct WgSmem {
-    static constexpr int SH = 3 * 66 * CIN * 2;     // input rows y-1, y, y+1, pixels x0-1 .. x0+64
-    static constexpr int SG = 64 * COUT * 2;        // gradient pixels x0 .. x0+63
-    static constexpr int AT = 128 * 64 * 2;         // A tile (K-major, K = 64)
-    static constexpr int BT = COUT * 64 * 2;        // B tile
-    static constexpr int SH_OFF = 0, SG_OFF = SH, A_OFF = SH + SG, B_OFF = A_OFF + AT, BAR_OFF = B_OFF + BT;
+struct WgCfg {
+    static constexpr bool HA = CIN == 64;                  // h is the M = 64 operand
+    static constexpr int NB = HA ? COUT : CIN;             // N of the GEMM
+    static constexpr int NG = (CIN == 64 && COUT == 64) ? 3 : 1;
+    static constexpr int TG = 9 / NG;                      // taps per group
+    static constexpr int SLICES = (2 * 152) / NG;          // items per group
+    static constexpr int RH = 130, RG = 128;               // pixels per staged h / g row
+    static constexpr int HROW = (CIN / 8) * RH * 16, GROW = (COUT / 8) * RG * 16;
+    static constexpr int NSH = NG == 3 ? 4 : 6, NSG = 4;
+    static constexpr int H_OFF = 0, G_OFF = NSH * HROW, BAR_OFF = G_OFF + NSG * GROW;
     static constexpr int BYTES = BAR_OFF + 64;
-    static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
-    static constexpr int TAPS = 128 / CIN;
-    static constexpr int MT = (9 + TAPS - 1) / TAPS;
+    static constexpr int TCOLS = TG * NB <= 32 ? 32 : (TG * NB <= 64 ? 64 : (TG * NB <= 128 ? 128 : 256));
+    static constexpr size_t PART = (size_t)NG * SLICES * TG * 64 * NB;   // floats
 };
 
 struct WgArgs {
     const __nv_bfloat16* h;      // padded NHWC CIN
     const __nv_bfloat16* g;      // padded NHWC COUT
-    float* part;                 // [nchunks][MT][128][COUT]
+    float* part;                 // [NG][SLICES][TG][64][NB]
     int B, NY, NX;
-    int rows_per_chunk;
     int* err;
 };
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128) k_conv_wgrad(WgArgs a)
+__global__ void __launch_bounds__(128, 1) k_conv_wgrad(WgArgs a)
 {
-    using S = WgSmem<CIN, COUT>;
+    using S = WgCfg<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(smem + S::SH_OFF);
-    __nv_bfloat16* sg = reinterpret_cast<__nv_bfloat16*>(smem + S::SG_OFF);
-    unsigned char* sA = smem + S::A_OFF;
-    unsigned char* sB = smem + S::B_OFF;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 16);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char* sH = smem + S::H_OFF;
+    unsigned char* sG = smem + S::G_OFF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);      // one per g slot
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 48);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NY = a.NY, NX = a.NX;
-    const int chunk = blockIdx.x, mt = blockIdx.y;
-    const int t_base = mt * S::TAPS;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+    const int ncb = NX / 128;
+    const int64_t R = (int64_t)a.B * ncb * NY;                 // row tiles, ordered (b, cb, y)
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(64, S::NB) | (1u << 15) | (1u << 16);   // both MN-major
 
-    if (warp == 0) tc::tmem_alloc(tslot, S::TMEM_COLS);
+    if (warp == 0) tc::tmem_alloc(tslot, S::TCOLS);
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
+        for (int k = 0; k < S::NSG; ++k) tc::mbar_init(&bar[k], 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    uint32_t ph = 0;
-    bool ok = true, issued = false;
+    uint32_t ph[S::NSG] = {};
+    bool ok = true;
 
-    const int row0 = chunk * a.rows_per_chunk;
-    const int nrows = a.B * NY;
-    const int row1 = min(row0 + a.rows_per_chunk, nrows);
-    const int segs = NX / 64;
-    int kstep = 0;
-    for (int row = row0; row < row1 && ok; ++row) {
-        const int y = row % NY, b = row / NY;
-        for (int sgi = 0; sgi < segs; ++sgi) {
-            const int x0 = sgi * 64;
-            // stage three input rows (pixels x0-1 .. x0+64) and 64 gradient pixels
-            for (int q = tid; q < 3 * 66 * (CIN / 8); q += 128) {
-                const int r = q / (66 * (CIN / 8)), rem = q - r * (66 * (CIN / 8));
-                const int px = rem / (CIN / 8), j = rem - px * (CIN / 8);
-                const __nv_bfloat16* src = a.h + pix_off(b, y + r - 1, x0 - 1 + px, NY, NX) * CIN + 8 * j;
-                tc::cp_async16(sh + ((r * 66 + px) * CIN + 8 * j), src);
-            }
-            for (int q = tid; q < 64 * (COUT / 8); q += 128) {
-                const int px = q / (COUT / 8), j = q - px * (COUT / 8);
-                tc::cp_async16(sg + (px * COUT + 8 * j), a.g + pix_off(b, y, x0 + px, NY, NX) * COUT + 8 * j);
-            }
-            tc::cp_async_commit_wait_all();
-            if (issued) {                      // previous MMAs have finished reading A and B
-                const bool w = tc::mbar_wait(&bar[0], ph);
-                ph ^= 1;
-                if (__syncthreads_or(!w)) { ok = false; break; }
-            } else {
+    auto commit = [] { asm volatile("cp.async.commit_group;\n" ::: "memory"); };
+    // padded h row pr, pixels x0 - 1 .. x0 + 128, into h slot pr mod NSH
+    auto load_h = [&](int b, int pr, int x0) {
+        unsigned char* dst = sH + (pr % S::NSH) * S::HROW;
+        const __nv_bfloat16* src = a.h + (((int64_t)b * (NY + 2) + pr) * (NX + 2) + x0) * CIN;
+        for (int q = tid; q < S::RH * (CIN / 8); q += 128) {
+            const int px = q / (CIN / 8), j = q - px * (CIN / 8);
+            tc::cp_async16(dst + j * (S::RH * 16) + px * 16, src + (int64_t)px * CIN + 8 * j);
+        }
+    };
+    // g row y, pixels x0 .. x0 + 127, into g slot y mod NSG
+    auto load_g = [&](int b, int y, int x0) {
+        unsigned char* dst = sG + (y % S::NSG) * S::GROW;
+        const __nv_bfloat16* src = a.g + (((int64_t)b * (NY + 2) + y + 1) * (NX + 2) + x0 + 1) * COUT;
+        for (int q = tid; q < S::RG * (COUT / 8); q += 128) {
+            const int px = q / (COUT / 8), j = q - px * (COUT / 8);
+            tc::cp_async16(dst + j * (S::RG * 16) + px * 16, src + (int64_t)px * COUT + 8 * j);
+        }
+    };
+    // everything output row y of this group reads that is not already staged
+    // by earlier rows: g row y and the newest h row(s)
+    auto load_rows_for = [&](int b, int y, int x0, int gi, bool first) {
+        load_g(b, y, x0);
+        if (S::NG == 3) {
+            load_h(b, y + gi, x0);                 // padded row y + dy + 1, dy = gi - 1
+        } else if (first) {
+            load_h(b, y, x0); load_h(b, y + 1, x0); load_h(b, y + 2, x0);
+        } else {
+            load_h(b, y + 2, x0);
+        }
+    };
+
+    for (int item = blockIdx.x; item < S::NG * S::SLICES && ok; item += gridDim.x) {
+        const int gi = item / S::SLICES, sl = item - gi * S::SLICES;
+        const int64_t r0 = R * sl / S::SLICES, r1 = R * (sl + 1) / S::SLICES;
+        const int t0 = gi * S::TG;
+        bool first_row = true;
+        for (int64_t r = r0; r < r1 && ok;) {
+            // one run of consecutive rows of one (image, column block)
+            const int64_t bc = r / NY;
+            const int ya = (int)(r - bc * NY);
+            const int64_t rend = min(r1, (bc + 1) * NY);
+            const int yb = ya + (int)(rend - r);
+            const int cb = (int)(bc % ncb), b = (int)(bc / ncb);
+            const int x0 = cb * 128;
+            load_rows_for(b, ya, x0, gi, true);
+            commit();
+            if (ya + 1 < yb) load_rows_for(b, ya + 1, x0, gi, false);
+            commit();
+            for (int y = ya; y < yb; ++y) {
+                asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // rows of output row y landed
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
                 __syncthreads();
-            }
-            // A[(t, i)][p] = h[p + off_t][i]: one 16-byte core row (8 pixels) per item
-            for (int q = tid; q < 128 * 8; q += 128) {
-                const int m = q >> 3, j = q & 7;
-                const int t = t_base + m / CIN, i = m % CIN;
-                __align__(16) __nv_bfloat16 v[8];
-                if (t < 9) {
-                    const int dy = t / 3 - 1, dx = t % 3 - 1;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] = sh[((dy + 1) * 66 + (8 * j + k + dx + 1)) * CIN + i];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] = __float2bfloat16_rn(0.f);
-                }
-                *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 8 * j, 64)) = *reinterpret_cast<const uint4*>(v);
-            }
-            // B[o][p] = g[p][o]
-            for (int q = tid; q < COUT * 8; q += 128) {
-                const int o = q >> 3, j = q & 7;
-                __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = sg[(8 * j + k) * COUT + o];
-                *reinterpret_cast<uint4*>(sB + tc::kmajor_offset(o, 8 * j, 64)) = *reinterpret_cast<const uint4*>(v);
-            }
-            tc::fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
                 tc::fence_after_sync();
-                const uint32_t ab = tc::smem_u32(sA), bb = tc::smem_u32(sB);
+                if (tid == 0) {
+                    const uint32_t gb = tc::smem_u32(sG + (y % S::NSG) * S::GROW);
 #pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    tc::mma_bf16(tmem, tc::smem_desc(ab + 256 * s, 128, 1024), tc::smem_desc(bb + 256 * s, 128, 1024),
-                                 idesc, (kstep > 0 || s > 0) ? 1u : 0u);
-                tc::mma_commit(&bar[0]);
+                    for (int j = 0; j < S::TG; ++j) {
+                        const int t = t0 + j, dy = t / 3 - 1, dx = t % 3 - 1;
+                        const uint32_t hb = tc::smem_u32(sH + ((y + dy + 1) % S::NSH) * S::HROW) + (dx + 1) * 16;
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) {            // 16 pixels per MMA
+                            const uint64_t hd = tc::smem_desc(hb + 256 * s, 128, S::RH * 16);
+                            const uint64_t gd = tc::smem_desc(gb + 256 * s, 128, S::RG * 16);
+                            tc::mma_bf16(tmem + (uint32_t)(j * S::NB), S::HA ? hd : gd, S::HA ? gd : hd, idesc,
+                                         (first_row && s == 0) ? 0u : 1u);
+                        }
+                    }
+                    tc::mma_commit(&bar[y % S::NSG]);
+                }
+                first_row = false;
+                if (y >= ya + 2) {   // MMAs of row y - 2 done: its slots may be refilled
+                    const int k = (y - 2) % S::NSG;
+                    const bool w = tc::mbar_wait(&bar[k], ph[k]);
+                    ph[k] ^= 1;
+                    if (__syncthreads_or(!w)) { ok = false; break; }
+                }
+                if (y + 2 < yb) load_rows_for(b, y + 2, x0, gi, false);
+                commit();
             }
-            issued = true;
-            ++kstep;
+            if (!ok) break;
+            for (int y = max(ya, yb - 2); y < yb; ++y) {   // the last two rows' MMAs
+                const int k = y % S::NSG;
+                const bool w = tc::mbar_wait(&bar[k], ph[k]);
+                ph[k] ^= 1;
+                if (__syncthreads_or(!w)) { ok = false; break; }
+            }
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            r = rend;
         }
-    }
-    if (ok && issued) {
-        const bool w = tc::mbar_wait(&bar[0], ph);
-        if (__syncthreads_or(!w)) ok = false;
-    }
-    if (ok) {
+        if (!ok) break;
+        // partial of this item: M = 64 accumulator rows 16 w + l sit in lanes 32 w + l, l < 16
+        float* dst = a.part + ((size_t)item * S::TG) * 64 * S::NB;
+        const int m = 16 * warp + lane;
+#pragma unroll
+        for (int j = 0; j < S::TG; ++j)
+#pragma unroll
+            for (int c0 = 0; c0 < S::NB; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * S::NB + c0), v);
+                if (lane < 16)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dst[((size_t)j * 64 + m) * S::NB + c0 + i] = first_row ? 0.f : v[i];
+            }
+        tc::fence_before_sync();
+        __syncthreads();   // accumulators read before the next item's first MMA
         tc::fence_after_sync();
-        float* dst = a.part + (((int64_t)chunk * S::MT + mt) * 128 + tid) * COUT;
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-            float v[16];
-            if (issued) tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            else
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) dst[c0 + i] = v[i];
-        }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (!ok && tid == 0) atomicExch(a.err, 1);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+    if (warp == 0) tc::tmem_dealloc(tmem, S::TCOLS);
 }
 
-// dW[t][o][i] = sum over chunks of part[chunk][t / TAPS][(t % TAPS) CIN + i][o]
+// dW[t][o][i] = sum over the group's items of part[item][t - t0][m][n]
 template <int CIN, int COUT>
-__global__ void k_wgrad_reduce(const float* __restrict__ part, int nchunks, float* __restrict__ dW)
+__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ dW)
 {
-    using S = WgSmem<CIN, COUT>;
+    using S = WgCfg<CIN, COUT>;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 9 * COUT * CIN) return;
     const int t = idx / (COUT * CIN), rem = idx - t * COUT * CIN;
     const int o = rem / CIN, i = rem - o * CIN;
-    const int mt = t / S::TAPS, m = (t % S::TAPS) * CIN + i;
+    const int gi = t / S::TG, j = t - gi * S::TG;
+    const int m = S::HA ? i : o, n = S::HA ? o : i;
     float acc = 0.f;
-    for (int c = 0; c < nchunks; ++c) acc += part[(((int64_t)c * S::MT + mt) * 128 + m) * COUT + o];
+    for (int sl = 0; sl < S::SLICES; ++sl)
+        acc += part[((((size_t)gi * S::SLICES + sl) * S::TG + j) * 64 + m) * S::NB + n];
     dW[idx] = acc;
 }
 
@@ -448,23 +484,18 @@ template <int CIN, int COUT>
 cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
                          size_t part_floats, float* dW, int* err, cudaStream_t s)
 {
-    using S = WgSmem<CIN, COUT>;
+    using S = WgCfg<CIN, COUT>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int nrows = B * NY;
-    int nchunks = (2 * 152 + S::MT - 1) / S::MT;                // about two CTAs per SM
-    if (nchunks > nrows) nchunks = nrows;
-    int rpc = (nrows + nchunks - 1) / nchunks;
-    nchunks = (nrows + rpc - 1) / rpc;
-    if ((size_t)nchunks * S::MT * 128 * COUT > part_floats) return cudaErrorInvalidValue;
-    WgArgs a{h, g, part, B, NY, NX, rpc, err};
-    k_conv_wgrad<CIN, COUT><<<dim3(nchunks, S::MT), 128, S::BYTES, s>>>(a);
+    if (part_floats < S::PART) return cudaErrorInvalidValue;
+    WgArgs a{h, g, part, B, NY, NX, err};
+    k_conv_wgrad<CIN, COUT><<<152, 128, S::BYTES, s>>>(a);
     const int n = 9 * COUT * CIN;
-    k_wgrad_reduce<CIN, COUT><<<(n + 255) / 256, 256, 0, s>>>(part, nchunks, dW);
+    k_wgrad_reduce<CIN, COUT><<<(n + 255) / 256, 256, 0, s>>>(part, dW);
     return cudaGetLastError();
 }
 
@@ -480,9 +511,10 @@ cudaError_t conv3x3_wgrad(int cin, int cout, const __nv_bfloat16* h, const __nv_
 // scratch floats the weight-gradient partials need for a (cin, cout) layer
 size_t wgrad_part_floats(int cin, int cout)
 {
-    const int MT = (9 + 128 / cin - 1) / (128 / cin);
-    const int nchunks = (2 * 152 + MT - 1) / MT;
-    return (size_t)nchunks * MT * 128 * cout;
+    if (cin == 16 && cout == 64) return WgCfg<16, 64>::PART;
+    if (cin == 64 && cout == 64) return WgCfg<64, 64>::PART;
+    if (cin == 64 && cout == 16) return WgCfg<64, 16>::PART;
+    return 0;
 }
 
 }  // namespace sur

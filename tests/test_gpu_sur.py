@@ -65,10 +65,13 @@ def test_conv3x3_forward(cin, cout, relu, use_resid, shape):
         assert np.all(np.abs(y4.cpu().double().numpy() - y_ref.numpy()) <= 1e-5 * scale)
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 64), (64, 64), (64, 16)])
-def test_conv3x3_weight_gradient(cin, cout):
+@pytest.mark.parametrize("cin,cout,shape", [
+    (16, 64, (2, 3, 128)), (64, 64, (2, 3, 128)), (64, 16, (2, 3, 128)),
+    (64, 64, (3, 41, 256)), (16, 64, (3, 41, 256)), (64, 16, (3, 41, 256)),   # runs cross images and blocks
+])
+def test_conv3x3_weight_gradient(cin, cout, shape):
     g_ = torch.Generator().manual_seed(7 * cin + cout)
-    B, NY, NX = 2, 3, 128
+    B, NY, NX = shape
     h = _rand((B, NY, NX, cin), 1.0, g_)
     gr = _rand((B, NY, NX, cout), 1.0, g_)
     dev = "cuda"
