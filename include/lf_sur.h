@@ -50,6 +50,7 @@ typedef struct {
     double t_surrogate_s;     /* device time in surrogate predictions                 */
     double t_shadow_s;        /* device time in shadow windows and comparisons        */
     double t_plain_s;         /* device time in plain windows                         */
+    int    rejected;          /* predictions not finite or with |u| > 0.2: plain window taken instead */
 } lf_sur_report;
 
 /* ---- network ------------------------------------------------------------- */
@@ -74,8 +75,13 @@ int lf_sur_set_params(lf_sur* s, const float* host);
  * with respect to every parameter (same order as the parameters).  Waits. */
 int lf_sur_grads(lf_sur* s, const float* x, const float* y, int B, double* loss, float* grads_host);
 
-/* One training step: loss, gradients (tensor cores), Adam (lr, 0.9, 0.999). */
+/* One training step: loss, gradients (tensor cores), Adam (lr, 0.9, 0.999)
+ * on the gradients scaled by min(1, max_norm / ||g||) with ||g|| the global
+ * norm over all parameters (lf_sur_set_clip; 1.0 after lf_sur_create). */
 int lf_sur_train_step(lf_sur* s, const float* x, const float* y, int B, float lr, double* loss);
+
+/* Global-norm gradient clipping threshold of lf_sur_train_step (0 = none). */
+int lf_sur_set_clip(lf_sur* s, float max_norm);
 
 /* y = net(x) in raw units, [B][4][NY][NX] FP32 device arrays; enqueued. */
 int lf_sur_predict(lf_sur* s, const float* x, float* y, int B);
@@ -85,8 +91,11 @@ int lf_sur_predict(lf_sur* s, const float* x, float* y, int B);
  * shadow_every-th surrogate window is also advanced by the plain method from
  * the same state; if max(phi relative L2 error, relative error of the S(k)
  * peak position or height) exceeds threshold, the plain result replaces the
- * prediction.  Kept predictions set phi and T and rebuild the populations as
- * the equilibrium at n0 and the predicted velocity.  Waits; fills *rep. */
+ * prediction.  A prediction with a non-finite value or |u| > 0.2 is never
+ * handed over: that window is advanced by lf_step instead (rep->rejected).
+ * Kept predictions set phi and T and move the equilibrium part of the
+ * populations from the current to the predicted velocity at the current
+ * density (the non-equilibrium part is kept).  Waits; fills *rep. */
 int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shadow_every, double threshold,
                lf_sur_report* rep);
 

@@ -163,14 +163,34 @@ struct AdamLayer {
     int cin, cout;
 };
 
-__global__ void k_adam(AdamLayer L, float lr, float b1, float b2, float eps, float c1, float c2, int do_update)
+// Squared norm of one layer's gradients (weights and biases) added to *acc.
+__global__ void k_grad_sumsq(const float* __restrict__ gw, int nw, const float* __restrict__ gb, int nb, double* acc)
+{
+    double v = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nw + nb; k += gridDim.x * blockDim.x) {
+        const double g = k < nw ? gw[k] : gb[k - nw];
+        v += g * g;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, v);
+}
+
+// Adam with the gradients scaled by min(1, clip / ||g||) (global norm
+// clipping; clip = 0 leaves them as they are).
+__global__ void k_adam(AdamLayer L, float lr, float b1, float b2, float eps, float c1, float c2, int do_update,
+                       const double* gnorm2, float clip)
 {
     const int nw = 9 * L.cout * L.cin;
+    float gs = 1.f;
+    if (do_update && clip > 0.f) {
+        const double n = sqrt(*gnorm2);
+        if (n > (double)clip) gs = (float)((double)clip / n);
+    }
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nw + L.cout; k += gridDim.x * blockDim.x) {
         if (k < nw) {
             float w = L.w[k];
             if (do_update) {
-                const float g = L.gw[k];
+                const float g = gs * L.gw[k];
                 const float m = b1 * L.m[k] + (1.f - b1) * g, v = b2 * L.v[k] + (1.f - b2) * g * g;
                 L.m[k] = m;
                 L.v[k] = v;
@@ -184,7 +204,7 @@ __global__ void k_adam(AdamLayer L, float lr, float b1, float b2, float eps, flo
             L.wtbf[((int64_t)(8 - t) * L.cin + i) * L.cout + o] = wb;    // W'[8-t][i][o] = W[t][o][i]
         } else if (do_update) {
             const int o = k - nw;
-            const float g = L.gb[o];
+            const float g = gs * L.gb[o];
             const float m = b1 * L.mb[o] + (1.f - b1) * g, v = b2 * L.vb[o] + (1.f - b2) * g * g;
             L.mb[o] = m;
             L.vb[o] = v;
@@ -224,6 +244,8 @@ struct lf_sur {
     double* loss_part;           // k_mse block partials
     int* err;
     int step;                    // Adam step count
+    double* gnorm2;              // squared global gradient norm of the last step
+    float clip;                  // largest global gradient norm Adam sees (0 = no clipping)
 };
 
 namespace {
@@ -243,10 +265,16 @@ int refresh_bf16(lf_sur* s, int do_update, float lr)
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = do_update ? (float)(1.0 / (1.0 - std::pow(b1, s->step))) : 1.f;
     const float c2 = do_update ? (float)(1.0 / (1.0 - std::pow(b2, s->step))) : 1.f;
+    if (do_update) {
+        if (cudaMemsetAsync(s->gnorm2, 0, sizeof(double), s->stream) != cudaSuccess) return LF_ECUDA;
+        for (int l = 0; l < kLayers; ++l)
+            k_grad_sumsq<<<64, 256, 0, s->stream>>>(s->gw[l], (int)wcount(l), s->gb[l], kCout[l], s->gnorm2);
+    }
     for (int l = 0; l < kLayers; ++l) {
         AdamLayer L{s->w[l], s->m[l], s->v[l], s->gw[l], s->b[l], s->mb[l], s->vb[l], s->gb[l], s->wbf[l], s->wtbf[l],
                     kCin[l], kCout[l]};
-        k_adam<<<blocks_for((int64_t)wcount(l) + kCout[l]), 256, 0, s->stream>>>(L, lr, b1, b2, eps, c1, c2, do_update);
+        k_adam<<<blocks_for((int64_t)wcount(l) + kCout[l]), 256, 0, s->stream>>>(L, lr, b1, b2, eps, c1, c2, do_update,
+                                                                               s->gnorm2, s->clip);
     }
     return cudaGetLastError() == cudaSuccess ? LF_OK : LF_ECUDA;
 }
@@ -342,7 +370,7 @@ int lf_sur_create(int NY, int NX, int max_batch, uint64_t seed, const lf_sur_nor
     for (int l = 0; l < kLayers; ++l)
         bytes += 4 * a256(4 * wcount(l)) + 4 * a256(4 * (size_t)kCout[l]) + 2 * a256(2 * wcount(l));
     bytes += a256(2 * pad_px * 16) * 2 + a256(2 * pad_px * 64) * (2 * 5 + 4);
-    bytes += 3 * a256(4 * px * 4) + a256(4 * s->part_floats) + a256(8 * 152 * 8) + 256;
+    bytes += 3 * a256(4 * px * 4) + a256(4 * s->part_floats) + a256(8 * 152 * 8) + 256 + 256;
     if (cudaMalloc((void**)&s->block, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -370,6 +398,8 @@ int lf_sur_create(int NY, int NX, int max_batch, uint64_t seed, const lf_sur_nor
     s->part = (float*)take(4 * s->part_floats);
     s->loss_part = (double*)take(8 * 152 * 8);
     s->err = (int*)take(4);
+    s->gnorm2 = (double*)take(8);
+    s->clip = 1.0f;
     // zero everything (halo rows of the activations stay zero for good), then
     // He-uniform weights from SplitMix64, the last layer scaled down so the
     // untrained network starts close to the identity map
@@ -394,6 +424,13 @@ int lf_sur_create(int NY, int NX, int max_batch, uint64_t seed, const lf_sur_nor
         return rc;
     }
     *out = s;
+    return LF_OK;
+}
+
+int lf_sur_set_clip(lf_sur* s, float max_norm)
+{
+    if (!s || !(max_norm >= 0.f)) return LF_EINVAL;
+    s->clip = max_norm;
     return LF_OK;
 }
 
@@ -487,21 +524,32 @@ void lf_sur_destroy(lf_sur* s)
 // ===========================================================================
 namespace {
 
-// populations of a 2D FP32 context := equilibrium at density n0 and the given
-// velocity (the surrogate predicts phi, T, u; the non-equilibrium part is not
-// predicted), stored as deviations w_i (n0 (3 e.u + 4.5 (e.u)^2 - 1.5 u.u))
-__global__ void k_set_feq2d(Geom g, float n0, const float* __restrict__ ux, const float* __restrict__ uy,
-                            float* __restrict__ f)
+// Hand a predicted velocity to the populations of a 2D FP32 context (stored
+// as deviations f_i - w_i n0): the equilibrium part moves from the current
+// velocity to the predicted one at the current density, the non-equilibrium
+// part (not predicted) is kept:
+//   f_i += w_i n (3 e.du + 4.5 ((e.u')^2 - (e.u)^2) - 1.5 (u'.u' - u.u)).
+__global__ void k_shift_u2d(Geom g, float n0, const float* __restrict__ ux0, const float* __restrict__ uy0,
+                            const float* __restrict__ ux1, const float* __restrict__ uy1, float* __restrict__ f)
 {
     const int64_t N = (int64_t)g.nx * g.ny;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(k % g.nx), y = (int)(k / g.nx);
         const int64_t site = (int64_t)y * g.pitch + x;
-        const float vx = ux[k], vy = uy[k], uu = vx * vx + vy * vy;
+        float df[D2Q9::Q], dn = 0.f;
 #pragma unroll
         for (int i = 0; i < D2Q9::Q; ++i) {
-            const float eu = (float)D2Q9::ex(i) * vx + (float)D2Q9::ey(i) * vy;
-            f[i * g.plane + site] = (float)D2Q9::w(i) * n0 * (3.f * eu + 4.5f * eu * eu - 1.5f * uu);
+            df[i] = f[i * g.plane + site];
+            dn += df[i];
+        }
+        const float n = n0 + dn;
+        const float ax = ux0[k], ay = uy0[k], bx = ux1[k], by = uy1[k];
+        const float du2 = (bx * bx + by * by) - (ax * ax + ay * ay);
+#pragma unroll
+        for (int i = 0; i < D2Q9::Q; ++i) {
+            const float ex = (float)D2Q9::ex(i), ey = (float)D2Q9::ey(i);
+            const float ea = ex * ax + ey * ay, eb = ex * bx + ey * by;
+            f[i * g.plane + site] = df[i] + (float)D2Q9::w(i) * n * (3.f * (eb - ea) + 4.5f * (eb * eb - ea * ea) - 1.5f * du2);
         }
     }
 }
@@ -526,6 +574,27 @@ __global__ void k_l2_parts(const float* __restrict__ a, const float* __restrict_
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = r0[0]; part[2 * blockIdx.x + 1] = r1[0]; }
 }
 
+// Validity of a prediction (phi, T, ux, uy planes of n sites): out[0] = 1 if
+// any value is not finite, out[1] = bits of max(|ux|, |uy|) (non-negative
+// floats order like their bit patterns).
+__global__ void k_pred_check(const float* __restrict__ y, int64_t n, unsigned* out)
+{
+    unsigned bad = 0, umax = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 4 * n; k += (int64_t)gridDim.x * blockDim.x) {
+        const float v = y[k];
+        if (!isfinite(v)) bad = 1;
+        else if (k >= 2 * n) umax = max(umax, __float_as_uint(fabsf(v)));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        umax = max(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&out[0], 1u);
+        atomicMax(&out[1], umax);
+    }
+}
+
 int rel_l2(const float* a, const float* b, int64_t n, double* scratch, cudaStream_t s, double* out)
 {
     const unsigned nb = blocks_for(n);
@@ -542,6 +611,10 @@ int rel_l2(const float* a, const float* b, int64_t n, double* scratch, cudaStrea
 }
 
 }  // namespace
+
+// Largest |u| (lattice units) a prediction may hand to the LB solver; the
+// second-order equilibrium needs |u| well below the sound speed 1/sqrt(3).
+constexpr float kMaxU = 0.2f;
 
 extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shadow_every, double threshold,
                           lf_sur_report* rep)
@@ -597,12 +670,35 @@ extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shado
         const int which[4] = {LF_FIELD_PHI, LF_FIELD_T, LF_FIELD_UX, LF_FIELD_UY};
         for (int c = 0; c < 4 && rc == LF_OK; ++c) rc = lf_fields(ctx, which[c], x + c * N, fb, 1);
         if (rc == LF_OK) rc = lf_sur_predict(s, x, y, 1);
+        unsigned chk[2] = {0u, 0u};
+        if (rc == LF_OK) {
+            unsigned* dchk = reinterpret_cast<unsigned*>(red);
+            if (cudaMemsetAsync(dchk, 0, 2 * sizeof(unsigned), st) != cudaSuccess) rc = LF_ECUDA;
+            if (rc == LF_OK) k_pred_check<<<152, 256, 0, st>>>(y, N, dchk);
+            if (rc == LF_OK && cudaMemcpyAsync(chk, dchk, sizeof(chk), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                rc = LF_ECUDA;
+        }
         if (rc == LF_OK) rc = wait_stream(st);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms_sur = 0;
         cudaEventElapsedTime(&ms_sur, e0, e1);
         rep->t_surrogate_s += ms_sur / 1e3;
+        float umax;
+        std::memcpy(&umax, &chk[1], sizeof(umax));
+        if (rc == LF_OK && (chk[0] != 0u || !(umax <= kMaxU))) {   // not a usable state: take the plain window
+            rep->rejected += 1;
+            cudaEventRecord(e0, st);
+            rc = lf_step(ctx, K);
+            if (rc == LF_OK) rc = wait_stream(st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            rep->t_plain_s += ms / 1e3;
+            rep->windows_done = w + 1;
+            continue;
+        }
         bool accept = true;
         if (rc == LF_OK && (w / 2) % shadow_every == 0) {        // plain shadow window as judge
             cudaEventRecord(e0, st);
@@ -640,8 +736,8 @@ extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shado
             rc = lf_fields_set(ctx, LF_FIELD_PHI, y, fb, 1);
             if (rc == LF_OK) rc = lf_fields_set(ctx, LF_FIELD_T, y + N, fb, 1);
             if (rc == LF_OK) {
-                k_set_feq2d<<<blocks_for(N), 256, 0, st>>>(ctx->g, (float)ctx->params.n0, y + 2 * N, y + 3 * N,
-                                                          (float*)ctx->f[ctx->fcur]);
+                k_shift_u2d<<<blocks_for(N), 256, 0, st>>>(ctx->g, (float)ctx->params.n0, x + 2 * N, x + 3 * N,
+                                                          y + 2 * N, y + 3 * N, (float*)ctx->f[ctx->fcur]);
                 rc = cudaGetLastError() == cudaSuccess ? wait_stream(st) : LF_ECUDA;
             }
             rep->surrogate_windows += 1;

@@ -474,7 +474,7 @@ class lf_sur_report(C.Structure):
     _fields_ = [("windows_done", C.c_int), ("surrogate_windows", C.c_int), ("shadow_checks", C.c_int),
                 ("fallbacks", C.c_int), ("max_phi_l2_err", C.c_double), ("max_sk_err", C.c_double),
                 ("last_err", C.c_double), ("t_surrogate_s", C.c_double), ("t_shadow_s", C.c_double),
-                ("t_plain_s", C.c_double)]
+                ("t_plain_s", C.c_double), ("rejected", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -496,11 +496,12 @@ def _sur2_lib():
         L.lf_sur_grads.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_double), vp]
         L.lf_sur_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.POINTER(C.c_double)]
         L.lf_sur_predict.argtypes = [vp, vp, vp, C.c_int]
+        L.lf_sur_set_clip.argtypes = [vp, C.c_float]
         L.lf_sur_run.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_double, C.POINTER(lf_sur_report)]
         L.lf_sur_destroy.argtypes = [vp]
         L.lf_sur_destroy.restype = None
         for fn in ("lf_sur_conv3x3_wgrad", "lf_sur_create", "lf_sur_get_params", "lf_sur_set_params",
-                   "lf_sur_grads", "lf_sur_train_step", "lf_sur_predict", "lf_sur_run"):
+                   "lf_sur_grads", "lf_sur_train_step", "lf_sur_predict", "lf_sur_run", "lf_sur_set_clip"):
             getattr(L, fn).restype = C.c_int
         L._sur2_ready = True
     return L
@@ -560,6 +561,9 @@ class Surrogate:
         loss = C.c_double()
         _ok(_sur2_lib().lf_sur_train_step(self.h, _p(x), _p(y), x.shape[0], lr, C.byref(loss)), "lf_sur_train_step")
         return loss.value
+
+    def set_clip(self, max_norm: float):
+        _ok(_sur2_lib().lf_sur_set_clip(self.h, max_norm), "lf_sur_set_clip")
 
     def predict(self, x):
         y = self.torch.empty_like(x)

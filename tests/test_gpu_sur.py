@@ -184,8 +184,15 @@ def test_interleaved_run_falls_back_to_plain():
     assert a.step_count == b.step_count
     pa, pb = a.get("phi", "fp32"), b.get("phi", "fp32")
     assert np.abs(pa - pb).max() <= 1e-4 * np.abs(pb).max()
-    # nothing rejected: the (untrained) predictions are kept as they are
+    # last layer zero: the network maps the state to itself (a usable
+    # prediction); with no threshold every such prediction is kept
+    p = sur.get_params()
+    p[-(9 * 16 * 64 + 16):] = 0.0
+    sur.set_params(p)
+    before = a.get("phi", "fp32")
     rep2 = sur.run(a, K, 4, 1, 1e30)
-    assert rep2["fallbacks"] == 0 and rep2["surrogate_windows"] == 2 and rep2["shadow_checks"] == 2
+    assert rep2["fallbacks"] == 0 and rep2["rejected"] == 0
+    assert rep2["surrogate_windows"] == 2 and rep2["shadow_checks"] == 2 and rep2["windows_done"] == 4
+    assert np.isfinite(a.get("phi", "fp32")).all() and not np.array_equal(a.get("phi", "fp32"), before)
     for o in (a, b, sur):
         o.close()
