@@ -223,7 +223,7 @@ int lf_load(lf_ctx* ctx, const char* path);
 
 /* Kernel variant of the step.  Both compute the same step (parity-tested
  * against the oracle); they differ in how work is mapped to the GPU:
- *   LF_VARIANT_MARCH (default for FP64 and 3D): one thread per column, a CTA
+ *   LF_VARIANT_MARCH (default for 2D FP64): one thread per column, a CTA
  *     marches down a segment of (param & 0xFFFF) rows (0 = chosen from the
  *     lattice size), inputs prefetched with cp.async; (param >> 16) == 1
  *     selects CTAs of 64 threads (56 columns) instead of 128 (120 columns);
@@ -233,11 +233,18 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     instead): a CTA owns two vertically adjacent segments of a strip that
  *     march away from their common row, carried in the two lanes of packed
  *     FP32x2 arithmetic; param = rows per segment (0 = chosen from the lattice
- *     size and the SM count).
+ *     size and the SM count);
+ *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a plane march
+ *     (param = planes per segment, 0 = automatic), then collision and
+ *     streaming, then the phi and T updates, one thread per site; mu, F and
+ *     u pass through the context's derived-field planes.  For 3D contexts
+ *     every other variant runs the fused plane march (param = planes per
+ *     segment).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
 #define LF_VARIANT_MARCH  0
 #define LF_VARIANT_TILE   1
 #define LF_VARIANT_MARCH2 2
+#define LF_VARIANT_SPLIT3 3
 int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
 
 /* Current step counter. */

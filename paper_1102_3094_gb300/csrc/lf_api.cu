@@ -140,7 +140,7 @@ int do_steps(lf_ctx* c, int64_t n)
 {
     const Phys<R> ph = phys_of<R>(c);
     for (int64_t k = 0; k < n; ++k) {
-        StepIO<R> io = io_of<R>(c, false);
+        StepIO<R> io = io_of<R>(c, true);      // the three-pass 3D step passes mu, F, u through aux
         if (launch_step_any<R>(c->g, ph, io, false, c->stream) != cudaSuccess) return LF_ECUDA;
         if (c->params.hydro) c->fcur ^= 1;
         c->pcur ^= 1;
@@ -355,7 +355,8 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
     c->g.plane = plane;
     c->g.walls = walls->walls;
     c->g.t_mode = walls->t_wall_mode;
-    c->g.variant = (grid->d == 2 && params->precision == LF_FP32) ? LF_VARIANT_MARCH2 : LF_VARIANT_MARCH;
+    c->g.variant = grid->d == 3 ? LF_VARIANT_SPLIT3
+                 : (params->precision == LF_FP32 ? LF_VARIANT_MARCH2 : LF_VARIANT_MARCH);
     c->g.tune = 0;
 
     if (params->workspace) {
@@ -535,7 +536,8 @@ int64_t lf_step_count(const lf_ctx* c) { return c ? c->step : -1; }
 
 int lf_set_kernel_variant(lf_ctx* c, int variant, int param)
 {
-    if (!c || (variant != LF_VARIANT_MARCH && variant != LF_VARIANT_TILE && variant != LF_VARIANT_MARCH2) ||
+    if (!c || (variant != LF_VARIANT_MARCH && variant != LF_VARIANT_TILE && variant != LF_VARIANT_MARCH2 &&
+               variant != LF_VARIANT_SPLIT3) ||
         param < 0)
         return LF_EINVAL;
     c->g.variant = variant;

@@ -99,6 +99,8 @@ template <typename R>
 cudaError_t launch_step3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux,
                           cudaStream_t s);
 template <typename R>
+cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);
+template <typename R>
 cudaError_t launch_tsub3d(const Geom& g, const Phys<R>& p, const R* Tin, R* Tout, cudaStream_t s);
 template <typename R>
 cudaError_t launch_tsub(const Geom& g, const Phys<R>& p, const R* Tin, R* Tout, cudaStream_t s);

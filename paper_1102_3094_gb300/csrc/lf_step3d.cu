@@ -431,6 +431,7 @@ __global__ void k_tsub3d(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __rest
 template <typename R>
 cudaError_t launch_step3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
+    if (!aux && g.variant == LF_VARIANT_SPLIT3) return launch_split3d<R>(g, p, io, s);
     if constexpr (sizeof(R) == 4) {
         return aux ? launch_cfg3<R, 32, 8, 256, true>(g, p, io, s) : launch_cfg3<R, 32, 8, 256, false>(g, p, io, s);
     } else {

@@ -175,7 +175,7 @@ def lf_load(ctx, path: str) -> None:
     _ok(lib().lf_load(ctx, path.encode()), "lf_load")
 
 
-LF_VARIANT_MARCH, LF_VARIANT_TILE, LF_VARIANT_MARCH2 = 0, 1, 2
+LF_VARIANT_MARCH, LF_VARIANT_TILE, LF_VARIANT_MARCH2, LF_VARIANT_SPLIT3 = 0, 1, 2, 3
 
 
 def lf_set_kernel_variant(ctx, variant: int, param: int = 0) -> None:
@@ -254,7 +254,8 @@ class Lattice:
         lf_step(self.ctx, n)
 
     def set_variant(self, variant: str = "march", param: int = 0):
-        code = {"march": LF_VARIANT_MARCH, "tile": LF_VARIANT_TILE, "march2": LF_VARIANT_MARCH2}[variant]
+        code = {"march": LF_VARIANT_MARCH, "tile": LF_VARIANT_TILE, "march2": LF_VARIANT_MARCH2,
+                "split3": LF_VARIANT_SPLIT3}[variant]
         lf_set_kernel_variant(self.ctx, code, param)
 
     def diag(self):

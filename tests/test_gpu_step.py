@@ -119,10 +119,16 @@ CASES3 = [
 ]
 
 
+VARIANTS3 = {"fused": ("march", 0), "split3": ("split3", 0), "split3-z3": ("split3", 3),
+             "split3-t16": ("split3", 1 << 16)}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS3))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
-def test_aux_and_step_parity_3d(case, prec):
+def test_aux_and_step_parity_3d(case, prec, variant):
     sim, cfg, st = make_pair(case, prec)
+    sim.set_variant(*VARIANTS3[variant])
     tol = TOL[prec]
     ax = O.aux(st)
     checks = {"mu": (sim.get("mu"), ax["mu"]), "rho": (sim.get("rho"), ax["n"])}
@@ -142,8 +148,10 @@ def test_aux_and_step_parity_3d(case, prec):
     sim.close()
 
 
-def test_multistep_3d_fp64():
+@pytest.mark.parametrize("variant", ["march", "split3"])
+def test_multistep_3d_fp64(variant):
     sim = lf.Lattice(d=3, nx=20, ny=16, nz=18, precision="fp64", xi=0.01)
+    sim.set_variant(variant, 0)
     st = O.init(O.make_cfg(d=3, nx=20, ny=16, nz=18, xi=0.01))
     sim.step(50)
     ref = O.run(st, 50)
