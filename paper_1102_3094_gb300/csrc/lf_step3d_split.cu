@@ -50,172 +50,166 @@ __device__ __forceinline__ void cp_async_s(void* dst, const void* src)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
 
+// Pass A layout.  A CTA owns a TX x TY tile and one thread per column of the
+// tile grown by 2 on every side ((TX + 4) x (TY + 4) threads), marching
+// along z.  Shared memory holds in-plane neighbours only: a ring of phi planes
+// (tile + 3), the psi plane and the five in-plane components of P (tile + 1),
+// each of the last two double-buffered; values along z stay in registers.
 template <typename R, int TX, int TY>
 struct Force3 {
-    static constexpr int W3 = TX + 6, H3 = TY + 6, A3 = W3 * H3;   // phi (r = 3)
-    static constexpr int W2 = TX + 4, H2 = TY + 4, A2 = W2 * H2;   // psi (r = 2)
-    static constexpr int W1 = TX + 2, H1 = TY + 2, A1 = W1 * H1;   // T, lam, P (r = 1)
-    static constexpr int NPHI = 5;                                  // planes k-3 .. k+1
-    static constexpr int NT = 4;                                    // T planes k-2 .. k+1
+    static constexpr int CW = TX + 4, CH = TY + 4, NTH = CW * CH;   // threads = columns of the psi region
+    static constexpr int W3 = TX + 6, H3 = TY + 6, A3 = W3 * H3;    // phi (r = 3)
+    static constexpr int A2 = CW * CH;                              // psi (r = 2)
+    static constexpr int NPHI = 4;                                  // phi planes k-2 .. k+1
     static constexpr int PHI = 0;
-    static constexpr int TT = PHI + NPHI * A3;
-    static constexpr int PSI = TT + NT * A1;                        // 3 planes
-    static constexpr int PIN = PSI + 3 * A2;                        // xx, xy, yy: 2 planes each
-    static constexpr int PZ = PIN + 6 * A1;                         // xz, yz, zz: 3 planes each
-    static constexpr int TOTAL = PZ + 9 * A1;
+    static constexpr int PSI = PHI + NPHI * A3;                     // 2 planes
+    static constexpr int PP = PSI + 2 * A2;                         // 5 comps x 2 planes, psi-region indexing
+    static constexpr int TOTAL = PP + 10 * A2;
     static constexpr size_t MAPS = sizeof(R) * TOTAL;
     static constexpr size_t BYTES = MAPS + sizeof(int) * (W3 + H3);
 };
 
-// Pass A.  A CTA owns a TX x TY tile and marches along z over [z0, z1):
-// iteration k prefetches phi / T of plane k + 1 and runs psi on plane k - 1,
-// lam / P / mu on plane k - 2 and F on plane k - 3.
-template <typename R, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_force3d(Geom g, Phys<R> p, StepIO<R> io, int Hz)
+// Pass A.  Iteration k: phi plane k + 1 is prefetched (cp.async) while
+//   psi   = lap(phi)                    on plane k - 1 (every column, r = 2),
+//   lam, P, mu                          on plane k - 2 (r = 1; mu stored on r = 0),
+//   F = -d_a P_ab                       on plane k - 3 (r = 0, stored)
+// run one plane apart; each stage reads only what earlier iterations wrote,
+// so one barrier per plane orders everything.
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(Force3<R, TX, TY>::NTH) k_force3d(Geom g, Phys<R> p, StepIO<R> io, int Hz)
 {
     using P3 = Force3<R, TX, TY>;
-    constexpr int W3 = P3::W3, W2 = P3::W2, W1 = P3::W1;
-    constexpr int A3 = P3::A3, A2 = P3::A2, A1 = P3::A1;
+    constexpr int W3 = P3::W3, CW = P3::CW, A3 = P3::A3, A2 = P3::A2, NTH = P3::NTH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
     R* sphi = sm + P3::PHI;
-    R* sT = sm + P3::TT;
     R* spsi = sm + P3::PSI;
-    R* sPin = sm + P3::PIN;   // [comp 0..2][plane parity][A1]: xx, xy, yy
-    R* sPz = sm + P3::PZ;     // [comp 0..2][plane mod 3][A1]: xz, yz, zz
-    int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);   // x0 - 3 + lx -> storage column
-    int* rowmap = colmap + W3;                                   // y0 - 3 + ly -> storage row
+    R* sP = sm + P3::PP;      // [plane parity][comp xx, xy, yy, xz, yz][A2]
+    int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);   // x0 - 3 + i -> storage column
+    int* rowmap = colmap + W3;                                   // y0 - 3 + j -> storage row
 
+    const int t = threadIdx.x;
+    const int cx = t % CW, cy = t / CW;                  // column of the psi region
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
     const int64_t zs = (int64_t)ny * pitch;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * Hz, z1 = min(z0 + Hz, nz);
     const int kbeg = z0 - 3, kend = z1 + 2;
     const R half = R(0.5);
+    const bool in1 = cx >= 1 && cx < CW - 1 && cy >= 1 && cy < P3::CH - 1;   // r = 1 region
+    const bool in0 = cx >= 2 && cx < CW - 2 && cy >= 2 && cy < P3::CH - 2;   // the tile
+    const int gx = x0 - 2 + cx, gy = y0 - 2 + cy;
+    const bool own = in0 && gx < nx && gy < ny;
     bool bad = false;
 
-    for (int q = threadIdx.x; q < W3 + P3::H3; q += NT) {
+    for (int q = t; q < W3 + P3::H3; q += NTH) {
         if (q < W3) colmap[q] = wrap_s(x0 - 3 + q, nx);
         else rowmap[q - W3] = wrap_s(y0 - 3 + (q - W3), ny);
     }
     __syncthreads();
+    // storage offset of this column inside a plane (wrapped)
+    const int64_t col_off = (int64_t)rowmap[cy + 1] * pitch + colmap[cx + 1];
+    const int c3 = (cy + 1) * W3 + cx + 1;               // own position in a phi plane
+    const int c2 = t;                                    // own position in a psi / P plane
 
-    auto ring = [&](int z, int n) { return (z - kbeg + 3 * n) % n; };
-    auto fetch = [&](int z) {             // phi (r = 3) and T (r = 1) of plane z
+    auto slot = [&](int z) { return (z - kbeg + 4 * P3::NPHI) % P3::NPHI; };
+    auto fetch = [&](int z) {
         if (z <= kend) {
-            const int gz = map_z(z, nz, walls);
-            R* dphi = sphi + ring(z, P3::NPHI) * A3;
-            R* dT = sT + ring(z, P3::NT) * A1;
-            for (int q = threadIdx.x; q < A3; q += NT) {
+            const int64_t pz = (int64_t)map_z(z, nz, walls) * zs;
+            R* d = sphi + slot(z) * A3;
+            for (int q = t; q < A3; q += NTH) {
                 const int ly = q / W3, lx = q - ly * W3;
-                const int64_t off = gz * zs + (int64_t)rowmap[ly] * pitch + colmap[lx];
-                cp_async_s<sizeof(R)>(&dphi[q], io.phi_in + off);
-                if (lx >= 2 && lx < W3 - 2 && ly >= 2 && ly < P3::H3 - 2)
-                    cp_async_s<sizeof(R)>(&dT[(ly - 2) * W1 + lx - 2], io.T_in + off);
+                cp_async_s<sizeof(R)>(&d[q], io.phi_in + pz + (int64_t)rowmap[ly] * pitch + colmap[lx]);
             }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
+    auto Tload = [&](int z) -> R {                       // T of this column (r = 1 columns only)
+        if (!in1 || z < kbeg || z > kend) return R(0);
+        return io.T_in[(int64_t)map_z(z, nz, walls) * zs + col_off];
+    };
+
+    // register windows along z (suffix = plane offset from k)
+    R phm1 = 0, phm2 = 0, phm3 = 0;          // own-column phi(k-1), phi(k-2), phi(k-3)
+    R psm1 = 0, psm2 = 0;                    // own-column psi(k-2), psi(k-3) (psi(k-1) is computed in iteration k)
+    R xzA = 0, xzB = 0, xzC = 0, yzA = 0, yzB = 0, yzC = 0, zzA = 0, zzB = 0, zzC = 0;   // P_az at k-2 .. k-4
+    R Tq0 = Tload(kbeg), Tq1 = 0, Tq2 = 0, Tq3 = 0;   // T(k) .. T(k-3)
 
     fetch(kbeg);
     for (int k = kbeg; k <= kend; ++k) {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
         fetch(k + 1);
-        const R* phk = sphi + ring(k, P3::NPHI) * A3;
-        const R* phm1 = sphi + ring(k - 1, P3::NPHI) * A3;
-        const R* phm2 = sphi + ring(k - 2, P3::NPHI) * A3;
-        const R* phm3 = sphi + ring(k - 3, P3::NPHI) * A3;
+        const R Tnext = Tload(k + 1);                    // consumed three iterations later
+        const R* pk = sphi + slot(k) * A3;
+        const R* p1 = sphi + slot(k - 1) * A3;
+        const R* p2 = sphi + slot(k - 2) * A3;
+        const R phk = pk[c3];
 
-        // ---- plane k-1: psi (r = 2) ------------------------------------------
-        const int z1p = k - 1;
-        if (z1p >= z0 - 2 && z1p <= z1 + 1) {
-            R* dst = spsi + ring(z1p, 3) * A2;
-            for (int q = threadIdx.x; q < A2; q += NT) {
-                const int ly = q / W2, lx = q - ly * W2;
-                const int c = (ly + 1) * W3 + lx + 1;
-                dst[q] = phm1[c - 1] + phm1[c + 1] + phm1[c - W3] + phm1[c + W3] + phm2[c] + phk[c]
-                       - R(6) * phm1[c];
-            }
-        }
-        __syncthreads();
+        // ---- plane k-1: psi (r = 2) ---------------------------------------------
+        const R psi_new = p1[c3 - 1] + p1[c3 + 1] + p1[c3 - W3] + p1[c3 + W3] + phm2 + phk - R(6) * phm1;
+        spsi[((k - 1 - kbeg) & 1) * A2 + c2] = psi_new;
 
-        // ---- plane k-2: lam, P (r = 1), mu (r = 0) ------------------------------
+        // ---- plane k-2: lam, P, mu (r = 1) -----------------------------------------
+        R xz = 0, yz = 0, zz = 0;
         const int z2 = k - 2;
-        if (z2 >= z0 - 1 && z2 <= z1) {
-            const R* ps0 = spsi + ring(z2, 3) * A2;
-            const R* psu = spsi + ring(z2 + 1, 3) * A2;
-            const R* psd = spsi + ring(z2 - 1, 3) * A2;
-            const R* tz = sT + ring(z2, P3::NT) * A1;
-            const int pin = ring(z2, 2), pz = ring(z2, 3);
-            const bool mu_plane = z2 >= z0 && z2 < z1;
-            for (int q = threadIdx.x; q < A1; q += NT) {
-                const int ly = q / W1, lx = q - ly * W1;
-                const int cp = (ly + 2) * W3 + lx + 2;
-                const int cs = (ly + 1) * W2 + lx + 1;
-                const R ph = phm2[cp], psi = ps0[cs];
-                const R lam = ps0[cs - 1] + ps0[cs + 1] + ps0[cs - W2] + ps0[cs + W2] + psu[cs] + psd[cs] - R(6) * psi;
-                const R av = (tz[q] - p.Tc) * p.inv_Tc;
-                if (mu_plane && lx >= 1 && lx < W1 - 1 && ly >= 1 && ly < P3::H1 - 1) {
-                    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-                    if (gx < nx && gy < ny) {
-                        const R mu = av * ph + p.b * ph * ph * ph - p.kappa * psi + p.c * lam;
-                        bad |= !isfinite(mu);
-                        io.mu[z2 * zs + (int64_t)gy * pitch + gx] = mu;
-                    }
-                }
-                if (p.hydro) {
-                    const R d0 = half * (phm2[cp + 1] - phm2[cp - 1]);
-                    const R d1 = half * (phm2[cp + W3] - phm2[cp - W3]);
-                    const R d2 = half * (phm1[cp] - phm3[cp]);
-                    const R s0 = half * (ps0[cs + 1] - ps0[cs - 1]);
-                    const R s1 = half * (ps0[cs + W2] - ps0[cs - W2]);
-                    const R s2 = half * (psu[cs] - psd[cs]);
-                    const R ph2 = ph * ph;
-                    const R iso = av * ph2 * half + R(0.75) * p.b * ph2 * ph2
-                                - p.kappa * (ph * psi + half * (d0 * d0 + d1 * d1 + d2 * d2))
-                                + p.c * (ph * lam + half * psi * psi + d0 * s0 + d1 * s1 + d2 * s2);
-                    sPin[(0 * 2 + pin) * A1 + q] = iso + p.kappa * d0 * d0 - R(2) * p.c * d0 * s0;
-                    sPin[(1 * 2 + pin) * A1 + q] = p.kappa * d0 * d1 - p.c * (d0 * s1 + d1 * s0);
-                    sPin[(2 * 2 + pin) * A1 + q] = iso + p.kappa * d1 * d1 - R(2) * p.c * d1 * s1;
-                    sPz[(0 * 3 + pz) * A1 + q] = p.kappa * d0 * d2 - p.c * (d0 * s2 + d2 * s0);
-                    sPz[(1 * 3 + pz) * A1 + q] = p.kappa * d1 * d2 - p.c * (d1 * s2 + d2 * s1);
-                    sPz[(2 * 3 + pz) * A1 + q] = iso + p.kappa * d2 * d2 - R(2) * p.c * d2 * s2;
-                }
+        if (in1 && z2 >= z0 - 1 && z2 <= z1) {
+            const R* ps = spsi + ((z2 - kbeg) & 1) * A2;   // psi(k-2), written one iteration ago
+            const R ph = phm2, psi = psm1;                  // phi(k-2), psi(k-2)
+            const R lam = ps[c2 - 1] + ps[c2 + 1] + ps[c2 - CW] + ps[c2 + CW] + psi_new + psm2 - R(6) * psi;
+            const R av = (Tq2 - p.Tc) * p.inv_Tc;
+            if (own && z2 >= z0 && z2 < z1) {
+                const R mu = av * ph + p.b * ph * ph * ph - p.kappa * psi + p.c * lam;
+                bad |= !isfinite(mu);
+                io.mu[(int64_t)z2 * zs + (int64_t)gy * pitch + gx] = mu;
+            }
+            if (p.hydro) {
+                const R d0 = half * (p2[c3 + 1] - p2[c3 - 1]);
+                const R d1 = half * (p2[c3 + W3] - p2[c3 - W3]);
+                const R d2 = half * (phm1 - phm3);
+                const R s0 = half * (ps[c2 + 1] - ps[c2 - 1]);
+                const R s1 = half * (ps[c2 + CW] - ps[c2 - CW]);
+                const R s2 = half * (psi_new - psm2);
+                const R ph2 = ph * ph;
+                const R iso = av * ph2 * half + R(0.75) * p.b * ph2 * ph2
+                            - p.kappa * (ph * psi + half * (d0 * d0 + d1 * d1 + d2 * d2))
+                            + p.c * (ph * lam + half * psi * psi + d0 * s0 + d1 * s1 + d2 * s2);
+                R* P = sP + ((z2 - kbeg) & 1) * 5 * A2;
+                P[0 * A2 + c2] = iso + p.kappa * d0 * d0 - R(2) * p.c * d0 * s0;
+                P[1 * A2 + c2] = p.kappa * d0 * d1 - p.c * (d0 * s1 + d1 * s0);
+                P[2 * A2 + c2] = iso + p.kappa * d1 * d1 - R(2) * p.c * d1 * s1;
+                xz = p.kappa * d0 * d2 - p.c * (d0 * s2 + d2 * s0);
+                yz = p.kappa * d1 * d2 - p.c * (d1 * s2 + d2 * s1);
+                zz = iso + p.kappa * d2 * d2 - R(2) * p.c * d2 * s2;
+                P[3 * A2 + c2] = xz;
+                P[4 * A2 + c2] = yz;
             }
         }
-        __syncthreads();
 
-        // ---- plane k-3: F (r = 0) -----------------------------------------------
+        // ---- plane k-3: F (r = 0) ---------------------------------------------------
         const int z3 = k - 3;
-        if (p.hydro && z3 >= z0 && z3 < z1) {
-            const int pin = ring(z3, 2);
-            const int pz0 = ring(z3, 3), pzu = ring(z3 + 1, 3), pzd = ring(z3 - 1, 3);
-            const R* Pxx = sPin + (0 * 2 + pin) * A1;
-            const R* Pxy = sPin + (1 * 2 + pin) * A1;
-            const R* Pyy = sPin + (2 * 2 + pin) * A1;
-            for (int q = threadIdx.x; q < TX * TY; q += NT) {
-                const int ly = q / TX, lx = q - ly * TX;
-                const int gx = x0 + lx, gy = y0 + ly;
-                if (gx >= nx || gy >= ny) continue;
-                const int c = (ly + 1) * W1 + lx + 1;
-                const R Fx = -(half * (Pxx[c + 1] - Pxx[c - 1]) + half * (Pxy[c + W1] - Pxy[c - W1])
-                               + half * (sPz[(0 * 3 + pzu) * A1 + c] - sPz[(0 * 3 + pzd) * A1 + c]));
-                const R Fy = -(half * (Pxy[c + 1] - Pxy[c - 1]) + half * (Pyy[c + W1] - Pyy[c - W1])
-                               + half * (sPz[(1 * 3 + pzu) * A1 + c] - sPz[(1 * 3 + pzd) * A1 + c]));
-                const R Fz = -(half * (sPz[(0 * 3 + pz0) * A1 + c + 1] - sPz[(0 * 3 + pz0) * A1 + c - 1])
-                               + half * (sPz[(1 * 3 + pz0) * A1 + c + W1] - sPz[(1 * 3 + pz0) * A1 + c - W1])
-                               + half * (sPz[(2 * 3 + pzu) * A1 + c] - sPz[(2 * 3 + pzd) * A1 + c]));
-                const int64_t site = z3 * zs + (int64_t)gy * pitch + gx;
-                io.F[0][site] = Fx;
-                io.F[1][site] = Fy;
-                io.F[2][site] = Fz;
-            }
+        if (p.hydro && own && z3 >= z0 && z3 < z1) {
+            const R* P = sP + ((z3 - kbeg) & 1) * 5 * A2;  // P(k-3), written one iteration ago
+            const R Fx = -(half * (P[0 * A2 + c2 + 1] - P[0 * A2 + c2 - 1]) + half * (P[1 * A2 + c2 + CW] - P[1 * A2 + c2 - CW])
+                           + half * (xz - xzC));
+            const R Fy = -(half * (P[1 * A2 + c2 + 1] - P[1 * A2 + c2 - 1]) + half * (P[2 * A2 + c2 + CW] - P[2 * A2 + c2 - CW])
+                           + half * (yz - yzC));
+            const R Fz = -(half * (P[3 * A2 + c2 + 1] - P[3 * A2 + c2 - 1]) + half * (P[4 * A2 + c2 + CW] - P[4 * A2 + c2 - CW])
+                           + half * (zz - zzC));
+            const int64_t site = (int64_t)z3 * zs + (int64_t)gy * pitch + gx;
+            io.F[0][site] = Fx;
+            io.F[1][site] = Fy;
+            io.F[2][site] = Fz;
         }
-        // the barrier at the top of the next iteration orders the rings
+
+        // shift the windows
+        phm3 = phm2; phm2 = phm1; phm1 = phk;
+        psm2 = psm1; psm1 = psi_new;
+        xzC = xzB; xzB = xz; yzC = yzB; yzB = yz; zzC = zzB; zzB = zz;
+        Tq3 = Tq2; Tq2 = Tq1; Tq1 = Tq0; Tq0 = Tnext;
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
 // Pass B: one thread per site.  Moments of f(t) with the half-force shift,
@@ -362,11 +356,11 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     if (bad) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
-template <typename R, int TX, int TY, int NT>
+template <typename R, int TX, int TY>
 cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
     using P3 = Force3<R, TX, TY>;
-    auto kern = k_force3d<R, TX, TY, NT>;
+    auto kern = k_force3d<R, TX, TY>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P3::BYTES);
@@ -375,14 +369,14 @@ cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
     }
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int Hz = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;
-    if (Hz <= 0) {   // about eight waves of four CTAs per SM, segments of at least 16 planes
-        const int want = (8 * 4 * 152 + tiles - 1) / tiles;
+    if (Hz <= 0) {   // about eight waves of two CTAs per SM, segments of at least 16 planes
+        const int want = (8 * 2 * 152 + tiles - 1) / tiles;
         Hz = (g.nz + want - 1) / want;
         if (Hz < 16) Hz = 16;
     }
     if (Hz > g.nz) Hz = g.nz;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + Hz - 1) / Hz);
-    kern<<<grid, NT, P3::BYTES, s>>>(g, p, io, Hz);
+    kern<<<grid, P3::NTH, P3::BYTES, s>>>(g, p, io, Hz);
     return cudaGetLastError();
 }
 
@@ -393,9 +387,9 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
 {
     cudaError_t e;
     if constexpr (sizeof(R) == 4)
-        e = (g.tune >> 16) == 1 ? launch_force<R, 32, 16, 512>(g, p, io, s) : launch_force<R, 32, 8, 256>(g, p, io, s);
+        e = (g.tune >> 16) == 1 ? launch_force<R, 60, 4>(g, p, io, s) : launch_force<R, 28, 12>(g, p, io, s);
     else
-        e = launch_force<R, 16, 8, 128>(g, p, io, s);
+        e = launch_force<R, 28, 12>(g, p, io, s);
     if (e != cudaSuccess) return e;
     if (p.hydro) {
         dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
