@@ -26,7 +26,7 @@ using namespace lf;
 
 namespace {
 
-constexpr int kNT = 128, kD = 3;
+constexpr int kNT = 64, kD = 3;     // 56-column strips: less idle width on 128^2 .. 512^2 lattices
 using MarchCfg = march::March2<kNT, kD>;
 
 struct EnsRun {
@@ -50,7 +50,7 @@ struct EnsTItem {
     int run, bx, by;
 };
 
-__global__ void __launch_bounds__(kNT, 3) k_ens_march2d(const EnsRun* __restrict__ runs,
+__global__ void __launch_bounds__(kNT, 6) k_ens_march2d(const EnsRun* __restrict__ runs,
                                                        const EnsItem* __restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -368,6 +368,9 @@ cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, 
     if constexpr (sizeof(R) == 4) {
         if (!aux && g.variant == LF_VARIANT_MARCH2 && g.ny >= 2)
         {
+            if ((g.tune >> 16) == 1)
+                return p.hydro ? launch_march_x2<64, 3, true, 6>(g, p, io, s)
+                               : launch_march_x2<64, 3, false, 6>(g, p, io, s);
             return p.hydro ? launch_march_x2<128, 3, true, 3>(g, p, io, s) : launch_march_x2<128, 3, false, 3>(g, p, io, s);
         }
     }

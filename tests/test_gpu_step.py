@@ -44,7 +44,8 @@ def to_oracle_f(f_lib, d):
 
 
 VARIANTS = {"march": ("march", 0), "march-h5": ("march", 5), "tile": ("tile", 0),
-            "march2": ("march2", 0), "march2-h5": ("march2", 5), "march2-h1": ("march2", 1)}
+            "march2": ("march2", 0), "march2-h5": ("march2", 5), "march2-h1": ("march2", 1),
+            "march2-n64": ("march2", 1 << 16)}
 
 
 def make_pair(case, prec, seed=11, variant="march"):
