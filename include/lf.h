@@ -232,8 +232,9 @@ int lf_load(lf_ctx* ctx, const char* path);
  *   LF_VARIANT_MARCH2 (default for 2D FP32; FP64 contexts run LF_VARIANT_MARCH
  *     instead): a CTA owns two vertically adjacent segments of a strip that
  *     march away from their common row, carried in the two lanes of packed
- *     FP32x2 arithmetic; param = rows per segment (0 = chosen from the lattice
- *     size and the SM count);
+ *     FP32x2 arithmetic; (param & 0xFFFF) = rows per segment (0 = chosen from
+ *     the lattice size and the SM count), (param >> 16) == 1 selects CTAs of
+ *     64 threads (56 columns) instead of 128 (120 columns);
  *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a plane march
  *     (param = planes per segment, 0 = automatic), then collision and
  *     streaming, then the phi and T updates, one thread per site; mu, F and
