@@ -17,6 +17,7 @@
 // tile, against + 3 / + 2 / + 1 in the fused kernel, and no population is
 // read outside its own site.
 #include "lf_internal.cuh"
+#include "lf_march2d_x2.cuh"      // packed FP32x2 helpers
 
 namespace lf {
 
@@ -212,6 +213,181 @@ __global__ void __launch_bounds__(Force3<R, TX, TY>::NTH) k_force3d(Geom g, Phys
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
+// Pass A on two z-segments at once (FP32): lane .x marches planes
+// [z0, z0 + H), lane .y planes [z0 + H, z0 + 2H) (shorter or empty at the top
+// of the lattice), both with the same lags, and all arithmetic runs on packed
+// FP32x2 instructions.  Layout and stages as in k_force3d, with float2
+// shared-memory planes.
+template <int TX, int TY>
+struct Force3x2 {
+    static constexpr int CW = TX + 4, CH = TY + 4, NTH = CW * CH;
+    static constexpr int W3 = TX + 6, H3 = TY + 6, A3 = W3 * H3;
+    static constexpr int A2 = CW * CH;
+    static constexpr int NPHI = 4;
+    static constexpr int PHI = 0;
+    static constexpr int PSI = PHI + NPHI * A3;
+    static constexpr int PP = PSI + 2 * A2;
+    static constexpr int TOTAL = PP + 10 * A2;                      // float2 elements
+    static constexpr size_t MAPS = sizeof(float2) * TOTAL;
+    static constexpr size_t BYTES = MAPS + sizeof(int) * (W3 + H3);
+};
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 1) k_force3d_x2(Geom g, Phys<float> p, StepIO<float> io, int H)
+{
+    using namespace march;
+    using P3 = Force3x2<TX, TY>;
+    constexpr int W3 = P3::W3, CW = P3::CW, A3 = P3::A3, A2 = P3::A2, NTH = P3::NTH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    float2* sphi = sm + P3::PHI;
+    float2* spsi = sm + P3::PSI;
+    float2* sP = sm + P3::PP;
+    int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);
+    int* rowmap = colmap + W3;
+
+    const int t = threadIdx.x;
+    const int cx = t % CW, cy = t / CW;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
+    const int64_t zs = (int64_t)ny * pitch;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int za0 = blockIdx.z * 2 * H, zb0 = za0 + H;                    // first plane of each lane
+    const int ha = min(H, nz - za0), hb = max(0, min(H, nz - zb0));     // planes per lane
+    const int hmax = ha > hb ? ha : hb;
+    const int nit = hmax + 6;                                            // relative iterations 0 .. nit-1
+    const float2 half = v2(0.5f), six = v2(6.f);
+    const bool in1 = cx >= 1 && cx < CW - 1 && cy >= 1 && cy < P3::CH - 1;
+    const bool in0 = cx >= 2 && cx < CW - 2 && cy >= 2 && cy < P3::CH - 2;
+    const int gx = x0 - 2 + cx, gy = y0 - 2 + cy;
+    const bool own = in0 && gx < nx && gy < ny;
+    bool bad = false;
+
+    for (int q = t; q < W3 + P3::H3; q += NTH) {
+        if (q < W3) colmap[q] = wrap_s(x0 - 3 + q, nx);
+        else rowmap[q - W3] = wrap_s(y0 - 3 + (q - W3), ny);
+    }
+    __syncthreads();
+    const int64_t col_off = (int64_t)rowmap[cy + 1] * pitch + colmap[cx + 1];
+    const int c3 = (cy + 1) * W3 + cx + 1;
+    const int c2 = t;
+    const int64_t own_off = (int64_t)gy * pitch + gx;
+
+    // relative plane j (iteration k = j + 3 loads relative plane k + 1 - 3 ... ): plane of lane L = z0_L + j
+    auto slot = [&](int j) { return (j + 4 * P3::NPHI) % P3::NPHI; };
+    auto fetch = [&](int j) {                             // relative plane j = -3 .. hmax + 2
+        if (j <= hmax + 2) {
+            const int64_t pa = (int64_t)map_z(za0 + j, nz, walls) * zs;
+            const int64_t pb = (int64_t)map_z(zb0 + j, nz, walls) * zs;
+            float* d = reinterpret_cast<float*>(sphi + slot(j) * A3);
+            for (int q = t; q < A3; q += NTH) {
+                const int ly = q / W3, lx = q - ly * W3;
+                const int64_t o = (int64_t)rowmap[ly] * pitch + colmap[lx];
+                cp_async_s<4>(d + 2 * q, io.phi_in + pa + o);
+                cp_async_s<4>(d + 2 * q + 1, io.phi_in + pb + o);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    auto Tload = [&](int j) -> float2 {
+        if (!in1 || j < -3 || j > hmax + 2) return v2(0.f);
+        return make_float2(io.T_in[(int64_t)map_z(za0 + j, nz, walls) * zs + col_off],
+                           io.T_in[(int64_t)map_z(zb0 + j, nz, walls) * zs + col_off]);
+    };
+
+    float2 phm1 = v2(0), phm2 = v2(0), phm3 = v2(0);
+    float2 psm1 = v2(0), psm2 = v2(0);
+    float2 xzB = v2(0), xzC = v2(0), yzB = v2(0), yzC = v2(0), zzB = v2(0), zzC = v2(0);
+    float2 Tq0 = Tload(-3), Tq1 = v2(0), Tq2 = v2(0);
+
+    fetch(-3);
+    // iteration i handles relative plane j = i - 3 as "k": fetch j + 1, psi on j - 1, P on j - 2, F on j - 3
+#pragma unroll 1
+    for (int j = -3; j < nit - 3; ++j) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        fetch(j + 1);
+        const float2 Tnext = Tload(j + 1);
+        const float2* pk = sphi + slot(j) * A3;
+        const float2* p1 = sphi + slot(j - 1) * A3;
+        const float2* p2 = sphi + slot(j - 2) * A3;
+        const float2 phk = pk[c3];
+
+        // psi of plane j - 1
+        const float2 psi_new = fma2(six, sub2(v2(0), phm1),
+                                    add2(add2(add2(p1[c3 - 1], p1[c3 + 1]), add2(p1[c3 - W3], p1[c3 + W3])), add2(phm2, phk)));
+        spsi[((j - 1) & 1) * A2 + c2] = psi_new;
+
+        // lam, P, mu of plane j - 2
+        float2 xz = v2(0), yz = v2(0), zz = v2(0);
+        const int r2 = j - 2;                              // relative plane
+        if (in1 && r2 >= -1 && r2 <= hmax) {
+            const float2* ps = spsi + ((j - 2) & 1) * A2;
+            const float2 ph = phm2, psi = psm1;
+            const float2 lam = fma2(six, sub2(v2(0), psi),
+                                    add2(add2(add2(ps[c2 - 1], ps[c2 + 1]), add2(ps[c2 - CW], ps[c2 + CW])), add2(psi_new, psm2)));
+            const float2 av = mul2(sub2(Tq2, v2(p.Tc)), v2(p.inv_Tc));
+            const float2 ph2 = mul2(ph, ph);
+            if (own && r2 >= 0) {
+                // mu = a phi + b phi^3 - kappa psi + c lam
+                const float2 mu = fma2(v2(p.c), lam, fma2(v2(-p.kappa), psi, mul2(ph, fma2(v2(p.b), ph2, av))));
+                if (r2 < ha) { bad |= !isfinite(mu.x); io.mu[(int64_t)(za0 + r2) * zs + own_off] = mu.x; }
+                if (r2 < hb) { bad |= !isfinite(mu.y); io.mu[(int64_t)(zb0 + r2) * zs + own_off] = mu.y; }
+            }
+            if (p.hydro) {
+                const float2 d0 = mul2(half, sub2(p2[c3 + 1], p2[c3 - 1]));
+                const float2 d1 = mul2(half, sub2(p2[c3 + W3], p2[c3 - W3]));
+                const float2 d2 = mul2(half, sub2(phm1, phm3));
+                const float2 s0 = mul2(half, sub2(ps[c2 + 1], ps[c2 - 1]));
+                const float2 s1 = mul2(half, sub2(ps[c2 + CW], ps[c2 - CW]));
+                const float2 s2 = mul2(half, sub2(psi_new, psm2));
+                const float2 gp2 = fma2(d0, d0, fma2(d1, d1, mul2(d2, d2)));
+                const float2 gpgs = fma2(d0, s0, fma2(d1, s1, mul2(d2, s2)));
+                // iso = a phi^2/2 + 3b phi^4/4 - kappa (phi psi + gp2/2) + c (phi lam + psi^2/2 + gpgs)
+                float2 iso = mul2(ph2, fma2(v2(0.75f * p.b), ph2, mul2(half, av)));
+                iso = fma2(v2(-p.kappa), fma2(half, gp2, mul2(ph, psi)), iso);
+                iso = fma2(v2(p.c), add2(fma2(ph, lam, mul2(half, mul2(psi, psi))), gpgs), iso);
+                const float2 k_ = v2(p.kappa), mc = v2(-p.c), m2c = v2(-2.f * p.c);
+                float2* P = sP + ((j - 2) & 1) * 5 * A2;
+                P[0 * A2 + c2] = fma2(k_, mul2(d0, d0), fma2(m2c, mul2(d0, s0), iso));
+                P[1 * A2 + c2] = fma2(k_, mul2(d0, d1), mul2(mc, fma2(d0, s1, mul2(d1, s0))));
+                P[2 * A2 + c2] = fma2(k_, mul2(d1, d1), fma2(m2c, mul2(d1, s1), iso));
+                xz = fma2(k_, mul2(d0, d2), mul2(mc, fma2(d0, s2, mul2(d2, s0))));
+                yz = fma2(k_, mul2(d1, d2), mul2(mc, fma2(d1, s2, mul2(d2, s1))));
+                zz = fma2(k_, mul2(d2, d2), fma2(m2c, mul2(d2, s2), iso));
+                P[3 * A2 + c2] = xz;
+                P[4 * A2 + c2] = yz;
+            }
+        }
+
+        // F of plane j - 3
+        const int r3 = j - 3;
+        if (p.hydro && own && r3 >= 0 && r3 < hmax) {
+            const float2* P = sP + ((j - 3) & 1) * 5 * A2;
+            const float2 Fx = sub2(v2(0), mul2(half, add2(add2(sub2(P[0 * A2 + c2 + 1], P[0 * A2 + c2 - 1]),
+                                                               sub2(P[1 * A2 + c2 + CW], P[1 * A2 + c2 - CW])), sub2(xz, xzC))));
+            const float2 Fy = sub2(v2(0), mul2(half, add2(add2(sub2(P[1 * A2 + c2 + 1], P[1 * A2 + c2 - 1]),
+                                                               sub2(P[2 * A2 + c2 + CW], P[2 * A2 + c2 - CW])), sub2(yz, yzC))));
+            const float2 Fz = sub2(v2(0), mul2(half, add2(add2(sub2(P[3 * A2 + c2 + 1], P[3 * A2 + c2 - 1]),
+                                                               sub2(P[4 * A2 + c2 + CW], P[4 * A2 + c2 - CW])), sub2(zz, zzC))));
+            if (r3 < ha) {
+                const int64_t site = (int64_t)(za0 + r3) * zs + own_off;
+                io.F[0][site] = Fx.x; io.F[1][site] = Fy.x; io.F[2][site] = Fz.x;
+            }
+            if (r3 < hb) {
+                const int64_t site = (int64_t)(zb0 + r3) * zs + own_off;
+                io.F[0][site] = Fx.y; io.F[1][site] = Fy.y; io.F[2][site] = Fz.y;
+            }
+        }
+
+        phm3 = phm2; phm2 = phm1; phm1 = phk;
+        psm2 = psm1; psm1 = psi_new;
+        xzC = xzB; xzB = xz; yzC = yzB; yzB = yz; zzC = zzB; zzB = zz;
+        Tq2 = Tq1; Tq1 = Tq0; Tq0 = Tnext;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
 // Pass B: one thread per site.  Moments of f(t) with the half-force shift,
 // collision per opposite pair, push to the neighbours (halfway bounce-back on
 // the walls at z = 0 and nz - 1); u(t) to the aux planes.
@@ -380,16 +556,45 @@ cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
     return cudaGetLastError();
 }
 
+template <int TX, int TY>
+cudaError_t launch_force_x2(const Geom& g, const Phys<float>& p, const StepIO<float>& io, cudaStream_t s)
+{
+    using P3 = Force3x2<TX, TY>;
+    auto kern = k_force3d_x2<TX, TY>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P3::BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    int H = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;     // planes per lane
+    if (H <= 0) {   // about eight waves of one CTA per SM, lanes of at least 16 planes
+        const int want = (8 * 152 + tiles - 1) / tiles;
+        H = (g.nz + 2 * want - 1) / (2 * want);
+        if (H < 16) H = 16;
+    }
+    if (H > g.nz) H = g.nz;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + 2 * H - 1) / (2 * H));
+    kern<<<grid, P3::NTH, P3::BYTES, s>>>(g, p, io, H);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename R>
 cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
     cudaError_t e;
-    if constexpr (sizeof(R) == 4)
-        e = (g.tune >> 16) == 1 ? launch_force<R, 60, 4>(g, p, io, s) : launch_force<R, 28, 12>(g, p, io, s);
-    else
+    if constexpr (sizeof(R) == 4) {
+        // (param >> 16): 0 = two z-lanes in packed FP32x2, 1 / 2 = one lane on 60x4 / 28x12 tiles
+        const int sel = g.tune >> 16;
+        e = sel == 1 ? launch_force<R, 60, 4>(g, p, io, s)
+          : sel == 2 ? launch_force<R, 28, 12>(g, p, io, s)
+                     : launch_force_x2<28, 12>(g, p, io, s);
+    } else {
         e = launch_force<R, 28, 12>(g, p, io, s);
+    }
     if (e != cudaSuccess) return e;
     if (p.hydro) {
         dim3 grid((g.nx + 127) / 128, g.ny, g.nz);

@@ -121,7 +121,7 @@ CASES3 = [
 
 
 VARIANTS3 = {"fused": ("march", 0), "split3": ("split3", 0), "split3-z3": ("split3", 3),
-             "split3-t16": ("split3", 1 << 16)}
+             "split3-60x4": ("split3", 1 << 16), "split3-scalar-z5": ("split3", (2 << 16) | 5)}
 
 
 @pytest.mark.parametrize("variant", list(VARIANTS3))
