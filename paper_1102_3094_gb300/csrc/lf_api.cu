@@ -293,6 +293,41 @@ int pending_status(lf_ctx* c)
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace lf {
+// lf_fields / lf_fields_set between a context and device memory, enqueued on
+// the context's stream without waiting (for code inside the library that
+// chains several copies before one wait).
+int fields_get_async(lf_ctx* c, int which, void* dst, size_t bytes)
+{
+    if (!c || !dst || which < 0 || which > LF_FIELD_FZ) return LF_EINVAL;
+    bool dbl;
+    int rc = elem_from_bytes(c, which, bytes, &dbl);
+    if (rc != LF_OK) return rc;
+    if (which != LF_FIELD_PHI && which != LF_FIELD_T && which != LF_FIELD_POP && (rc = ensure_aux(c)) != LF_OK)
+        return rc;
+    const int nplanes = which == LF_FIELD_POP ? c->Q : 1;
+    const PlaneAdd add = plane_offsets(c, which);
+    const void* src = field_plane(c, which, 0);
+    return c->prec == LF_FP64 ? pack_dispatch<double>(c, src, dst, nplanes, add, 1, dbl)
+                              : pack_dispatch<float>(c, src, dst, nplanes, add, 1, dbl);
+}
+
+int fields_set_async(lf_ctx* c, int which, const void* src, size_t bytes)
+{
+    if (!c || !src) return LF_EINVAL;
+    if (which != LF_FIELD_PHI && which != LF_FIELD_T && which != LF_FIELD_POP) return LF_EINVAL;
+    bool dbl;
+    int rc = elem_from_bytes(c, which, bytes, &dbl);
+    if (rc != LF_OK) return rc;
+    const int nplanes = which == LF_FIELD_POP ? c->Q : 1;
+    const PlaneAdd sub = plane_offsets(c, which);
+    void* dst = const_cast<void*>(field_plane(c, which, 0));
+    c->aux_valid = false;
+    return c->prec == LF_FP64 ? unpack_dispatch<double>(c, src, dst, nplanes, sub, 1, dbl)
+                              : unpack_dispatch<float>(c, src, dst, nplanes, sub, 1, dbl);
+}
+}  // namespace lf
+
 extern "C" {
 
 int lf_lattice(int d, int* e, double* w)
@@ -425,6 +460,7 @@ int lf_step(lf_ctx* c, int64_t nsteps)
     if (rc != LF_OK) return rc;
     return c->prec == LF_FP64 ? do_steps<double>(c, nsteps) : do_steps<float>(c, nsteps);
 }
+
 
 int lf_fields(lf_ctx* c, int which, void* dst, size_t bytes, int dst_on_device)
 {

@@ -31,3 +31,9 @@ struct lf_ctx {
     bool ens_member;      // stepped by an ensemble; lf_step on it is refused
 };
 
+namespace lf {
+// lf_fields / lf_fields_set with device memory on the other side, enqueued
+// on the context's stream without waiting (library-internal).
+int fields_get_async(lf_ctx* c, int which, void* dst, size_t bytes);
+int fields_set_async(lf_ctx* c, int which, const void* src, size_t bytes);
+}  // namespace lf

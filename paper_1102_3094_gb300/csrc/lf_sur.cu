@@ -645,13 +645,14 @@ extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shado
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const cudaStream_t st = ctx->stream;
+    // state copy between two contexts of the same shape, on the stream (no waits)
     auto copy_state = [&](lf_ctx* from, lf_ctx* to) {
-        int r = lf_fields(from, LF_FIELD_POP, pop, 9 * fb, 1);
-        if (r == LF_OK) r = lf_fields_set(to, LF_FIELD_POP, pop, 9 * fb, 1);
-        if (r == LF_OK) r = lf_fields(from, LF_FIELD_PHI, x, fb, 1);
-        if (r == LF_OK) r = lf_fields_set(to, LF_FIELD_PHI, x, fb, 1);
-        if (r == LF_OK) r = lf_fields(from, LF_FIELD_T, x, fb, 1);
-        if (r == LF_OK) r = lf_fields_set(to, LF_FIELD_T, x, fb, 1);
+        int r = fields_get_async(from, LF_FIELD_POP, pop, 9 * fb);
+        if (r == LF_OK) r = fields_set_async(to, LF_FIELD_POP, pop, 9 * fb);
+        if (r == LF_OK) r = fields_get_async(from, LF_FIELD_PHI, phi_plain, fb);
+        if (r == LF_OK) r = fields_set_async(to, LF_FIELD_PHI, phi_plain, fb);
+        if (r == LF_OK) r = fields_get_async(from, LF_FIELD_T, phi_plain, fb);
+        if (r == LF_OK) r = fields_set_async(to, LF_FIELD_T, phi_plain, fb);
         return r;
     };
     for (int w = 0; w < nwindows && rc == LF_OK; ++w) {
@@ -668,7 +669,7 @@ extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shado
         }
         // surrogate window: x = (phi, T, ux, uy) of the current state
         const int which[4] = {LF_FIELD_PHI, LF_FIELD_T, LF_FIELD_UX, LF_FIELD_UY};
-        for (int c = 0; c < 4 && rc == LF_OK; ++c) rc = lf_fields(ctx, which[c], x + c * N, fb, 1);
+        for (int c = 0; c < 4 && rc == LF_OK; ++c) rc = fields_get_async(ctx, which[c], x + c * N, fb);
         if (rc == LF_OK) rc = lf_sur_predict(s, x, y, 1);
         unsigned chk[2] = {0u, 0u};
         if (rc == LF_OK) {
