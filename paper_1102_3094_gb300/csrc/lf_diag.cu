@@ -362,6 +362,29 @@ int64_t lmin_of(const Geom& g)
     return l;
 }
 
+// Forward DFT (kernel e^{-2 pi i j k / n}) of every line along axis a of a
+// packed [nz][ny][nx] complex FP64 array, in place.
+cudaError_t fft_lines_axis(const Geom& g, double2* data, int a, const FftPlan& plan, cudaStream_t s)
+{
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    const int n = plan.n;
+    int C = 4096 / n;
+    if (C < 1) C = 1;
+    if (C > 16) C = 16;
+    int64_t nlines, inner, inner_stride, outer_stride, es;
+    if (a == 0) { nlines = N / n; inner = 1; inner_stride = 0; outer_stride = n; es = 1; }
+    else if (a == 1) { nlines = N / n; inner = g.nx; inner_stride = 1; outer_stride = (int64_t)g.nx * g.ny; es = g.nx; }
+    else { nlines = N / n; inner = (int64_t)g.nx * g.ny; inner_stride = 1; outer_stride = 0; es = (int64_t)g.nx * g.ny; }
+    const size_t smem = sizeof(double2) * (size_t)(C + 1) * n;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = (unsigned)((nlines + C - 1) / C);
+    k_fft_lines<<<blocks, kThreads, smem, s>>>(data, plan, es, nlines, inner, inner_stride, outer_stride, C);
+    return cudaGetLastError();
+}
+
 // FFT of phi into sc.fft and the shell sums into sc.bins (device).  Returns
 // false when a lattice size has a prime factor above kMaxRadix or a line does
 // not fit in shared memory.
@@ -379,21 +402,8 @@ bool enqueue_sk(const DiagInput& in, const Scratch& sc, cudaStream_t s, cudaErro
     if (in.prec == LF_FP64) k_fft_fill<double><<<grid_n(N), kThreads, 0, s>>>(g, (const double*)in.phi, sc.fft);
     else k_fft_fill<float><<<grid_n(N), kThreads, 0, s>>>(g, (const float*)in.phi, sc.fft);
     for (int a = 0; a < g.d; ++a) {
-        const int n = sizes[a];
-        int C = 4096 / n;
-        if (C < 1) C = 1;
-        if (C > 16) C = 16;
-        int64_t nlines, inner, inner_stride, outer_stride, es;
-        if (a == 0) { nlines = N / n; inner = 1; inner_stride = 0; outer_stride = n; es = 1; }
-        else if (a == 1) { nlines = N / n; inner = g.nx; inner_stride = 1; outer_stride = (int64_t)g.nx * g.ny; es = g.nx; }
-        else { nlines = N / n; inner = (int64_t)g.nx * g.ny; inner_stride = 1; outer_stride = 0; es = (int64_t)g.nx * g.ny; }
-        const size_t smem = sizeof(double2) * (size_t)(C + 1) * n;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) { *err = e; return true; }
-        }
-        const unsigned blocks = (unsigned)((nlines + C - 1) / C);
-        k_fft_lines<<<blocks, kThreads, smem, s>>>(sc.fft, plans[a], es, nlines, inner, inner_stride, outer_stride, C);
+        const cudaError_t e = fft_lines_axis(g, sc.fft, a, plans[a], s);
+        if (e != cudaSuccess) { *err = e; return true; }
     }
     cudaMemsetAsync(sc.bins, 0, sizeof(double) * 2 * (B + 1), s);
     const size_t hs = B <= kShellSmemBins ? sizeof(double) * 2 * (B + 1) : 0;
@@ -432,6 +442,18 @@ size_t diag_scratch_bytes(int d, int64_t nx, int64_t ny, int64_t nz)
     const int64_t B = lmin / 2;
     return a256(sizeof(double) * kBlocks * DQ_N) + a256(sizeof(double) * DQ_N) + a256(sizeof(double) * 2 * L) +
            a256(sizeof(double) * 2 * (B + 1)) + a256(sizeof(double2) * (size_t)(nx * ny * nz));
+}
+
+double2* fft_buffer(const Geom& g, void* scratch) { return carve(g, scratch).fft; }
+
+bool fft_supported(int n) { FftPlan p; return n <= 4096 && make_plan(n, &p); }
+
+cudaError_t fft_forward_axis(const Geom& g, double2* data, int axis, cudaStream_t s)
+{
+    const int sizes[3] = {g.nx, g.ny, g.nz};
+    FftPlan plan;
+    if (!make_plan(sizes[axis], &plan) || sizes[axis] > 4096) return cudaErrorInvalidValue;
+    return fft_lines_axis(g, data, axis, plan, s);
 }
 
 int run_diag(const DiagInput& in, DiagResult* r, cudaStream_t s)

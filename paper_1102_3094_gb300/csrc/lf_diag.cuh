@@ -37,6 +37,13 @@ struct DiagResult {
 
 size_t diag_scratch_bytes(int d, int64_t nx, int64_t ny, int64_t nz);
 
+// The N complex doubles of FFT scratch inside a context's diagnostics area.
+double2* fft_buffer(const Geom& g, void* scratch);
+// Whether a line of length n is within the FFT's reach (prime factors up to 31, n <= 4096).
+bool fft_supported(int n);
+// Forward DFT along one axis of a packed [nz][ny][nx] complex FP64 array, in place.
+cudaError_t fft_forward_axis(const Geom& g, double2* data, int axis, cudaStream_t s);
+
 // Blocking (bounded wait) runs; results land in host memory.
 int run_diag(const DiagInput& in, DiagResult* r, cudaStream_t s);
 int run_layers(const DiagInput& in, double* out_host, cudaStream_t s);
