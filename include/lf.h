@@ -250,6 +250,23 @@ int lf_load(lf_ctx* ctx, const char* path);
 #define LF_VARIANT_SPLIT3 3
 int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
 
+/* Time discretisation of the temperature (d_t T = xi lap T, Sec. 2 after Eq.
+ * massdiff):
+ *   LF_TSOLVER_EXPLICIT (default): explicit Euler in n_sub = lf_nsub(xi, d)
+ *     sub-steps of xi / n_sub, the first fused into the step kernel;
+ *   LF_TSOLVER_IMPLICIT: one backward-Euler step (I - xi L) T(t+1) = T(t) per
+ *     time step with the same Laplacian L and wall rules, solved by an FP64
+ *     DFT along the periodic axes and a tridiagonal solve along the wall
+ *     normal (a division when every axis is periodic).  Unconditionally
+ *     stable: one solve per step at any xi.  Needs the periodic lattice sizes
+ *     to be at most 4096 with prime factors up to 31.
+ * The phi, f update always uses T(t).  Returns LF_EINVAL for an unknown
+ * solver, an unsupported size, or an ensemble member (ensembles always take
+ * explicit sub-steps).  Not stored in checkpoints. */
+#define LF_TSOLVER_EXPLICIT 0
+#define LF_TSOLVER_IMPLICIT 1
+int lf_set_t_solver(lf_ctx* ctx, int solver);
+
 /* Current step counter. */
 int64_t lf_step_count(const lf_ctx* ctx);
 

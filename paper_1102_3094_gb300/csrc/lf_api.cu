@@ -98,7 +98,8 @@ Phys<R> phys_of(const lf_ctx* c)
     ph.T_w = (R)c->walls.T_w;
     ph.inv_Tc = (R)(1.0 / p.Tc);
     ph.t_update = !(std::isinf(p.xi) || p.xi == 0.0);
-    ph.dxi = ph.t_update ? (R)(p.xi / c->nsub) : R(0);
+    // the implicit solver takes the whole diffusion after the step kernel, which then keeps T
+    ph.dxi = (ph.t_update && c->t_solver != LF_TSOLVER_IMPLICIT) ? (R)(p.xi / c->nsub) : R(0);
     ph.inv_tau = (R)(1.0 / p.tau);
     ph.guo = (R)(1.0 - 1.0 / (2.0 * p.tau));
     ph.n0 = (R)p.n0;
@@ -145,7 +146,10 @@ int do_steps(lf_ctx* c, int64_t n)
         if (c->params.hydro) c->fcur ^= 1;
         c->pcur ^= 1;
         c->tcur ^= 1;
-        if (ph.t_update) {
+        if (ph.t_update && c->t_solver == LF_TSOLVER_IMPLICIT) {
+            const int rc = t_implicit_step<R>(c, c->params.xi, c->walls.T_w);
+            if (rc != LF_OK) return rc;
+        } else if (ph.t_update) {
             for (int s = 1; s < c->nsub; ++s) {
                 if (launch_tsub<R>(c->g, ph, (const R*)c->T[c->tcur], (R*)c->T[c->tcur ^ 1], c->stream) != cudaSuccess)
                     return LF_ECUDA;
@@ -393,6 +397,7 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
     c->g.variant = grid->d == 3 ? LF_VARIANT_SPLIT3
                  : (params->precision == LF_FP32 ? LF_VARIANT_MARCH2 : LF_VARIANT_MARCH);
     c->g.tune = 0;
+    c->t_solver = LF_TSOLVER_EXPLICIT;
 
     if (params->workspace) {
         if (params->workspace_bytes < L.total || ((uintptr_t)params->workspace % kAlign) != 0) {
@@ -569,6 +574,14 @@ int lf_structure_factor(lf_ctx* c, double* out, int64_t nb)
 }
 
 int64_t lf_step_count(const lf_ctx* c) { return c ? c->step : -1; }
+
+int lf_set_t_solver(lf_ctx* c, int solver)
+{
+    if (!c || (solver != LF_TSOLVER_EXPLICIT && solver != LF_TSOLVER_IMPLICIT) || c->ens_member) return LF_EINVAL;
+    if (solver == LF_TSOLVER_IMPLICIT && !t_implicit_supported(c->g)) return LF_EINVAL;
+    c->t_solver = solver;
+    return LF_OK;
+}
 
 int lf_set_kernel_variant(lf_ctx* c, int variant, int param)
 {

@@ -29,6 +29,7 @@ struct lf_ctx {
     int64_t step;
     bool aux_valid;
     bool ens_member;      // stepped by an ensemble; lf_step on it is refused
+    int t_solver;         // LF_TSOLVER_EXPLICIT (n_sub sub-steps) or LF_TSOLVER_IMPLICIT
 };
 
 namespace lf {
@@ -36,4 +37,12 @@ namespace lf {
 // on the context's stream without waiting (library-internal).
 int fields_get_async(lf_ctx* c, int which, void* dst, size_t bytes);
 int fields_set_async(lf_ctx* c, int which, const void* src, size_t bytes);
+}  // namespace lf
+
+namespace lf {
+// Implicit (backward-Euler) temperature step of the current T, in place
+// (lf_timplicit.cu); requires t_implicit_supported(g).
+bool t_implicit_supported(const Geom& g);
+template <typename R>
+int t_implicit_step(lf_ctx* c, double xi, double T_w);
 }  // namespace lf

@@ -1,0 +1,194 @@
+// lf_timplicit.cu -- implicit temperature step (lf_set_t_solver).
+//
+// The temperature obeys d_t T = xi lap T (arXiv:1102.3094, Sec. 2, after Eq.
+// massdiff).  The explicit update needs xi / n_sub <= 1/(2d) per sub-step,
+// i.e. hundreds of sub-steps per time step at the paper's largest xi.  The
+// implicit option takes one backward-Euler step per time step,
+//   (I - xi L) T(t+1) = T(t),
+// with the same 5-/7-point Laplacian L and wall rules as the explicit update.
+// L is diagonal in a lattice Fourier basis along the periodic axes, so the
+// solve is: FP64 DFT along x (2D) or x and y (3D); for every Fourier mode a
+// tridiagonal system along the wall normal (Thomas algorithm, one thread per
+// mode) -- or a plain division when every axis is periodic; the inverse DFT
+// as conj(DFT(conj(.))) / n; back to the state's precision.
+#include <cmath>
+
+#include "lf_ctx.cuh"
+#include "lf_diag.cuh"
+
+namespace lf {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+template <typename R>
+__global__ void k_t_load(Geom g, const R* __restrict__ T, double2* __restrict__ buf)
+{
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = k / g.nx;
+        const int x = (int)(k - row * g.nx);
+        buf[k] = make_double2((double)T[row * g.pitch + x], 0.0);
+    }
+}
+
+template <typename R>
+__global__ void k_t_store(Geom g, const double2* __restrict__ buf, double scale, R* __restrict__ T,
+                          int* __restrict__ flag)
+{
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    bool bad = false;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = k / g.nx;
+        const int x = (int)(k - row * g.nx);
+        const double v = buf[k].x * scale;
+        bad |= !isfinite(v);
+        T[row * g.pitch + x] = (R)v;
+    }
+    if (bad) *reinterpret_cast<volatile int*>(flag) = 1;
+}
+
+// Eigenvalue of -L along the periodic axes for the mode with packed index m
+// over those axes (x fastest).
+__device__ __forceinline__ double lam_of(const Geom& g, int64_t m, int nper_axes)
+{
+    const int kx = (int)(m % g.nx);
+    double lam = 2.0 * (1.0 - cos(kTwoPi * kx / g.nx));
+    if (nper_axes >= 2) {
+        const int ky = (int)((m / g.nx) % g.ny);
+        lam += 2.0 * (1.0 - cos(kTwoPi * ky / g.ny));
+    }
+    if (nper_axes >= 3) {
+        const int kz = (int)(m / ((int64_t)g.nx * g.ny));
+        lam += 2.0 * (1.0 - cos(kTwoPi * kz / g.nz));
+    }
+    return lam;
+}
+
+// Walls along the last axis: one thread per Fourier mode m of the periodic
+// axes (M modes), Thomas algorithm along the L layers of the wall normal;
+// element (j, m) at j * M + m.  Writes the conjugate of the solution.
+__global__ void k_t_thomas(Geom g, double2* __restrict__ buf, double* __restrict__ cp, double xi, double Tw_hat0,
+                           int t_mode)
+{
+    const int d = g.d;
+    const int64_t M = d == 2 ? (int64_t)g.nx : (int64_t)g.nx * g.ny;
+    const int L = d == 2 ? g.ny : g.nz;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double lam = lam_of(g, m, d - 1);
+    const double b = 1.0 + xi * (lam + 2.0);
+    const double a = -xi;                    // sub- and super-diagonal
+    auto at = [&](int j) -> double2& { return buf[(int64_t)j * M + m]; };
+    int j0 = 0, j1 = L - 1;                  // unknown layers
+    double2 lo_add = make_double2(0.0, 0.0), hi_add = make_double2(0.0, 0.0);
+    double b0 = b, b1 = b;
+    if (t_mode == LF_TWALL_LAYERS) {         // held layers 0 and L-1 enter the right-hand side
+        j0 = 1;
+        j1 = L - 2;
+        lo_add = make_double2(xi * at(0).x, xi * at(0).y);
+        hi_add = make_double2(xi * at(L - 1).x, xi * at(L - 1).y);
+    } else {                                 // ghost 2 T_w - T: +xi on the diagonal, 2 xi T_w in the rhs
+        b0 += xi;
+        b1 += xi;
+        const double w = m == 0 ? 2.0 * xi * Tw_hat0 : 0.0;
+        lo_add = make_double2(w, 0.0);
+        hi_add = make_double2(w, 0.0);
+    }
+    if (j1 < j0) {                           // no unknown layer
+        for (int j = 0; j < L; ++j) at(j) = make_double2(at(j).x, -at(j).y);
+        return;
+    }
+    // forward sweep: cp_j = a / (b_j - a cp_{j-1}),  dp_j = (d_j - a dp_{j-1}) / (b_j - a cp_{j-1})
+    double cprev = 0.0;
+    double2 dprev = make_double2(0.0, 0.0);
+    for (int j = j0; j <= j1; ++j) {
+        double bj = b;
+        double2 dj = at(j);
+        if (j == j0) { bj = t_mode == LF_TWALL_LAYERS ? b : b0; dj.x += lo_add.x; dj.y += lo_add.y; }
+        if (j == j1) {
+            if (t_mode != LF_TWALL_LAYERS) bj = (j0 == j1) ? b0 + (b1 - b) : b1;
+            dj.x += hi_add.x; dj.y += hi_add.y;
+        }
+        const double den = bj - a * cprev;
+        const double cj = a / den;
+        const double2 dp = make_double2((dj.x - a * dprev.x) / den, (dj.y - a * dprev.y) / den);
+        cp[(int64_t)j * M + m] = cj;
+        at(j) = dp;
+        cprev = cj;
+        dprev = dp;
+    }
+    // back substitution, storing conj(x)
+    double2 xnext = at(j1);
+    at(j1) = make_double2(xnext.x, -xnext.y);
+    for (int j = j1 - 1; j >= j0; --j) {
+        const double cj = cp[(int64_t)j * M + m];
+        const double2 dp = at(j);
+        const double2 x = make_double2(dp.x - cj * xnext.x, dp.y - cj * xnext.y);
+        at(j) = make_double2(x.x, -x.y);
+        xnext = x;
+    }
+    for (int j = 0; j < j0; ++j) at(j) = make_double2(at(j).x, -at(j).y);          // held layers
+    for (int j = j1 + 1; j < L; ++j) at(j) = make_double2(at(j).x, -at(j).y);
+}
+
+// Every axis periodic: the mode is divided by 1 + xi lam; writes the conjugate.
+__global__ void k_t_divide(Geom g, double2* __restrict__ buf, double xi)
+{
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        const double s = 1.0 / (1.0 + xi * lam_of(g, k, g.d));
+        buf[k] = make_double2(buf[k].x * s, -buf[k].y * s);
+    }
+}
+
+unsigned grid_t(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+bool t_implicit_supported(const Geom& g)
+{
+    if (!fft_supported(g.nx)) return false;
+    if ((g.d == 3 || !g.walls) && !fft_supported(g.ny)) return false;
+    if (g.d == 3 && !g.walls && !fft_supported(g.nz)) return false;
+    return true;
+}
+
+template <typename R>
+int t_implicit_step(lf_ctx* c, double xi, double T_w)
+{
+    const Geom& g = c->g;
+    const cudaStream_t s = c->stream;
+    const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+    double2* buf = fft_buffer(g, c->scratch);
+    double* cp = (double*)c->stage;
+    R* T = (R*)c->T[c->tcur];
+    const int nper_axes = g.walls ? g.d - 1 : g.d;
+    int64_t nper = g.nx;
+    if (nper_axes >= 2) nper *= g.ny;
+    if (nper_axes >= 3) nper *= g.nz;
+    k_t_load<R><<<grid_t(N), 256, 0, s>>>(g, T, buf);
+    for (int a = 0; a < nper_axes; ++a)
+        if (fft_forward_axis(g, buf, a, s) != cudaSuccess) return LF_ECUDA;
+    if (g.walls) {
+        const int64_t M = N / (g.d == 2 ? g.ny : g.nz);
+        k_t_thomas<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(g, buf, cp, xi, T_w * (double)nper, g.t_mode);
+    } else {
+        k_t_divide<<<grid_t(N), 256, 0, s>>>(g, buf, xi);
+    }
+    for (int a = 0; a < nper_axes; ++a)
+        if (fft_forward_axis(g, buf, a, s) != cudaSuccess) return LF_ECUDA;
+    k_t_store<R><<<grid_t(N), 256, 0, s>>>(g, buf, 1.0 / (double)nper, T, c->flag_dev);
+    return cudaGetLastError() == cudaSuccess ? LF_OK : LF_ECUDA;
+}
+
+template int t_implicit_step<float>(lf_ctx*, double, double);
+template int t_implicit_step<double>(lf_ctx*, double, double);
+
+}  // namespace lf

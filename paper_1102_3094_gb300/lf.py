@@ -88,6 +88,8 @@ def lib():
             L.lf_load.argtypes = [vp, C.c_char_p]
             L.lf_set_kernel_variant.argtypes = [vp, C.c_int, C.c_int]
             L.lf_set_kernel_variant.restype = C.c_int
+            L.lf_set_t_solver.argtypes = [vp, C.c_int]
+            L.lf_set_t_solver.restype = C.c_int
             L.lf_step_count.argtypes = [vp]
             L.lf_step_count.restype = i64
             L.lf_destroy.argtypes = [vp]
@@ -257,6 +259,10 @@ class Lattice:
         code = {"march": LF_VARIANT_MARCH, "tile": LF_VARIANT_TILE, "march2": LF_VARIANT_MARCH2,
                 "split3": LF_VARIANT_SPLIT3}[variant]
         lf_set_kernel_variant(self.ctx, code, param)
+
+    def set_t_solver(self, solver: str = "explicit"):
+        code = {"explicit": 0, "implicit": 1}[solver]
+        _ok(lib().lf_set_t_solver(self.ctx, code), "lf_set_t_solver")
 
     def diag(self):
         d, rc = lf_diag(self.ctx)
