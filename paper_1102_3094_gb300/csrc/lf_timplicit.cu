@@ -100,34 +100,55 @@ __global__ void k_t_thomas(Geom g, double2* __restrict__ buf, double* __restrict
         for (int j = 0; j < L; ++j) at(j) = make_double2(at(j).x, -at(j).y);
         return;
     }
-    // forward sweep: cp_j = a / (b_j - a cp_{j-1}),  dp_j = (d_j - a dp_{j-1}) / (b_j - a cp_{j-1})
+    // forward sweep: cp_j = a / (b_j - a cp_{j-1}),  dp_j = (d_j - a dp_{j-1}) / (b_j - a cp_{j-1}).
+    // The right-hand sides of the next kB layers are loaded before the
+    // recurrence runs over them, so the loads do not sit in the serial chain.
+    constexpr int kB = 8;
     double cprev = 0.0;
     double2 dprev = make_double2(0.0, 0.0);
-    for (int j = j0; j <= j1; ++j) {
-        double bj = b;
-        double2 dj = at(j);
-        if (j == j0) { bj = t_mode == LF_TWALL_LAYERS ? b : b0; dj.x += lo_add.x; dj.y += lo_add.y; }
-        if (j == j1) {
-            if (t_mode != LF_TWALL_LAYERS) bj = (j0 == j1) ? b0 + (b1 - b) : b1;
-            dj.x += hi_add.x; dj.y += hi_add.y;
+    for (int jb = j0; jb <= j1; jb += kB) {
+        double2 dv[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+            if (jb + u <= j1) dv[u] = at(jb + u);
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int j = jb + u;
+            if (j > j1) break;
+            double bj = b;
+            double2 dj = dv[u];
+            if (j == j0) { bj = t_mode == LF_TWALL_LAYERS ? b : b0; dj.x += lo_add.x; dj.y += lo_add.y; }
+            if (j == j1) {
+                if (t_mode != LF_TWALL_LAYERS) bj = (j0 == j1) ? b0 + (b1 - b) : b1;
+                dj.x += hi_add.x; dj.y += hi_add.y;
+            }
+            const double inv = 1.0 / (bj - a * cprev);
+            const double cj = a * inv;
+            const double2 dp = make_double2((dj.x - a * dprev.x) * inv, (dj.y - a * dprev.y) * inv);
+            cp[(int64_t)j * M + m] = cj;
+            at(j) = dp;
+            cprev = cj;
+            dprev = dp;
         }
-        const double den = bj - a * cprev;
-        const double cj = a / den;
-        const double2 dp = make_double2((dj.x - a * dprev.x) / den, (dj.y - a * dprev.y) / den);
-        cp[(int64_t)j * M + m] = cj;
-        at(j) = dp;
-        cprev = cj;
-        dprev = dp;
     }
-    // back substitution, storing conj(x)
+    // back substitution x_j = dp_j - cp_j x_{j+1}, storing conj(x); the
+    // coefficients of the next kB layers (downwards) are loaded first
     double2 xnext = at(j1);
     at(j1) = make_double2(xnext.x, -xnext.y);
-    for (int j = j1 - 1; j >= j0; --j) {
-        const double cj = cp[(int64_t)j * M + m];
-        const double2 dp = at(j);
-        const double2 x = make_double2(dp.x - cj * xnext.x, dp.y - cj * xnext.y);
-        at(j) = make_double2(x.x, -x.y);
-        xnext = x;
+    for (int jb = j1 - 1; jb >= j0; jb -= kB) {
+        double cv[kB];
+        double2 pv[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+            if (jb - u >= j0) { cv[u] = cp[(int64_t)(jb - u) * M + m]; pv[u] = at(jb - u); }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int j = jb - u;
+            if (j < j0) break;
+            const double2 x = make_double2(pv[u].x - cv[u] * xnext.x, pv[u].y - cv[u] * xnext.y);
+            at(j) = make_double2(x.x, -x.y);
+            xnext = x;
+        }
     }
     for (int j = 0; j < j0; ++j) at(j) = make_double2(at(j).x, -at(j).y);          // held layers
     for (int j = j1 + 1; j < L; ++j) at(j) = make_double2(at(j).x, -at(j).y);
@@ -178,7 +199,7 @@ int t_implicit_step(lf_ctx* c, double xi, double T_w)
         if (fft_forward_axis(g, buf, a, s) != cudaSuccess) return LF_ECUDA;
     if (g.walls) {
         const int64_t M = N / (g.d == 2 ? g.ny : g.nz);
-        k_t_thomas<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(g, buf, cp, xi, T_w * (double)nper, g.t_mode);
+        k_t_thomas<<<(unsigned)((M + 31) / 32), 32, 0, s>>>(g, buf, cp, xi, T_w * (double)nper, g.t_mode);
     } else {
         k_t_divide<<<grid_t(N), 256, 0, s>>>(g, buf, xi);
     }
