@@ -15,7 +15,10 @@
  *
  * Readings of the paper that this file takes (the paper is silent on them):
  *   - Stencils (Sec. 2, "second-order finite-difference scheme"): 5-point /
- *     7-point Laplacian, central first differences, nabla^4 = nabla^2 nabla^2.
+ *     7-point Laplacian, central first differences, nabla^4 = nabla^2 nabla^2
+ *     (stencil 0).  stencil 1 takes every first and second derivative with
+ *     the weights of the velocity set instead (isotropic 9-point / 19-point
+ *     operators, see iso_grad / iso_lap below).
  *   - Walls (Sec. 2, boundary paragraph): the first and last layer along the
  *     last axis are fluid sites; the wall sits half a spacing outside them.
  *     Neutral wetting and the two conservation conditions (a.grad phi =
@@ -43,7 +46,7 @@ typedef struct {
     int t_wall_mode;     /* 0: T = T_w held on the wall layers; 1: halfway ghost */
     int hydro;           /* 1: LB coupled (Eqs. mass, momentum); 0: phi/T only */
     int nsub;            /* temperature sub-steps per step */
-    int pad_;
+    int stencil;         /* 0: compact 5/7-point, central; 1: isotropic 9/19-point */
     int64_t nx, ny, nz;  /* nz = 1 when d = 2 */
     double b, kappa, c, Gamma, Tc, T0, T_w, xi, tau, n0, phi_amp;
     uint64_t seed;
@@ -189,6 +192,76 @@ static double central_diff(const geom* G, const double* a, int64_t s, int axis, 
     return 0.5 * (nb_value(G, a, s, axis, +1, odd) - nb_value(G, a, s, axis, -1, odd));
 }
 
+/* Isotropic operators (stencil 1).  With the lattice weights w_i, e_i of the
+ * velocity set (D2Q9 in 2D, D3Q19 in 3D) and c_s^2 = 1/3,
+ *   d_a A   = (1/c_s^2) sum_i w_i e_ia A(r + e_i),
+ *   lap A   = (2/c_s^2) sum_i w_i [A(r + e_i) - A(r)],
+ * which are second-order accurate and isotropic to the next order (Thampi,
+ * Ansumali, Adhikari & Succi, J. Comput. Phys. 234 (2013) 1; Kumar,
+ * J. Comput. Phys. 201 (2004) 109).  In 2D the Laplacian is
+ * [4 (nearest) + (diagonal) - 20 A]/6.  An offset that leaves the lattice
+ * through a wall reads the mirror image of the site across the plane half a
+ * spacing out (the wall-normal coordinate stays, the others move), with the
+ * field's parity, exactly like the compact stencils. */
+static int64_t offset_site(const geom* G, int64_t s, const int* e, int* crossed)
+{
+    int64_t c[3];
+    coords(G, s, c);
+    *crossed = 0;
+    for (int a = 0; a < G->d; ++a) {
+        int64_t v = c[a] + e[a];
+        if (G->walls && a == G->wall_axis) {
+            if (v < 0 || v >= G->n[a]) { *crossed = 1; v = c[a]; }
+        } else {
+            v = (v % G->n[a] + G->n[a]) % G->n[a];
+        }
+        c[a] = v;
+    }
+    return index_of(G, c);
+}
+
+static double iso_grad(const geom* G, const double* A, int64_t s, int axis, int odd)
+{
+    int e[19 * 3]; double w[19];
+    int Q = or_velocity_set(G->d, e, w);
+    double acc = 0.0;
+    for (int i = 0; i < Q; ++i) {
+        if (e[3 * i + axis] == 0) continue;
+        int crossed;
+        int64_t t = offset_site(G, s, &e[3 * i], &crossed);
+        double v = (crossed && odd) ? -A[t] : A[t];
+        acc += w[i] * e[3 * i + axis] * v;
+    }
+    return 3.0 * acc;
+}
+
+/* Laplacian of an even field; with `dirichlet` set, a ghost across a wall is
+ * 2 value_w - A(mirror site) instead (halfway Dirichlet rule of T). */
+static double iso_lap(const geom* G, const double* A, int64_t s, int dirichlet, double value_w)
+{
+    int e[19 * 3]; double w[19];
+    int Q = or_velocity_set(G->d, e, w);
+    double acc = 0.0;
+    for (int i = 0; i < Q; ++i) {   /* the rest vector adds zero */
+        int crossed;
+        int64_t t = offset_site(G, s, &e[3 * i], &crossed);
+        double v = (crossed && dirichlet) ? 2.0 * value_w - A[t] : A[t];
+        acc += w[i] * (v - A[s]);
+    }
+    return 6.0 * acc;
+}
+
+/* The operators the configuration selects. */
+static double op_lap(const or_cfg* g, const geom* G, const double* A, int64_t s)
+{
+    return g->stencil ? iso_lap(G, A, s, 0, 0.0) : laplacian(G, A, s);
+}
+
+static double op_grad(const or_cfg* g, const geom* G, const double* A, int64_t s, int axis, int odd)
+{
+    return g->stencil ? iso_grad(G, A, s, axis, odd) : central_diff(G, A, s, axis, odd);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Local LB pieces.                                                           */
 /* ------------------------------------------------------------------------ */
@@ -287,15 +360,15 @@ static void thermo_fields(const or_cfg* g, const geom* G, const double* phi, con
 
     /* nabla^2 phi */
     #pragma omp parallel for schedule(static)
-    for (int64_t s = 0; s < N; ++s) W->psi[s] = laplacian(G, phi, s);
+    for (int64_t s = 0; s < N; ++s) W->psi[s] = op_lap(g, G, phi, s);
 
     /* nabla^4 phi = nabla^2 (nabla^2 phi); gradients of phi and nabla^2 phi */
     #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < N; ++s) {
-        W->lam[s] = laplacian(G, W->psi, s);
+        W->lam[s] = op_lap(g, G, W->psi, s);
         for (int ax = 0; ax < 3; ++ax) {
-            W->dphi[ax][s] = (ax < d) ? central_diff(G, phi, s, ax, 0) : 0.0;
-            W->dpsi[ax][s] = (ax < d) ? central_diff(G, W->psi, s, ax, 0) : 0.0;
+            W->dphi[ax][s] = (ax < d) ? op_grad(g, G, phi, s, ax, 0) : 0.0;
+            W->dpsi[ax][s] = (ax < d) ? op_grad(g, G, W->psi, s, ax, 0) : 0.0;
         }
     }
 
@@ -338,7 +411,7 @@ static void thermo_fields(const or_cfg* g, const geom* G, const double* phi, con
             if (be < d)
                 for (int al = 0; al < d; ++al) {
                     int odd = ((al == wa) ^ (be == wa));   /* reflection sign of P_ab */
-                    acc += central_diff(G, W->P[al][be], s, al, odd);
+                    acc += op_grad(g, G, W->P[al][be], s, al, odd);
                 }
             W->F[be][s] = -acc;
         }
@@ -438,8 +511,8 @@ void or_step(const or_cfg* g, const double* f, const double* phi, const double* 
     #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < N; ++s) {
         double div = 0.0;
-        for (int a = 0; a < d; ++a) div += central_diff(&G, flux[a], s, a, a == wa);
-        phi_new[s] = phi[s] - div + g->Gamma * laplacian(&G, W.mu, s);
+        for (int a = 0; a < d; ++a) div += op_grad(g, &G, flux[a], s, a, a == wa);
+        phi_new[s] = phi[s] - div + g->Gamma * op_lap(g, &G, W.mu, s);
     }
     for (int a = 0; a < 3; ++a) free(flux[a]);
 
@@ -457,13 +530,17 @@ void or_step(const or_cfg* g, const double* f, const double* phi, const double* 
                 int on_wall_layer = G.walls && (c[wa] == 0 || c[wa] == G.n[wa] - 1);
                 if (G.walls && g->t_wall_mode == 0 && on_wall_layer) { T_new[s] = g->T_w; continue; }
                 double lap = 0.0;
-                for (int ax = 0; ax < d; ++ax)
-                    for (int st = -1; st <= 1; st += 2) {
-                        int crossed;
-                        int64_t t = neighbour(&G, s, ax, st, &crossed);
-                        lap += crossed ? (2.0 * g->T_w - Tc[s]) : Tc[t];
-                    }
-                lap -= 2.0 * d * Tc[s];
+                if (g->stencil) {
+                    lap = iso_lap(&G, Tc, s, 1, g->T_w);
+                } else {
+                    for (int ax = 0; ax < d; ++ax)
+                        for (int st = -1; st <= 1; st += 2) {
+                            int crossed;
+                            int64_t t = neighbour(&G, s, ax, st, &crossed);
+                            lap += crossed ? (2.0 * g->T_w - Tc[s]) : Tc[t];
+                        }
+                    lap -= 2.0 * d * Tc[s];
+                }
                 T_new[s] = Tc[s] + dxi * lap;
             }
         }

@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class OrCfg(C.Structure):
     _fields_ = [
         ("d", C.c_int), ("walls", C.c_int), ("t_wall_mode", C.c_int), ("hydro", C.c_int),
-        ("nsub", C.c_int), ("pad_", C.c_int),
+        ("nsub", C.c_int), ("stencil", C.c_int),
         ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64),
         ("b", C.c_double), ("kappa", C.c_double), ("c", C.c_double), ("Gamma", C.c_double),
         ("Tc", C.c_double), ("T0", C.c_double), ("T_w", C.c_double), ("xi", C.c_double),
@@ -91,12 +91,13 @@ def nsub_for(xi: float, d: int) -> int:
 
 def make_cfg(d=2, nx=64, ny=64, nz=1, walls=1, t_wall_mode=0, hydro=1, b=1.0,
              kappa=-0.025, c=0.02, Gamma=0.05, Tc=1.0, T0=1.1, T_w=0.5, xi=0.01,
-             tau=1.0, n0=1.0, phi_amp=0.05, seed=1, nsub=None) -> OrCfg:
+             tau=1.0, n0=1.0, phi_amp=0.05, seed=1, nsub=None, stencil=0) -> OrCfg:
     if d == 2:
         nz = 1
     cfg = OrCfg()
     cfg.d, cfg.walls, cfg.t_wall_mode, cfg.hydro = d, walls, t_wall_mode, hydro
     cfg.nsub = nsub_for(xi, d) if nsub is None else nsub
+    cfg.stencil = stencil
     cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
     cfg.b, cfg.kappa, cfg.c, cfg.Gamma = b, kappa, c, Gamma
     cfg.Tc, cfg.T0, cfg.T_w, cfg.xi = Tc, T0, T_w, xi

@@ -163,7 +163,7 @@ def test_mu_is_variational_derivative_of_free_energy(d, walls):
     np.testing.assert_allclose(mu, p.grad.numpy(), rtol=0, atol=1e-13)
 
 
-def _force_case(L, terms, d=2, amp=0.4):
+def _force_case(L, terms, d=2, amp=0.4, stencil=0):
     """Oracle F against the continuum -phi grad mu + (phi^2/2) grad a for a smooth
     periodic field, with only the free-energy terms in `terms` switched on."""
     import sympy as sp
@@ -187,7 +187,7 @@ def _force_case(L, terms, d=2, amp=0.4):
     grids = np.meshgrid(*[np.arange(L, dtype=float)] * d, indexing="ij")  # (x, y[, z])
     ev = lambda ex: np.broadcast_to(sp.lambdify(X, ex, "numpy")(*grids), grids[0].shape)
     to_arr = lambda v: np.ascontiguousarray(np.transpose(v))  # -> (z, y, x)
-    cfg = O.make_cfg(d=d, nx=L, ny=L, nz=L, walls=0, b=b, kappa=kap, c=c, Tc=1.0)
+    cfg = O.make_cfg(d=d, nx=L, ny=L, nz=L, walls=0, b=b, kappa=kap, c=c, Tc=1.0, stencil=stencil)
     st = O.init(cfg)
     st.phi = to_arr(ev(phi_e))
     st.T = to_arr(1.0 + ev(a_e))
@@ -207,6 +207,18 @@ def test_force_converges_to_continuum_identity(terms):
     r1, r2 = e1 / s1, e2 / s2          # relative errors (F itself scales with k)
     assert s1 > 0 and r1 < 0.2
     assert 3.5 < r1 / r2 < 4.5, (r1, r2)
+
+
+@pytest.mark.parametrize("d,terms", [(2, ("a", "b")), (2, ("kappa",)), (2, ("c",)), (3, ("a", "b"))])
+def test_force_converges_isotropic_stencils(d, terms):
+    """The same continuum identity with every derivative on the isotropic
+    stencils (stencil 1): still second order."""
+    L1 = 32 if d == 2 else 24
+    e1, s1 = _force_case(L1, terms, d=d, stencil=1)
+    e2, s2 = _force_case(2 * L1, terms, d=d, stencil=1)
+    r1, r2 = e1 / s1, e2 / s2
+    assert s1 > 0 and r1 < 0.25
+    assert 3.3 < r1 / r2 < 4.7, (r1, r2)
 
 
 @pytest.mark.parametrize("terms", [("a", "b"), ("kappa",), ("c",)])
