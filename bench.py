@@ -104,12 +104,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000, d=2, nz=1, tau=1.0):
+def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000, d=2, nz=1, tau=1.0, stencil=0):
     """The FP64 CPU oracle as it stands on a bounded sample: steps of an
     nx x ny (x nz) lattice with the workload's physics, for about `seconds`."""
     from oracle import oracle as O
 
-    cfg = O.make_cfg(d=d, nx=nx, ny=ny, nz=nz, xi=xi, tau=tau)
+    cfg = O.make_cfg(d=d, nx=nx, ny=ny, nz=nz, xi=xi, tau=tau, stencil=stencil)
     st = O.init(cfg)
     st = O.run(st, 1)   # warm: compile/load, first touch
     steps, t0 = 0, time.perf_counter()
@@ -420,6 +420,10 @@ def run_ours(args):
     if variant == "auto":
         variant = "split3" if d == 3 else ("march2" if prec == "fp32" else "march")
     sim.set_variant(variant, args.tune)
+    iso = args.stencil == "isotropic"
+    if iso:
+        sim.set_stencil("isotropic")        # runs the tile kernel
+        variant = "tile"
     N = nx * ny * nz
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     flush_rd = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if args.flush == "write+read" else None
@@ -528,7 +532,7 @@ def run_ours(args):
             rate, steps, el, cores = oracle_rate(64, 64, args.xi, seconds=args.cpu_seconds, d=3, nz=64, tau=tau)
             smp = "64x64x64"
         else:
-            rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds)
+            rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds, stencil=int(iso))
             smp = "256x256"
         cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} FP64 oracle steps of a {smp} lattice with the workload's physics "
@@ -541,7 +545,8 @@ def run_ours(args):
             "config": {"workload": (f"prec1024: 2D D2Q9 lamellar quench between cold walls, {nx}x{ny}, "
                                     if d == 2 else
                                     f"cube384: 3D D3Q19 lamellar quench between cold walls (z), {nx}x{ny}x{nz}, ")
-                                   + f"{prec.upper()} state (deviation populations), xi={args.xi}, tau={tau}",
+                                   + f"{prec.upper()} state (deviation populations), xi={args.xi}, tau={tau}"
+                                   + (", isotropic 9-point stencils" if iso else ""),
                        "sites": N, "l2": ("flushed before every timed step (256 MiB write"
                                           + (", then a 256 MiB read so no dirty flush lines are written back "
                                              "inside the timed step" if args.flush == "write+read" else "")
@@ -586,6 +591,8 @@ def main():
     ap.add_argument("--flush", choices=["write", "write+read"], default="write+read",
                     help="L2 eviction between timed steps (2D and 3D single-lattice workloads)")
     ap.add_argument("--tune", type=int, default=0, help="march: rows per CTA segment (0 = automatic)")
+    ap.add_argument("--stencil", choices=["compact", "isotropic"], default="compact",
+                    help="finite-difference stencils (2D only; isotropic runs the tile kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

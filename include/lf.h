@@ -261,11 +261,31 @@ int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
  *     stable: one solve per step at any xi.  Needs the periodic lattice sizes
  *     to be at most 4096 with prime factors up to 31.
  * The phi, f update always uses T(t).  Returns LF_EINVAL for an unknown
- * solver, an unsupported size, or an ensemble member (ensembles always take
- * explicit sub-steps).  Not stored in checkpoints. */
+ * solver, an unsupported size, an ensemble member (ensembles always take
+ * explicit sub-steps), or LF_TSOLVER_IMPLICIT on a context with isotropic
+ * stencils.  Not stored in checkpoints. */
 #define LF_TSOLVER_EXPLICIT 0
 #define LF_TSOLVER_IMPLICIT 1
 int lf_set_t_solver(lf_ctx* ctx, int solver);
+
+/* Finite-difference stencils of every derivative of the step (Sec. 2 names a
+ * "second-order finite-difference scheme" without fixing it):
+ *   LF_STENCIL_COMPACT (default): 5-point (2D) / 7-point (3D) Laplacian and
+ *     central first differences along the axes;
+ *   LF_STENCIL_ISOTROPIC: the operators built from the lattice weights,
+ *     d_a A = 3 sum_i w_i e_ia A(r + e_i) and lap A = 6 sum_i w_i [A(r + e_i) -
+ *     A(r)] (D2Q9: the 9-point Laplacian [4 (nearest) + (diagonal) - 20 A]/6),
+ *     isotropic to fourth order in the wavenumber (Thampi et al., J. Comput.
+ *     Phys. 234 (2013) 1).  Applies to psi, lam, grad phi, grad psi, F, the
+ *     flux divergence, lap mu and lap T; the wall images are those of the
+ *     compact stencils, applied to the diagonal neighbours too.  Runs the
+ *     LF_VARIANT_TILE kernel whatever variant is set.
+ * Returns LF_EINVAL for an unknown stencil, a 3D context, a context whose
+ * temperature solver is LF_TSOLVER_IMPLICIT, or an ensemble member.  Not
+ * stored in checkpoints. */
+#define LF_STENCIL_COMPACT   0
+#define LF_STENCIL_ISOTROPIC 1
+int lf_set_stencil(lf_ctx* ctx, int stencil);
 
 /* Current step counter. */
 int64_t lf_step_count(const lf_ctx* ctx);

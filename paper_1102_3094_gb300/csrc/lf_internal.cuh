@@ -63,6 +63,7 @@ struct Geom {
     int t_mode;
     int variant;     // LF_VARIANT_MARCH or LF_VARIANT_TILE
     int tune;        // march: rows per segment (0 = automatic)
+    int stencil;     // LF_STENCIL_COMPACT or LF_STENCIL_ISOTROPIC
 };
 
 // Physical parameters in the precision of the arithmetic.

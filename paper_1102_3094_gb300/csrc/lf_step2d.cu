@@ -22,6 +22,13 @@
 // then computed from the reflected state, which is the wall rule itself.  The
 // one odd quantity, the wall-normal flux g_y, is reflected with a sign flip
 // in the last stage.  Populations are stored as deviations f_i - w_i n0.
+//
+// With ISO set, every derivative takes the isotropic 9-point form instead:
+// lap A = [4 (nearest) + (diagonal) - 20 A]/6 and d_x A = [4 (E - W) + (NE - NW)
+// + (SE - SW)]/12 (the D2Q9 weights: d_a = 3 sum w_i e_ia A(r + e_i), lap = 6
+// sum w_i [A(r + e_i) - A(r)]).  The regions are the same; the flux g is then
+// also needed on the corners of the r = 1 ring, and the wall images of g and
+// of the halfway temperature ghost are applied to whole rows.
 #include "lf_internal.cuh"
 #include "lf_march2d.cuh"
 #include "lf_march2d_x2.cuh"
@@ -45,6 +52,37 @@ __device__ __forceinline__ int map_axis(int v, int n, int walls)
     return m < n ? m : 2 * n - 1 - m;
 }
 
+// Stencils on a row-major shared-memory region of row length W, centre c.
+template <typename R, int W, bool ISO>
+__device__ __forceinline__ R lap_s(const R* a, int c)
+{
+    if constexpr (ISO)
+        return (R(4) * (a[c - 1] + a[c + 1] + a[c - W] + a[c + W])
+                + (a[c - W - 1] + a[c - W + 1] + a[c + W - 1] + a[c + W + 1]) - R(20) * a[c]) * R(1.0 / 6.0);
+    else
+        return a[c - 1] + a[c + 1] + a[c - W] + a[c + W] - R(4) * a[c];
+}
+
+template <typename R, int W, bool ISO>
+__device__ __forceinline__ R dx_s(const R* a, int c)
+{
+    if constexpr (ISO)
+        return (R(4) * (a[c + 1] - a[c - 1]) + (a[c + W + 1] - a[c + W - 1]) + (a[c - W + 1] - a[c - W - 1]))
+               * R(1.0 / 12.0);
+    else
+        return R(0.5) * (a[c + 1] - a[c - 1]);
+}
+
+template <typename R, int W, bool ISO>
+__device__ __forceinline__ R dy_s(const R* a, int c)
+{
+    if constexpr (ISO)
+        return (R(4) * (a[c + W] - a[c - W]) + (a[c + W + 1] - a[c - W + 1]) + (a[c + W - 1] - a[c - W - 1]))
+               * R(1.0 / 12.0);
+    else
+        return R(0.5) * (a[c + W] - a[c - W]);
+}
+
 template <typename R, int TX, int TY>
 struct Tile {
     static constexpr int W4 = TX + 8, H4 = TY + 8;
@@ -64,7 +102,7 @@ struct Tile {
     static_assert(2 * W1 * H1 <= 3 * W2 * H2, "g must fit in the P area");
 };
 
-template <typename R, int TX, int TY, int NT, bool AUX>
+template <typename R, int TX, int TY, int NT, bool AUX, bool ISO>
 __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
 {
     using L = D2Q9;
@@ -110,7 +148,7 @@ __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
     for (int k = threadIdx.x; k < W3 * H3; k += NT) {
         const int ly = k / W3, lx = k - ly * W3;
         const int c = (ly + 1) * W4 + lx + 1;
-        spsi[k] = sphi[c - 1] + sphi[c + 1] + sphi[c - W4] + sphi[c + W4] - R(4) * sphi[c];
+        spsi[k] = lap_s<R, W4, ISO>(sphi, c);
     }
     __syncthreads();
 
@@ -120,14 +158,14 @@ __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
         const int cp = (ly + 2) * W4 + lx + 2;
         const int cs = (ly + 1) * W3 + lx + 1;
         const R ph = sphi[cp], psi = spsi[cs];
-        const R lam = spsi[cs - 1] + spsi[cs + 1] + spsi[cs - W3] + spsi[cs + W3] - R(4) * psi;
+        const R lam = lap_s<R, W3, ISO>(spsi, cs);
         slam[k] = lam;
         if (AUX || p.hydro) {
             const R av = (sT[k] - p.Tc) / p.Tc;
-            const R dpx = half * (sphi[cp + 1] - sphi[cp - 1]);
-            const R dpy = half * (sphi[cp + W4] - sphi[cp - W4]);
-            const R dsx = half * (spsi[cs + 1] - spsi[cs - 1]);
-            const R dsy = half * (spsi[cs + W3] - spsi[cs - W3]);
+            const R dpx = dx_s<R, W4, ISO>(sphi, cp);
+            const R dpy = dy_s<R, W4, ISO>(sphi, cp);
+            const R dsx = dx_s<R, W3, ISO>(spsi, cs);
+            const R dsy = dy_s<R, W3, ISO>(spsi, cs);
             const R ph2 = ph * ph;
             const R iso = av * ph2 * half + R(0.75) * p.b * ph2 * ph2
                         - p.kappa * (ph * psi + half * (dpx * dpx + dpy * dpy))
@@ -149,8 +187,8 @@ __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
         const R av = (sT[c2] - p.Tc) / p.Tc;
         smu[k] = av * ph + p.b * ph * ph * ph - p.kappa * spsi[cs] + p.c * slam[c2];
         if (AUX || p.hydro) {
-            sFx[k] = -(half * (sPxx[c2 + 1] - sPxx[c2 - 1]) + half * (sPxy[c2 + W2] - sPxy[c2 - W2]));
-            sFy[k] = -(half * (sPxy[c2 + 1] - sPxy[c2 - 1]) + half * (sPyy[c2 + W2] - sPyy[c2 - W2]));
+            sFx[k] = -(dx_s<R, W2, ISO>(sPxx, c2) + dy_s<R, W2, ISO>(sPxy, c2));
+            sFy[k] = -(dx_s<R, W2, ISO>(sPxy, c2) + dy_s<R, W2, ISO>(sPyy, c2));
         } else {
             sFx[k] = R(0);
             sFy[k] = R(0);
@@ -158,12 +196,12 @@ __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
     }
     __syncthreads();
 
-    // ---- stage 5: moments, flux g = phi u (r = 1, no corners); interior
-    //      sites collide and push --------------------------------------------
+    // ---- stage 5: moments, flux g = phi u (r = 1, corners only for the
+    //      isotropic divergence); interior sites collide and push -------------
     for (int k = threadIdx.x; k < W1 * H1; k += NT) {
         const int ly = k / W1, lx = k - ly * W1;
         const bool edge_x = (lx == 0 || lx == W1 - 1), edge_y = (ly == 0 || ly == H1 - 1);
-        if (edge_x && edge_y) continue;
+        if (!ISO && edge_x && edge_y) continue;
         const int ux = x0 - 1 + lx, uy = y0 - 1 + ly;        // unwrapped position
         if (walls && (uy < 0 || uy >= ny)) continue;         // ghost row: see stage 6
         const bool inner = !edge_x && !edge_y;
@@ -241,15 +279,28 @@ __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
         }
         const int cp = (ly + 4) * W4 + lx + 4;
         const int c2 = (ly + 2) * W2 + lx + 2;
-        const R lapmu = smu[c1 - 1] + smu[c1 + 1] + smu[c1 - W1] + smu[c1 + W1] - R(4) * smu[c1];
+        const R lapmu = lap_s<R, W1, ISO>(smu, c1);
         R div = R(0);
         if (p.hydro) {
-            R gyu = sgy[c1 + W1], gyd = sgy[c1 - W1];
-            if (walls) {                                     // no flux through the walls
-                if (gy == 0) gyd = -sgy[c1];
-                if (gy == ny - 1) gyu = -sgy[c1];
+            if constexpr (ISO) {
+                // rows below / at / above: a row beyond a wall is the image of
+                // the site's own row (g_x even, g_y odd: no flux through it)
+                const bool lo = walls && gy == 0, hi = walls && gy == ny - 1;
+                const int rd = lo ? c1 : c1 - W1, ru = hi ? c1 : c1 + W1;
+                const R sd = lo ? R(-1) : R(1), su = hi ? R(-1) : R(1);
+                const R dgx = R(4) * (sgx[c1 + 1] - sgx[c1 - 1]) + (sgx[ru + 1] - sgx[ru - 1])
+                            + (sgx[rd + 1] - sgx[rd - 1]);
+                const R dgy = R(4) * (su * sgy[ru] - sd * sgy[rd]) + (su * sgy[ru + 1] - sd * sgy[rd + 1])
+                            + (su * sgy[ru - 1] - sd * sgy[rd - 1]);
+                div = (dgx + dgy) * R(1.0 / 12.0);
+            } else {
+                R gyu = sgy[c1 + W1], gyd = sgy[c1 - W1];
+                if (walls) {                                 // no flux through the walls
+                    if (gy == 0) gyd = -sgy[c1];
+                    if (gy == ny - 1) gyu = -sgy[c1];
+                }
+                div = half * (sgx[c1 + 1] - sgx[c1 - 1]) + half * (gyu - gyd);
             }
-            div = half * (sgx[c1 + 1] - sgx[c1 - 1]) + half * (gyu - gyd);
         }
         const R phn = sphi[cp] - div + p.Gamma * lapmu;
         const R Tc0 = sT[c2];
@@ -257,6 +308,19 @@ __global__ void __launch_bounds__(NT) k_step2d(Geom g, Phys<R> p, StepIO<R> io)
         if (p.t_update) {
             if (walls && g.t_mode == LF_TWALL_LAYERS && (gy == 0 || gy == ny - 1)) {
                 Tn = p.T_w;
+            } else if constexpr (ISO) {
+                // halfway ghosts: 2 T_w minus the mirror image the halo row holds
+                const bool lo = walls && g.t_mode == LF_TWALL_HALFWAY && gy == 0;
+                const bool hi = walls && g.t_mode == LF_TWALL_HALFWAY && gy == ny - 1;
+                const R* rd = sT + c2 - W2;
+                const R* ru = sT + c2 + W2;
+                const R d0 = lo ? R(2) * p.T_w - rd[0] : rd[0], dl = lo ? R(2) * p.T_w - rd[-1] : rd[-1];
+                const R dr = lo ? R(2) * p.T_w - rd[1] : rd[1];
+                const R u0 = hi ? R(2) * p.T_w - ru[0] : ru[0], ul = hi ? R(2) * p.T_w - ru[-1] : ru[-1];
+                const R ur = hi ? R(2) * p.T_w - ru[1] : ru[1];
+                const R lap = (R(4) * (sT[c2 - 1] + sT[c2 + 1] + u0 + d0) + (ul + ur + dl + dr) - R(20) * Tc0)
+                              * R(1.0 / 6.0);
+                Tn = Tc0 + p.dxi * lap;
             } else {
                 R tu = sT[c2 + W2], td = sT[c2 - W2];
                 if (walls && g.t_mode == LF_TWALL_HALFWAY) {
@@ -332,11 +396,11 @@ cudaError_t launch_march(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
     return cudaGetLastError();
 }
 
-template <typename R, int TX, int TY, int NT, bool AUX>
+template <typename R, int TX, int TY, int NT, bool AUX, bool ISO>
 cudaError_t launch_cfg(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
     constexpr size_t bytes = Tile<R, TX, TY>::BYTES;
-    auto kern = k_step2d<R, TX, TY, NT, AUX>;
+    auto kern = k_step2d<R, TX, TY, NT, AUX, ISO>;
     static bool attr_set = false;   // per instantiation; harmless to repeat
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -360,11 +424,49 @@ __global__ void k_tsub2d(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __rest
     march::tsub2d_site(g, p, Tin, Tout, x, y);
 }
 
+// The same sub-step with the isotropic 9-point Laplacian.  A row beyond a wall
+// holds 2 T_w - T of the site's own row (halfway ghost); with held wall
+// layers the interior never reaches past them.
+template <typename R>
+__global__ void k_tsub2d_iso(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __restrict__ Tout)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = g.nx, ny = g.ny, pitch = g.pitch;
+    if (x >= nx || y >= ny) return;
+    const int64_t site = (int64_t)y * pitch + x;
+    const R t0 = Tin[site];
+    if (g.walls && g.t_mode == LF_TWALL_LAYERS && (y == 0 || y == ny - 1)) {
+        Tout[site] = p.T_w;
+        return;
+    }
+    const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+    const bool lo = g.walls && y == 0, hi = g.walls && y == ny - 1;
+    const int yd = lo ? 0 : (y == 0 ? ny - 1 : y - 1);
+    const int yu = hi ? y : (y == ny - 1 ? 0 : y + 1);
+    const R* rd = Tin + (int64_t)yd * pitch;
+    const R* r0 = Tin + (int64_t)y * pitch;
+    const R* ru = Tin + (int64_t)yu * pitch;
+    const R two_w = R(2) * p.T_w;
+    const R d0 = lo ? two_w - rd[x] : rd[x], dl = lo ? two_w - rd[xl] : rd[xl], dr = lo ? two_w - rd[xr] : rd[xr];
+    const R u0 = hi ? two_w - ru[x] : ru[x], ul = hi ? two_w - ru[xl] : ru[xl], ur = hi ? two_w - ru[xr] : ru[xr];
+    const R lap = (R(4) * (r0[xl] + r0[xr] + u0 + d0) + (ul + ur + dl + dr) - R(20) * t0) * R(1.0 / 6.0);
+    Tout[site] = t0 + p.dxi * lap;
+}
+
 }  // namespace
 
 template <typename R>
 cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
+    if (g.stencil == LF_STENCIL_ISOTROPIC) {           // tile kernel only
+        if constexpr (sizeof(R) == 4)
+            return aux ? launch_cfg<R, 64, 16, 256, true, true>(g, p, io, s)
+                       : launch_cfg<R, 64, 16, 256, false, true>(g, p, io, s);
+        else
+            return aux ? launch_cfg<R, 32, 16, 256, true, true>(g, p, io, s)
+                       : launch_cfg<R, 32, 16, 256, false, true>(g, p, io, s);
+    }
     if constexpr (sizeof(R) == 4) {
         if (!aux && g.variant == LF_VARIANT_MARCH2 && g.ny >= 2)
         {
@@ -377,11 +479,11 @@ cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, 
     if (!aux && (g.variant == LF_VARIANT_MARCH || g.variant == LF_VARIANT_MARCH2))
         return (g.tune >> 16) == 1 ? launch_march<R, 64, 3>(g, p, io, s) : launch_march<R, 128, 3>(g, p, io, s);
     if constexpr (sizeof(R) == 4) {
-        return aux ? launch_cfg<R, 64, 16, 256, true>(g, p, io, s)
-                   : launch_cfg<R, 64, 16, 256, false>(g, p, io, s);
+        return aux ? launch_cfg<R, 64, 16, 256, true, false>(g, p, io, s)
+                   : launch_cfg<R, 64, 16, 256, false, false>(g, p, io, s);
     } else {
-        return aux ? launch_cfg<R, 32, 16, 256, true>(g, p, io, s)
-                   : launch_cfg<R, 32, 16, 256, false>(g, p, io, s);
+        return aux ? launch_cfg<R, 32, 16, 256, true, false>(g, p, io, s)
+                   : launch_cfg<R, 32, 16, 256, false, false>(g, p, io, s);
     }
 }
 
@@ -390,7 +492,10 @@ cudaError_t launch_tsub(const Geom& g, const Phys<R>& p, const R* Tin, R* Tout, 
 {
     if (g.d == 3) return launch_tsub3d<R>(g, p, Tin, Tout, s);
     dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8);
-    k_tsub2d<R><<<grd, blk, 0, s>>>(g, p, Tin, Tout);
+    if (g.stencil == LF_STENCIL_ISOTROPIC)
+        k_tsub2d_iso<R><<<grd, blk, 0, s>>>(g, p, Tin, Tout);
+    else
+        k_tsub2d<R><<<grd, blk, 0, s>>>(g, p, Tin, Tout);
     return cudaGetLastError();
 }
 

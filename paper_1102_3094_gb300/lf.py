@@ -90,6 +90,8 @@ def lib():
             L.lf_set_kernel_variant.restype = C.c_int
             L.lf_set_t_solver.argtypes = [vp, C.c_int]
             L.lf_set_t_solver.restype = C.c_int
+            L.lf_set_stencil.argtypes = [vp, C.c_int]
+            L.lf_set_stencil.restype = C.c_int
             L.lf_step_count.argtypes = [vp]
             L.lf_step_count.restype = i64
             L.lf_destroy.argtypes = [vp]
@@ -178,6 +180,7 @@ def lf_load(ctx, path: str) -> None:
 
 
 LF_VARIANT_MARCH, LF_VARIANT_TILE, LF_VARIANT_MARCH2, LF_VARIANT_SPLIT3 = 0, 1, 2, 3
+LF_STENCIL_COMPACT, LF_STENCIL_ISOTROPIC = 0, 1
 
 
 def lf_set_kernel_variant(ctx, variant: int, param: int = 0) -> None:
@@ -263,6 +266,10 @@ class Lattice:
     def set_t_solver(self, solver: str = "explicit"):
         code = {"explicit": 0, "implicit": 1}[solver]
         _ok(lib().lf_set_t_solver(self.ctx, code), "lf_set_t_solver")
+
+    def set_stencil(self, stencil: str = "compact"):
+        code = {"compact": LF_STENCIL_COMPACT, "isotropic": LF_STENCIL_ISOTROPIC}[stencil]
+        _ok(lib().lf_set_stencil(self.ctx, code), "lf_set_stencil")
 
     def diag(self):
         d, rc = lf_diag(self.ctx)

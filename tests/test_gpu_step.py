@@ -48,7 +48,7 @@ VARIANTS = {"march": ("march", 0), "march-h5": ("march", 5), "tile": ("tile", 0)
             "march2-n64": ("march2", 1 << 16)}
 
 
-def make_pair(case, prec, seed=11, variant="march"):
+def make_pair(case, prec, seed=11, variant="march", stencil="compact"):
     """A GPU lattice and an oracle config with the same parameters, the GPU set
     to a random state; returns (sim, cfg, oracle_state_read_back)."""
     kw = dict(synth.BASE)
@@ -56,7 +56,8 @@ def make_pair(case, prec, seed=11, variant="march"):
     d = kw.get("d", 2)
     sim = lf.Lattice(precision=prec, **{k: v for k, v in kw.items() if k not in ("d",)}, d=d)
     sim.set_variant(*VARIANTS[variant])
-    cfg = O.make_cfg(d=d, nx=kw["nx"], ny=kw["ny"], nz=kw.get("nz", 1), walls=kw["walls"],
+    sim.set_stencil(stencil)
+    cfg = O.make_cfg(stencil=int(stencil == "isotropic"), d=d, nx=kw["nx"], ny=kw["ny"], nz=kw.get("nz", 1), walls=kw["walls"],
                      t_wall_mode=kw["t_wall_mode"], hydro=kw["hydro"], b=kw["b"], kappa=kw["kappa"],
                      c=kw["c"], Gamma=kw["Gamma"], Tc=kw["Tc"], T0=kw["T0"], T_w=kw["T_w"], xi=kw["xi"],
                      tau=kw["tau"], n0=kw["n0"], phi_amp=kw["phi_amp"], seed=kw.get("seed", 1))
@@ -91,6 +92,55 @@ CASES = [
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny")) + str(c))
 def test_aux_and_step_parity(case, prec, variant):
     sim, cfg, st = make_pair(case, prec, variant=variant)
+    _check_aux_and_step(sim, st, prec)
+
+
+@pytest.mark.parametrize("variant", ["march2", "tile"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny")) + str(c))
+def test_isotropic_stencil_parity(case, prec, variant):
+    """Isotropic 9-point stencils (runs the tile kernel whatever the variant)."""
+    sim, cfg, st = make_pair(case, prec, variant=variant, stencil="isotropic")
+    _check_aux_and_step(sim, st, prec)
+
+
+def test_isotropic_multistep_fp64():
+    """200 coupled steps with the isotropic stencils: walls with the halfway T
+    ghost and nsub = 2, then a fully periodic lattice."""
+    for kw in (dict(nx=64, ny=48, t_wall_mode=1, xi=0.3), dict(nx=40, ny=36, walls=0, xi=0.01)):
+        sim = lf.Lattice(precision="fp64", **kw)
+        sim.set_stencil("isotropic")
+        st = O.init(O.make_cfg(stencil=1, **kw))
+        sim.step(200)
+        ref = O.run(st, 200)
+        for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                                ("f", to_oracle_f(sim.get("pop"), 2), ref.f)):
+            assert relerr(got, want) < 1e-10, (kw, name, relerr(got, want))
+        sim.close()
+
+
+def test_isotropic_stencil_refusals():
+    sim = lf.Lattice(d=3, nx=8, ny=8, nz=8, precision="fp32")
+    with pytest.raises(lf.LFError):
+        sim.set_stencil("isotropic")
+    sim.close()
+    sim = lf.Lattice(nx=32, ny=32, precision="fp64", xi=0.5)
+    sim.set_t_solver("implicit")
+    with pytest.raises(lf.LFError):
+        sim.set_stencil("isotropic")
+    sim.set_t_solver("explicit")
+    sim.set_stencil("isotropic")
+    with pytest.raises(lf.LFError):
+        sim.set_t_solver("implicit")
+    # switching back restores the compact step exactly
+    sim.set_stencil("compact")
+    st = O.State(O.make_cfg(nx=32, ny=32, xi=0.5), to_oracle_f(sim.get("pop"), 2), sim.get("phi"), sim.get("T"))
+    sim.step(1)
+    assert relerr(sim.get("phi"), O.step(st).phi) < 1e-12
+    sim.close()
+
+
+def _check_aux_and_step(sim, st, prec):
     tol = TOL[prec]
     d = 2
     ax = O.aux(st)
