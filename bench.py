@@ -422,8 +422,8 @@ def run_ours(args):
     sim.set_variant(variant, args.tune)
     iso = args.stencil == "isotropic"
     if iso:
-        sim.set_stencil("isotropic")        # runs the tile kernel
-        variant = "tile"
+        sim.set_stencil("isotropic")        # runs the 2D tile kernel / the fused 3D plane march
+        variant = "tile" if d == 2 else "march"
     N = nx * ny * nz
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     flush_rd = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev) if args.flush == "write+read" else None
@@ -529,7 +529,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
         if d == 3:
-            rate, steps, el, cores = oracle_rate(64, 64, args.xi, seconds=args.cpu_seconds, d=3, nz=64, tau=tau)
+            rate, steps, el, cores = oracle_rate(64, 64, args.xi, seconds=args.cpu_seconds, d=3, nz=64, tau=tau,
+                                                 stencil=int(iso))
             smp = "64x64x64"
         else:
             rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds, stencil=int(iso))
@@ -546,7 +547,8 @@ def run_ours(args):
                                     if d == 2 else
                                     f"cube384: 3D D3Q19 lamellar quench between cold walls (z), {nx}x{ny}x{nz}, ")
                                    + f"{prec.upper()} state (deviation populations), xi={args.xi}, tau={tau}"
-                                   + (", isotropic 9-point stencils" if iso else ""),
+                                   + ((", isotropic 9-point stencils" if d == 2 else ", isotropic 19-point stencils")
+                                      if iso else ""),
                        "sites": N, "l2": ("flushed before every timed step (256 MiB write"
                                           + (", then a 256 MiB read so no dirty flush lines are written back "
                                              "inside the timed step" if args.flush == "write+read" else "")
@@ -592,7 +594,7 @@ def main():
                     help="L2 eviction between timed steps (2D and 3D single-lattice workloads)")
     ap.add_argument("--tune", type=int, default=0, help="march: rows per CTA segment (0 = automatic)")
     ap.add_argument("--stencil", choices=["compact", "isotropic"], default="compact",
-                    help="finite-difference stencils (2D only; isotropic runs the tile kernel)")
+                    help="finite-difference stencils (isotropic runs the 2D tile kernel or the fused 3D march)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -102,7 +102,7 @@ typedef struct {
     int      precision;   /* LF_FP64 or LF_FP32                                   */
     int      hydro;       /* 1: LB coupled; 0: Eq. massdiff without convection    */
     int      ideal_mode;  /* must be 0: ideal pressure n c_s^2 kept by the LB     */
-    int      pad_;
+    int      stencil;     /* LF_STENCIL_COMPACT (0) or LF_STENCIL_ISOTROPIC (1)  */
     void*    stream;      /* cudaStream_t to enqueue on (borrowed, not owned)     */
     void*    workspace;   /* optional caller device buffer for all state          */
     size_t   workspace_bytes; /* its size; see lf_workspace_bytes                 */
@@ -146,7 +146,8 @@ int lf_workspace_bytes(const lf_grid* grid, const lf_walls* walls,
 /* ---- life cycle -------------------------------------------------------- */
 /* Validates the arguments (LF_EINVAL), the stability of the explicit schemes
  * (LF_EUNSTABLE: tau <= 1/2 with hydro, or Gamma lam (a + kappa lam + c lam^2)
- * >= 2 for some lattice eigenvalue lam at the largest a in the run), places
+ * >= 2 for some Laplacian eigenvalue lam of the chosen stencils at the
+ * largest a in the run), places
  * the state in params->workspace (if given; LF_ENOMEM if too small) or in its
  * own device allocation, and enqueues the initial state: phi from SplitMix64,
  * T = T0 (T_w on the wall layers; T_w everywhere for xi = +INFINITY),
@@ -269,7 +270,8 @@ int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
 int lf_set_t_solver(lf_ctx* ctx, int solver);
 
 /* Finite-difference stencils of every derivative of the step (Sec. 2 names a
- * "second-order finite-difference scheme" without fixing it):
+ * "second-order finite-difference scheme" without fixing it); chosen at
+ * lf_create by params->stencil, or changed later by lf_set_stencil:
  *   LF_STENCIL_COMPACT (default): 5-point (2D) / 7-point (3D) Laplacian and
  *     central first differences along the axes;
  *   LF_STENCIL_ISOTROPIC: the operators built from the lattice weights,
@@ -279,10 +281,14 @@ int lf_set_t_solver(lf_ctx* ctx, int solver);
  *     Phys. 234 (2013) 1).  Applies to psi, lam, grad phi, grad psi, F, the
  *     flux divergence, lap mu and lap T; the wall images are those of the
  *     compact stencils, applied to the diagonal neighbours too.  Runs the
- *     LF_VARIANT_TILE kernel whatever variant is set.
- * Returns LF_EINVAL for an unknown stencil, a 3D context, a context whose
- * temperature solver is LF_TSOLVER_IMPLICIT, or an ensemble member.  Not
- * stored in checkpoints. */
+ *     LF_VARIANT_TILE kernel (2D) or the fused plane march (3D) whatever
+ *     variant is set.  Its largest Laplacian eigenvalue is 16/3 in 2D and 3D
+ *     (8 and 12 for the compact stencils), which the stability check of
+ *     lf_create uses.
+ * Returns LF_EINVAL for an unknown stencil, a context whose temperature
+ * solver is LF_TSOLVER_IMPLICIT, or an ensemble member, and LF_EUNSTABLE if
+ * the context's parameters are unstable with the new stencil (the context
+ * keeps its stencil then).  Not stored in checkpoints. */
 #define LF_STENCIL_COMPACT   0
 #define LF_STENCIL_ISOTROPIC 1
 int lf_set_stencil(lf_ctx* ctx, int stencil);

@@ -30,7 +30,8 @@ typedef struct lf_ens lf_ens;
  * stream, workspace and workspace_bytes fields of params are ignored), all in
  * one device arena, enqueued on `stream` (a cudaStream_t; 0 = a private
  * stream the ensemble creates).  LF_EINVAL if a run is not d = 2 / LF_FP32 /
- * ny >= 2 or fails lf_create's checks (then nothing is allocated). */
+ * ny >= 2 / LF_STENCIL_COMPACT or fails lf_create's checks (then nothing is
+ * allocated). */
 int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const lf_params* params,
                   void* stream, lf_ens** out);
 

@@ -45,6 +45,7 @@ int validate(const lf_grid* grid, const lf_walls* walls, const lf_params* p)
     if (p->precision != LF_FP64 && p->precision != LF_FP32) return LF_EINVAL;
     if (p->hydro != 0 && p->hydro != 1) return LF_EINVAL;
     if (p->ideal_mode != 0) return LF_EINVAL;
+    if (p->stencil != LF_STENCIL_COMPACT && p->stencil != LF_STENCIL_ISOTROPIC) return LF_EINVAL;
     const double vals[] = {p->b, p->kappa, p->c, p->Gamma, p->Tc, p->T0, p->tau, p->n0,
                            p->phi_amp, walls->T_w};
     for (double v : vals)
@@ -53,11 +54,12 @@ int validate(const lf_grid* grid, const lf_walls* walls, const lf_params* p)
     if (std::isnan(p->xi) || p->xi < 0) return LF_EINVAL;
     if (p->hydro && !(p->tau > 0.5)) return LF_EUNSTABLE;
     // Linear stability of the explicit phi update: a lattice eigenmode with
-    // Laplacian eigenvalue lam in [0, 4d] is multiplied per step by
+    // Laplacian eigenvalue lam in [0, lmax] is multiplied per step by
     // 1 - Gamma lam (a + kappa lam + c lam^2); require that factor > -1 at the
-    // largest a the run can see.
+    // largest a the run can see.  lmax = 4d for the compact stencils and 16/3
+    // for the isotropic ones (2D: at q = (pi, pi); 3D: at q = (pi, pi, 0)).
     const double amax = (std::fmax(p->T0, walls->T_w) - p->Tc) / p->Tc;
-    const double lmax = 4.0 * grid->d;
+    const double lmax = p->stencil == LF_STENCIL_ISOTROPIC ? 16.0 / 3.0 : 4.0 * grid->d;
     for (int k = 0; k <= 4000; ++k) {
         const double lam = lmax * k / 4000.0;
         if (p->Gamma * lam * (amax + p->kappa * lam + p->c * lam * lam) >= 2.0) return LF_EUNSTABLE;
@@ -397,6 +399,7 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
     c->g.variant = grid->d == 3 ? LF_VARIANT_SPLIT3
                  : (params->precision == LF_FP32 ? LF_VARIANT_MARCH2 : LF_VARIANT_MARCH);
     c->g.tune = 0;
+    c->g.stencil = params->stencil;
     c->t_solver = LF_TSOLVER_EXPLICIT;
 
     if (params->workspace) {
@@ -587,8 +590,13 @@ int lf_set_t_solver(lf_ctx* c, int solver)
 int lf_set_stencil(lf_ctx* c, int stencil)
 {
     if (!c || (stencil != LF_STENCIL_COMPACT && stencil != LF_STENCIL_ISOTROPIC) || c->ens_member) return LF_EINVAL;
-    if (stencil == LF_STENCIL_ISOTROPIC && (c->g.d != 2 || c->t_solver == LF_TSOLVER_IMPLICIT)) return LF_EINVAL;
+    if (stencil == LF_STENCIL_ISOTROPIC && c->t_solver == LF_TSOLVER_IMPLICIT) return LF_EINVAL;
+    lf_params p = c->params;
+    p.stencil = stencil;
+    const int rc = validate(&c->grid, &c->walls, &p);
+    if (rc != LF_OK) return rc;
     if (stencil != c->g.stencil) c->aux_valid = false;
+    c->params.stencil = stencil;
     c->g.stencil = stencil;
     return LF_OK;
 }

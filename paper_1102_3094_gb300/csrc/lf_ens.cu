@@ -310,7 +310,9 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
     std::vector<size_t> ws(nruns);
     size_t total = 0;
     for (int r = 0; r < nruns; ++r) {
-        if (grids[r].d != 2 || params[r].precision != LF_FP32 || grids[r].ny < 2) return LF_EINVAL;
+        if (grids[r].d != 2 || params[r].precision != LF_FP32 || grids[r].ny < 2 ||
+            params[r].stencil != LF_STENCIL_COMPACT)
+            return LF_EINVAL;
         lf_params p = params[r];
         p.workspace = nullptr;
         p.workspace_bytes = 0;

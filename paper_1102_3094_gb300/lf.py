@@ -42,7 +42,7 @@ class lf_params(C.Structure):
     _fields_ = [("b", C.c_double), ("kappa", C.c_double), ("c", C.c_double), ("Gamma", C.c_double),
                 ("Tc", C.c_double), ("T0", C.c_double), ("xi", C.c_double), ("tau", C.c_double),
                 ("n0", C.c_double), ("phi_amp", C.c_double), ("seed", C.c_uint64),
-                ("precision", C.c_int), ("hydro", C.c_int), ("ideal_mode", C.c_int), ("pad_", C.c_int),
+                ("precision", C.c_int), ("hydro", C.c_int), ("ideal_mode", C.c_int), ("stencil", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
 
 
@@ -202,7 +202,8 @@ class Lattice:
 
     def __init__(self, d=2, nx=64, ny=64, nz=1, walls=1, t_wall_mode=0, T_w=0.5, b=1.0, kappa=-0.025,
                  c=0.02, Gamma=0.05, Tc=1.0, T0=1.1, xi=0.01, tau=1.0, n0=1.0, phi_amp=0.05, seed=1,
-                 precision="fp64", hydro=1, stream=None, device=None, use_torch_workspace=True):
+                 precision="fp64", hydro=1, stream=None, device=None, use_torch_workspace=True,
+                 stencil="compact"):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda:0")
@@ -214,6 +215,7 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.params = lf_params(b=b, kappa=kappa, c=c, Gamma=Gamma, Tc=Tc, T0=T0, xi=xi, tau=tau, n0=n0,
                                 phi_amp=phi_amp, seed=seed, precision=self.prec, hydro=hydro, ideal_mode=0,
+                                stencil={"compact": LF_STENCIL_COMPACT, "isotropic": LF_STENCIL_ISOTROPIC}[stencil],
                                 stream=self.stream.cuda_stream, workspace=None, workspace_bytes=0)
         self.ws = None
         if use_torch_workspace:

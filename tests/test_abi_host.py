@@ -74,6 +74,7 @@ def _args(L, **kw):
     (dict(d=4), -1), (dict(nx=0), -1), (dict(nz=2), -1), (dict(precision=7), -1),
     (dict(ideal_mode=1), -1), (dict(Tc=0.0), -1), (dict(xi=-1.0), -1), (dict(xi=float("nan")), -1),
     (dict(ny=1), -1), (dict(walls=2), -1), (dict(t_wall_mode=3), -1), (dict(b=float("inf")), -1),
+    (dict(stencil=2), -1), (dict(stencil=-1), -1),
 ])
 def test_validation_codes(L, kw, code):
     g, w, p = _args(L, **kw)
@@ -83,6 +84,26 @@ def test_validation_codes(L, kw, code):
     ctx = C.c_void_p()
     assert L.lib().lf_create(C.byref(g), C.byref(w), C.byref(p), C.byref(ctx)) == code
     assert not ctx.value
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_stability_limit_follows_the_stencil(L, d):
+    """The explicit phi update is checked against the largest Laplacian
+    eigenvalue of the chosen stencils: 4d (compact) or 16/3 (isotropic).  At
+    the parameters of the paper's runs (b = 0.1, kappa = -c = -0.03, Gamma =
+    0.1, T_w = 0.9 Tc) the 3D compact step is unstable and the isotropic one
+    is not; a larger Gamma makes both unstable."""
+    kw = dict(d=d, nz=24 if d == 3 else 1, b=0.1, kappa=-0.03, c=0.03, Gamma=0.1, Tc=0.005, T0=0.0055,
+              T_w=0.0045)
+    n = C.c_size_t()
+
+    def rc(**more):
+        g, w, p = _args(L, **dict(kw, **more))
+        return L.lib().lf_workspace_bytes(C.byref(g), C.byref(w), C.byref(p), C.byref(n))
+
+    assert rc(stencil=0) == (-2 if d == 3 else 0)
+    assert rc(stencil=1) == 0
+    assert rc(stencil=1, Gamma=1.0) == -2
 
 
 def test_workspace_bytes_scale(L):

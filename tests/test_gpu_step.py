@@ -120,9 +120,16 @@ def test_isotropic_multistep_fp64():
 
 
 def test_isotropic_stencil_refusals():
-    sim = lf.Lattice(d=3, nx=8, ny=8, nz=8, precision="fp32")
+    # parameters of the paper's 3D runs: unstable with the 7-point Laplacian only
+    fig3 = dict(d=3, nx=16, ny=16, nz=24, b=0.1, kappa=-0.03, c=0.03, Gamma=0.1, Tc=0.005, T0=0.0055,
+                T_w=0.0045, phi_amp=0.01, precision="fp32")
     with pytest.raises(lf.LFError):
-        sim.set_stencil("isotropic")
+        lf.Lattice(**fig3)
+    sim = lf.Lattice(stencil="isotropic", **fig3)
+    with pytest.raises(lf.LFError):
+        sim.set_stencil("compact")             # unstable: the context keeps its stencil
+    sim.step(10)
+    assert sim.diag()["rc"] == 0
     sim.close()
     sim = lf.Lattice(nx=32, ny=32, precision="fp64", xi=0.5)
     sim.set_t_solver("implicit")
@@ -180,6 +187,32 @@ VARIANTS3 = {"fused": ("march", 0), "split3": ("split3", 0), "split3-z3": ("spli
 def test_aux_and_step_parity_3d(case, prec, variant):
     sim, cfg, st = make_pair(case, prec)
     sim.set_variant(*VARIANTS3[variant])
+    _check_aux_and_step_3d(sim, st, prec)
+
+
+@pytest.mark.parametrize("variant", ["split3", "fused"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
+def test_isotropic_stencil_parity_3d(case, prec, variant):
+    """Isotropic 19-point stencils (runs the fused plane march whatever the variant)."""
+    sim, cfg, st = make_pair(case, prec, stencil="isotropic")
+    sim.set_variant(*VARIANTS3[variant])
+    _check_aux_and_step_3d(sim, st, prec)
+
+
+def test_isotropic_multistep_3d_fp64():
+    kw = dict(d=3, nx=20, ny=16, nz=18, xi=0.3, t_wall_mode=1)
+    sim = lf.Lattice(precision="fp64", stencil="isotropic", **kw)
+    st = O.init(O.make_cfg(stencil=1, **kw))
+    sim.step(50)
+    ref = O.run(st, 50)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), 3), ref.f)):
+        assert relerr(got, want) < 1e-10, (name, relerr(got, want))
+    sim.close()
+
+
+def _check_aux_and_step_3d(sim, st, prec):
     tol = TOL[prec]
     ax = O.aux(st)
     checks = {"mu": (sim.get("mu"), ax["mu"]), "rho": (sim.get("rho"), ax["n"])}

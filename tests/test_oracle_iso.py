@@ -224,3 +224,21 @@ def test_isotropy_equal_wavenumber_modes(d):
     spread_i = abs(i_ax - i_off) / q2
     assert spread_c > 5e-3
     assert spread_i < 0.02 * spread_c, (spread_i, spread_c)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_largest_isotropic_eigenvalue(d):
+    """The largest -(Laplacian eigenvalue) of the isotropic stencils is 16/3, at
+    q = (pi, pi) in 2D and q = (pi, pi, 0) in 3D (the stability limit of the
+    explicit phi update uses it); the compact stencils reach 4d there."""
+    if d == 2:
+        shape, mode = (8, 8), (4, 4)
+        q = np.linspace(-np.pi, np.pi, 121)
+        grid_max = (-iso_lap2(q[:, None], q[None, :])).max()
+    else:
+        shape, mode = (6, 8, 8), (0, 4, 4)
+        q = np.linspace(-np.pi, np.pi, 49)
+        grid_max = (-iso_lap3(q[:, None, None], q[None, :, None], q[None, None, :])).max()
+    compact, iso = _decay_rate(d, shape, mode)
+    assert abs(iso - 16 / 3) < 1e-9 and abs(compact - 8) < 1e-9
+    assert abs(grid_max - 16 / 3) < 1e-12
