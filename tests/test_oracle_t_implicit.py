@@ -3,7 +3,9 @@ closed forms and limits that fix it independently of its own matrix."""
 import math
 
 import numpy as np
+import pytest
 
+from oracle import oracle as O
 from oracle import t_implicit as TI
 
 
@@ -74,3 +76,62 @@ def test_small_xi_matches_one_explicit_step_to_second_order():
     expl = T + xi * lap
     expl[0] = expl[-1] = Tw
     assert np.abs(out - expl).max() < 50 * xi ** 2
+
+
+# ---- isotropic 9-/19-point stencil (stencil = 1) ----------------------------
+def _iso_lap2(qx, qy):
+    # Fourier symbol of [4 (nearest) + (diagonal) - 20 A] / 6
+    return (8 * (math.cos(qx) + math.cos(qy)) + 4 * math.cos(qx) * math.cos(qy) - 20) / 6
+
+
+def _iso_lap3(qx, qy, qz):
+    cx, cy, cz = math.cos(qx), math.cos(qy), math.cos(qz)
+    return (4 * (cx + cy + cz) + 4 * (cx * cy + cx * cz + cy * cz) - 24) / 6
+
+
+def test_iso_periodic_modes_are_divided_by_one_minus_xi_symbol():
+    ny, nx, xi = 6, 8, 0.7
+    y, x = np.mgrid[0:ny, 0:nx]
+    T = np.cos(2 * math.pi * 3 * x / nx + 2 * math.pi * 1 * y / ny)
+    out = TI.implicit_step(T, xi, 0.0, walls=0, t_mode=0, stencil=1)
+    np.testing.assert_allclose(out, T / (1 - xi * _iso_lap2(2 * math.pi * 3 / nx, 2 * math.pi / ny)), atol=1e-12)
+    nz, ny, nx, xi = 5, 4, 6, 2.5
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx]
+    T = np.sin(2 * math.pi * (2 * x / nx + y / ny - z / nz)) + 0.3
+    out = TI.implicit_step(T, xi, 0.0, walls=0, t_mode=0, stencil=1)
+    lam = _iso_lap3(2 * math.pi * 2 / nx, 2 * math.pi / ny, -2 * math.pi / nz)
+    np.testing.assert_allclose(out, 0.3 + (T - 0.3) / (1 - xi * lam), atol=1e-12)
+
+
+@pytest.mark.parametrize("t_mode", [0, 1])
+def test_iso_wall_modes_with_diagonal_ghosts(t_mode):
+    """T - T_w = eps cos(kx x) s(j), s the Dirichlet eigenvector of the wall rule:
+    the x dependence makes the diagonal neighbours (and their ghosts) count, and
+    the mode is divided by 1 - xi Lambda(kx, q) with Lambda the 9-point symbol."""
+    L, nx, xi, Tw = 9, 6, 1.3, 0.5
+    j = np.arange(L)[:, None]
+    x = np.arange(nx)[None, :]
+    kx, m = 2 * math.pi * 2 / nx, 3
+    q = math.pi * m / (L - 1) if t_mode == 0 else math.pi * m / L
+    s = np.sin(q * j) if t_mode == 0 else np.sin(q * (j + 0.5))
+    dev = 0.2 * np.cos(kx * x) * s
+    out = TI.implicit_step(Tw + dev, xi, Tw, walls=1, t_mode=t_mode, stencil=1)
+    np.testing.assert_allclose(out, Tw + dev / (1 - xi * _iso_lap2(kx, q)), atol=1e-12)
+
+
+@pytest.mark.parametrize("t_mode", [0, 1])
+def test_iso_small_xi_matches_one_explicit_oracle_step(t_mode):
+    """To first order in xi the implicit step is the oracle's explicit step with
+    the same stencil and wall rule (the two differ at O(xi^2))."""
+    ny, nx, Tw, xi = 8, 7, 0.5, 1e-4
+    cfg = O.make_cfg(nx=nx, ny=ny, walls=1, t_wall_mode=t_mode, hydro=0, phi_amp=0.0, xi=xi, T0=1.0,
+                     T_w=Tw, stencil=1)
+    assert cfg.nsub == 1
+    st = O.init(cfg)
+    st.T = 1.0 + 0.1 * np.random.default_rng(3).standard_normal((ny, nx))
+    if t_mode == 0:
+        st.T[0] = st.T[-1] = Tw
+    expl = O.step(st).T
+    out = TI.implicit_step(st.T, xi, Tw, walls=1, t_mode=t_mode, stencil=1)
+    assert np.abs(out - expl).max() < 50 * xi ** 2
+    assert np.abs(out - st.T).max() > 1e3 * xi ** 2          # the step itself is O(xi)
