@@ -262,9 +262,8 @@ int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
  *     stable: one solve per step at any xi.  Needs the periodic lattice sizes
  *     to be at most 4096 with prime factors up to 31.
  * The phi, f update always uses T(t).  Returns LF_EINVAL for an unknown
- * solver, an unsupported size, an ensemble member (ensembles always take
- * explicit sub-steps), or LF_TSOLVER_IMPLICIT on a context with isotropic
- * stencils.  Not stored in checkpoints. */
+ * solver, an unsupported size, or an ensemble member (ensembles always take
+ * explicit sub-steps).  Not stored in checkpoints. */
 #define LF_TSOLVER_EXPLICIT 0
 #define LF_TSOLVER_IMPLICIT 1
 int lf_set_t_solver(lf_ctx* ctx, int solver);
@@ -285,8 +284,7 @@ int lf_set_t_solver(lf_ctx* ctx, int solver);
  *     variant is set.  Its largest Laplacian eigenvalue is 16/3 in 2D and 3D
  *     (8 and 12 for the compact stencils), which the stability check of
  *     lf_create uses.
- * Returns LF_EINVAL for an unknown stencil, a context whose temperature
- * solver is LF_TSOLVER_IMPLICIT, or an ensemble member, and LF_EUNSTABLE if
+ * Returns LF_EINVAL for an unknown stencil or an ensemble member, and LF_EUNSTABLE if
  * the context's parameters are unstable with the new stencil (the context
  * keeps its stencil then).  Not stored in checkpoints. */
 #define LF_STENCIL_COMPACT   0

@@ -581,8 +581,7 @@ int64_t lf_step_count(const lf_ctx* c) { return c ? c->step : -1; }
 int lf_set_t_solver(lf_ctx* c, int solver)
 {
     if (!c || (solver != LF_TSOLVER_EXPLICIT && solver != LF_TSOLVER_IMPLICIT) || c->ens_member) return LF_EINVAL;
-    if (solver == LF_TSOLVER_IMPLICIT && (!t_implicit_supported(c->g) || c->g.stencil != LF_STENCIL_COMPACT))
-        return LF_EINVAL;
+    if (solver == LF_TSOLVER_IMPLICIT && !t_implicit_supported(c->g)) return LF_EINVAL;
     c->t_solver = solver;
     return LF_OK;
 }
@@ -590,7 +589,6 @@ int lf_set_t_solver(lf_ctx* c, int solver)
 int lf_set_stencil(lf_ctx* c, int stencil)
 {
     if (!c || (stencil != LF_STENCIL_COMPACT && stencil != LF_STENCIL_ISOTROPIC) || c->ens_member) return LF_EINVAL;
-    if (stencil == LF_STENCIL_ISOTROPIC && c->t_solver == LF_TSOLVER_IMPLICIT) return LF_EINVAL;
     lf_params p = c->params;
     p.stencil = stencil;
     const int rc = validate(&c->grid, &c->walls, &p);

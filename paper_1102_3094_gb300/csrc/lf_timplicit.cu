@@ -5,12 +5,21 @@
 // i.e. hundreds of sub-steps per time step at the paper's largest xi.  The
 // implicit option takes one backward-Euler step per time step,
 //   (I - xi L) T(t+1) = T(t),
-// with the same 5-/7-point Laplacian L and wall rules as the explicit update.
-// L is diagonal in a lattice Fourier basis along the periodic axes, so the
-// solve is: FP64 DFT along x (2D) or x and y (3D); for every Fourier mode a
-// tridiagonal system along the wall normal (Thomas algorithm, one thread per
-// mode) -- or a plain division when every axis is periodic; the inverse DFT
-// as conj(DFT(conj(.))) / n; back to the state's precision.
+// with the same Laplacian L (compact 5-/7-point or isotropic 9-/19-point) and
+// wall rules as the explicit update.  L is diagonal in a lattice Fourier basis
+// along the periodic axes and couples only neighbouring layers along the wall
+// normal, so the solve is: FP64 DFT along x (2D) or x and y (3D); for every
+// Fourier mode a tridiagonal system along the wall normal (Thomas algorithm,
+// one thread per mode) -- or a plain division when every axis is periodic;
+// the inverse DFT as conj(DFT(conj(.))) / n; back to the state's precision.
+//
+// For a mode with in-plane wavenumbers (kx[, ky]) L acts on the layer
+// amplitudes as alpha (A_{j+1} + A_{j-1}) + beta A_j:
+//   compact:        alpha = 1,                 beta = -2 - sum 2 (1 - cos k)
+//   isotropic, 2D:  alpha = (4 + 2 cx) / 6,     beta = (8 cx - 20) / 6
+//   isotropic, 3D:  alpha = (2 + 2 cx + 2 cy)/6, beta = (4 cx + 4 cy + 4 cx cy - 24) / 6
+// (c = cos k).  Every offset that crosses a wall has the wall-normal step of
+// the axis neighbour, so the ghost rules enter with the same alpha.
 #include <cmath>
 
 #include "lf_ctx.cuh"
@@ -49,21 +58,49 @@ __global__ void k_t_store(Geom g, const double2* __restrict__ buf, double scale,
     if (bad) *reinterpret_cast<volatile int*>(flag) = 1;
 }
 
-// Eigenvalue of -L along the periodic axes for the mode with packed index m
-// over those axes (x fastest).
-__device__ __forceinline__ double lam_of(const Geom& g, int64_t m, int nper_axes)
+// Cosines of the wavenumbers of the mode with packed index m over the
+// periodic axes (x fastest); 1 for the others.
+__device__ __forceinline__ void mode_cos(const Geom& g, int64_t m, int nper_axes, double c[3])
 {
-    const int kx = (int)(m % g.nx);
-    double lam = 2.0 * (1.0 - cos(kTwoPi * kx / g.nx));
-    if (nper_axes >= 2) {
-        const int ky = (int)((m / g.nx) % g.ny);
-        lam += 2.0 * (1.0 - cos(kTwoPi * ky / g.ny));
+    c[0] = cos(kTwoPi * (int)(m % g.nx) / g.nx);
+    c[1] = nper_axes >= 2 ? cos(kTwoPi * (int)((m / g.nx) % g.ny) / g.ny) : 1.0;
+    c[2] = nper_axes >= 3 ? cos(kTwoPi * (int)(m / ((int64_t)g.nx * g.ny)) / g.nz) : 1.0;
+}
+
+// Every axis periodic: eigenvalue of -L for mode m.
+__device__ __forceinline__ double lam_periodic(const Geom& g, int64_t m)
+{
+    double c[3];
+    mode_cos(g, m, g.d, c);
+    if (g.stencil == LF_STENCIL_ISOTROPIC) {
+        if (g.d == 2) return -(8.0 * (c[0] + c[1]) + 4.0 * c[0] * c[1] - 20.0) / 6.0;
+        return -(4.0 * (c[0] + c[1] + c[2]) + 4.0 * (c[0] * c[1] + c[0] * c[2] + c[1] * c[2]) - 24.0) / 6.0;
     }
-    if (nper_axes >= 3) {
-        const int kz = (int)(m / ((int64_t)g.nx * g.ny));
-        lam += 2.0 * (1.0 - cos(kTwoPi * kz / g.nz));
-    }
+    double lam = 0.0;
+    for (int a = 0; a < g.d; ++a) lam += 2.0 * (1.0 - c[a]);
     return lam;
+}
+
+// Walls: L on the layer amplitudes of in-plane mode m is alpha (A_{j+1} +
+// A_{j-1}) + beta A_j.
+__device__ __forceinline__ void layer_coeffs(const Geom& g, int64_t m, double* alpha, double* beta)
+{
+    double c[3];
+    mode_cos(g, m, g.d - 1, c);
+    if (g.stencil == LF_STENCIL_ISOTROPIC) {
+        if (g.d == 2) {
+            *alpha = (4.0 + 2.0 * c[0]) / 6.0;
+            *beta = (8.0 * c[0] - 20.0) / 6.0;
+        } else {
+            *alpha = (2.0 + 2.0 * c[0] + 2.0 * c[1]) / 6.0;
+            *beta = (4.0 * c[0] + 4.0 * c[1] + 4.0 * c[0] * c[1] - 24.0) / 6.0;
+        }
+        return;
+    }
+    double lam = 2.0 * (1.0 - c[0]);
+    if (g.d == 3) lam += 2.0 * (1.0 - c[1]);
+    *alpha = 1.0;
+    *beta = -2.0 - lam;
 }
 
 // Walls along the last axis: one thread per Fourier mode m of the periodic
@@ -77,9 +114,10 @@ __global__ void k_t_thomas(Geom g, double2* __restrict__ buf, double* __restrict
     const int L = d == 2 ? g.ny : g.nz;
     const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (m >= M) return;
-    const double lam = lam_of(g, m, d - 1);
-    const double b = 1.0 + xi * (lam + 2.0);
-    const double a = -xi;                    // sub- and super-diagonal
+    double alpha, beta;
+    layer_coeffs(g, m, &alpha, &beta);
+    const double b = 1.0 - xi * beta;
+    const double a = -xi * alpha;            // sub- and super-diagonal
     auto at = [&](int j) -> double2& { return buf[(int64_t)j * M + m]; };
     int j0 = 0, j1 = L - 1;                  // unknown layers
     double2 lo_add = make_double2(0.0, 0.0), hi_add = make_double2(0.0, 0.0);
@@ -87,12 +125,12 @@ __global__ void k_t_thomas(Geom g, double2* __restrict__ buf, double* __restrict
     if (t_mode == LF_TWALL_LAYERS) {         // held layers 0 and L-1 enter the right-hand side
         j0 = 1;
         j1 = L - 2;
-        lo_add = make_double2(xi * at(0).x, xi * at(0).y);
-        hi_add = make_double2(xi * at(L - 1).x, xi * at(L - 1).y);
-    } else {                                 // ghost 2 T_w - T: +xi on the diagonal, 2 xi T_w in the rhs
-        b0 += xi;
-        b1 += xi;
-        const double w = m == 0 ? 2.0 * xi * Tw_hat0 : 0.0;
+        lo_add = make_double2(-a * at(0).x, -a * at(0).y);
+        hi_add = make_double2(-a * at(L - 1).x, -a * at(L - 1).y);
+    } else {                                 // ghost 2 T_w - T: +xi alpha on the diagonal, 2 xi alpha T_w in the rhs
+        b0 -= a;
+        b1 -= a;
+        const double w = m == 0 ? -2.0 * a * Tw_hat0 : 0.0;
         lo_add = make_double2(w, 0.0);
         hi_add = make_double2(w, 0.0);
     }
@@ -159,7 +197,7 @@ __global__ void k_t_divide(Geom g, double2* __restrict__ buf, double xi)
 {
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
-        const double s = 1.0 / (1.0 + xi * lam_of(g, k, g.d));
+        const double s = 1.0 / (1.0 + xi * lam_periodic(g, k));
         buf[k] = make_double2(buf[k].x * s, -buf[k].y * s);
     }
 }

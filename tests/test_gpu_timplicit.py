@@ -33,14 +33,15 @@ def _oracle_step(cfg, st, xi):
     cfg0.xi = 0.0
     cfg0.nsub = 1
     out = O.step(O.State(cfg0, st.f, st.phi, st.T))
-    Tn = TI.implicit_step(st.T, xi, cfg.T_w, cfg.walls, cfg.t_wall_mode)   # wall normal on axis 0
+    Tn = TI.implicit_step(st.T, xi, cfg.T_w, cfg.walls, cfg.t_wall_mode, cfg.stencil)   # wall normal on axis 0
     return out.phi, Tn, out.f
 
 
+@pytest.mark.parametrize("stencil", ["compact", "isotropic"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c.get(k, "")) for k in ("nx", "ny", "nz")) + str(c))
-def test_implicit_temperature_step(case, prec):
-    sim, cfg, st = make_pair(case, prec)
+def test_implicit_temperature_step(case, prec, stencil):
+    sim, cfg, st = make_pair(case, prec, stencil=stencil)
     sim.set_t_solver("implicit")
     sim.step(1)
     phi_w, T_w, f_w = _oracle_step(cfg, st, case["xi"])
@@ -52,9 +53,10 @@ def test_implicit_temperature_step(case, prec):
     sim.close()
 
 
-def test_implicit_multistep_fp64():
+@pytest.mark.parametrize("stencil", ["compact", "isotropic"])
+def test_implicit_multistep_fp64(stencil):
     case = dict(nx=32, ny=24, xi=8.0)
-    sim, cfg, st = make_pair(case, "fp64")
+    sim, cfg, st = make_pair(case, "fp64", stencil=stencil)
     sim.set_t_solver("implicit")
     for _ in range(10):
         phi, T, f = _oracle_step(cfg, st, case["xi"])
