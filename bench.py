@@ -485,6 +485,8 @@ def run_ours(args):
         kname = "k_force3d+k_lb3d+k_phi3d" if variant == "split3" else "k_march3d"
     else:
         kname = {"march": "k_march2d", "march2": "k_march2d_x2", "tile": "k_step2d"}[variant]
+    if iso:
+        kname += "_iso"                     # the ISO instantiation of the tile / fused kernel
     if kname == "k_march2d_x2" and prec == "fp64":
         kname = "k_march2d"                 # the packed kernel is FP32 only
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
