@@ -106,6 +106,22 @@ def test_stability_limit_follows_the_stencil(L, d):
     assert rc(stencil=1, Gamma=1.0) == -2
 
 
+def test_largest_lattice_accepted(L):
+    """Element indices of one population field stay below 2^31: 9 x pitch x ny
+    for 2D (pitch = nx rounded up to 32), 19 x pitch x ny x nz for 3D."""
+    n = C.c_size_t()
+
+    def rc(**kw):
+        g, w, p = _args(L, **kw)
+        return L.lib().lf_workspace_bytes(C.byref(g), C.byref(w), C.byref(p), C.byref(n))
+
+    assert rc(nx=16384, ny=14560, precision=1) == 0
+    assert rc(nx=16384, ny=14564, precision=1) == -1
+    assert rc(nx=16383, ny=14560, precision=1) == 0          # pitch 16384 as well
+    assert rc(d=3, nx=416, ny=416, nz=653, precision=1) == 0     # 19 * 416 * 416 * 653 < 2^31
+    assert rc(d=3, nx=416, ny=416, nz=654, precision=1) == -1
+
+
 def test_workspace_bytes_scale(L):
     g, w, p = _args(L)
     b64 = L.lf_workspace_bytes(g, w, p)

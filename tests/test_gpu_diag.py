@@ -69,3 +69,32 @@ def test_small64_run_statistics_match_oracle():
         assert abs(d["orient_s"] - s_ref) < 0.02, (k, d["orient_s"], s_ref)
         assert d["mach"] < 0.1
     sim.close()
+
+
+@pytest.mark.parametrize("xi,stencil", [(1e-3, "compact"), (0.1, "isotropic")])
+def test_prec1024_fp32_against_fp64_over_seeds(xi, stencil):
+    """1024 x 1024 at both fronts of the workload: the FP32 deviation-population
+    state against the FP64 state from the same eight seeds; the seed means of
+    the S(k) peak position and height agree within 2 % and the orientation
+    within 0.02 at every report (every 500 steps, 2000 steps).  The fast front
+    (xi = 0.1) runs with the isotropic stencils: with the compact ones the step
+    diverges within 500 steps at these parameters, in the oracle as well."""
+    seeds = range(1, 9)
+    sims = {p: [lf.Lattice(nx=1024, ny=1024, precision=p, xi=xi, seed=s, stencil=stencil) for s in seeds]
+            for p in ("fp32", "fp64")}
+    for k in range(4):
+        means = {}
+        for p, runs in sims.items():
+            ds = []
+            for sim in runs:
+                sim.step(500)
+                ds.append(sim.diag())
+            assert all(d["rc"] == 0 for d in ds)
+            means[p] = {key: float(np.mean([d[key] for d in ds])) for key in ("k_peak", "s_peak", "orient_s")}
+        a, b = means["fp32"], means["fp64"]
+        assert abs(a["k_peak"] / b["k_peak"] - 1) < 0.02, (k, a, b)
+        assert abs(a["s_peak"] / b["s_peak"] - 1) < 0.02, (k, a, b)
+        assert abs(a["orient_s"] - b["orient_s"]) < 0.02, (k, a, b)
+    for runs in sims.values():
+        for sim in runs:
+            sim.close()

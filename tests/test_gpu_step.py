@@ -284,6 +284,75 @@ def test_full_size_one_step_fp32():
     sim.close()
 
 
+def _sampled_window_parity(sim, d, okw, centres, half=8):
+    """One step of `sim` checked on sub-lattices: around each sampled centre
+    (x0 in 2D, (x0, y0) in 3D) the oracle steps a 2*half-wide window, periodic
+    along x (and y), over the whole wall-normal extent.  The step reaches 4 sites
+    (phi -> psi -> lam, grad psi -> P -> F -> u -> div(phi u)), so the window's
+    own wrap cannot reach its core |x - x0| < half - 4, which is compared site by
+    site with the GPU step (FP32 tolerance)."""
+    torch_ = sim.torch
+    perm = perm_to_oracle(d)
+    before = {k: sim.get(k, device=True) for k in ("pop", "phi", "T")}
+    sim.step(1)
+    after = {k: sim.get(k, device=True) for k in ("pop", "phi", "T")}
+    nx, ny = sim.shape[-1], sim.shape[-2]
+    w = 2 * half
+    core = slice(half - 4, half + 4)
+    for c in centres:
+        ix = torch_.tensor([(c[0] - half + i) % nx for i in range(w)], device=sim.device)
+        iy = torch_.tensor([(c[1] - half + i) % ny for i in range(w)], device=sim.device) if d == 3 else None
+
+        def win(t):
+            t = torch_.index_select(t, t.dim() - 1, ix)
+            if d == 3:
+                t = torch_.index_select(t, t.dim() - 2, iy)
+            return t.cpu().numpy()
+
+        f0 = win(before["pop"])
+        fo = np.empty_like(f0)
+        for i, j in enumerate(perm):
+            fo[j] = f0[i]
+        shp = dict(nx=w, ny=w, nz=sim.shape[0]) if d == 3 else dict(nx=w, ny=ny)
+        cfg = O.make_cfg(d=d, **shp, **okw)
+        ref = O.step(O.State(cfg, fo, win(before["phi"]), win(before["T"])))
+        f1 = to_oracle_f(win(after["pop"]), d)
+        sel = (Ellipsis, core, core) if d == 3 else (Ellipsis, core)
+        for name, got, want in (("phi", win(after["phi"]), ref.phi), ("T", win(after["T"]), ref.T),
+                                ("f", f1, ref.f)):
+            assert relerr(got[sel], want[sel]) < 2e-6, (c, name, relerr(got[sel], want[sel]))
+
+
+def test_cube384_sampled_windows_fp32():
+    """The 384^3 FP32 workload in the launch configuration the benchmark times
+    (the three-pass step, seed 1): one step, checked on six 8 x 8 columns of all
+    384 planes against the oracle on 16 x 16 x 384 windows."""
+    kw = synth.WORKLOADS["cube384"]
+    sim = lf.Lattice(d=3, nx=384, ny=384, nz=384, precision="fp32", xi=kw["xi"], tau=kw["tau"], seed=1)
+    sim.step(3)            # leave the trivial initial populations
+    rng = np.random.default_rng(21)
+    centres = [tuple(int(v) for v in rng.integers(0, 384, 2)) for _ in range(5)] + [(0, 383)]
+    _sampled_window_parity(sim, 3, dict(xi=kw["xi"], tau=kw["tau"]), centres)
+    sim.close()
+
+
+def test_largest_2d_lattice_fp32():
+    """The largest 2D FP32 lattice the library accepts with 32-bit element
+    indices (9 x pitch x ny < 2^31: 16384 x 14563, 238.6 M sites), one step of
+    the default kernel checked on sampled 16-column windows of all rows, with the
+    wrap at x = 0 among them."""
+    nx, ny = 16384, 14563
+    assert 9 * nx * ny < 2 ** 31 <= 9 * nx * (ny + 1)
+    sim = lf.Lattice(nx=nx, ny=ny, precision="fp32", xi=0.01)
+    sim.step(2)
+    rng = np.random.default_rng(22)
+    centres = [(int(v),) for v in rng.integers(0, nx, 3)] + [(0,), (nx - 3,)]
+    _sampled_window_parity(sim, 2, dict(xi=0.01), centres)
+    d = sim.diag()
+    assert d["rc"] == 0 and abs(d["mass"] / (nx * ny) - 1) < 1e-6
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_checkpoint_resume_bit_identical(prec):
     a = lf.Lattice(nx=70, ny=37, precision=prec)

@@ -551,3 +551,35 @@ def test_mach_number_small_config0():
         s = D.sums(O.aux(st), st.phi)
         assert s["mach"] < 0.1
         assert np.isfinite(st.phi).all()
+
+
+# ------------------------------------------------------------ locality
+@pytest.mark.parametrize("d", [2, 3])
+def test_step_reaches_four_sites(d):
+    """One step reaches exactly 4 sites (phi -> psi -> lam, grad psi -> P -> F ->
+    u -> div(phi u)): stepping a 16-wide window of the state, periodic along the
+    in-plane axes, reproduces the full-lattice step bit for bit on its 8-wide
+    core, and not on the ring one site further out.  The full-size GPU parity
+    tests check sampled windows this way."""
+    shp = dict(nx=40, ny=36) if d == 2 else dict(nx=24, ny=20, nz=18)
+    st = O.run(O.init(O.make_cfg(d=d, xi=0.01, tau=0.8, **shp)), 30)
+    ref = O.step(st)
+    half, w = 8, 16
+    c = (21, 3)
+    ix = [(c[0] - half + i) % shp["nx"] for i in range(w)]
+    iy = [(c[1] - half + i) % shp["ny"] for i in range(w)]
+
+    def win(a):
+        a = np.take(a, ix, axis=-1)
+        return np.ascontiguousarray(np.take(a, iy, axis=-2) if d == 3 else a)
+
+    sub = dict(nx=w, ny=w, nz=shp["nz"]) if d == 3 else dict(nx=w, ny=shp["ny"])
+    r2 = O.step(O.State(O.make_cfg(d=d, xi=0.01, tau=0.8, **sub), win(st.f), win(st.phi), win(st.T)))
+
+    def sel(r):
+        s_ = slice(half - r, half + r)
+        return (Ellipsis, s_, s_) if d == 3 else (Ellipsis, s_)
+
+    for a, b in ((win(ref.phi), r2.phi), (win(ref.T), r2.T), (win(ref.f), r2.f)):
+        np.testing.assert_array_equal(a[sel(4)], b[sel(4)])
+    assert np.abs(win(ref.phi)[sel(5)] - r2.phi[sel(5)]).max() > 1e-8
