@@ -255,7 +255,7 @@ def run_surrogate(args):
     """Learned surrogate at 256 x 256: trajectories of the plain solver (an
     ensemble, xi log-uniform in [1e-4, 1]) -> (state, state K steps later)
     pairs; training on the tensor-core kernels; then the same number of steps
-    of a fresh run done plain-only and interleaved (surrogate windows judged by
+    of a fresh run done plain-only and interleaved (surrogate windows checked by
     plain shadow windows), time-to-solution and S(k) error compared."""
     import numpy as np
     import torch

@@ -42,11 +42,11 @@ typedef struct {
 typedef struct {
     int    windows_done;      /* windows completed (surrogate and plain)              */
     int    surrogate_windows; /* surrogate windows whose prediction was kept          */
-    int    shadow_checks;     /* surrogate windows judged by a plain shadow window    */
-    int    fallbacks;         /* judged windows replaced by the plain result          */
+    int    shadow_checks;     /* surrogate windows checked by a plain shadow window   */
+    int    fallbacks;         /* checked windows replaced by the plain result         */
     double max_phi_l2_err;    /* largest ||phi_sur - phi_plain|| / ||phi_plain||     */
     double max_sk_err;        /* largest relative error of S(k) peak position/height  */
-    double last_err;          /* error of the last judged window                      */
+    double last_err;          /* error of the last checked window                     */
     double t_surrogate_s;     /* device time in surrogate predictions                 */
     double t_shadow_s;        /* device time in shadow windows and comparisons        */
     double t_plain_s;         /* device time in plain windows                         */

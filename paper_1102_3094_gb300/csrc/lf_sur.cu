@@ -2,7 +2,7 @@
 // and backward passes built from the tensor-core convolutions of
 // lf_sur_conv.cu, MSE loss, Adam with FP32 master weights, and the run that
 // interleaves surrogate windows with plain steps of a context, with a plain
-// shadow window as judge and fallback.
+// shadow window as check and fallback.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -519,7 +519,7 @@ void lf_sur_destroy(lf_sur* s)
 
 // ===========================================================================
 // Interleaved run: surrogate windows of K steps alternate with plain windows;
-// a plain shadow window from the same state judges every shadow_every-th
+// a plain shadow window from the same state checks every shadow_every-th
 // surrogate window and replaces its result when the error is too large.
 // ===========================================================================
 namespace {
@@ -701,7 +701,7 @@ extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shado
             continue;
         }
         bool accept = true;
-        if (rc == LF_OK && (w / 2) % shadow_every == 0) {        // plain shadow window as judge
+        if (rc == LF_OK && (w / 2) % shadow_every == 0) {        // plain shadow window as the check
             cudaEventRecord(e0, st);
             rc = copy_state(ctx, shadow);
             if (rc == LF_OK) rc = lf_step(shadow, K);

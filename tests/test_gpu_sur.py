@@ -178,7 +178,7 @@ def test_interleaved_run_falls_back_to_plain():
     b = lf.Lattice(nx=NX, ny=NY, precision="fp32", xi=0.01, seed=9)
     a.step(100)
     b.step(100)
-    rep = sur.run(a, K, 6, 1, 1e-9)           # every surrogate window judged and rejected
+    rep = sur.run(a, K, 6, 1, 1e-9)           # every surrogate window checked and rejected
     b.step(6 * K)
     assert rep["windows_done"] == 6 and rep["shadow_checks"] == 3 and rep["fallbacks"] == 3
     assert a.step_count == b.step_count
