@@ -233,7 +233,7 @@ struct Force3x2 {
 };
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 1) k_force3d_x2(Geom g, Phys<float> p, StepIO<float> io, int H)
+__global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g, Phys<float> p, StepIO<float> io, int H)
 {
     using namespace march;
     using P3 = Force3x2<TX, TY>;
@@ -474,41 +474,64 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     const int xl = x == 0 ? nx - 1 : x - 1, xr = x + 1 == nx ? 0 : x + 1;
     const int64_t ryl = (int64_t)(y == 0 ? ny - 1 : y - 1) * pitch, ryr = (int64_t)(y + 1 == ny ? 0 : y + 1) * pitch;
     const R half = R(0.5);
-    const R* mu = io.mu;
-    const R* ph = io.phi_in;
-    const R* T = io.T_in;
-    const R* uz = io.u[2];
+    const R* __restrict__ mu = io.mu;
+    const R* __restrict__ ph = io.phi_in;
+    const R* __restrict__ T = io.T_in;
+    const R* __restrict__ ux = io.u[0];
+    const R* __restrict__ uy = io.u[1];
+    const R* __restrict__ uz = io.u[2];
+    R* __restrict__ phi_out = io.phi_out;
+    R* __restrict__ T_out = io.T_out;
     // plane index of the neighbour below / above: wrap (periodic) or the plane itself (walls)
     auto below = [&](int z) { return z == 0 ? (walls ? 0 : nz - 1) : z - 1; };
     auto above = [&](int z) { return z + 1 == nz ? (walls ? z : 0) : z + 1; };
     const bool hyd = p.hydro != 0;
+    // in-plane neighbours of plane z, loaded one plane ahead of their use so
+    // that two planes of loads are in flight per thread
+    struct Nb {
+        R mxl, mxr, myl, myr, txl, txr, tyl, tyr, gxl, gxr, gyl, gyr, pc;
+    };
+    auto load_nb = [&](int z) {
+        Nb v;
+        const int64_t pz = (int64_t)z * zs;
+        v.mxl = mu[pz + row + xl]; v.mxr = mu[pz + row + xr];
+        v.myl = mu[pz + ryl + x]; v.myr = mu[pz + ryr + x];
+        v.txl = T[pz + row + xl]; v.txr = T[pz + row + xr];
+        v.tyl = T[pz + ryl + x]; v.tyr = T[pz + ryr + x];
+        v.pc = ph[pz + row + x];
+        if (hyd) {
+            v.gxl = ph[pz + row + xl] * ux[pz + row + xl];
+            v.gxr = ph[pz + row + xr] * ux[pz + row + xr];
+            v.gyl = ph[pz + ryl + x] * uy[pz + ryl + x];
+            v.gyr = ph[pz + ryr + x] * uy[pz + ryr + x];
+        } else {
+            v.gxl = v.gxr = v.gyl = v.gyr = R(0);
+        }
+        return v;
+    };
     int64_t o = below(za) * zs + row + x;
     R mu_d = mu[o], T_d = T[o], gz_d = hyd ? ph[o] * uz[o] : R(0);
     o = (int64_t)za * zs + row + x;
     R mu_c = mu[o], T_c = T[o], gz_c = hyd ? ph[o] * uz[o] : R(0);
+    Nb nb = load_nb(za);
     bool bad = false;
     for (int z = za; z < zb; ++z) {
-        const int64_t pz = (int64_t)z * zs;
-        const int64_t site = pz + row + x;
+        const int64_t site = (int64_t)z * zs + row + x;
         const int64_t ou = above(z) * zs + row + x;
         const R mu_u = mu[ou], T_u = T[ou], gz_u = hyd ? ph[ou] * uz[ou] : R(0);
-        const R lapmu = mu[pz + row + xl] + mu[pz + row + xr] + mu[pz + ryl + x] + mu[pz + ryr + x] + mu_u + mu_d
-                      - R(6) * mu_c;
+        const Nb nxt = load_nb(z + 1 < zb ? z + 1 : z);
+        const R lapmu = nb.mxl + nb.mxr + nb.myl + nb.myr + mu_u + mu_d - R(6) * mu_c;
         R div = 0;
         if (hyd) {
-            const R gxl = ph[pz + row + xl] * io.u[0][pz + row + xl];
-            const R gxr = ph[pz + row + xr] * io.u[0][pz + row + xr];
-            const R gyl = ph[pz + ryl + x] * io.u[1][pz + ryl + x];
-            const R gyr = ph[pz + ryr + x] * io.u[1][pz + ryr + x];
             R up = gz_u, dn = gz_d;
             if (walls) {                                   // no flux through the walls
                 if (z == 0) dn = -gz_c;
                 if (z == nz - 1) up = -gz_c;
             }
-            div = half * (gxr - gxl) + half * (gyr - gyl) + half * (up - dn);
+            div = half * (nb.gxr - nb.gxl) + half * (nb.gyr - nb.gyl) + half * (up - dn);
         }
-        const R phn = ph[site] - div + p.Gamma * lapmu;
-        io.phi_out[site] = phn;
+        const R phn = nb.pc - div + p.Gamma * lapmu;
+        phi_out[site] = phn;
         R Tn = T_c;
         if (p.t_update) {
             if (walls && g.t_mode == LF_TWALL_LAYERS && (z == 0 || z == nz - 1)) {
@@ -519,15 +542,15 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
                     if (z == 0) td = R(2) * p.T_w - T_c;
                     if (z == nz - 1) tu = R(2) * p.T_w - T_c;
                 }
-                Tn = T_c + p.dxi * (T[pz + row + xl] + T[pz + row + xr] + T[pz + ryl + x] + T[pz + ryr + x] + tu + td -
-                                    R(6) * T_c);
+                Tn = T_c + p.dxi * (nb.txl + nb.txr + nb.tyl + nb.tyr + tu + td - R(6) * T_c);
             }
         }
-        io.T_out[site] = Tn;
+        T_out[site] = Tn;
         bad |= !isfinite(phn) || !isfinite(Tn);
         mu_d = mu_c; mu_c = mu_u;
         T_d = T_c; T_c = T_u;
         gz_d = gz_c; gz_c = gz_u;
+        nb = nxt;
     }
     if (bad) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
@@ -569,7 +592,7 @@ cudaError_t launch_force_x2(const Geom& g, const Phys<float>& p, const StepIO<fl
     }
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int H = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;     // planes per lane
-    if (H <= 0) {   // about eight waves of one CTA per SM, lanes of at least 16 planes
+    if (H <= 0) {   // about eight CTAs per SM (two resident), lanes of at least 16 planes
         const int want = (8 * 152 + tiles - 1) / tiles;
         H = (g.nz + 2 * want - 1) / (2 * want);
         if (H < 16) H = 16;
