@@ -34,7 +34,10 @@
  *   - Work is enqueued on params.stream (a cudaStream_t; 0 = legacy default
  *     stream).  lf_step returns without waiting; lf_fields, lf_fields_set,
  *     lf_diag, lf_save and lf_load wait for the stream, with a time limit
- *     (LF_ETIMEOUT).
+ *     (LF_ETIMEOUT: 120 s, or LF_WAIT_TIMEOUT_S seconds from the
+ *     environment).  After LF_ETIMEOUT the context stays usable, but a copy
+ *     to or from a device or pinned caller buffer may still be in flight on
+ *     the stream: synchronize the stream before reusing that buffer.
  */
 #ifndef LF_H
 #define LF_H

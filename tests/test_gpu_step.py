@@ -373,6 +373,28 @@ def test_checkpoint_resume_bit_identical(prec):
     b.close()
 
 
+def test_bounded_wait_reports_timeout_and_recovers(monkeypatch):
+    """A blocking call whose wait for the stream runs out returns LF_ETIMEOUT
+    (here: a 1 us limit behind ~100 queued steps) without breaking the context;
+    after the stream drains, the same call succeeds and sees the finished state."""
+    sim = lf.Lattice(nx=2048, ny=2048, precision="fp32", xi=1e-3)
+    sim.step(1)
+    torch.cuda.synchronize()
+    out = torch.empty(sim.shape, dtype=torch.float32, device=sim.device)
+    monkeypatch.setenv("LF_WAIT_TIMEOUT_S", "1e-6")
+    sim.step(100)
+    with pytest.raises(lf.LFError) as ei:
+        lf.lf_fields(sim.ctx, lf.FIELDS["phi"], out.data_ptr(), out.numel() * 4, True)
+    assert ei.value.code == lf.LF_ETIMEOUT
+    monkeypatch.delenv("LF_WAIT_TIMEOUT_S")
+    torch.cuda.synchronize()
+    a = sim.get("phi", "fp32")
+    lf.lf_fields(sim.ctx, lf.FIELDS["phi"], out.data_ptr(), out.numel() * 4, True)
+    np.testing.assert_array_equal(out.cpu().numpy(), a)
+    assert lf.lf_step_count(sim.ctx) == 101 and sim.diag()["rc"] == 0
+    sim.close()
+
+
 def test_nonfinite_is_reported():
     sim = lf.Lattice(nx=40, ny=24, precision="fp32")
     phi = sim.get("phi", "fp32")
