@@ -47,6 +47,24 @@ def ranks():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over all ranks (every rank gets it); x itself
+    without an initialised process group of more than one rank."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput in millions of units per second: the units of all
+    ranks (each rank runs its own replica) over the slowest rank's time."""
+    return 1e-6 * units_per_rank * steps * world / seconds
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -185,6 +203,9 @@ def run_ensemble(args):
     rank, world, local = ranks()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:                       # one replica of the whole ensemble per GPU
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
     stream = torch.cuda.Stream(dev)
     members = synth.ensemble_members()
     sites = sum(m["nx"] * m["ny"] for m in members)
@@ -215,19 +236,19 @@ def run_ensemble(args):
             torch.cuda.synchronize(dev)
             te = time.time()
         clk.window(tb, te + 0.15)
-        t_batch = ev[0].elapsed_time(ev[1]) / 1e3
-        t_seq = ev[2].elapsed_time(ev[3]) / 1e3
+        t_batch = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, dev)
+        t_seq = max_over_ranks(ev[2].elapsed_time(ev[3]) / 1e3, dev)
         identical, nonfinite = True, 0
         for r in range(len(members)):
             a = ens.run(r).get("phi", "fp32")
             b = singles[r].get("phi", "fp32")
             identical &= bool(np.array_equal(a, b, equal_nan=True))
             nonfinite += int(not np.isfinite(a).all())
-    value = 1e-6 * sites * args.steps / t_batch
+    value = job_rate(sites, args.steps, world, t_batch)
     peak, peak_kind = peaks()
     achieved = 88 * sites * args.steps / t_batch / 1e9
     line = {
-        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ens96: 96 independent 2D runs, 24 each of 128^2, 256^2, 384^2, 512^2, xi "
@@ -244,10 +265,16 @@ def run_ensemble(args):
                                           "method itself at these parameters (the CPU oracle diverges the same way)"},
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if world > 1:
+        line["config"]["parallelism"] = f"replicas x{world} (the whole ensemble on every GPU)"
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     ens.close()
     for s_ in singles:
         s_.close()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
     return 0
 
 
@@ -262,8 +289,11 @@ def run_surrogate(args):
 
     from paper_1102_3094_gb300 import lf
 
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    rank, world, local = ranks()
+    if rank != 0:
+        return 0        # a single-GPU workload: the other ranks of a multi-GPU launch have no work
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     NY = NX = 256
     K = 50
@@ -464,13 +494,9 @@ def run_ours(args):
         t_end = time.time()
     clk.window(t_begin, t_end + 0.15)
     times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = sum(times_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(times_ms) / 1e3, dev)
     dg = sim.diag()
-    value = 1e-6 * N * args.steps * world / total_s
+    value = job_rate(N, args.steps, world, total_s)
     ms = 1e3 * total_s / args.steps
     bps = BYTES_PER_SITE[(prec, d)]
     peak, peak_kind = peaks()
@@ -517,12 +543,8 @@ def run_ours(args):
             lf.lf_fields_set(sim.ctx, lf.FIELDS["T"], T_h.data_ptr(), T_h.numel() * es, False)
             lf.lf_step(sim.ctx, 1)
             lf.lf_fields(sim.ctx, lf.FIELDS["phi"], out_h.data_ptr(), out_h.numel() * es, False)
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": 1e-6 * N * args.e2e_steps * world / el, "unit": "MLUPS",
+        el = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": job_rate(N, args.e2e_steps, world, el), "unit": "MLUPS",
                "h2d_bytes_per_step": (sim.Q + 2) * N * es, "d2h_bytes_per_step": N * es,
                "steps": args.e2e_steps,
                "what": "per step: lf_fields_set of f, phi, T from pinned host, lf_step(1), lf_fields of phi to "
