@@ -395,6 +395,40 @@ def test_bounded_wait_reports_timeout_and_recovers(monkeypatch):
     sim.close()
 
 
+def test_checkpoint_failures_leave_the_context_intact():
+    """lf_save to a path that cannot be written, lf_load of a checkpoint of
+    another lattice, a truncated file and a file with a wrong header all return
+    LF_EIO; the context keeps its state and steps on."""
+    a = lf.Lattice(nx=40, ny=24, precision="fp32")
+    a.step(3)
+    phi0 = a.get("phi", "fp32")
+    with tempfile.TemporaryDirectory() as tmp:
+        with pytest.raises(lf.LFError) as ei:
+            a.save(os.path.join(tmp, "no_such_dir", "c.lfck"))
+        assert ei.value.code == lf.LF_EIO
+        good = os.path.join(tmp, "good.lfck")
+        a.save(good)
+        other = lf.Lattice(nx=40, ny=26, precision="fp32")
+        other_path = os.path.join(tmp, "other.lfck")
+        other.save(other_path)
+        other.close()
+        raw = open(good, "rb").read()
+        trunc = os.path.join(tmp, "trunc.lfck")
+        open(trunc, "wb").write(raw[: len(raw) // 2])
+        bad_magic = os.path.join(tmp, "magic.lfck")
+        open(bad_magic, "wb").write(b"XXXXXXXX" + raw[8:])
+        for path in (other_path, trunc, bad_magic, os.path.join(tmp, "missing.lfck")):
+            with pytest.raises(lf.LFError) as ei:
+                a.load(path)
+            assert ei.value.code == lf.LF_EIO, path
+            np.testing.assert_array_equal(a.get("phi", "fp32"), phi0)
+        a.load(good)
+        np.testing.assert_array_equal(a.get("phi", "fp32"), phi0)
+    a.step(2)
+    assert a.diag()["rc"] == 0 and lf.lf_step_count(a.ctx) == 5
+    a.close()
+
+
 def test_nonfinite_is_reported():
     sim = lf.Lattice(nx=40, ny=24, precision="fp32")
     phi = sim.get("phi", "fp32")
