@@ -282,9 +282,9 @@ int lf_set_t_solver(lf_ctx* ctx, int solver);
  *     isotropic to fourth order in the wavenumber (Thampi et al., J. Comput.
  *     Phys. 234 (2013) 1).  Applies to psi, lam, grad phi, grad psi, F, the
  *     flux divergence, lap mu and lap T; the wall images are those of the
- *     compact stencils, applied to the diagonal neighbours too.  Runs the
- *     LF_VARIANT_TILE kernel (2D) or the fused plane march (3D) whatever
- *     variant is set.  Its largest Laplacian eigenvalue is 16/3 in 2D and 3D
+ *     compact stencils, applied to the diagonal neighbours too.  In 2D it
+ *     runs the LF_VARIANT_TILE kernel whatever variant is set; in 3D the
+ *     variant set (three passes by default, or the fused plane march).  Its largest Laplacian eigenvalue is 16/3 in 2D and 3D
  *     (8 and 12 for the compact stencils), which the stability check of
  *     lf_create uses.
  * Returns LF_EINVAL for an unknown stencil or an ensemble member, and LF_EUNSTABLE if

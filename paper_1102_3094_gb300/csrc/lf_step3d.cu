@@ -27,6 +27,7 @@
 // beyond a wall is replaced by the image of the wall plane itself (g_z odd,
 // the halfway temperature ghost 2 T_w - T).
 #include "lf_internal.cuh"
+#include "lf_iso3.cuh"
 
 namespace lf {
 
@@ -59,34 +60,6 @@ __device__ __forceinline__ void cp_async3(void* dst, const void* src)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-// Isotropic 19-point operators on three planes (below, at, above) of a
-// row-major region of row length W, centre c.
-template <typename R, int W>
-__device__ __forceinline__ R lap19(const R* dn, const R* md, const R* up, int c)
-{
-    const R nn = md[c - 1] + md[c + 1] + md[c - W] + md[c + W] + dn[c] + up[c];
-    const R ed = (md[c - W - 1] + md[c - W + 1] + md[c + W - 1] + md[c + W + 1])
-               + (dn[c - 1] + dn[c + 1] + dn[c - W] + dn[c + W])
-               + (up[c - 1] + up[c + 1] + up[c - W] + up[c + W]);
-    return (R(2) * nn + ed - R(24) * md[c]) * R(1.0 / 6.0);
-}
-
-template <typename R, int W>
-__device__ __forceinline__ R grad19(const R* dn, const R* md, const R* up, int c, int axis)
-{
-    R v;
-    if (axis == 0)
-        v = R(2) * (md[c + 1] - md[c - 1]) + (md[c + W + 1] - md[c + W - 1]) + (md[c - W + 1] - md[c - W - 1])
-          + (up[c + 1] - up[c - 1]) + (dn[c + 1] - dn[c - 1]);
-    else if (axis == 1)
-        v = R(2) * (md[c + W] - md[c - W]) + (md[c + W + 1] - md[c - W + 1]) + (md[c + W - 1] - md[c - W - 1])
-          + (up[c + W] - up[c - W]) + (dn[c + W] - dn[c - W]);
-    else
-        v = R(2) * (up[c] - dn[c]) + (up[c + 1] - dn[c + 1]) + (up[c - 1] - dn[c - 1])
-          + (up[c + W] - dn[c + W]) + (up[c - W] - dn[c - W]);
-    return v * R(1.0 / 12.0);
 }
 
 template <typename R, int TX, int TY, bool ISO = false>
@@ -572,7 +545,8 @@ __global__ void k_tsub3d_iso(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __
 template <typename R>
 cudaError_t launch_step3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
-    if (g.stencil == LF_STENCIL_ISOTROPIC) {           // the fused march only
+    if (!aux && g.variant == LF_VARIANT_SPLIT3) return launch_split3d<R>(g, p, io, s);
+    if (g.stencil == LF_STENCIL_ISOTROPIC) {
         if constexpr (sizeof(R) == 4)
             return aux ? launch_cfg3<R, 32, 8, 256, true, true>(g, p, io, s)
                        : launch_cfg3<R, 32, 8, 256, false, true>(g, p, io, s);
@@ -580,7 +554,6 @@ cudaError_t launch_step3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, 
             return aux ? launch_cfg3<R, 16, 16, 256, true, true>(g, p, io, s)
                        : launch_cfg3<R, 16, 16, 256, false, true>(g, p, io, s);
     }
-    if (!aux && g.variant == LF_VARIANT_SPLIT3) return launch_split3d<R>(g, p, io, s);
     if constexpr (sizeof(R) == 4) {
         return aux ? launch_cfg3<R, 32, 8, 256, true, false>(g, p, io, s)
                    : launch_cfg3<R, 32, 8, 256, false, false>(g, p, io, s);

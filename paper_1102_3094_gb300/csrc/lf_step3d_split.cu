@@ -16,8 +16,15 @@
 // consumer needs: psi on the tile + 2, P on the tile + 1, F and mu on the
 // tile, against + 3 / + 2 / + 1 in the fused kernel, and no population is
 // read outside its own site.
+//
+// With the isotropic stencils (ISO) pass A keeps three planes of psi and of
+// all six components of P in shared memory (the 19-point operators reach the
+// in-plane neighbours of the planes above and below) and takes a barrier
+// after each of the psi and P stages, and pass C is k_phi3d_iso, one thread
+// per site.
 #include "lf_internal.cuh"
 #include "lf_march2d_x2.cuh"      // packed FP32x2 helpers
+#include "lf_iso3.cuh"
 
 namespace lf {
 
@@ -56,16 +63,19 @@ __device__ __forceinline__ void cp_async_s(void* dst, const void* src)
 // along z.  Shared memory holds in-plane neighbours only: a ring of phi planes
 // (tile + 3), the psi plane and the five in-plane components of P (tile + 1),
 // each of the last two double-buffered; values along z stay in registers.
-template <typename R, int TX, int TY>
+template <typename R, int TX, int TY, bool ISO = false>
 struct Force3 {
     static constexpr int CW = TX + 4, CH = TY + 4, NTH = CW * CH;   // threads = columns of the psi region
     static constexpr int W3 = TX + 6, H3 = TY + 6, A3 = W3 * H3;    // phi (r = 3)
     static constexpr int A2 = CW * CH;                              // psi (r = 2)
-    static constexpr int NPHI = 4;                                  // phi planes k-2 .. k+1
+    static constexpr int NPHI = ISO ? 5 : 4;                        // phi planes k-2 (k-3 with ISO) .. k+1
+    static constexpr int NPSI = ISO ? 3 : 2;                        // psi planes
+    static constexpr int NPC = ISO ? 6 : 5;                         // stored components of P
+    static constexpr int NPP = ISO ? 3 : 2;                         // planes of P
     static constexpr int PHI = 0;
-    static constexpr int PSI = PHI + NPHI * A3;                     // 2 planes
-    static constexpr int PP = PSI + 2 * A2;                         // 5 comps x 2 planes, psi-region indexing
-    static constexpr int TOTAL = PP + 10 * A2;
+    static constexpr int PSI = PHI + NPHI * A3;
+    static constexpr int PP = PSI + NPSI * A2;                      // [plane][comp][A2], psi-region indexing
+    static constexpr int TOTAL = PP + NPC * NPP * A2;
     static constexpr size_t MAPS = sizeof(R) * TOTAL;
     static constexpr size_t BYTES = MAPS + sizeof(int) * (W3 + H3);
 };
@@ -76,16 +86,16 @@ struct Force3 {
 //   F = -d_a P_ab                       on plane k - 3 (r = 0, stored)
 // run one plane apart; each stage reads only what earlier iterations wrote,
 // so one barrier per plane orders everything.
-template <typename R, int TX, int TY>
-__global__ void __launch_bounds__(Force3<R, TX, TY>::NTH) k_force3d(Geom g, Phys<R> p, StepIO<R> io, int Hz)
+template <typename R, int TX, int TY, bool ISO = false>
+__global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g, Phys<R> p, StepIO<R> io, int Hz)
 {
-    using P3 = Force3<R, TX, TY>;
+    using P3 = Force3<R, TX, TY, ISO>;
     constexpr int W3 = P3::W3, CW = P3::CW, A3 = P3::A3, A2 = P3::A2, NTH = P3::NTH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
     R* sphi = sm + P3::PHI;
     R* spsi = sm + P3::PSI;
-    R* sP = sm + P3::PP;      // [plane parity][comp xx, xy, yy, xz, yz][A2]
+    R* sP = sm + P3::PP;      // [plane slot][comp xx, xy, yy, xz, yz (, zz with ISO)][A2]
     int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);   // x0 - 3 + i -> storage column
     int* rowmap = colmap + W3;                                   // y0 - 3 + j -> storage row
 
@@ -136,6 +146,68 @@ __global__ void __launch_bounds__(Force3<R, TX, TY>::NTH) k_force3d(Geom g, Phys
     R xzA = 0, xzB = 0, xzC = 0, yzA = 0, yzB = 0, yzC = 0, zzA = 0, zzB = 0, zzC = 0;   // P_az at k-2 .. k-4
     R Tq0 = Tload(kbeg), Tq1 = 0, Tq2 = 0, Tq3 = 0;   // T(k) .. T(k-3)
 
+    // The isotropic iteration: psi(k-1), barrier, lam / P / mu (k-2), barrier,
+    // F (k-3); shared rings of three psi and three P planes, phi(k-3) kept in
+    // the phi ring.  Register windows carry only T.
+    auto ring3 = [&](int z) { return (z - kbeg + 3 * 8) % 3; };
+    auto stage_iso = [&](int k, const R* pk, const R* p1, const R* p2) {
+        const R* p3 = sphi + slot(k - 3) * A3;
+        spsi[ring3(k - 1) * A2 + c2] = lap19<R, W3>(p2, p1, pk, c3);
+        __syncthreads();
+        const int z2 = k - 2;
+        if (in1 && z2 >= z0 - 1 && z2 <= z1) {
+            const R* psd = spsi + ring3(z2 - 1) * A2;
+            const R* ps0 = spsi + ring3(z2) * A2;
+            const R* psu = spsi + ring3(z2 + 1) * A2;
+            const R ph = p2[c3], psi = ps0[c2];
+            const R lam = lap19<R, CW>(psd, ps0, psu, c2);
+            const R av = (Tq2 - p.Tc) * p.inv_Tc;
+            if (own && z2 >= z0 && z2 < z1) {
+                const R mu = av * ph + p.b * ph * ph * ph - p.kappa * psi + p.c * lam;
+                bad |= !isfinite(mu);
+                io.mu[(int64_t)z2 * zs + (int64_t)gy * pitch + gx] = mu;
+            }
+            if (p.hydro) {
+                const R d0 = grad19<R, W3>(p3, p2, p1, c3, 0);
+                const R d1 = grad19<R, W3>(p3, p2, p1, c3, 1);
+                const R d2 = grad19<R, W3>(p3, p2, p1, c3, 2);
+                const R s0 = grad19<R, CW>(psd, ps0, psu, c2, 0);
+                const R s1 = grad19<R, CW>(psd, ps0, psu, c2, 1);
+                const R s2 = grad19<R, CW>(psd, ps0, psu, c2, 2);
+                const R ph2 = ph * ph;
+                const R iso = av * ph2 * half + R(0.75) * p.b * ph2 * ph2
+                            - p.kappa * (ph * psi + half * (d0 * d0 + d1 * d1 + d2 * d2))
+                            + p.c * (ph * lam + half * psi * psi + d0 * s0 + d1 * s1 + d2 * s2);
+                R* P = sP + ring3(z2) * 6 * A2;
+                P[0 * A2 + c2] = iso + p.kappa * d0 * d0 - R(2) * p.c * d0 * s0;
+                P[1 * A2 + c2] = p.kappa * d0 * d1 - p.c * (d0 * s1 + d1 * s0);
+                P[2 * A2 + c2] = iso + p.kappa * d1 * d1 - R(2) * p.c * d1 * s1;
+                P[3 * A2 + c2] = p.kappa * d0 * d2 - p.c * (d0 * s2 + d2 * s0);
+                P[4 * A2 + c2] = p.kappa * d1 * d2 - p.c * (d1 * s2 + d2 * s1);
+                P[5 * A2 + c2] = iso + p.kappa * d2 * d2 - R(2) * p.c * d2 * s2;
+            }
+        }
+        __syncthreads();
+        const int z3 = k - 3;
+        if (p.hydro && own && z3 >= z0 && z3 < z1) {
+            // F_b = -d_a P_ab on the planes z3 - 1, z3, z3 + 1 (written in the last three iterations)
+            const R* Pd = sP + ring3(z3 - 1) * 6 * A2;
+            const R* P0 = sP + ring3(z3) * 6 * A2;
+            const R* Pu = sP + ring3(z3 + 1) * 6 * A2;
+            auto D = [&](int comp, int axis) {
+                return grad19<R, CW>(Pd + comp * A2, P0 + comp * A2, Pu + comp * A2, c2, axis);
+            };
+            const R Fx = -(D(0, 0) + D(1, 1) + D(3, 2));
+            const R Fy = -(D(1, 0) + D(2, 1) + D(4, 2));
+            const R Fz = -(D(3, 0) + D(4, 1) + D(5, 2));
+            const int64_t site = (int64_t)z3 * zs + (int64_t)gy * pitch + gx;
+            io.F[0][site] = Fx;
+            io.F[1][site] = Fy;
+            io.F[2][site] = Fz;
+        }
+        Tq3 = Tq2; Tq2 = Tq1; Tq1 = Tq0;
+    };
+
     fetch(kbeg);
     for (int k = kbeg; k <= kend; ++k) {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -148,6 +220,11 @@ __global__ void __launch_bounds__(Force3<R, TX, TY>::NTH) k_force3d(Geom g, Phys
         const R phk = pk[c3];
 
         // ---- plane k-1: psi (r = 2) ---------------------------------------------
+        if constexpr (ISO) {
+            stage_iso(k, pk, p1, p2);
+            Tq0 = Tnext;
+            continue;
+        }
         const R psi_new = p1[c3 - 1] + p1[c3 + 1] + p1[c3 - W3] + p1[c3 + W3] + phm2 + phk - R(6) * phm1;
         spsi[((k - 1 - kbeg) & 1) * A2 + c2] = psi_new;
 
@@ -555,11 +632,137 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     if (bad) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
-template <typename R, int TX, int TY>
+// Pass C with the isotropic 19-point stencils.  A 32 x 8 block marches kZC
+// planes; a ring of four shared planes holds mu, T and the fluxes g = phi u on
+// the tile grown by one site (planes z - 1, z, z + 1 in use, z + 2 arriving:
+// each thread loads its share of plane z + 2 into registers before the
+// arithmetic of plane z and stores it afterwards, so one barrier per plane
+// orders the ring).  A plane beyond a wall holds the wall plane itself; the
+// rules apply when it is read: mu, g_x, g_y even, g_z odd, T the halfway ghost
+// 2 T_w - T (with held wall planes the interior never reaches past them).
+constexpr int kIsoTW = 34, kIsoTA = kIsoTW * 10, kIsoNF = 5;   // tile + 1 (32 x 8 + halo); mu, T, g_x, g_y, g_z
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> io)
+{
+    constexpr int TW = kIsoTW, TA = kIsoTA, NF = kIsoNF;
+    extern __shared__ __align__(16) unsigned char smem_iso[];
+    R (*sm)[NF][TA] = reinterpret_cast<R (*)[NF][TA]>(smem_iso);     // [4 slots][NF][TA]
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
+    const int64_t zs = (int64_t)ny * pitch;
+    const bool hyd = p.hydro != 0;
+    const R* __restrict__ mu = io.mu;
+    const R* __restrict__ ph = io.phi_in;
+    const R* __restrict__ T = io.T_in;
+    const R* __restrict__ ux = io.u[0];
+    const R* __restrict__ uy = io.u[1];
+    const R* __restrict__ uz = io.u[2];
+    // storage plane of logical plane zl: the wall plane beyond a wall, else periodic
+    auto zmap = [&](int zl) -> int64_t {
+        int z = zl;
+        if (walls) z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
+        else z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        return (int64_t)z * zs;
+    };
+    // the (up to) two tile positions of this thread and their in-plane offsets
+    int64_t off[2];
+    bool has[2];
+    for (int i = 0; i < 2; ++i) {
+        const int q = t + 256 * i;
+        has[i] = q < TA;
+        const int ly = has[i] ? q / TW : 0, lx = has[i] ? q - ly * TW : 0;
+        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        off[i] = (int64_t)gy * pitch + gx;
+    }
+    R v[2][NF];
+    auto fetch = [&](int zl) {
+        const int64_t pz = zmap(zl);
+        for (int i = 0; i < 2; ++i) {
+            if (!has[i]) continue;
+            const int64_t o = pz + off[i];
+            v[i][0] = mu[o];
+            v[i][1] = T[o];
+            const R f = ph[o];
+            v[i][2] = hyd ? f * ux[o] : R(0);
+            v[i][3] = hyd ? f * uy[o] : R(0);
+            v[i][4] = hyd ? f * uz[o] : R(0);
+        }
+    };
+    auto put = [&](int zl) {
+        const int sl = (zl - za + 4) & 3;
+        for (int i = 0; i < 2; ++i)
+            if (has[i])
+                for (int f = 0; f < NF; ++f) sm[sl][f][t + 256 * i] = v[i][f];
+    };
+    fetch(za - 1); put(za - 1);
+    fetch(za); put(za);
+    fetch(za + 1); put(za + 1);
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const int c = (ty + 1) * TW + tx + 1;
+    bool bad = false;
+    for (int z = za; z < zb; ++z) {
+        __syncthreads();                                    // planes z - 1 .. z + 1 are in the ring
+        if (z + 2 < zb + 1) fetch(z + 2);                   // in flight during the arithmetic below
+        if (act) {
+            const bool lo = walls && z == 0, hi = walls && z == nz - 1;
+            const int sd = (z - 1 - za + 4) & 3, s0 = (z - za) & 3, su = (z + 1 - za) & 3;
+            // 19-point sum with the plane below / above transformed (ghosts and odd parity)
+            auto lapT = [&](const R* dn, const R* md, const R* up, R sd_, R ad, R su_, R au) {
+                auto d = [&](int o) { return sd_ * dn[c + o] + ad; };
+                auto u = [&](int o) { return su_ * up[c + o] + au; };
+                const R nn = md[c - 1] + md[c + 1] + md[c - TW] + md[c + TW] + d(0) + u(0);
+                const R ed = (md[c - TW - 1] + md[c - TW + 1] + md[c + TW - 1] + md[c + TW + 1])
+                           + (d(-1) + d(1) + d(-TW) + d(TW)) + (u(-1) + u(1) + u(-TW) + u(TW));
+                return (R(2) * nn + ed - R(24) * md[c]) * R(1.0 / 6.0);
+            };
+            const R lapmu = lap19<R, TW>(sm[sd][0], sm[s0][0], sm[su][0], c);
+            R div = 0;
+            if (hyd) {
+                const R* gzd = sm[sd][4];
+                const R* gzu = sm[su][4];
+                const R fd = lo ? R(-1) : R(1), fu = hi ? R(-1) : R(1);
+                auto zd = [&](int o) { return fd * gzd[c + o]; };
+                auto zu = [&](int o) { return fu * gzu[c + o]; };
+                const R dz = (R(2) * (zu(0) - zd(0)) + (zu(1) - zd(1)) + (zu(-1) - zd(-1)) + (zu(TW) - zd(TW))
+                              + (zu(-TW) - zd(-TW))) * R(1.0 / 12.0);
+                div = grad19<R, TW>(sm[sd][2], sm[s0][2], sm[su][2], c, 0)
+                    + grad19<R, TW>(sm[sd][3], sm[s0][3], sm[su][3], c, 1) + dz;
+            }
+            const int64_t site = (int64_t)z * zs + (int64_t)y * pitch + x;
+            const R phn = ph[site] - div + p.Gamma * lapmu;
+            io.phi_out[site] = phn;
+            const R Tc0 = sm[s0][1][c];
+            R Tn = Tc0;
+            if (p.t_update) {
+                if (walls && g.t_mode == LF_TWALL_LAYERS && (z == 0 || z == nz - 1)) {
+                    Tn = p.T_w;
+                } else {
+                    const bool gh = walls && g.t_mode == LF_TWALL_HALFWAY;
+                    const R tw2 = R(2) * p.T_w;
+                    const R lt = lapT(sm[sd][1], sm[s0][1], sm[su][1], (gh && lo) ? R(-1) : R(1),
+                                      (gh && lo) ? tw2 : R(0), (gh && hi) ? R(-1) : R(1), (gh && hi) ? tw2 : R(0));
+                    Tn = Tc0 + p.dxi * lt;
+                }
+            }
+            io.T_out[site] = Tn;
+            bad |= !isfinite(phn) || !isfinite(Tn);
+        }
+        if (z + 2 < zb + 1) put(z + 2);                     // slot of plane z - 2, read by nobody now
+    }
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
+template <typename R, int TX, int TY, bool ISO = false>
 cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
-    using P3 = Force3<R, TX, TY>;
-    auto kern = k_force3d<R, TX, TY>;
+    using P3 = Force3<R, TX, TY, ISO>;
+    auto kern = k_force3d<R, TX, TY, ISO>;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P3::BYTES);
@@ -609,7 +812,10 @@ template <typename R>
 cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
     cudaError_t e;
-    if constexpr (sizeof(R) == 4) {
+    const bool iso = g.stencil == LF_STENCIL_ISOTROPIC;
+    if (iso) {
+        e = launch_force<R, 28, 12, true>(g, p, io, s);
+    } else if constexpr (sizeof(R) == 4) {
         // (param >> 16): 0 = two z-lanes in packed FP32x2, 1 / 2 = one lane on 60x4 / 28x12 tiles
         const int sel = g.tune >> 16;
         e = sel == 1 ? launch_force<R, 60, 4>(g, p, io, s)
@@ -625,7 +831,18 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kZC - 1) / kZC);
-    k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io);
+    if (iso) {
+        constexpr size_t bytes = sizeof(R) * 4 * kIsoNF * kIsoTA;
+        static bool attr_set = false;
+        if (!attr_set) {
+            if ((e = cudaFuncSetAttribute(k_phi3d_iso<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) !=
+                cudaSuccess)
+                return e;
+            attr_set = true;
+        }
+        k_phi3d_iso<R><<<gc, 256, bytes, s>>>(g, p, io);
+    } else
+        k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io);
     return cudaGetLastError();
 }
 
