@@ -184,11 +184,12 @@ def test_aux_and_step_parity_3d(case, prec, variant):
     _check_aux_and_step_3d(sim, st, prec)
 
 
-@pytest.mark.parametrize("variant", ["split3", "fused"])
+@pytest.mark.parametrize("variant", ["split3", "split3-z3", "fused"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
 def test_isotropic_stencil_parity_3d(case, prec, variant):
-    """Isotropic 19-point stencils (runs the fused plane march whatever the variant)."""
+    """Isotropic 19-point stencils: the three-pass step (with segments of 3
+    planes as well) and the fused plane march."""
     sim, cfg, st = make_pair(case, prec, stencil="isotropic")
     sim.set_variant(*VARIANTS3[variant])
     _check_aux_and_step_3d(sim, st, prec)
