@@ -54,9 +54,8 @@ def make_pair(case, prec, seed=11, variant="march", stencil="compact"):
     kw = dict(synth.BASE)
     kw.update(case)
     d = kw.get("d", 2)
-    sim = lf.Lattice(precision=prec, **{k: v for k, v in kw.items() if k not in ("d",)}, d=d)
+    sim = lf.Lattice(precision=prec, **{k: v for k, v in kw.items() if k not in ("d",)}, d=d, stencil=stencil)
     sim.set_variant(*VARIANTS[variant])
-    sim.set_stencil(stencil)
     cfg = O.make_cfg(stencil=int(stencil == "isotropic"), d=d, nx=kw["nx"], ny=kw["ny"], nz=kw.get("nz", 1), walls=kw["walls"],
                      t_wall_mode=kw["t_wall_mode"], hydro=kw["hydro"], b=kw["b"], kappa=kw["kappa"],
                      c=kw["c"], Gamma=kw["Gamma"], Tc=kw["Tc"], T0=kw["T0"], T_w=kw["T_w"], xi=kw["xi"],
@@ -484,4 +483,46 @@ def test_fields_through_pinned_host_buffers(prec):
         pin = torch.from_numpy(v.copy()).pin_memory()
         lf.lf_fields_set(sim.ctx, lf.FIELDS[name], pin.data_ptr(), pin.numel() * pin.element_size(), False)
         np.testing.assert_array_equal(sim.get(name, native), a)
+    sim.close()
+
+
+def _random_case(rng):
+    """A random configuration: lattice (ragged sizes), walls and T wall rule,
+    hydrodynamics, stencil, step variant and parameters inside the stability
+    limits."""
+    d = int(rng.choice([2, 3]))
+    case = dict(d=d, nx=int(rng.integers(3, 70)), ny=int(rng.integers(3, 50)),
+                walls=int(rng.integers(0, 2)), t_wall_mode=int(rng.integers(0, 2)), hydro=int(rng.integers(0, 2)),
+                b=float(rng.uniform(0.0, 1.5)), kappa=float(rng.uniform(-0.05, 0.05)), c=float(rng.uniform(0.0, 0.04)),
+                Gamma=float(rng.uniform(0.01, 0.08)), Tc=1.0, T0=float(rng.uniform(0.6, 1.3)),
+                T_w=float(rng.uniform(0.4, 0.9)), tau=float(rng.uniform(0.6, 3.0)),
+                xi=float(rng.choice([0.0, 1e-3, 0.05, 0.3, 2.0, math.inf])))
+    if d == 3:
+        case.update(nx=int(rng.integers(3, 30)), ny=int(rng.integers(3, 24)), nz=int(rng.integers(3, 24)))
+    stencil = str(rng.choice(["compact", "isotropic"]))
+    variant = str(rng.choice(["march", "tile", "march2"] if d == 2 else ["march", "split3"]))
+    return case, stencil, variant
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("seed", range(24))
+def test_random_configurations_one_step(seed, prec):
+    """Seeded random configurations (every switch of the step drawn at random)
+    against the oracle, one step from a random state."""
+    rng = np.random.default_rng(1000 + seed)
+    case, stencil, variant = _random_case(rng)
+    try:
+        sim, cfg, st = make_pair(case, prec, seed=seed, stencil=stencil)
+    except lf.LFError as ex:                       # outside the stability limits of the explicit schemes
+        assert ex.code == lf.LF_EUNSTABLE, (case, ex)
+        return
+    if case["d"] == 3:
+        sim.set_variant(*{"march": ("march", 0), "split3": ("split3", 0)}[variant])
+    else:
+        sim.set_variant(*VARIANTS[variant])
+    sim.step(1)
+    ref = O.step(st)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), case["d"]), ref.f)):
+        assert relerr(got, want) < TOL[prec], (case, stencil, variant, name, relerr(got, want))
     sim.close()
