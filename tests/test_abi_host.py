@@ -134,3 +134,14 @@ def test_workspace_bytes_scale(L):
 def test_strerror_covers_codes(L):
     for c in range(0, -8, -1):
         assert L.strerror(c) != "unknown error"
+
+
+def test_ensemble_refuses_isotropic_runs_before_allocating(L):
+    """Ensembles run the compact packed march only: a run with the isotropic
+    stencils is refused (LF_EINVAL) by the argument checks, before any device
+    allocation."""
+    g, w, p = _args(L, precision=1)
+    p.stencil = 1
+    with pytest.raises(L.LFError) as ei:
+        L.lf_ens_create([g], [w], [p])
+    assert ei.value.code == -1
