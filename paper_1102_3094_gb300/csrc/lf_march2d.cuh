@@ -355,9 +355,11 @@ inline int march2_rows_for(int nx, int ny, int U, int param, int sms)
 {
     if (param > 0) return param < ny ? param : ny;
     const int strips = (nx + U - 1) / U;
-    int best = 8;
+    int best = 1;
     int64_t best_cost = -1;
-    for (int h = 8; h <= ny && h <= 512; ++h) {
+    // from one row per lane: on small lattices the step is a chain of H + 4
+    // dependent row iterations, so short lanes cut its latency
+    for (int h = 1; h <= ny && h <= 512; ++h) {
         int pairs = (ny + 2 * h - 1) / (2 * h);
         if (pairs > ny / 2) pairs = ny / 2;
         if (pairs < 1) break;
