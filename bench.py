@@ -208,6 +208,8 @@ def run_ensemble(args):
         tdist.init_process_group("nccl")
     stream = torch.cuda.Stream(dev)
     members = synth.ensemble_members()
+    if args.stencil == "isotropic":
+        members = [dict(m, stencil="isotropic") for m in members]
     sites = sum(m["nx"] * m["ny"] for m in members)
     with torch.cuda.stream(stream):
         ens = lf.Ensemble(members, stream=stream)
@@ -253,11 +255,13 @@ def run_ensemble(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ens96: 96 independent 2D runs, 24 each of 128^2, 256^2, 384^2, 512^2, xi "
                                "log-uniform in [1e-4, 1], tau in {0.6, 1, 3}, one persistent launch per step "
-                               "replayed from a CUDA graph, tuned segment heights",
+                               "replayed from a CUDA graph, tuned segment heights"
+                               + (", isotropic 9-point stencils (tile items)" if args.stencil == "isotropic" else ""),
                    "sites_per_step": sites, "l2": "inputs (1 GB of state) larger than L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_site": 88,
-                     "kernel": "k_ens_march2d (+ k_ens_tsub2d for runs with xi/nsub sub-steps)"},
+                     "kernel": ("k_ens_tile2d_iso" if args.stencil == "isotropic" else "k_ens_march2d")
+                               + " (+ k_ens_tsub2d for runs with xi/nsub sub-steps)"},
         "batched_vs_sequential": {"t_batched_s": t_batch, "t_sequential_s": t_seq, "speedup": t_seq / t_batch,
                                   "bit_identical_phi": identical, "tune_s": tune_s,
                                   "runs_nonfinite": nonfinite,

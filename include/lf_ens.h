@@ -10,7 +10,10 @@
  * (run, strip, segment pair) items, and the steps are replayed from a CUDA
  * graph.  Results are bit-identical to stepping every run alone with lf_step
  * under LF_VARIANT_MARCH2 with param = lf_ens_rows(e, r) (the per-site
- * arithmetic is the same code and the rows are split the same way).
+ * arithmetic is the same code and the rows are split the same way).  Runs
+ * created with params.stencil = LF_STENCIL_ISOTROPIC are (run, 64 x 16 tile)
+ * items of a second persistent kernel, the tile form a single isotropic 2D run
+ * uses, and are bit-identical to that run stepped alone.
  *
  * Restrictions: every run is two-dimensional (d = 2), LF_FP32, ny >= 2.
  * Conventions (return codes, layouts, ownership) are those of lf.h.
@@ -30,8 +33,8 @@ typedef struct lf_ens lf_ens;
  * stream, workspace and workspace_bytes fields of params are ignored), all in
  * one device arena, enqueued on `stream` (a cudaStream_t; 0 = a private
  * stream the ensemble creates).  LF_EINVAL if a run is not d = 2 / LF_FP32 /
- * ny >= 2 / LF_STENCIL_COMPACT or fails lf_create's checks (then nothing is
- * allocated). */
+ * ny >= 2 or fails lf_create's checks (then nothing is allocated).  Runs of
+ * either stencil may be mixed. */
 int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const lf_params* params,
                   void* stream, lf_ens** out);
 
@@ -42,7 +45,7 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
 int lf_ens_tune(lf_ens* e, int reps);
 
 /* Rows per segment the work list uses for run r (after tuning, or the
- * default min(16, ny / 2)). */
+ * default min(16, ny / 2)); not used by isotropic runs, which the tuner skips. */
 int lf_ens_rows(const lf_ens* e, int run);
 
 /* Enqueues nsteps steps of every run on the ensemble's stream (graph

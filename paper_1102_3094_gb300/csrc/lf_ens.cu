@@ -6,9 +6,12 @@
 // two-lane row-marching step of lf_march2d_x2.cuh (two segments of a strip
 // marching away from their common row) -- followed, when some runs need extra
 // temperature sub-steps, by one launch per sub-step over the tiles of those
-// runs.  Every run returns to its starting buffers after two steps (f and phi
-// flip once per step, T flips nsub times), so two steps are captured in one
-// CUDA graph and replayed; single-step graphs handle odd counts.
+// runs.  Runs with the isotropic stencils are (run, tile) items of a second
+// persistent kernel that runs the tile form of the step (lf_tile2d.cuh), the
+// code a single isotropic run uses.  Every run returns to its starting buffers
+// after two steps (f and phi flip once per step, T flips nsub times), so two
+// steps are captured in one CUDA graph and replayed; single-step graphs handle
+// odd counts.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -21,6 +24,7 @@
 #include "lf_ctx.cuh"
 #include "lf_ens.h"
 #include "lf_march2d_x2.cuh"
+#include "lf_tile2d.cuh"
 
 using namespace lf;
 
@@ -28,6 +32,8 @@ namespace {
 
 constexpr int kNT = 64, kD = 3;     // 56-column strips: less idle width on 128^2 .. 512^2 lattices
 using MarchCfg = march::March2<kNT, kD>;
+constexpr int kTX = 64, kTY = 16, kTNT = 256;   // the FP32 tile of the single-run isotropic step
+using TileCfg = tile::Tile<float, kTX, kTY>;
 
 struct EnsRun {
     Geom g;
@@ -49,6 +55,21 @@ struct EnsT {
 struct EnsTItem {
     int run, bx, by;
 };
+
+// (run, tile) items of the isotropic runs, in the same struct as the T tiles.
+using EnsTile = EnsTItem;
+
+__global__ void __launch_bounds__(kTNT) k_ens_tile2d_iso(const EnsRun* __restrict__ runs,
+                                                        const EnsTile* __restrict__ items, int nitems)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const EnsTile w = items[it];
+        const EnsRun r = runs[w.run];
+        tile::step2d_tile<float, kTX, kTY, kTNT, false, true>(r.g, r.p, r.io, w.bx, w.by, smem_raw);
+        __syncthreads();   // the next item reuses the tile
+    }
+}
 
 __global__ void __launch_bounds__(kNT, 6) k_ens_march2d(const EnsRun* __restrict__ runs,
                                                        const EnsItem* __restrict__ items, int nitems)
@@ -81,7 +102,10 @@ __global__ void __launch_bounds__(256) k_ens_tsub2d(const EnsT* __restrict__ run
         const EnsTItem w = items[it];
         const EnsT r = runs[w.run];
         const int x = w.bx * 32 + (threadIdx.x & 31), y = w.by * 8 + (threadIdx.x >> 5);
-        if (x < r.g.nx && y < r.g.ny) march::tsub2d_site(r.g, r.p, r.Tin, r.Tout, x, y);
+        if (x < r.g.nx && y < r.g.ny) {
+            if (r.g.stencil == LF_STENCIL_ISOTROPIC) tile::tsub2d_site_iso(r.g, r.p, r.Tin, r.Tout, x, y);
+            else march::tsub2d_site(r.g, r.p, r.Tin, r.Tout, x, y);
+        }
     }
 }
 
@@ -119,6 +143,7 @@ struct lf_ens {
     int parity;                     // 0: the next step is step A of the cycle, 1: step B
     std::vector<Cursor> base;       // buffer cursors at the start of step A
     int march_blocks;
+    int tile_blocks;
 };
 
 namespace {
@@ -139,13 +164,16 @@ struct Half {
     std::vector<EnsT*> ts;          // per extra sub-step s = 1 .. max_nsub - 1
 };
 
-int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsItem* items, int nitems,
-            const std::vector<EnsTItem*>& titems, const std::vector<int>& ntitems, cudaGraphExec_t* out)
+int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsItem* items, int nitems, EnsTile* tiles,
+            int ntiles, const std::vector<EnsTItem*>& titems, const std::vector<int>& ntitems, cudaGraphExec_t* out)
 {
     cudaGraph_t graph;
     if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LF_ECUDA;
     for (int h : halves) {
-        k_ens_march2d<<<e->march_blocks, kNT, MarchCfg::BYTES, e->stream>>>(H[h].runs, items, nitems);
+        if (nitems > 0)
+            k_ens_march2d<<<e->march_blocks, kNT, MarchCfg::BYTES, e->stream>>>(H[h].runs, items, nitems);
+        if (ntiles > 0)
+            k_ens_tile2d_iso<<<e->tile_blocks, kTNT, TileCfg::BYTES, e->stream>>>(H[h].runs, tiles, ntiles);
         for (size_t s = 0; s < H[h].ts.size(); ++s) {
             if (ntitems[s] == 0) continue;
             const int blocks = std::min(ntitems[s], 152 * 8);
@@ -207,10 +235,17 @@ int build(lf_ens* e)
             }
         }
     }
-    // work lists: march items sorted by cost (longest lane first), T tiles per sub-step
+    // work lists: march items sorted by cost (longest lane first), the tiles
+    // of the isotropic runs, T tiles per sub-step
     std::vector<EnsItem> items;
+    std::vector<EnsTile> tiles;
     for (int r = 0; r < R; ++r) {
         const lf_ctx* c = e->runs[r];
+        if (c->g.stencil == LF_STENCIL_ISOTROPIC) {
+            for (int by = 0; by < (c->g.ny + kTY - 1) / kTY; ++by)
+                for (int bx = 0; bx < (c->g.nx + kTX - 1) / kTX; ++bx) tiles.push_back({r, bx, by});
+            continue;
+        }
         const int np = pairs_for(c->g.ny, e->rows[r]);
         const int strips = (c->g.nx + MarchCfg::U - 1) / MarchCfg::U;
         for (int pr = 0; pr < np; ++pr)
@@ -232,7 +267,8 @@ int build(lf_ens* e)
         }
     // one device block for everything
     auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
-    size_t bytes = 2 * a256(sizeof(EnsRun) * R) + a256(sizeof(EnsItem) * items.size());
+    size_t bytes = 2 * a256(sizeof(EnsRun) * R) + a256(sizeof(EnsItem) * items.size()) +
+                   a256(sizeof(EnsTile) * tiles.size());
     for (int s = 1; s < max_nsub; ++s) bytes += 2 * a256(sizeof(EnsT) * R) + a256(sizeof(EnsTItem) * titems[s - 1].size());
     if (cudaMalloc((void**)&e->tables, bytes) != cudaSuccess) { cudaGetLastError(); return LF_ENOMEM; }
     unsigned char* p = e->tables;
@@ -246,6 +282,9 @@ int build(lf_ens* e)
     EnsItem* d_items = (EnsItem*)p;
     copies.push_back({p, {items.data(), sizeof(EnsItem) * items.size()}});
     p += a256(sizeof(EnsItem) * items.size());
+    EnsTile* d_tiles = (EnsTile*)p;
+    copies.push_back({p, {tiles.data(), sizeof(EnsTile) * tiles.size()}});
+    p += a256(sizeof(EnsTile) * tiles.size());
     std::vector<EnsTItem*> d_titems;
     std::vector<int> ntitems;
     for (int s = 1; s < max_nsub; ++s) {
@@ -267,18 +306,25 @@ int build(lf_ens* e)
     if (rc != LF_OK) return rc;
 
     if (cudaFuncSetAttribute(k_ens_march2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg::BYTES) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_ens_tile2d_iso, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg::BYTES) !=
+            cudaSuccess)
         return LF_ECUDA;
-    int per_sm = 0, sms = 0, dev = 0;
+    int per_sm = 0, per_sm_t = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_march2d, kNT, MarchCfg::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_ens_tile2d_iso, kTNT, TileCfg::BYTES);
     e->march_blocks = std::max(1, std::min((int)items.size(), std::max(1, per_sm) * std::max(1, sms)));
+    e->tile_blocks = std::max(1, std::min((int)tiles.size(), std::max(1, per_sm_t) * std::max(1, sms)));
 
-    const int nitems = (int)items.size();
-    if ((rc = capture(e, {0}, halves, d_items, nitems, d_titems, ntitems, &e->gA)) != LF_OK) return rc;
-    if ((rc = capture(e, {1}, halves, d_items, nitems, d_titems, ntitems, &e->gB)) != LF_OK) return rc;
-    if ((rc = capture(e, {0, 1}, halves, d_items, nitems, d_titems, ntitems, &e->gAB)) != LF_OK) return rc;
+    const int nitems = (int)items.size(), ntiles = (int)tiles.size();
+    if ((rc = capture(e, {0}, halves, d_items, nitems, d_tiles, ntiles, d_titems, ntitems, &e->gA)) != LF_OK)
+        return rc;
+    if ((rc = capture(e, {1}, halves, d_items, nitems, d_tiles, ntiles, d_titems, ntitems, &e->gB)) != LF_OK)
+        return rc;
+    if ((rc = capture(e, {0, 1}, halves, d_items, nitems, d_tiles, ntiles, d_titems, ntitems, &e->gAB)) != LF_OK)
+        return rc;
     e->parity = 0;
     return LF_OK;
 }
@@ -310,9 +356,7 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
     std::vector<size_t> ws(nruns);
     size_t total = 0;
     for (int r = 0; r < nruns; ++r) {
-        if (grids[r].d != 2 || params[r].precision != LF_FP32 || grids[r].ny < 2 ||
-            params[r].stencil != LF_STENCIL_COMPACT)
-            return LF_EINVAL;
+        if (grids[r].d != 2 || params[r].precision != LF_FP32 || grids[r].ny < 2) return LF_EINVAL;
         lf_params p = params[r];
         p.workspace = nullptr;
         p.workspace_bytes = 0;
@@ -370,6 +414,7 @@ int lf_ens_tune(lf_ens* e, int reps)
     std::map<std::pair<int, int>, int> best;   // (nx, ny) -> rows
     for (int r = 0; r < e->nruns; ++r) {
         lf_ctx* c = e->runs[r];
+        if (c->g.stencil == LF_STENCIL_ISOTROPIC) continue;     // tiles: nothing to tune
         const auto key = std::make_pair(c->g.nx, c->g.ny);
         if (best.count(key)) continue;
         lf_params p = c->params;
@@ -402,7 +447,9 @@ int lf_ens_tune(lf_ens* e, int reps)
         if (rc != LF_OK) return rc;
         best[key] = best_h;
     }
-    for (int r = 0; r < e->nruns; ++r) e->rows[r] = best[std::make_pair(e->runs[r]->g.nx, e->runs[r]->g.ny)];
+    for (int r = 0; r < e->nruns; ++r)
+        if (e->runs[r]->g.stencil != LF_STENCIL_ISOTROPIC)
+            e->rows[r] = best[std::make_pair(e->runs[r]->g.nx, e->runs[r]->g.ny)];
     return build(e);
 }
 

@@ -416,7 +416,9 @@ class Ensemble:
                                     Gamma=kw.get("Gamma", 0.05), Tc=kw.get("Tc", 1.0), T0=kw.get("T0", 1.1),
                                     xi=kw.get("xi", 0.01), tau=kw.get("tau", 1.0), n0=kw.get("n0", 1.0),
                                     phi_amp=kw.get("phi_amp", 0.05), seed=kw.get("seed", 1), precision=LF_FP32,
-                                    hydro=kw.get("hydro", 1), ideal_mode=0))
+                                    hydro=kw.get("hydro", 1), ideal_mode=0,
+                                    stencil={"compact": LF_STENCIL_COMPACT,
+                                             "isotropic": LF_STENCIL_ISOTROPIC}[kw.get("stencil", "compact")]))
             self.shapes.append((kw["ny"], kw["nx"]))
         self.ens = lf_ens_create(grids, walls, params, self.stream.cuda_stream)
         self.n = len(members)

@@ -136,12 +136,12 @@ def test_strerror_covers_codes(L):
         assert L.strerror(c) != "unknown error"
 
 
-def test_ensemble_refuses_isotropic_runs_before_allocating(L):
-    """Ensembles run the compact packed march only: a run with the isotropic
-    stencils is refused (LF_EINVAL) by the argument checks, before any device
-    allocation."""
-    g, w, p = _args(L, precision=1)
-    p.stencil = 1
+@pytest.mark.parametrize("kw", [dict(precision=0), dict(precision=1, d=3, nz=8), dict(precision=1, ny=1, walls=0),
+                                dict(precision=1, stencil=2)])
+def test_ensemble_refuses_bad_runs_before_allocating(L, kw):
+    """Ensembles take 2D FP32 runs with ny >= 2: anything else is refused
+    (LF_EINVAL) by the argument checks, before any device allocation."""
+    g, w, p = _args(L, **kw)
     with pytest.raises(L.LFError) as ei:
         L.lf_ens_create([g], [w], [p])
     assert ei.value.code == -1

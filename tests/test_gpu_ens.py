@@ -78,3 +78,29 @@ def test_ensemble_run_refuses_lf_step():
         lf.lf_step(ctx, 1)
     assert ei.value.code == lf.LF_EINVAL
     ens.close()
+
+
+ISO_MEMBERS = [
+    dict(nx=64, ny=64, xi=0.01, tau=1.0, seed=21, stencil="isotropic"),
+    dict(nx=96, ny=80, xi=0.5, tau=0.6, seed=22, stencil="isotropic", t_wall_mode=1),   # 3 sub-steps, halfway T
+    dict(nx=130, ny=70, xi=1e-3, tau=3.0, seed=23),                                    # compact, in the same launch
+    dict(nx=33, ny=17, xi=0.2, tau=0.8, seed=24, walls=0, stencil="isotropic"),         # periodic, ragged tiles
+]
+
+
+def test_isotropic_runs_in_an_ensemble_equal_single_runs():
+    """Runs with the isotropic stencils (tile items) and a compact run (march
+    items) in one ensemble, each equal bit for bit to the run stepped alone."""
+    ens = lf.Ensemble(ISO_MEMBERS)
+    ens.tune(reps=2)                     # skips the isotropic runs
+    ens.step(5)
+    ens.step(6)
+    for r, m in enumerate(ISO_MEMBERS):
+        ref = lf.Lattice(precision="fp32", **m)
+        ref.set_variant("march2", ens.rows(r))
+        ref.step(11)
+        run = ens.run(r)
+        for name in ("phi", "T", "pop"):
+            np.testing.assert_array_equal(run.get(name, "fp32"), ref.get(name, "fp32"), err_msg=f"run {r} {name}")
+        ref.close()
+    ens.close()
