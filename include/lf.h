@@ -225,7 +225,7 @@ int lf_diag_sums_noalloc(int d, int64_t nx, int64_t ny, int64_t nz, int walls, i
 int lf_save(lf_ctx* ctx, const char* path);
 int lf_load(lf_ctx* ctx, const char* path);
 
-/* Kernel variant of the step.  Both compute the same step (parity-tested
+/* Kernel variant of the step.  All compute the same step (parity-tested
  * against the oracle); they differ in how work is mapped to the GPU:
  *   LF_VARIANT_MARCH (default for 2D FP64): one thread per column, a CTA
  *     marches down a segment of (param & 0xFFFF) rows (0 = chosen from the
@@ -239,12 +239,13 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     FP32x2 arithmetic; (param & 0xFFFF) = rows per segment (0 = chosen from
  *     the lattice size and the SM count), (param >> 16) == 1 selects CTAs of
  *     64 threads (56 columns) instead of 128 (120 columns);
- *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a plane march
- *     ((param & 0xFFFF) = planes per segment, 0 = automatic; in FP32 two
- *     segments run in the lanes of packed FP32x2 arithmetic unless
- *     (param >> 16) is 1 or 2, which select one lane on 60x4 or 28x12 tiles), then collision and
- *     streaming, then the phi and T updates, one thread per site; mu, F and
- *     u pass through the context's derived-field planes.  For 3D contexts
+  *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a
+ *     plane march ((param & 0xFFFF) = planes per segment, 0 = automatic; in
+ *     FP32 two segments run in the lanes of packed FP32x2 arithmetic unless
+ *     (param >> 16) is 1 or 2, which select one lane on 60x4 or 28x12
+ *     tiles), then collision and streaming, then the phi and T updates, one
+ *     thread per site; mu, F and u pass through the context's derived-field
+ *     planes.  For 3D contexts
  *     every other variant runs the fused plane march (param = planes per
  *     segment).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
@@ -279,17 +280,18 @@ int lf_set_t_solver(lf_ctx* ctx, int solver);
  *   LF_STENCIL_ISOTROPIC: the operators built from the lattice weights,
  *     d_a A = 3 sum_i w_i e_ia A(r + e_i) and lap A = 6 sum_i w_i [A(r + e_i) -
  *     A(r)] (D2Q9: the 9-point Laplacian [4 (nearest) + (diagonal) - 20 A]/6),
- *     isotropic to fourth order in the wavenumber (Thampi et al., J. Comput.
+ *     second order with an isotropic leading error (Thampi et al., J. Comput.
  *     Phys. 234 (2013) 1).  Applies to psi, lam, grad phi, grad psi, F, the
  *     flux divergence, lap mu and lap T; the wall images are those of the
  *     compact stencils, applied to the diagonal neighbours too.  In 2D it
  *     runs the LF_VARIANT_TILE kernel whatever variant is set; in 3D the
- *     variant set (three passes by default, or the fused plane march).  Its largest Laplacian eigenvalue is 16/3 in 2D and 3D
- *     (8 and 12 for the compact stencils), which the stability check of
- *     lf_create uses.
- * Returns LF_EINVAL for an unknown stencil or an ensemble member, and LF_EUNSTABLE if
- * the context's parameters are unstable with the new stencil (the context
- * keeps its stencil then).  Not stored in checkpoints. */
+ *     variant set (three passes by default, or the fused plane march).  Its
+ *     largest Laplacian eigenvalue is 16/3 in 2D and 3D (8 and 12 for the
+ *     compact stencils), which the stability check of lf_create uses.
+ * Returns LF_EINVAL for an unknown stencil or an ensemble member (an
+ * ensemble's runs take their stencil from params at lf_ens_create), and
+ * LF_EUNSTABLE if the context's parameters are unstable with the new stencil
+ * (the context keeps its stencil then).  lf_load does not restore it. */
 #define LF_STENCIL_COMPACT   0
 #define LF_STENCIL_ISOTROPIC 1
 int lf_set_stencil(lf_ctx* ctx, int stencil);
