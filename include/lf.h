@@ -239,15 +239,14 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     FP32x2 arithmetic; (param & 0xFFFF) = rows per segment (0 = chosen from
  *     the lattice size and the SM count), (param >> 16) == 1 selects CTAs of
  *     64 threads (56 columns) instead of 128 (120 columns);
-  *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a
+ *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a
  *     plane march ((param & 0xFFFF) = planes per segment, 0 = automatic; in
  *     FP32 two segments run in the lanes of packed FP32x2 arithmetic unless
  *     (param >> 16) is 1 or 2, which select one lane on 60x4 or 28x12
  *     tiles), then collision and streaming, then the phi and T updates, one
  *     thread per site; mu, F and u pass through the context's derived-field
- *     planes.  For 3D contexts
- *     every other variant runs the fused plane march (param = planes per
- *     segment).
+ *     planes.  For 3D contexts every other variant runs the fused plane
+ *     march (param = planes per segment).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
 #define LF_VARIANT_MARCH  0
 #define LF_VARIANT_TILE   1
