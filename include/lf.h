@@ -38,6 +38,13 @@
  *     environment).  After LF_ETIMEOUT the context stays usable, but a copy
  *     to or from a device or pinned caller buffer may still be in flight on
  *     the stream: synchronize the stream before reusing that buffer.
+ *   - Checked mode: with LF_CHECKED=1 in the environment when
+ *     lf_workspace_bytes and lf_create run, every device buffer of the
+ *     context is followed by a 64 KiB guard band (one more before the first)
+ *     filled with the byte 0xA5, and every lf_step call ends with a kernel
+ *     that verifies all of them; the next call that reports pending errors
+ *     (lf_step) returns LF_ECORRUPT if any guard byte changed.  The workspace
+ *     grows by 640 KiB; the state, its layout and the results are unchanged.
  */
 #ifndef LF_H
 #define LF_H
@@ -58,6 +65,7 @@ extern "C" {
 #define LF_ENONFINITE -5  /* a NaN or Inf appeared in phi, T or the density         */
 #define LF_ETIMEOUT   -6  /* a bounded wait for the GPU ran out                     */
 #define LF_EIO        -7  /* checkpoint file could not be written / read / matched  */
+#define LF_ECORRUPT   -8  /* checked mode: a guard band of a buffer was overwritten */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define LF_FP64 0         /* all state and arithmetic in double                     */

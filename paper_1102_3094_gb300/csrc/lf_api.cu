@@ -68,8 +68,46 @@ int validate(const lf_grid* grid, const lf_walls* walls, const lf_params* p)
 }
 
 struct Layout {
-    size_t f, phi, T, aux, stage, scratch, total;
+    size_t f, phi, T, aux, stage, scratch, guard, total;
 };
+
+// Checked mode: LF_CHECKED=1 in the environment when the workspace is sized and
+// the context created.
+constexpr size_t kGuard = 64 * 1024;        // bytes per guard band
+constexpr unsigned char kGuardByte = 0xA5;
+
+bool checked_mode()
+{
+    const char* v = std::getenv("LF_CHECKED");
+    return v && v[0] == '1';
+}
+
+// Every byte of the ten guard bands still holds kGuardByte; clears *bad otherwise.
+struct GuardOffsets {
+    unsigned long long off[10];
+};
+
+__global__ void k_guard_check(const unsigned char* __restrict__ base, GuardOffsets g, int* __restrict__ bad)
+{
+    constexpr int W = (int)(kGuard / 16);
+    const uint4 want = make_uint4(0xA5A5A5A5u, 0xA5A5A5A5u, 0xA5A5A5A5u, 0xA5A5A5A5u);
+    bool ok = true;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 10 * W; i += gridDim.x * blockDim.x) {
+        const uint4 v = reinterpret_cast<const uint4*>(base + g.off[i / W])[i % W];
+        ok &= v.x == want.x && v.y == want.y && v.z == want.z && v.w == want.w;
+    }
+    if (!ok) *reinterpret_cast<volatile int*>(bad) = 1;
+}
+
+// Checked mode: enqueue the verification of every guard band.
+int check_guards(lf_ctx* c)
+{
+    if (!c->checked) return LF_OK;
+    GuardOffsets g;
+    for (int i = 0; i < 10; ++i) g.off[i] = c->guard_off[i];
+    k_guard_check<<<152, 256, 0, c->stream>>>(c->base, g, c->guard_dev);
+    return check(cudaGetLastError());
+}
 
 Layout layout_for(const lf_grid* grid, const lf_params* p, int64_t* plane_out, int* pitch_out)
 {
@@ -85,7 +123,8 @@ Layout layout_for(const lf_grid* grid, const lf_params* p, int64_t* plane_out, i
     L.aux = align_up((size_t)8 * plane * esz, kAlign);
     L.stage = align_up((size_t)N * 8, kAlign);
     L.scratch = align_up(diag_scratch_bytes(grid->d, grid->nx, grid->ny, grid->nz), kAlign);
-    L.total = 2 * L.f + 2 * L.phi + 2 * L.T + L.aux + L.stage + L.scratch;
+    L.guard = checked_mode() ? kGuard : 0;
+    L.total = 2 * L.f + 2 * L.phi + 2 * L.T + L.aux + L.stage + L.scratch + 10 * L.guard;
     if (plane_out) *plane_out = plane;
     if (pitch_out) *pitch_out = pitch;
     return L;
@@ -161,7 +200,7 @@ int do_steps(lf_ctx* c, int64_t n)
         c->step += 1;
     }
     c->aux_valid = false;
-    return LF_OK;
+    return check_guards(c);
 }
 
 template <typename R>
@@ -290,9 +329,11 @@ int pending_status(lf_ctx* c)
 {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return LF_ECUDA;
+    if (c->guard_host && *c->guard_host) return LF_ECORRUPT;
     if (c->flag_host && *c->flag_host) return LF_ENONFINITE;
     return LF_OK;
 }
+
 
 }  // namespace
 
@@ -418,20 +459,28 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
         c->own = true;
     }
     c->bytes = L.total;
+    c->checked = L.guard > 0;
     unsigned char* p = c->base;
-    c->f[0] = p; p += L.f;
-    c->f[1] = p; p += L.f;
-    c->phi[0] = p; p += L.phi;
-    c->phi[1] = p; p += L.phi;
-    c->T[0] = p; p += L.T;
-    c->T[1] = p; p += L.T;
-    c->aux = p; p += L.aux;
-    c->stage = p; p += L.stage;
-    c->scratch = p; p += L.scratch;
+    int ng = 0;
+    auto guard = [&]() {                     // a guard band (checked mode only)
+        if (!c->checked) return;
+        c->guard_off[ng++] = (size_t)(p - c->base);
+        p += L.guard;
+    };
+    guard();
+    c->f[0] = p; p += L.f; guard();
+    c->f[1] = p; p += L.f; guard();
+    c->phi[0] = p; p += L.phi; guard();
+    c->phi[1] = p; p += L.phi; guard();
+    c->T[0] = p; p += L.T; guard();
+    c->T[1] = p; p += L.T; guard();
+    c->aux = p; p += L.aux; guard();
+    c->stage = p; p += L.stage; guard();
+    c->scratch = p; p += L.scratch; guard();
     c->scratch_bytes = L.scratch;
 
     int* fh = nullptr;
-    if (cudaHostAlloc((void**)&fh, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+    if (cudaHostAlloc((void**)&fh, 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&c->flag_dev, fh, 0) != cudaSuccess) {
         cudaGetLastError();
         if (fh) cudaFreeHost(fh);
@@ -439,10 +488,17 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
         delete c;
         return LF_ECUDA;
     }
-    *fh = 0;
+    fh[0] = fh[1] = 0;
     c->flag_host = fh;
+    c->guard_host = fh + 1;
+    c->guard_dev = c->flag_dev + 1;
 
-    rc = check(cudaMemsetAsync(c->base, 0, 2 * L.f + 2 * L.phi + 2 * L.T + L.aux, c->stream));
+    rc = LF_OK;
+    for (int i = 0; i < (c->checked ? 10 : 0) && rc == LF_OK; ++i)
+        rc = check(cudaMemsetAsync(c->base + c->guard_off[i], kGuardByte, L.guard, c->stream));
+    for (void* b : {c->f[0], c->f[1], c->phi[0], c->phi[1], c->T[0], c->T[1]})
+        if (rc == LF_OK) rc = check(cudaMemsetAsync(b, 0, b == c->f[0] || b == c->f[1] ? L.f : L.phi, c->stream));
+    if (rc == LF_OK) rc = check(cudaMemsetAsync(c->aux, 0, L.aux, c->stream));
     const int quench = std::isinf(params->xi) ? 1 : 0;
     if (rc == LF_OK) {
         if (c->prec == LF_FP64)
@@ -724,6 +780,7 @@ const char* lf_strerror(int code)
     case LF_ENONFINITE: return "non-finite value (NaN/Inf) in the state";
     case LF_ETIMEOUT: return "timed out waiting for the GPU";
     case LF_EIO: return "checkpoint I/O error or mismatch";
+    case LF_ECORRUPT: return "a guard band around a device buffer was overwritten (checked mode)";
     default: return "unknown error";
     }
 }

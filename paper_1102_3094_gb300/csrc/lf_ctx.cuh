@@ -26,6 +26,11 @@ struct lf_ctx {
     size_t scratch_bytes;
     int* flag_dev;
     volatile int* flag_host;
+    // checked mode (LF_CHECKED=1 at creation): guard bands around every buffer
+    bool checked;
+    int* guard_dev;                 // set to 1 by the guard check when a band changed
+    volatile int* guard_host;
+    size_t guard_off[10];           // offsets of the guard bands from base
     int64_t step;
     bool aux_valid;
     bool ens_member;      // stepped by an ensemble; lf_step on it is refused

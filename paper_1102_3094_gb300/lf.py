@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblf.so")
 
 LF_OK, LF_EINVAL, LF_EUNSTABLE, LF_ENOMEM, LF_ECUDA, LF_ENONFINITE, LF_ETIMEOUT, LF_EIO = 0, -1, -2, -3, -4, -5, -6, -7
+LF_ECORRUPT = -8
 LF_FP64, LF_FP32 = 0, 1
 LF_TWALL_LAYERS, LF_TWALL_HALFWAY = 0, 1
 FIELDS = {"phi": 0, "T": 1, "rho": 2, "ux": 3, "uy": 4, "uz": 5, "pop": 6, "mu": 7, "Fx": 8, "Fy": 9, "Fz": 10}

@@ -132,7 +132,7 @@ def test_workspace_bytes_scale(L):
 
 
 def test_strerror_covers_codes(L):
-    for c in range(0, -8, -1):
+    for c in range(0, -9, -1):
         assert L.strerror(c) != "unknown error"
 
 
@@ -145,3 +145,11 @@ def test_ensemble_refuses_bad_runs_before_allocating(L, kw):
     with pytest.raises(L.LFError) as ei:
         L.lf_ens_create([g], [w], [p])
     assert ei.value.code == -1
+
+
+def test_checked_mode_adds_guard_bands(L, monkeypatch):
+    """LF_CHECKED=1 grows the workspace by the ten 64 KiB guard bands."""
+    g, w, p = _args(L)
+    plain = L.lf_workspace_bytes(g, w, p)
+    monkeypatch.setenv("LF_CHECKED", "1")
+    assert L.lf_workspace_bytes(g, w, p) == plain + 10 * 64 * 1024

@@ -547,3 +547,38 @@ def test_paper_parameters_multistep_fp64(stencil, hydro, tau, xi):
                             ("f", to_oracle_f(sim.get("pop"), 2), ref.f)):
         assert relerr(got, want) < 1e-10, (name, relerr(got, want))
     sim.close()
+
+
+
+def test_checked_mode_guard_bands(monkeypatch):
+    """Checked mode (LF_CHECKED=1): every step kind on odd sizes leaves the guard
+    bands around the device buffers intact; a byte changed in a guard band
+    (written here into the front band of the workspace through the torch
+    tensor that holds it) makes the next lf_step return LF_ECORRUPT."""
+    monkeypatch.setenv("LF_CHECKED", "1")
+    cases = [(dict(nx=37, ny=29, xi=0.5), "march2", "compact"), (dict(nx=37, ny=29, xi=0.5), "march", "compact"),
+             (dict(nx=5, ny=3, xi=0.01, t_wall_mode=1), "tile", "isotropic"),
+             (dict(nx=70, ny=37, xi=0.5, t_wall_mode=1), "march2", "isotropic"),
+             (dict(d=3, nx=13, ny=11, nz=7, xi=0.4), "split3", "compact"),
+             (dict(d=3, nx=13, ny=11, nz=7, xi=0.4, walls=0), "march", "isotropic")]
+    for kw, variant, stencil in cases:
+        for prec in ("fp32", "fp64"):
+            sim = lf.Lattice(precision=prec, stencil=stencil, **kw)
+            sim.set_variant(variant, 0)
+            sim.step(3)
+            sim.diag()
+            sim.set("phi", sim.get("phi"))
+            sim.step(2)
+            sim.step(0)                                 # reports what the last steps left
+            assert sim.diag()["rc"] == 0
+            sim.close()
+    sim = lf.Lattice(nx=64, ny=48, precision="fp32")
+    sim.step(1)
+    base = sim.params.workspace - sim.ws.data_ptr()     # the front guard band starts here
+    sim.ws[base + 100] = 0
+    sim.step(1)                                        # its guard check sees the change
+    torch.cuda.synchronize()
+    with pytest.raises(lf.LFError) as ei:
+        sim.step(1)
+    assert ei.value.code == lf.LF_ECORRUPT
+    sim.close()
