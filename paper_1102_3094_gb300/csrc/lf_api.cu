@@ -519,6 +519,7 @@ int lf_create(const lf_grid* grid, const lf_walls* walls, const lf_params* param
 
 int lf_step(lf_ctx* c, int64_t nsteps)
 {
+    lf::NvtxRange nvtx_range("lf_step");
     if (!c || nsteps < 0 || c->ens_member) return LF_EINVAL;
     int rc = pending_status(c);
     if (rc != LF_OK) return rc;
@@ -528,6 +529,7 @@ int lf_step(lf_ctx* c, int64_t nsteps)
 
 int lf_fields(lf_ctx* c, int which, void* dst, size_t bytes, int dst_on_device)
 {
+    lf::NvtxRange nvtx_range("lf_fields");
     if (!c || !dst || which < 0 || which > LF_FIELD_FZ) return LF_EINVAL;
     bool dbl;
     int rc = elem_from_bytes(c, which, bytes, &dbl);
@@ -548,6 +550,7 @@ int lf_fields(lf_ctx* c, int which, void* dst, size_t bytes, int dst_on_device)
 
 int lf_fields_set(lf_ctx* c, int which, const void* src, size_t bytes, int src_on_device)
 {
+    lf::NvtxRange nvtx_range("lf_fields_set");
     if (!c || !src) return LF_EINVAL;
     if (which != LF_FIELD_PHI && which != LF_FIELD_T && which != LF_FIELD_POP) return LF_EINVAL;
     bool dbl;
@@ -566,6 +569,7 @@ int lf_fields_set(lf_ctx* c, int which, const void* src, size_t bytes, int src_o
 
 int lf_diag(lf_ctx* c, lf_diag_t* out)
 {
+    lf::NvtxRange nvtx_range("lf_diag");
     if (!c || !out) return LF_EINVAL;
     std::memset(out, 0, sizeof(*out));
     int rc = ensure_aux(c);
@@ -698,6 +702,7 @@ int raw_copy(lf_ctx* c, const void* plane_dev, void* host, bool to_host)
 
 int lf_save(lf_ctx* c, const char* path)
 {
+    lf::NvtxRange nvtx_range("lf_save");
     if (!c || !path) return LF_EINVAL;
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
@@ -730,6 +735,7 @@ int lf_save(lf_ctx* c, const char* path)
 
 int lf_load(lf_ctx* c, const char* path)
 {
+    lf::NvtxRange nvtx_range("lf_load");
     if (!c || !path) return LF_EINVAL;
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return LF_EIO;

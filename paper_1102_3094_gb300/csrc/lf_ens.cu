@@ -461,6 +461,7 @@ int lf_ens_rows(const lf_ens* e, int run)
 
 int lf_ens_step(lf_ens* e, int64_t nsteps)
 {
+    lf::NvtxRange nvtx_range("lf_ens_step");
     if (!e || nsteps < 0) return LF_EINVAL;
     if (cudaGetLastError() != cudaSuccess) return LF_ECUDA;
     int64_t n = nsteps;

@@ -11,7 +11,18 @@
 
 #include "lf.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lf {
+
+// A named NVTX range for the duration of a scope (one per public call, so that
+// profilers can filter and attribute the kernels a call launches).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Velocity sets (Sec. 2: moduli 0, c, sqrt(2) c; weights 4/9, 1/9, 1/36).

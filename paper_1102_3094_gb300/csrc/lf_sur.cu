@@ -491,6 +491,7 @@ int lf_sur_grads(lf_sur* s, const float* x, const float* y, int B, double* loss,
 
 int lf_sur_train_step(lf_sur* s, const float* x, const float* y, int B, float lr, double* loss)
 {
+    lf::NvtxRange nvtx_range("lf_sur_train_step");
     if (!s || !x || !y || !loss || B < 1 || B > s->maxB || !(lr > 0)) return LF_EINVAL;
     int rc = loss_and_grads(s, x, y, B, loss, true);
     if (rc == LF_OK) rc = refresh_bf16(s, 1, lr);
@@ -499,6 +500,7 @@ int lf_sur_train_step(lf_sur* s, const float* x, const float* y, int B, float lr
 
 int lf_sur_predict(lf_sur* s, const float* x, float* y, int B)
 {
+    lf::NvtxRange nvtx_range("lf_sur_predict");
     if (!s || !x || !y || B < 1 || B > s->maxB) return LF_EINVAL;
     int rc = forward(s, x, B);
     if (rc != LF_OK) return rc;
@@ -619,6 +621,7 @@ constexpr float kMaxU = 0.2f;
 extern "C" int lf_sur_run(lf_sur* s, lf_ctx* ctx, int K, int nwindows, int shadow_every, double threshold,
                           lf_sur_report* rep)
 {
+    lf::NvtxRange nvtx_range("lf_sur_run");
     if (!s || !ctx || !rep || K < 1 || nwindows < 0 || shadow_every < 1 || !(threshold > 0)) return LF_EINVAL;
     if (ctx->g.d != 2 || ctx->prec != LF_FP32 || !ctx->params.hydro || ctx->ens_member || ctx->g.nx != s->NX ||
         ctx->g.ny != s->NY)
