@@ -393,6 +393,47 @@ def test_no_slip_walls_decay():
     assert abs(nu_fit / nu - 1) < 0.02, (nu_fit, nu)
 
 
+def _ux_profile_3d(st):
+    e, _ = O.velocity_set(3)
+    return np.einsum("i,izyx->zyx", e[:, 0].astype(float), st.f).mean(axis=(1, 2))
+
+
+def _shear_nu_3d(tau, nz, walls=0, U=1e-4):
+    """u_x(z) mode on a 4 x 4 x nz D3Q19 lattice (walls along z: the half-sample
+    sine between the bounce-back planes, else a periodic sine); returns the
+    fitted kinematic viscosity."""
+    cfg = O.make_cfg(d=3, nx=4, ny=4, nz=nz, walls=walls, hydro=1, phi_amp=0.0, xi=0.0, tau=tau)
+    st = O.init(cfg)
+    z = np.arange(nz)
+    if walls:
+        s, k2 = np.sin(np.pi * (z + 0.5) / nz), (np.pi / nz) ** 2
+    else:
+        s, k2 = np.sin(2 * np.pi * z / nz), (2 * np.pi / nz) ** 2
+    fe = np.stack([O.feq(3, 1.0, [U * s[j], 0, 0]) for j in range(nz)], axis=1)     # (Q, nz)
+    st.f = np.ascontiguousarray(fe[:, :, None, None] * np.ones((1, 1, 4, 4)))
+    t = int(round(1.0 / ((tau - 0.5) / 3 * k2)))
+    out = O.run(st, t)
+    return -math.log((_ux_profile_3d(out) @ s) / (_ux_profile_3d(st) @ s)) / (k2 * t)
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 3.0])
+def test_shear_wave_viscosity_3d(tau):
+    """D3Q19: nu = (tau - 1/2)/3 from a periodic shear wave, at k and k/2 and
+    extrapolated to k -> 0."""
+    nu = (tau - 0.5) / 3
+    nu1, nu2 = _shear_nu_3d(tau, 32), _shear_nu_3d(tau, 64)
+    nu0 = (4 * nu2 - nu1) / 3
+    assert abs(nu2 / nu - 1) < 0.05
+    assert abs(nu0 / nu - 1) < 0.005, (nu1, nu2, nu0, nu)
+
+
+def test_no_slip_walls_decay_3d():
+    """D3Q19 halfway bounce-back at z = -1/2 and nz - 1/2: the slowest shear mode
+    sin(pi (z + 1/2)/nz) decays at nu (pi/nz)^2."""
+    nu = (1.0 - 0.5) / 3
+    assert abs(_shear_nu_3d(1.0, 32, walls=1) / nu - 1) < 0.02
+
+
 def test_bounce_back_streaming_brute_force():
     """One step of Eq. evoleqn on 8 x 8 with walls: collision per site (pinned
     above), then streaming written out with numpy rolls and reflection."""
