@@ -343,6 +343,27 @@ def test_momentum_conserved_periodic():
     assert abs(p1[0] - p0[0]) < 1e-13 and abs(p1[1] - p0[1]) < 1e-13
 
 
+def test_conservation_3d():
+    """D3Q19 with walls along z: total mass and sum(phi) are exact; on a fully
+    periodic box the momentum n u - F/2 is exact too and sum F = 0."""
+    cfg = O.make_cfg(d=3, nx=12, ny=10, nz=9, xi=0.01)
+    st = O.init(cfg)
+    out = O.run(st, 40)
+    m0, m1 = O.aux(st)["n"].sum(), O.aux(out)["n"].sum()
+    assert abs(m1 - m0) / m0 < 1e-13
+    assert abs(out.phi.sum() - st.phi.sum()) < 1e-12
+    cfg = O.make_cfg(d=3, nx=10, ny=8, nz=9, walls=0, xi=0.0, T0=0.6)
+    st = O.init(cfg)
+    st.T[:] = 0.6
+    mom = lambda s_: (lambda ax: [(ax["n"] * ax["u"][a]).sum() - 0.5 * ax["F"][a].sum()
+                                  for a in range(3)])(O.aux(s_))
+    ax = O.aux(st)
+    assert max(abs(ax["F"][a].sum()) for a in range(3)) < 1e-14
+    p0 = mom(st)
+    p1 = mom(O.run(st, 30))
+    assert max(abs(p1[a] - p0[a]) for a in range(3)) < 1e-13
+
+
 # ------------------------------------------------------- viscosity / walls
 def _ux_profile(st):
     e, _ = O.velocity_set(2)
