@@ -90,6 +90,16 @@ __device__ __forceinline__ int map_row(int v, int n, int walls)
     return map_axis(v, n, walls);
 }
 
+// Periodic index with the same shortcut: one add or subtract for v in
+// [-n, 2n), the division only beyond.
+__device__ __forceinline__ int wrap_near(int v, int n)
+{
+    if (v >= 0 && v < n) return v;
+    const int m = v < 0 ? v + n : v - n;
+    if (m >= 0 && m < n) return m;
+    return wrap_any(v, n);
+}
+
 template <typename R, int NT, int D>
 __device__ __forceinline__ void march2d_segment(const Geom& g, const Phys<R>& p, const StepIO<R>& io, int strip, int seg,
                                                 int H, unsigned char* smem_raw)

@@ -44,8 +44,13 @@ __device__ __forceinline__ R recip3(R x) { return R(1) / x; }
 template <>
 __device__ __forceinline__ float recip3<float>(float x) { return __frcp_rn(x); }
 
+// Storage plane of an unwrapped z (periodic, or mirrored about the half-way
+// walls with period 2n); the division only for v outside [-n, 2n).
 __device__ __forceinline__ int map_axis3(int v, int n, int walls)
 {
+    if (v >= 0 && v < n) return v;
+    const int d = walls ? (v < 0 ? -1 - v : 2 * n - 1 - v) : (v < 0 ? v + n : v - n);
+    if (d >= 0 && d < n) return d;
     if (!walls) return wrap_any3(v, n);
     const int m = wrap_any3(v, 2 * n);
     return m < n ? m : 2 * n - 1 - m;
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
             R* gx_dst = sgxy + (0 * NPIN + ring(z3, NPIN)) * A1;
             R* gy_dst = sgxy + (1 * NPIN + ring(z3, NPIN)) * A1;
             R* gz_dst = sgz + ring(z3, 3) * A1;
-            const int gzp = ghost ? 0 : (walls ? z3 : wrap_any3(z3, nz));
+            const int gzp = ghost ? 0 : (walls ? z3 : map_axis3(z3, nz, 0));
             for (int q = threadIdx.x; q < A1; q += NT) {
                 const int ly = q / W1, lx = q - ly * W1;
                 const bool ex_ = (lx == 0 || lx == W1 - 1), ey_ = (ly == 0 || ly == P3::H1 - 1);

@@ -36,8 +36,13 @@ __device__ __forceinline__ int wrap_s(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// Storage plane of an unwrapped z (periodic, or mirrored about the half-way
+// walls with period 2n); the division only for v outside [-n, 2n).
 __device__ __forceinline__ int map_z(int v, int n, int walls)
 {
+    if (v >= 0 && v < n) return v;
+    const int d = walls ? (v < 0 ? -1 - v : 2 * n - 1 - v) : (v < 0 ? v + n : v - n);
+    if (d >= 0 && d < n) return d;
     if (!walls) return wrap_s(v, n);
     const int m = wrap_s(v, 2 * n);
     return m < n ? m : 2 * n - 1 - m;

@@ -11,8 +11,8 @@
 namespace lf {
 namespace tile {
 
-using march::wrap_any;
-using march::map_axis;
+using march::wrap_near;
+using march::map_row;
 
 // Stencils on a row-major shared-memory region of row length W, centre c.
 template <typename R, int W, bool ISO>
@@ -99,12 +99,12 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
     // ---- stage 1: phi (r = 4) and T (r = 2) -----------------------------
     for (int k = threadIdx.x; k < W4 * H4; k += NT) {
         const int ly = k / W4, lx = k - ly * W4;
-        const int gx = wrap_any(x0 - 4 + lx, nx), gy = map_axis(y0 - 4 + ly, ny, walls);
+        const int gx = wrap_near(x0 - 4 + lx, nx), gy = map_row(y0 - 4 + ly, ny, walls);
         sphi[k] = io.phi_in[(int64_t)gy * pitch + gx];
     }
     for (int k = threadIdx.x; k < W2 * H2; k += NT) {
         const int ly = k / W2, lx = k - ly * W2;
-        const int gx = wrap_any(x0 - 2 + lx, nx), gy = map_axis(y0 - 2 + ly, ny, walls);
+        const int gx = wrap_near(x0 - 2 + lx, nx), gy = map_row(y0 - 2 + ly, ny, walls);
         sT[k] = io.T_in[(int64_t)gy * pitch + gx];
     }
     __syncthreads();
@@ -176,7 +176,7 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
             sgy[k] = R(0);
             continue;
         }
-        const int gx = wrap_any(ux, nx), gy = walls ? uy : wrap_any(uy, ny);
+        const int gx = wrap_near(ux, nx), gy = walls ? uy : wrap_near(uy, ny);
         const int64_t site = (int64_t)gy * pitch + gx;
         R df[L::Q];
         R dn = R(0), jx = R(0), jy = R(0);
