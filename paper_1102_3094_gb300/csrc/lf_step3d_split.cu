@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
     const int t = threadIdx.x;
     const int cx = t % CW, cy = t / CW;                  // column of the psi region
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int64_t zs = (int64_t)ny * pitch;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * Hz, z1 = min(z0 + Hz, nz);
     const int kbeg = z0 - 3, kend = z1 + 2;
@@ -124,32 +124,38 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
     }
     __syncthreads();
     // storage offset of this column inside a plane (wrapped)
-    const int64_t col_off = (int64_t)rowmap[cy + 1] * pitch + colmap[cx + 1];
+    const int col_off = rowmap[cy + 1] * pitch + colmap[cx + 1];
     const int c3 = (cy + 1) * W3 + cx + 1;               // own position in a phi plane
     const int c2 = t;                                    // own position in a psi / P plane
+    // the phi elements this thread copies into every plane of the ring:
+    // q = t and q = t + NTH (when inside the r = 3 region), as in-plane offsets
+    static_assert(A3 <= 2 * NTH, "at most two phi elements per thread");
+    const int qe = t + NTH;
+    const bool two = qe < A3;
+    const int oe0 = rowmap[t / W3] * pitch + colmap[t % W3];
+    const int oe1 = two ? rowmap[qe / W3] * pitch + colmap[qe % W3] : 0;
 
     auto slot = [&](int z) { return (z - kbeg + 4 * P3::NPHI) % P3::NPHI; };
-    auto fetch = [&](int z) {
+    // pz: storage offset of plane z (z in [kbeg, kend])
+    auto fetch = [&](int z, int pz) {
         if (z <= kend) {
-            const int64_t pz = (int64_t)map_z(z, nz, walls) * zs;
             R* d = sphi + slot(z) * A3;
-            for (int q = t; q < A3; q += NTH) {
-                const int ly = q / W3, lx = q - ly * W3;
-                cp_async_s<sizeof(R)>(&d[q], io.phi_in + pz + (int64_t)rowmap[ly] * pitch + colmap[lx]);
-            }
+            cp_async_s<sizeof(R)>(&d[t], io.phi_in + (pz + oe0));
+            if (two) cp_async_s<sizeof(R)>(&d[qe], io.phi_in + (pz + oe1));
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    auto Tload = [&](int z) -> R {                       // T of this column (r = 1 columns only)
-        if (!in1 || z < kbeg || z > kend) return R(0);
-        return io.T_in[(int64_t)map_z(z, nz, walls) * zs + col_off];
+    auto Tload = [&](int z, int pz) -> R {               // T of this column (r = 1 columns only)
+        if (!in1 || z > kend) return R(0);
+        return io.T_in[pz + col_off];
     };
 
     // register windows along z (suffix = plane offset from k)
     R phm1 = 0, phm2 = 0, phm3 = 0;          // own-column phi(k-1), phi(k-2), phi(k-3)
     R psm1 = 0, psm2 = 0;                    // own-column psi(k-2), psi(k-3) (psi(k-1) is computed in iteration k)
     R xzA = 0, xzB = 0, xzC = 0, yzA = 0, yzB = 0, yzC = 0, zzA = 0, zzB = 0, zzC = 0;   // P_az at k-2 .. k-4
-    R Tq0 = Tload(kbeg), Tq1 = 0, Tq2 = 0, Tq3 = 0;   // T(k) .. T(k-3)
+    const int pz0 = map_z(kbeg, nz, walls) * zs;
+    R Tq0 = Tload(kbeg, pz0), Tq1 = 0, Tq2 = 0, Tq3 = 0;   // T(k) .. T(k-3)
 
     // The isotropic iteration: psi(k-1), barrier, lam / P / mu (k-2), barrier,
     // F (k-3); shared rings of three psi and three P planes, phi(k-3) kept in
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
             if (own && z2 >= z0 && z2 < z1) {
                 const R mu = av * ph + p.b * ph * ph * ph - p.kappa * psi + p.c * lam;
                 bad |= !isfinite(mu);
-                io.mu[(int64_t)z2 * zs + (int64_t)gy * pitch + gx] = mu;
+                io.mu[z2 * zs + gy * pitch + gx] = mu;
             }
             if (p.hydro) {
                 const R d0 = grad19<R, W3>(p3, p2, p1, c3, 0);
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
             const R Fx = -(D(0, 0) + D(1, 1) + D(3, 2));
             const R Fy = -(D(1, 0) + D(2, 1) + D(4, 2));
             const R Fz = -(D(3, 0) + D(4, 1) + D(5, 2));
-            const int64_t site = (int64_t)z3 * zs + (int64_t)gy * pitch + gx;
+            const int site = z3 * zs + gy * pitch + gx;
             io.F[0][site] = Fx;
             io.F[1][site] = Fy;
             io.F[2][site] = Fz;
@@ -213,12 +219,13 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
         Tq3 = Tq2; Tq2 = Tq1; Tq1 = Tq0;
     };
 
-    fetch(kbeg);
+    fetch(kbeg, pz0);
     for (int k = kbeg; k <= kend; ++k) {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        fetch(k + 1);
-        const R Tnext = Tload(k + 1);                    // consumed three iterations later
+        const int pzn = k + 1 <= kend ? map_z(k + 1, nz, walls) * zs : 0;
+        fetch(k + 1, pzn);
+        const R Tnext = Tload(k + 1, pzn);               // consumed three iterations later
         const R* pk = sphi + slot(k) * A3;
         const R* p1 = sphi + slot(k - 1) * A3;
         const R* p2 = sphi + slot(k - 2) * A3;
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
             if (own && z2 >= z0 && z2 < z1) {
                 const R mu = av * ph + p.b * ph * ph * ph - p.kappa * psi + p.c * lam;
                 bad |= !isfinite(mu);
-                io.mu[(int64_t)z2 * zs + (int64_t)gy * pitch + gx] = mu;
+                io.mu[z2 * zs + gy * pitch + gx] = mu;
             }
             if (p.hydro) {
                 const R d0 = half * (p2[c3 + 1] - p2[c3 - 1]);
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
                            + half * (yz - yzC));
             const R Fz = -(half * (P[3 * A2 + c2 + 1] - P[3 * A2 + c2 - 1]) + half * (P[4 * A2 + c2 + CW] - P[4 * A2 + c2 - CW])
                            + half * (zz - zzC));
-            const int64_t site = (int64_t)z3 * zs + (int64_t)gy * pitch + gx;
+            const int site = z3 * zs + gy * pitch + gx;
             io.F[0][site] = Fx;
             io.F[1][site] = Fy;
             io.F[2][site] = Fz;
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
     const int t = threadIdx.x;
     const int cx = t % CW, cy = t / CW;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int64_t zs = (int64_t)ny * pitch;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int za0 = blockIdx.z * 2 * H, zb0 = za0 + H;                    // first plane of each lane
     const int ha = min(H, nz - za0), hb = max(0, min(H, nz - zb0));     // planes per lane
@@ -349,46 +356,57 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
         else rowmap[q - W3] = wrap_s(y0 - 3 + (q - W3), ny);
     }
     __syncthreads();
-    const int64_t col_off = (int64_t)rowmap[cy + 1] * pitch + colmap[cx + 1];
+    const int col_off = rowmap[cy + 1] * pitch + colmap[cx + 1];
     const int c3 = (cy + 1) * W3 + cx + 1;
     const int c2 = t;
-    const int64_t own_off = (int64_t)gy * pitch + gx;
+    const int own_off = gy * pitch + gx;
+    // the phi elements this thread copies into every plane of the ring:
+    // q = t and q = t + NTH (when inside the r = 3 region), as in-plane offsets
+    static_assert(A3 <= 2 * NTH, "at most two phi elements per thread");
+    const int qe = t + NTH;
+    const bool two = qe < A3;
+    const int oe0 = rowmap[t / W3] * pitch + colmap[t % W3];
+    const int oe1 = two ? rowmap[qe / W3] * pitch + colmap[qe % W3] : 0;
 
     // relative plane j (iteration k = j + 3 loads relative plane k + 1 - 3 ... ): plane of lane L = z0_L + j
     auto slot = [&](int j) { return (j + 4 * P3::NPHI) % P3::NPHI; };
-    auto fetch = [&](int j) {                             // relative plane j = -3 .. hmax + 2
+    // storage offsets pa, pb of relative plane j in the two lanes, j = -3 .. hmax + 2
+    auto fetch = [&](int j, int pa, int pb) {
         if (j <= hmax + 2) {
-            const int64_t pa = (int64_t)map_z(za0 + j, nz, walls) * zs;
-            const int64_t pb = (int64_t)map_z(zb0 + j, nz, walls) * zs;
             float* d = reinterpret_cast<float*>(sphi + slot(j) * A3);
-            for (int q = t; q < A3; q += NTH) {
-                const int ly = q / W3, lx = q - ly * W3;
-                const int64_t o = (int64_t)rowmap[ly] * pitch + colmap[lx];
-                cp_async_s<4>(d + 2 * q, io.phi_in + pa + o);
-                cp_async_s<4>(d + 2 * q + 1, io.phi_in + pb + o);
+            cp_async_s<4>(d + 2 * t, io.phi_in + (pa + oe0));
+            cp_async_s<4>(d + 2 * t + 1, io.phi_in + (pb + oe0));
+            if (two) {
+                cp_async_s<4>(d + 2 * qe, io.phi_in + (pa + oe1));
+                cp_async_s<4>(d + 2 * qe + 1, io.phi_in + (pb + oe1));
             }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    auto Tload = [&](int j) -> float2 {
-        if (!in1 || j < -3 || j > hmax + 2) return v2(0.f);
-        return make_float2(io.T_in[(int64_t)map_z(za0 + j, nz, walls) * zs + col_off],
-                           io.T_in[(int64_t)map_z(zb0 + j, nz, walls) * zs + col_off]);
+    auto Tload = [&](int j, int pa, int pb) -> float2 {
+        if (!in1 || j > hmax + 2) return v2(0.f);
+        return make_float2(io.T_in[pa + col_off], io.T_in[pb + col_off]);
     };
 
     float2 phm1 = v2(0), phm2 = v2(0), phm3 = v2(0);
     float2 psm1 = v2(0), psm2 = v2(0);
     float2 xzB = v2(0), xzC = v2(0), yzB = v2(0), yzC = v2(0), zzB = v2(0), zzC = v2(0);
-    float2 Tq0 = Tload(-3), Tq1 = v2(0), Tq2 = v2(0);
+    const int pa0 = map_z(za0 - 3, nz, walls) * zs, pb0 = map_z(zb0 - 3, nz, walls) * zs;
+    float2 Tq0 = Tload(-3, pa0, pb0), Tq1 = v2(0), Tq2 = v2(0);
 
-    fetch(-3);
+    fetch(-3, pa0, pb0);
     // iteration i handles relative plane j = i - 3 as "k": fetch j + 1, psi on j - 1, P on j - 2, F on j - 3
 #pragma unroll 1
     for (int j = -3; j < nit - 3; ++j) {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        fetch(j + 1);
-        const float2 Tnext = Tload(j + 1);
+        int pan = 0, pbn = 0;
+        if (j + 1 <= hmax + 2) {
+            pan = map_z(za0 + j + 1, nz, walls) * zs;
+            pbn = map_z(zb0 + j + 1, nz, walls) * zs;
+        }
+        fetch(j + 1, pan, pbn);
+        const float2 Tnext = Tload(j + 1, pan, pbn);
         const float2* pk = sphi + slot(j) * A3;
         const float2* p1 = sphi + slot(j - 1) * A3;
         const float2* p2 = sphi + slot(j - 2) * A3;
@@ -412,8 +430,8 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
             if (own && r2 >= 0) {
                 // mu = a phi + b phi^3 - kappa psi + c lam
                 const float2 mu = fma2(v2(p.c), lam, fma2(v2(-p.kappa), psi, mul2(ph, fma2(v2(p.b), ph2, av))));
-                if (r2 < ha) { bad |= !isfinite(mu.x); io.mu[(int64_t)(za0 + r2) * zs + own_off] = mu.x; }
-                if (r2 < hb) { bad |= !isfinite(mu.y); io.mu[(int64_t)(zb0 + r2) * zs + own_off] = mu.y; }
+                if (r2 < ha) { bad |= !isfinite(mu.x); io.mu[(za0 + r2) * zs + own_off] = mu.x; }
+                if (r2 < hb) { bad |= !isfinite(mu.y); io.mu[(zb0 + r2) * zs + own_off] = mu.y; }
             }
             if (p.hydro) {
                 const float2 d0 = mul2(half, sub2(p2[c3 + 1], p2[c3 - 1]));
@@ -452,11 +470,11 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
             const float2 Fz = sub2(v2(0), mul2(half, add2(add2(sub2(P[3 * A2 + c2 + 1], P[3 * A2 + c2 - 1]),
                                                                sub2(P[4 * A2 + c2 + CW], P[4 * A2 + c2 - CW])), sub2(zz, zzC))));
             if (r3 < ha) {
-                const int64_t site = (int64_t)(za0 + r3) * zs + own_off;
+                const int site = (za0 + r3) * zs + own_off;
                 io.F[0][site] = Fx.x; io.F[1][site] = Fy.x; io.F[2][site] = Fz.x;
             }
             if (r3 < hb) {
-                const int64_t site = (int64_t)(zb0 + r3) * zs + own_off;
+                const int site = (zb0 + r3) * zs + own_off;
                 io.F[0][site] = Fx.y; io.F[1][site] = Fy.y; io.F[2][site] = Fz.y;
             }
         }
@@ -480,8 +498,8 @@ __global__ void __launch_bounds__(128) k_lb3d(Geom g, Phys<R> p, StepIO<R> io)
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int64_t plane = g.plane, zs = (int64_t)ny * pitch;
-    const int64_t site = z * zs + (int64_t)y * pitch + x;
+    const int plane = (int)g.plane, zs = ny * pitch;   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int site = z * zs + y * pitch + x;
     R df[L::Q];
     R dn = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -510,12 +528,11 @@ __global__ void __launch_bounds__(128) k_lb3d(Geom g, Phys<R> p, StepIO<R> io)
     const bool wall_lo = walls && z == 0, wall_hi = walls && z == nz - 1;
     R* out = io.f_out;
     out[site] = keep * df[0] + R(L::w(0)) * C0;
-    auto dest = [&](int ex, int ey, int ez) -> int64_t {
-        const int tx = ex > 0 ? gxp : (ex < 0 ? gxm : x);
-        const int ty = ey > 0 ? gyp : (ey < 0 ? gym : y);
-        const int tz = ez > 0 ? gzu : (ez < 0 ? gzd : z);
-        return tz * zs + (int64_t)ty * pitch + tx;
-    };
+    // neighbour offsets per axis, indexed by the velocity component + 1
+    const int rx[3] = {gxm, x, gxp};
+    const int ry[3] = {gym * pitch, y * pitch, gyp * pitch};
+    const int rz[3] = {gzd * zs, z * zs, gzu * zs};
+    auto dest = [&](int ex, int ey, int ez) -> int { return rz[ez + 1] + ry[ey + 1] + rx[ex + 1]; };
 #pragma unroll
     for (int i = 1; i < L::Q; i += 2) {           // (i, i + 1) are opposite
         const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
@@ -551,10 +568,10 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
     if (x >= g.nx || y >= g.ny) return;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int64_t zs = (int64_t)ny * pitch;
-    const int64_t row = (int64_t)y * pitch;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int row = y * pitch;
     const int xl = x == 0 ? nx - 1 : x - 1, xr = x + 1 == nx ? 0 : x + 1;
-    const int64_t ryl = (int64_t)(y == 0 ? ny - 1 : y - 1) * pitch, ryr = (int64_t)(y + 1 == ny ? 0 : y + 1) * pitch;
+    const int ryl = (y == 0 ? ny - 1 : y - 1) * pitch, ryr = (y + 1 == ny ? 0 : y + 1) * pitch;
     const R half = R(0.5);
     const R* __restrict__ mu = io.mu;
     const R* __restrict__ ph = io.phi_in;
@@ -575,7 +592,7 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     };
     auto load_nb = [&](int z) {
         Nb v;
-        const int64_t pz = (int64_t)z * zs;
+        const int pz = z * zs;
         v.mxl = mu[pz + row + xl]; v.mxr = mu[pz + row + xr];
         v.myl = mu[pz + ryl + x]; v.myr = mu[pz + ryr + x];
         v.txl = T[pz + row + xl]; v.txr = T[pz + row + xr];
@@ -591,15 +608,15 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
         }
         return v;
     };
-    int64_t o = below(za) * zs + row + x;
+    int o = below(za) * zs + row + x;
     R mu_d = mu[o], T_d = T[o], gz_d = hyd ? ph[o] * uz[o] : R(0);
-    o = (int64_t)za * zs + row + x;
+    o = za * zs + row + x;
     R mu_c = mu[o], T_c = T[o], gz_c = hyd ? ph[o] * uz[o] : R(0);
     Nb nb = load_nb(za);
     bool bad = false;
     for (int z = za; z < zb; ++z) {
-        const int64_t site = (int64_t)z * zs + row + x;
-        const int64_t ou = above(z) * zs + row + x;
+        const int site = z * zs + row + x;
+        const int ou = above(z) * zs + row + x;
         const R mu_u = mu[ou], T_u = T[ou], gz_u = hyd ? ph[ou] * uz[ou] : R(0);
         const Nb nxt = load_nb(z + 1 < zb ? z + 1 : z);
         const R lapmu = nb.mxl + nb.mxr + nb.myl + nb.myr + mu_u + mu_d - R(6) * mu_c;
@@ -657,7 +674,7 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
     const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int64_t zs = (int64_t)ny * pitch;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
     const bool hyd = p.hydro != 0;
     const R* __restrict__ mu = io.mu;
     const R* __restrict__ ph = io.phi_in;
@@ -666,14 +683,14 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
     const R* __restrict__ uy = io.u[1];
     const R* __restrict__ uz = io.u[2];
     // storage plane of logical plane zl: the wall plane beyond a wall, else periodic
-    auto zmap = [&](int zl) -> int64_t {
+    auto zmap = [&](int zl) -> int {
         int z = zl;
         if (walls) z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
         else z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-        return (int64_t)z * zs;
+        return z * zs;
     };
     // the (up to) two tile positions of this thread and their in-plane offsets
-    int64_t off[2];
+    int off[2];
     bool has[2];
     for (int i = 0; i < 2; ++i) {
         const int q = t + 256 * i;
@@ -682,14 +699,14 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
         int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-        off[i] = (int64_t)gy * pitch + gx;
+        off[i] = gy * pitch + gx;
     }
     R v[2][NF];
     auto fetch = [&](int zl) {
-        const int64_t pz = zmap(zl);
+        const int pz = zmap(zl);
         for (int i = 0; i < 2; ++i) {
             if (!has[i]) continue;
-            const int64_t o = pz + off[i];
+            const int o = pz + off[i];
             v[i][0] = mu[o];
             v[i][1] = T[o];
             const R f = ph[o];
@@ -739,7 +756,7 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
                 div = grad19<R, TW>(sm[sd][2], sm[s0][2], sm[su][2], c, 0)
                     + grad19<R, TW>(sm[sd][3], sm[s0][3], sm[su][3], c, 1) + dz;
             }
-            const int64_t site = (int64_t)z * zs + (int64_t)y * pitch + x;
+            const int site = z * zs + y * pitch + x;
             const R phn = ph[site] - div + p.Gamma * lapmu;
             io.phi_out[site] = phn;
             const R Tc0 = sm[s0][1][c];
