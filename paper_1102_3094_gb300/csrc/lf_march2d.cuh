@@ -326,7 +326,7 @@ __device__ __forceinline__ void tsub2d_site(const Geom& g, const Phys<R>& p, con
                                             R* __restrict__ Tout, int x, int y)
 {
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
-    const int64_t site = (int64_t)y * pitch + x;
+    const int site = y * pitch + x;
     const R t0 = Tin[site];
     if (g.walls && g.t_mode == LF_TWALL_LAYERS && (y == 0 || y == ny - 1)) {
         Tout[site] = p.T_w;
@@ -338,10 +338,10 @@ __device__ __forceinline__ void tsub2d_site(const Geom& g, const Phys<R>& p, con
         td = y == 0 ? R(2) * p.T_w - t0 : Tin[site - pitch];
         tu = y == ny - 1 ? R(2) * p.T_w - t0 : Tin[site + pitch];
     } else {
-        td = Tin[(int64_t)(y == 0 ? ny - 1 : y - 1) * pitch + x];
-        tu = Tin[(int64_t)(y == ny - 1 ? 0 : y + 1) * pitch + x];
+        td = Tin[(y == 0 ? ny - 1 : y - 1) * pitch + x];
+        tu = Tin[(y == ny - 1 ? 0 : y + 1) * pitch + x];
     }
-    Tout[site] = t0 + p.dxi * (Tin[(int64_t)y * pitch + xl] + Tin[(int64_t)y * pitch + xr] + tu + td - R(4) * t0);
+    Tout[site] = t0 + p.dxi * (Tin[y * pitch + xl] + Tin[y * pitch + xr] + tu + td - R(4) * t0);
 }
 
 // Segment height for a lattice: about four CTAs of four warps per SM

@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
     int* rowmap = colmap + W4;                                   // y0 - 4 + ly -> storage row
 
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int64_t plane = g.plane;                   // one population field
-    const int64_t zs = (int64_t)ny * pitch;          // one z plane
+    const int plane = (int)g.plane;                  // one population field (Q * padded sites < 2^31)
+    const int zs = ny * pitch;                      // one z plane
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * Hz, z1 = min(z0 + Hz, nz);
     const int kbeg = z0 - 4, kend = z1 + 3;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
             R* dT = sT + ring(z, P3::NT_) * A2;
             for (int q = threadIdx.x; q < A4; q += NT) {
                 const int ly = q / W4, lx = q - ly * W4;
-                const int64_t off = gz * zs + (int64_t)rowmap[ly] * pitch + colmap[lx];
+                const int off = gz * zs + rowmap[ly] * pitch + colmap[lx];
                 cp_async3<sizeof(R)>(&dphi[q], io.phi_in + off);
                 if (lx >= 2 && lx < W4 - 2 && ly >= 2 && ly < P3::H4 - 2)
                     cp_async3<sizeof(R)>(&dT[(ly - 2) * W2 + lx - 2], io.T_in + off);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
                     }
                 }
                 bad |= !isfinite(Tn);
-                io.T_out[z1p * zs + (int64_t)gy * pitch + gx] = Tn;
+                io.T_out[z1p * zs + gy * pitch + gx] = Tn;
             }
         }
         __syncthreads();
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
                     }
                     const int ux = x0 - 1 + lx, uy = y0 - 1 + ly;
                     const int gx = colmap[lx + 3], gy = rowmap[ly + 3];
-                    const int64_t site = gzp * zs + (int64_t)gy * pitch + gx;
+                    const int site = gzp * zs + gy * pitch + gx;
                     R df[L::Q];
                     R dn = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -356,11 +356,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
                             const bool wall_lo = walls && gzp == 0, wall_hi = walls && gzp == nz - 1;
                             R* out = io.f_out;
                             out[site] = keep * df[0] + R(L::w(0)) * C0;
-                            auto dest = [&](int ex, int ey, int ez) -> int64_t {
+                            auto dest = [&](int ex, int ey, int ez) -> int {
                                 const int tx = ex > 0 ? gxp : (ex < 0 ? gxm : gx);
                                 const int ty = ey > 0 ? gyp : (ey < 0 ? gym : gy);
                                 const int tz = ez > 0 ? gzu : (ez < 0 ? gzd : gzp);
-                                return tz * zs + (int64_t)ty * pitch + tx;
+                                return tz * zs + ty * pitch + tx;
                             };
 #pragma unroll
                             for (int i = 1; i < L::Q; i += 2) {           // (i, i + 1) are opposite
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? (ISO ? 2 : 3) : 1)
                 const int gx = x0 + lx, gy = y0 + ly;
                 if (gx >= nx || gy >= ny) continue;
                 const int c1 = (ly + 1) * W1 + lx + 1;
-                const int64_t site = z4 * zs + (int64_t)gy * pitch + gx;
+                const int site = z4 * zs + gy * pitch + gx;
                 if (AUX) {
                     io.mu[site] = mu0[c1];
                     continue;
@@ -490,8 +490,8 @@ __global__ void k_tsub3d(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __rest
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch;
-    const int64_t zs = (int64_t)ny * pitch;
-    const int64_t site = z * zs + (int64_t)y * pitch + x;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int site = z * zs + y * pitch + x;
     const R t0 = Tin[site];
     if (g.walls && g.t_mode == LF_TWALL_LAYERS && (z == 0 || z == nz - 1)) {
         Tout[site] = p.T_w;
@@ -504,12 +504,12 @@ __global__ void k_tsub3d(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __rest
         td = z == 0 ? R(2) * p.T_w - t0 : Tin[site - zs];
         tu = z == nz - 1 ? R(2) * p.T_w - t0 : Tin[site + zs];
     } else {
-        td = Tin[(z == 0 ? nz - 1 : z - 1) * zs + (int64_t)y * pitch + x];
-        tu = Tin[(z == nz - 1 ? 0 : z + 1) * zs + (int64_t)y * pitch + x];
+        td = Tin[(z == 0 ? nz - 1 : z - 1) * zs + y * pitch + x];
+        tu = Tin[(z == nz - 1 ? 0 : z + 1) * zs + y * pitch + x];
     }
-    const int64_t row = z * zs;
-    Tout[site] = t0 + p.dxi * (Tin[row + (int64_t)y * pitch + xl] + Tin[row + (int64_t)y * pitch + xr] +
-                               Tin[row + (int64_t)yl * pitch + x] + Tin[row + (int64_t)yr * pitch + x] + tu + td -
+    const int row = z * zs;
+    Tout[site] = t0 + p.dxi * (Tin[row + y * pitch + xl] + Tin[row + y * pitch + xr] +
+                               Tin[row + yl * pitch + x] + Tin[row + yr * pitch + x] + tu + td -
                                R(6) * t0);
 }
 
@@ -523,8 +523,8 @@ __global__ void k_tsub3d_iso(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch;
-    const int64_t zs = (int64_t)ny * pitch;
-    const int64_t site = z * zs + (int64_t)y * pitch + x;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int site = z * zs + y * pitch + x;
     const R t0 = Tin[site];
     if (g.walls && g.t_mode == LF_TWALL_LAYERS && (z == 0 || z == nz - 1)) {
         Tout[site] = p.T_w;
@@ -536,7 +536,7 @@ __global__ void k_tsub3d_iso(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __
     const int zd = lo ? 0 : (z == 0 ? nz - 1 : z - 1);
     const int zu = hi ? z : (z == nz - 1 ? 0 : z + 1);
     const R tw2 = R(2) * p.T_w;
-    auto at = [&](int zz, int yy, int xx) { return Tin[zz * zs + (int64_t)yy * pitch + xx]; };
+    auto at = [&](int zz, int yy, int xx) { return Tin[zz * zs + yy * pitch + xx]; };
     auto dn = [&](int yy, int xx) { return lo ? tw2 - at(zd, yy, xx) : at(zd, yy, xx); };
     auto up = [&](int yy, int xx) { return hi ? tw2 - at(zu, yy, xx) : at(zu, yy, xx); };
     const R nn = at(z, y, xl) + at(z, y, xr) + at(z, yl, x) + at(z, yr, x) + dn(y, x) + up(y, x);

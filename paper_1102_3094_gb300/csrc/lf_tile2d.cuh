@@ -91,7 +91,7 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
     R* sgy = sgx + W1 * H1;
 
     const int nx = g.nx, ny = g.ny, pitch = g.pitch, walls = g.walls;
-    const int64_t plane = g.plane;
+    const int plane = (int)g.plane;        // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
     const int x0 = bx * TX, y0 = by * TY;
     const R half = R(0.5);
     bool bad = false;
@@ -100,12 +100,12 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
     for (int k = threadIdx.x; k < W4 * H4; k += NT) {
         const int ly = k / W4, lx = k - ly * W4;
         const int gx = wrap_near(x0 - 4 + lx, nx), gy = map_row(y0 - 4 + ly, ny, walls);
-        sphi[k] = io.phi_in[(int64_t)gy * pitch + gx];
+        sphi[k] = io.phi_in[gy * pitch + gx];
     }
     for (int k = threadIdx.x; k < W2 * H2; k += NT) {
         const int ly = k / W2, lx = k - ly * W2;
         const int gx = wrap_near(x0 - 2 + lx, nx), gy = map_row(y0 - 2 + ly, ny, walls);
-        sT[k] = io.T_in[(int64_t)gy * pitch + gx];
+        sT[k] = io.T_in[gy * pitch + gx];
     }
     __syncthreads();
 
@@ -177,7 +177,7 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
             continue;
         }
         const int gx = wrap_near(ux, nx), gy = walls ? uy : wrap_near(uy, ny);
-        const int64_t site = (int64_t)gy * pitch + gx;
+        const int site = gy * pitch + gx;
         R df[L::Q];
         R dn = R(0), jx = R(0), jy = R(0);
 #pragma unroll
@@ -223,7 +223,7 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
             } else {
                 tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
                 ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-                io.f_out[i * plane + (int64_t)ty * pitch + tx] = post;
+                io.f_out[i * plane + ty * pitch + tx] = post;
             }
         }
     }
@@ -234,7 +234,7 @@ __device__ __forceinline__ void step2d_tile(const Geom& g, const Phys<R>& p, con
         const int ly = k / TX, lx = k - ly * TX;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= nx || gy >= ny) continue;
-        const int64_t site = (int64_t)gy * pitch + gx;
+        const int site = gy * pitch + gx;
         const int c1 = (ly + 1) * W1 + lx + 1;
         if (AUX) {
             io.mu[site] = smu[c1];
@@ -311,7 +311,7 @@ __device__ __forceinline__ void tsub2d_site_iso(const Geom& g, const Phys<R>& p,
                                                 R* __restrict__ Tout, int x, int y)
 {
     const int nx = g.nx, ny = g.ny, pitch = g.pitch;
-    const int64_t site = (int64_t)y * pitch + x;
+    const int site = y * pitch + x;
     const R t0 = Tin[site];
     if (g.walls && g.t_mode == LF_TWALL_LAYERS && (y == 0 || y == ny - 1)) {
         Tout[site] = p.T_w;
@@ -321,9 +321,9 @@ __device__ __forceinline__ void tsub2d_site_iso(const Geom& g, const Phys<R>& p,
     const bool lo = g.walls && y == 0, hi = g.walls && y == ny - 1;
     const int yd = lo ? 0 : (y == 0 ? ny - 1 : y - 1);
     const int yu = hi ? y : (y == ny - 1 ? 0 : y + 1);
-    const R* rd = Tin + (int64_t)yd * pitch;
-    const R* r0 = Tin + (int64_t)y * pitch;
-    const R* ru = Tin + (int64_t)yu * pitch;
+    const R* rd = Tin + yd * pitch;
+    const R* r0 = Tin + y * pitch;
+    const R* ru = Tin + yu * pitch;
     const R two_w = R(2) * p.T_w;
     const R d0 = lo ? two_w - rd[x] : rd[x], dl = lo ? two_w - rd[xl] : rd[xl], dr = lo ? two_w - rd[xr] : rd[xr];
     const R u0 = hi ? two_w - ru[x] : ru[x], ul = hi ? two_w - ru[xl] : ru[xl], ur = hi ? two_w - ru[xr] : ru[xr];
