@@ -568,10 +568,10 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
     if (x >= g.nx || y >= g.ny) return;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
-    const int row = y * pitch;
+    const int64_t zs = (int64_t)ny * pitch;
+    const int64_t row = (int64_t)y * pitch;
     const int xl = x == 0 ? nx - 1 : x - 1, xr = x + 1 == nx ? 0 : x + 1;
-    const int ryl = (y == 0 ? ny - 1 : y - 1) * pitch, ryr = (y + 1 == ny ? 0 : y + 1) * pitch;
+    const int64_t ryl = (int64_t)(y == 0 ? ny - 1 : y - 1) * pitch, ryr = (int64_t)(y + 1 == ny ? 0 : y + 1) * pitch;
     const R half = R(0.5);
     const R* __restrict__ mu = io.mu;
     const R* __restrict__ ph = io.phi_in;
@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
     };
     auto load_nb = [&](int z) {
         Nb v;
-        const int pz = z * zs;
+        const int64_t pz = (int64_t)z * zs;
         v.mxl = mu[pz + row + xl]; v.mxr = mu[pz + row + xr];
         v.myl = mu[pz + ryl + x]; v.myr = mu[pz + ryr + x];
         v.txl = T[pz + row + xl]; v.txr = T[pz + row + xr];
@@ -608,15 +608,15 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
         }
         return v;
     };
-    int o = below(za) * zs + row + x;
+    int64_t o = below(za) * zs + row + x;
     R mu_d = mu[o], T_d = T[o], gz_d = hyd ? ph[o] * uz[o] : R(0);
-    o = za * zs + row + x;
+    o = (int64_t)za * zs + row + x;
     R mu_c = mu[o], T_c = T[o], gz_c = hyd ? ph[o] * uz[o] : R(0);
     Nb nb = load_nb(za);
     bool bad = false;
     for (int z = za; z < zb; ++z) {
-        const int site = z * zs + row + x;
-        const int ou = above(z) * zs + row + x;
+        const int64_t site = (int64_t)z * zs + row + x;
+        const int64_t ou = above(z) * zs + row + x;
         const R mu_u = mu[ou], T_u = T[ou], gz_u = hyd ? ph[ou] * uz[ou] : R(0);
         const Nb nxt = load_nb(z + 1 < zb ? z + 1 : z);
         const R lapmu = nb.mxl + nb.mxr + nb.myl + nb.myr + mu_u + mu_d - R(6) * mu_c;
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
     const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
-    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int64_t zs = (int64_t)ny * pitch;
     const bool hyd = p.hydro != 0;
     const R* __restrict__ mu = io.mu;
     const R* __restrict__ ph = io.phi_in;
@@ -683,14 +683,14 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
     const R* __restrict__ uy = io.u[1];
     const R* __restrict__ uz = io.u[2];
     // storage plane of logical plane zl: the wall plane beyond a wall, else periodic
-    auto zmap = [&](int zl) -> int {
+    auto zmap = [&](int zl) -> int64_t {
         int z = zl;
         if (walls) z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
         else z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-        return z * zs;
+        return (int64_t)z * zs;
     };
     // the (up to) two tile positions of this thread and their in-plane offsets
-    int off[2];
+    int64_t off[2];
     bool has[2];
     for (int i = 0; i < 2; ++i) {
         const int q = t + 256 * i;
@@ -699,14 +699,14 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
         int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-        off[i] = gy * pitch + gx;
+        off[i] = (int64_t)gy * pitch + gx;
     }
     R v[2][NF];
     auto fetch = [&](int zl) {
-        const int pz = zmap(zl);
+        const int64_t pz = zmap(zl);
         for (int i = 0; i < 2; ++i) {
             if (!has[i]) continue;
-            const int o = pz + off[i];
+            const int64_t o = pz + off[i];
             v[i][0] = mu[o];
             v[i][1] = T[o];
             const R f = ph[o];
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
                 div = grad19<R, TW>(sm[sd][2], sm[s0][2], sm[su][2], c, 0)
                     + grad19<R, TW>(sm[sd][3], sm[s0][3], sm[su][3], c, 1) + dz;
             }
-            const int site = z * zs + y * pitch + x;
+            const int64_t site = (int64_t)z * zs + (int64_t)y * pitch + x;
             const R phn = ph[site] - div + p.Gamma * lapmu;
             io.phi_out[site] = phn;
             const R Tc0 = sm[s0][1][c];
