@@ -83,6 +83,8 @@ CASES = [
     dict(nx=40, ny=24, hydro=0, xi=0.1),                          # no hydrodynamics
     dict(nx=130, ny=70, tau=0.6, xi=1e-3),                        # several tiles, low viscosity
     dict(nx=36, ny=30, xi=math.inf, tau=3.0),                     # instantaneous quench
+    dict(nx=3, ny=2, xi=0.01),                                    # thinner than every halo: the
+    dict(nx=2, ny=3, walls=0, xi=0.01),                           # index maps' general path
 ]
 
 
@@ -167,6 +169,8 @@ CASES3 = [
     dict(d=3, nx=14, ny=11, nz=8, t_wall_mode=1, xi=0.4),          # halfway T ghost, 3 sub-steps
     dict(d=3, nx=10, ny=9, nz=7, hydro=0, xi=0.1),                 # no hydrodynamics
     dict(d=3, nx=36, ny=17, nz=5, tau=0.6, xi=1e-3),               # thin in z
+    dict(d=3, nx=3, ny=2, nz=2, xi=0.01),                          # thinner than every halo: the
+    dict(d=3, nx=2, ny=3, nz=3, walls=0, xi=0.01),                 # index maps' general path
 ]
 
 
@@ -207,17 +211,22 @@ def test_isotropic_multistep_3d_fp64():
 
 
 def _check_aux_and_step_3d(sim, st, prec):
+    """Components of F and u are measured against the largest component of
+    their vector: on a lattice two sites thick a y-derivative is zero, exactly
+    on the GPU and up to rounding (1e-19) in the oracle's 19-point sums."""
     tol = TOL[prec]
     ax = O.aux(st)
-    checks = {"mu": (sim.get("mu"), ax["mu"]), "rho": (sim.get("rho"), ax["n"])}
-    for a, name in enumerate(("x", "y", "z")):
-        checks["F" + name] = (sim.get("F" + name), ax["F"][a])
-        checks["u" + name] = (sim.get("u" + name), ax["u"][a])
-    for k, (g, w) in checks.items():
-        if np.abs(w).max() == 0:
-            assert np.abs(g).max() == 0, k
-            continue
+    for k, (g, w) in {"mu": (sim.get("mu"), ax["mu"]), "rho": (sim.get("rho"), ax["n"])}.items():
         assert relerr(g, w) < tol, (k, relerr(g, w))
+    for vec, key in (("F", "F"), ("u", "u")):
+        scale = max(np.abs(c).max() for c in ax[key])
+        for a, name in enumerate(("x", "y", "z")):
+            g, w = sim.get(vec + name), ax[key][a]
+            if scale == 0:
+                assert np.abs(g).max() == 0, vec + name
+                continue
+            err = np.abs(g - w).max() / scale
+            assert err < tol, (vec + name, err)
     sim.step(1)
     ref = O.step(st)
     for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
