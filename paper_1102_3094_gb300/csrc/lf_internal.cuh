@@ -161,4 +161,40 @@ inline int wait_stream(cudaStream_t s)
     return rc;
 }
 
+// A kernel's dynamic shared-memory limit and the SM count belong to the
+// current device, and one process may drive several devices: both are kept
+// per device ordinal (0 .. 63; beyond that the attribute is set on every call).
+constexpr int kMaxDevices = 64;
+
+template <typename K>
+cudaError_t raise_smem_limit(K kern, int bytes, unsigned long long* done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < kMaxDevices ? 1ull << dev : 0ull;
+    if (bit && (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);
+    return e;
+}
+
+inline cudaError_t device_sms(int* sms)
+{
+    static int cache[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < kMaxDevices) {
+        const int c = __atomic_load_n(&cache[dev], __ATOMIC_ACQUIRE);
+        if (c > 0) { *sms = c; return cudaSuccess; }
+    }
+    int n = 0;
+    if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    n = n > 0 ? n : 1;
+    if (dev < kMaxDevices) __atomic_store_n(&cache[dev], n, __ATOMIC_RELEASE);
+    *sms = n;
+    return cudaSuccess;
+}
+
 }  // namespace lf

@@ -70,15 +70,11 @@ cudaError_t launch_march_x2(const Geom& g, const Phys<float>& p, const StepIO<fl
 {
     using M = march::March2<NT, D>;
     auto kern = k_march2d_x2<NT, D, HYDRO, MINB>;
-    static int sms = 0;
-    if (sms == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::BYTES);
-        if (e != cudaSuccess) return e;
-        int dev = 0, n = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        sms = n > 0 ? n : 1;
-    }
+    static unsigned long long attr_done = 0;
+    cudaError_t e = raise_smem_limit(kern, (int)M::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = device_sms(&sms)) != cudaSuccess) return e;
     const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
     int npairs = (g.ny + 2 * H - 1) / (2 * H);
     if (npairs > g.ny / 2) npairs = g.ny / 2;       // every lane keeps at least one row
@@ -92,15 +88,11 @@ cudaError_t launch_march(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
 {
     using M = march::March<R, NT, D>;
     auto kern = k_march2d<R, NT, D>;
-    static int sms = 0;
-    if (sms == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M::BYTES);
-        if (e != cudaSuccess) return e;
-        int dev = 0, n = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        sms = n > 0 ? n : 1;
-    }
+    static unsigned long long attr_done = 0;
+    cudaError_t e = raise_smem_limit(kern, (int)M::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = device_sms(&sms)) != cudaSuccess) return e;
     const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
     dim3 grid((g.nx + M::U - 1) / M::U, (g.ny + H - 1) / H);
     kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
@@ -112,12 +104,9 @@ cudaError_t launch_cfg(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cud
 {
     constexpr size_t bytes = tile::Tile<R, TX, TY>::BYTES;
     auto kern = k_step2d<R, TX, TY, NT, AUX, ISO>;
-    static bool attr_set = false;   // per instantiation; harmless to repeat
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    const cudaError_t e = raise_smem_limit(kern, (int)bytes, &attr_done);
+    if (e != cudaSuccess) return e;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
     kern<<<grid, NT, bytes, s>>>(g, p, io);
     return cudaGetLastError();

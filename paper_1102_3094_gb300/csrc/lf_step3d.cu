@@ -463,12 +463,9 @@ cudaError_t launch_cfg3(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cu
 {
     using P3 = Plane3<R, TX, TY, ISO>;
     auto kern = k_march3d<R, TX, TY, NT, AUX, ISO>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P3::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    const cudaError_t e = raise_smem_limit(kern, (int)P3::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int Hz = g.tune > 0 ? g.tune : g.nz;
     if (g.tune <= 0) {   // about eight waves of three CTAs per SM, segments of at least 16 planes

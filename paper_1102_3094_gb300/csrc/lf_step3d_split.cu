@@ -785,12 +785,9 @@ cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
 {
     using P3 = Force3<R, TX, TY, ISO>;
     auto kern = k_force3d<R, TX, TY, ISO>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P3::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    const cudaError_t e = raise_smem_limit(kern, (int)P3::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int Hz = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;
     if (Hz <= 0) {   // about eight waves of two CTAs per SM, segments of at least 16 planes
@@ -809,12 +806,9 @@ cudaError_t launch_force_x2(const Geom& g, const Phys<float>& p, const StepIO<fl
 {
     using P3 = Force3x2<TX, TY>;
     auto kern = k_force3d_x2<TX, TY>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P3::BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    const cudaError_t e = raise_smem_limit(kern, (int)P3::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
     int H = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;     // planes per lane
     if (H <= 0) {   // about eight CTAs per SM (two resident), lanes of at least 16 planes
@@ -855,13 +849,8 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
     dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kZC - 1) / kZC);
     if (iso) {
         constexpr size_t bytes = sizeof(R) * 4 * kIsoNF * kIsoTA;
-        static bool attr_set = false;
-        if (!attr_set) {
-            if ((e = cudaFuncSetAttribute(k_phi3d_iso<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)) !=
-                cudaSuccess)
-                return e;
-            attr_set = true;
-        }
+        static unsigned long long attr_done = 0;
+        if ((e = raise_smem_limit(k_phi3d_iso<R>, (int)bytes, &attr_done)) != cudaSuccess) return e;
         k_phi3d_iso<R><<<gc, 256, bytes, s>>>(g, p, io);
     } else
         k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io);

@@ -252,12 +252,8 @@ template <int CIN, int COUT>
 cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
 {
     using S = ConvSmem<CIN, COUT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    if (cudaError_t e = raise_smem_limit(k_conv3x3<CIN, COUT>, (int)S::BYTES, &attr_done); e != cudaSuccess) return e;
     // rows per item: at least ~4 rows (prologue of 4 loaded rows) and about
     // two items per SM over the whole launch
     const int cols = a.B * (a.NX / 128);
@@ -485,12 +481,9 @@ cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, 
                          size_t part_floats, float* dW, int* err, cudaStream_t s)
 {
     using S = WgCfg<CIN, COUT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    if (cudaError_t e = raise_smem_limit(k_conv_wgrad<CIN, COUT>, (int)S::BYTES, &attr_done); e != cudaSuccess)
+        return e;
     if (part_floats < S::PART) return cudaErrorInvalidValue;
     WgArgs a{h, g, part, B, NY, NX, err};
     k_conv_wgrad<CIN, COUT><<<152, 128, S::BYTES, s>>>(a);
