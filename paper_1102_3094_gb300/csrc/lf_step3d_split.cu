@@ -371,9 +371,9 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
     // relative plane j (iteration k = j + 3 loads relative plane k + 1 - 3 ... ): plane of lane L = z0_L + j
     auto slot = [&](int j) { return (j + 4 * P3::NPHI) % P3::NPHI; };
     // storage offsets pa, pb of relative plane j in the two lanes, j = -3 .. hmax + 2
-    auto fetch = [&](int j, int pa, int pb) {
+    auto fetch_s = [&](int sl, int j, int pa, int pb) {      // into ring slot sl
         if (j <= hmax + 2) {
-            float* d = reinterpret_cast<float*>(sphi + slot(j) * A3);
+            float* d = reinterpret_cast<float*>(sphi + sl * A3);
             cp_async_s<4>(d + 2 * t, io.phi_in + (pa + oe0));
             cp_async_s<4>(d + 2 * t + 1, io.phi_in + (pb + oe0));
             if (two) {
@@ -394,10 +394,14 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
     const int pa0 = map_z(za0 - 3, nz, walls) * zs, pb0 = map_z(zb0 - 3, nz, walls) * zs;
     float2 Tq0 = Tload(-3, pa0, pb0), Tq1 = v2(0), Tq2 = v2(0);
 
-    fetch(-3, pa0, pb0);
-    // iteration i handles relative plane j = i - 3 as "k": fetch j + 1, psi on j - 1, P on j - 2, F on j - 3
-#pragma unroll 1
-    for (int j = -3; j < nit - 3; ++j) {
+    fetch_s(slot(-3), -3, pa0, pb0);
+    // iteration j handles relative plane j as "k": fetch j + 1, psi on j - 1, P on j - 2, F on j - 3.
+    // Four iterations per trip with j = U - 3 (mod 4) in sub-iteration U, so
+    // ring slots and buffer parities are constants and the register windows
+    // of depth two need no copies; iterations past the last plane (up to three
+    // in the last trip) do only guarded-off work.
+    auto iter = [&](const int j, auto utag) {
+        constexpr int U = decltype(utag)::value;
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
         int pan = 0, pbn = 0;
@@ -405,23 +409,23 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
             pan = map_z(za0 + j + 1, nz, walls) * zs;
             pbn = map_z(zb0 + j + 1, nz, walls) * zs;
         }
-        fetch(j + 1, pan, pbn);
+        fetch_s((2 + U) & 3, j + 1, pan, pbn);
         const float2 Tnext = Tload(j + 1, pan, pbn);
-        const float2* pk = sphi + slot(j) * A3;
-        const float2* p1 = sphi + slot(j - 1) * A3;
-        const float2* p2 = sphi + slot(j - 2) * A3;
+        const float2* pk = sphi + ((1 + U) & 3) * A3;
+        const float2* p1 = sphi + (U & 3) * A3;
+        const float2* p2 = sphi + ((U + 3) & 3) * A3;
         const float2 phk = pk[c3];
 
         // psi of plane j - 1
         const float2 psi_new = fma2(six, sub2(v2(0), phm1),
                                     add2(add2(add2(p1[c3 - 1], p1[c3 + 1]), add2(p1[c3 - W3], p1[c3 + W3])), add2(phm2, phk)));
-        spsi[((j - 1) & 1) * A2 + c2] = psi_new;
+        spsi[(U & 1) * A2 + c2] = psi_new;
 
         // lam, P, mu of plane j - 2
         float2 xz = v2(0), yz = v2(0), zz = v2(0);
         const int r2 = j - 2;                              // relative plane
         if (in1 && r2 >= -1 && r2 <= hmax) {
-            const float2* ps = spsi + ((j - 2) & 1) * A2;
+            const float2* ps = spsi + ((U + 1) & 1) * A2;
             const float2 ph = phm2, psi = psm1;
             const float2 lam = fma2(six, sub2(v2(0), psi),
                                     add2(add2(add2(ps[c2 - 1], ps[c2 + 1]), add2(ps[c2 - CW], ps[c2 + CW])), add2(psi_new, psm2)));
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
                 iso = fma2(v2(-p.kappa), fma2(half, gp2, mul2(ph, psi)), iso);
                 iso = fma2(v2(p.c), add2(fma2(ph, lam, mul2(half, mul2(psi, psi))), gpgs), iso);
                 const float2 k_ = v2(p.kappa), mc = v2(-p.c), m2c = v2(-2.f * p.c);
-                float2* P = sP + ((j - 2) & 1) * 5 * A2;
+                float2* P = sP + ((U + 1) & 1) * 5 * A2;
                 P[0 * A2 + c2] = fma2(k_, mul2(d0, d0), fma2(m2c, mul2(d0, s0), iso));
                 P[1 * A2 + c2] = fma2(k_, mul2(d0, d1), mul2(mc, fma2(d0, s1, mul2(d1, s0))));
                 P[2 * A2 + c2] = fma2(k_, mul2(d1, d1), fma2(m2c, mul2(d1, s1), iso));
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
         // F of plane j - 3
         const int r3 = j - 3;
         if (p.hydro && own && r3 >= 0 && r3 < hmax) {
-            const float2* P = sP + ((j - 3) & 1) * 5 * A2;
+            const float2* P = sP + (U & 1) * 5 * A2;
             const float2 Fx = sub2(v2(0), mul2(half, add2(add2(sub2(P[0 * A2 + c2 + 1], P[0 * A2 + c2 - 1]),
                                                                sub2(P[1 * A2 + c2 + CW], P[1 * A2 + c2 - CW])), sub2(xz, xzC))));
             const float2 Fy = sub2(v2(0), mul2(half, add2(add2(sub2(P[1 * A2 + c2 + 1], P[1 * A2 + c2 - 1]),
@@ -483,6 +487,13 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
         psm2 = psm1; psm1 = psi_new;
         xzC = xzB; xzB = xz; yzC = yzB; yzB = yz; zzC = zzB; zzB = zz;
         Tq2 = Tq1; Tq1 = Tq0; Tq0 = Tnext;
+    };
+#pragma unroll 1
+    for (int j = -3; j < nit - 3; j += 4) {
+        iter(j, std::integral_constant<int, 0>{});
+        iter(j + 1, std::integral_constant<int, 1>{});
+        iter(j + 2, std::integral_constant<int, 2>{});
+        iter(j + 3, std::integral_constant<int, 3>{});
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
@@ -815,6 +826,7 @@ cudaError_t launch_force_x2(const Geom& g, const Phys<float>& p, const StepIO<fl
         const int want = (8 * 152 + tiles - 1) / tiles;
         H = (g.nz + 2 * want - 1) / (2 * want);
         if (H < 16) H = 16;
+        H += (6 - H % 4) % 4;   // H + 6 iterations: whole trips of four
     }
     if (H > g.nz) H = g.nz;
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + 2 * H - 1) / (2 * H));
