@@ -272,9 +272,13 @@ int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
  *     normal (a division when every axis is periodic).  Unconditionally
  *     stable: one solve per step at any xi.  Needs the periodic lattice sizes
  *     to be at most 4096 with prime factors up to 31.
- * The phi, f update always uses T(t).  Returns LF_EINVAL for an unknown
- * solver, an unsupported size, or an ensemble member (ensembles always take
- * explicit sub-steps).  Not stored in checkpoints. */
+ * The phi, f update always uses T(t).  With walls, switching to the implicit
+ * solver allocates 16 bytes per site of device memory for the tridiagonal
+ * coefficients (c' and the reciprocal pivots of every Fourier mode, rebuilt
+ * when xi, the wall rule or the stencil change; freed by lf_destroy).
+ * Returns LF_EINVAL for an unknown solver, an unsupported size, or an
+ * ensemble member (ensembles always take explicit sub-steps), LF_ENOMEM if
+ * the coefficient tables cannot be allocated.  Not stored in checkpoints. */
 #define LF_TSOLVER_EXPLICIT 0
 #define LF_TSOLVER_IMPLICIT 1
 int lf_set_t_solver(lf_ctx* ctx, int solver);

@@ -642,6 +642,15 @@ int lf_set_t_solver(lf_ctx* c, int solver)
 {
     if (!c || (solver != LF_TSOLVER_EXPLICIT && solver != LF_TSOLVER_IMPLICIT) || c->ens_member) return LF_EINVAL;
     if (solver == LF_TSOLVER_IMPLICIT && !t_implicit_supported(c->g)) return LF_EINVAL;
+    if (solver == LF_TSOLVER_IMPLICIT && c->g.walls && !c->tcoef) {
+        void* t = nullptr;
+        if (cudaMalloc(&t, sizeof(double) * 2 * (size_t)c->N) != cudaSuccess) {
+            cudaGetLastError();
+            return LF_ENOMEM;
+        }
+        c->tcoef = (double*)t;
+        c->tcoef_valid = false;
+    }
     c->t_solver = solver;
     return LF_OK;
 }
@@ -770,6 +779,7 @@ void lf_destroy(lf_ctx* c)
     if (!c) return;
     wait_stream(c->stream);
     if (c->own && c->base) cudaFree(c->base);
+    if (c->tcoef) cudaFree(c->tcoef);
     if (c->flag_host) cudaFreeHost(const_cast<int*>(c->flag_host));
     cudaGetLastError();
     delete c;

@@ -35,6 +35,13 @@ struct lf_ctx {
     bool aux_valid;
     bool ens_member;      // stepped by an ensemble; lf_step on it is refused
     int t_solver;         // LF_TSOLVER_EXPLICIT (n_sub sub-steps) or LF_TSOLVER_IMPLICIT
+    // implicit solver with walls: c'_j and the reciprocal pivots of the
+    // tridiagonal solve, per Fourier mode and layer (2 N doubles, allocated by
+    // lf_set_t_solver), valid for the xi, wall rule and stencil recorded here
+    double* tcoef;
+    bool tcoef_valid;
+    double tcoef_xi;
+    int tcoef_mode, tcoef_stencil;
 };
 
 namespace lf {

@@ -103,33 +103,91 @@ __device__ __forceinline__ void layer_coeffs(const Geom& g, int64_t m, double* a
     *beta = -2.0 - lam;
 }
 
-// Walls along the last axis: one thread per Fourier mode m of the periodic
-// axes (M modes), Thomas algorithm along the L layers of the wall normal;
-// element (j, m) at j * M + m.  Writes the conjugate of the solution.
-__global__ void k_t_thomas(Geom g, double2* __restrict__ buf, double* __restrict__ cp, double xi, double Tw_hat0,
-                           int t_mode)
+// The tridiagonal system of Fourier mode m along the wall normal: constant
+// off-diagonal a, diagonal b (b0 / b1 on the first / last unknown layer with
+// the halfway ghost), unknown layers j0 .. j1.
+struct TriSys {
+    double a, b, b0, b1;
+    int j0, j1;
+};
+
+__device__ __forceinline__ TriSys tri_sys(const Geom& g, int64_t m, double xi, int t_mode, int L)
+{
+    double alpha, beta;
+    layer_coeffs(g, m, &alpha, &beta);
+    TriSys t;
+    t.b = 1.0 - xi * beta;
+    t.a = -xi * alpha;                       // sub- and super-diagonal
+    t.b0 = t.b;
+    t.b1 = t.b;
+    t.j0 = 0;
+    t.j1 = L - 1;
+    if (t_mode == LF_TWALL_LAYERS) {         // held layers 0 and L-1 enter the right-hand side
+        t.j0 = 1;
+        t.j1 = L - 2;
+    } else {                                 // ghost 2 T_w - T: +xi alpha on the diagonal
+        t.b0 -= t.a;
+        t.b1 -= t.a;
+    }
+    return t;
+}
+
+// Diagonal of unknown layer j.
+__device__ __forceinline__ double tri_diag(const TriSys& t, int j, int t_mode)
+{
+    double bj = t.b;
+    if (j == t.j0) bj = t_mode == LF_TWALL_LAYERS ? t.b : t.b0;
+    if (j == t.j1 && t_mode != LF_TWALL_LAYERS) bj = (t.j0 == t.j1) ? t.b0 + (t.b1 - t.b) : t.b1;
+    return bj;
+}
+
+// The part of the Thomas algorithm that does not depend on the right-hand
+// side: c'_j = a / (b_j - a c'_{j-1}) and the reciprocal pivot
+// 1 / (b_j - a c'_{j-1}) of every unknown layer of every mode, stored at
+// j * M + m (c') and N + j * M + m (pivot).  The coefficients do not change
+// from step to step, so the divisions leave the per-step recurrence.
+__global__ void k_t_coef(Geom g, double* __restrict__ coef, double xi, int t_mode)
 {
     const int d = g.d;
     const int64_t M = d == 2 ? (int64_t)g.nx : (int64_t)g.nx * g.ny;
     const int L = d == 2 ? g.ny : g.nz;
+    const int64_t N = M * L;
     const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (m >= M) return;
-    double alpha, beta;
-    layer_coeffs(g, m, &alpha, &beta);
-    const double b = 1.0 - xi * beta;
-    const double a = -xi * alpha;            // sub- and super-diagonal
+    const TriSys t = tri_sys(g, m, xi, t_mode, L);
+    double cprev = 0.0;
+    for (int j = t.j0; j <= t.j1; ++j) {
+        const double inv = 1.0 / (tri_diag(t, j, t_mode) - t.a * cprev);
+        const double cj = t.a * inv;
+        coef[(int64_t)j * M + m] = cj;
+        coef[N + (int64_t)j * M + m] = inv;
+        cprev = cj;
+    }
+}
+
+// Walls along the last axis: one thread per Fourier mode m of the periodic
+// axes (M modes), the Thomas sweeps along the L layers of the wall normal
+// with c' and the pivots from k_t_coef; element (j, m) at j * M + m.  The
+// serial chain holds only multiply-adds: dp_j = (d_j - a dp_{j-1}) pivot_j,
+// x_j = dp_j - c'_j x_{j+1}.  Writes the conjugate of the solution.
+__global__ void k_t_thomas(Geom g, double2* __restrict__ buf, const double* __restrict__ coef, double xi,
+                           double Tw_hat0, int t_mode)
+{
+    const int d = g.d;
+    const int64_t M = d == 2 ? (int64_t)g.nx : (int64_t)g.nx * g.ny;
+    const int L = d == 2 ? g.ny : g.nz;
+    const int64_t N = M * L;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const TriSys t = tri_sys(g, m, xi, t_mode, L);
+    const double a = t.a;
+    const int j0 = t.j0, j1 = t.j1;
     auto at = [&](int j) -> double2& { return buf[(int64_t)j * M + m]; };
-    int j0 = 0, j1 = L - 1;                  // unknown layers
-    double2 lo_add = make_double2(0.0, 0.0), hi_add = make_double2(0.0, 0.0);
-    double b0 = b, b1 = b;
-    if (t_mode == LF_TWALL_LAYERS) {         // held layers 0 and L-1 enter the right-hand side
-        j0 = 1;
-        j1 = L - 2;
+    double2 lo_add, hi_add;
+    if (t_mode == LF_TWALL_LAYERS) {
         lo_add = make_double2(-a * at(0).x, -a * at(0).y);
         hi_add = make_double2(-a * at(L - 1).x, -a * at(L - 1).y);
-    } else {                                 // ghost 2 T_w - T: +xi alpha on the diagonal, 2 xi alpha T_w in the rhs
-        b0 -= a;
-        b1 -= a;
+    } else {                                 // 2 xi alpha T_w in the right-hand side of mode 0
         const double w = m == 0 ? -2.0 * a * Tw_hat0 : 0.0;
         lo_add = make_double2(w, 0.0);
         hi_add = make_double2(w, 0.0);
@@ -138,55 +196,60 @@ __global__ void k_t_thomas(Geom g, double2* __restrict__ buf, double* __restrict
         for (int j = 0; j < L; ++j) at(j) = make_double2(at(j).x, -at(j).y);
         return;
     }
-    // forward sweep: cp_j = a / (b_j - a cp_{j-1}),  dp_j = (d_j - a dp_{j-1}) / (b_j - a cp_{j-1}).
-    // The right-hand sides of the next kB layers are loaded before the
-    // recurrence runs over them, so the loads do not sit in the serial chain.
+    // Forward sweep in blocks of kB layers: the right-hand sides and pivots of
+    // block b + 1 are loaded while the recurrence runs over block b, so only
+    // the multiply-adds sit in the serial chain.
     constexpr int kB = 8;
-    double cprev = 0.0;
-    double2 dprev = make_double2(0.0, 0.0);
-    for (int jb = j0; jb <= j1; jb += kB) {
-        double2 dv[kB];
+    double2 dv[kB], dn[kB];
+    double pv[kB], pn[kB];
+    auto load_fw = [&](int jb, double2* dd, double* pp) {
 #pragma unroll
         for (int u = 0; u < kB; ++u)
-            if (jb + u <= j1) dv[u] = at(jb + u);
+            if (jb + u <= j1) {
+                dd[u] = at(jb + u);
+                pp[u] = coef[N + (int64_t)(jb + u) * M + m];
+            }
+    };
+    load_fw(j0, dv, pv);
+    double2 dprev = make_double2(0.0, 0.0);
+    for (int jb = j0; jb <= j1; jb += kB) {
+        if (jb + kB <= j1) load_fw(jb + kB, dn, pn);
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
             const int j = jb + u;
             if (j > j1) break;
-            double bj = b;
             double2 dj = dv[u];
-            if (j == j0) { bj = t_mode == LF_TWALL_LAYERS ? b : b0; dj.x += lo_add.x; dj.y += lo_add.y; }
-            if (j == j1) {
-                if (t_mode != LF_TWALL_LAYERS) bj = (j0 == j1) ? b0 + (b1 - b) : b1;
-                dj.x += hi_add.x; dj.y += hi_add.y;
-            }
-            const double inv = 1.0 / (bj - a * cprev);
-            const double cj = a * inv;
-            const double2 dp = make_double2((dj.x - a * dprev.x) * inv, (dj.y - a * dprev.y) * inv);
-            cp[(int64_t)j * M + m] = cj;
+            if (j == j0) { dj.x += lo_add.x; dj.y += lo_add.y; }
+            if (j == j1) { dj.x += hi_add.x; dj.y += hi_add.y; }
+            const double2 dp = make_double2((dj.x - a * dprev.x) * pv[u], (dj.y - a * dprev.y) * pv[u]);
             at(j) = dp;
-            cprev = cj;
             dprev = dp;
         }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) { dv[u] = dn[u]; pv[u] = pn[u]; }
     }
-    // back substitution x_j = dp_j - cp_j x_{j+1}, storing conj(x); the
-    // coefficients of the next kB layers (downwards) are loaded first
+    // back substitution x_j = dp_j - c'_j x_{j+1}, storing conj(x), in blocks
+    // of kB layers downwards with the next block's loads in flight
     double2 xnext = at(j1);
     at(j1) = make_double2(xnext.x, -xnext.y);
-    for (int jb = j1 - 1; jb >= j0; jb -= kB) {
-        double cv[kB];
-        double2 pv[kB];
+    auto load_bw = [&](int jb, double* cc, double2* dd) {
 #pragma unroll
         for (int u = 0; u < kB; ++u)
-            if (jb - u >= j0) { cv[u] = cp[(int64_t)(jb - u) * M + m]; pv[u] = at(jb - u); }
+            if (jb - u >= j0) { cc[u] = coef[(int64_t)(jb - u) * M + m]; dd[u] = at(jb - u); }
+    };
+    if (j1 - 1 >= j0) load_bw(j1 - 1, pv, dv);
+    for (int jb = j1 - 1; jb >= j0; jb -= kB) {
+        if (jb - kB >= j0) load_bw(jb - kB, pn, dn);
 #pragma unroll
         for (int u = 0; u < kB; ++u) {
             const int j = jb - u;
             if (j < j0) break;
-            const double2 x = make_double2(pv[u].x - cv[u] * xnext.x, pv[u].y - cv[u] * xnext.y);
+            const double2 x = make_double2(dv[u].x - pv[u] * xnext.x, dv[u].y - pv[u] * xnext.y);
             at(j) = make_double2(x.x, -x.y);
             xnext = x;
         }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) { dv[u] = dn[u]; pv[u] = pn[u]; }
     }
     for (int j = 0; j < j0; ++j) at(j) = make_double2(at(j).x, -at(j).y);          // held layers
     for (int j = j1 + 1; j < L; ++j) at(j) = make_double2(at(j).x, -at(j).y);
@@ -226,7 +289,6 @@ int t_implicit_step(lf_ctx* c, double xi, double T_w)
     const cudaStream_t s = c->stream;
     const int64_t N = (int64_t)g.nx * g.ny * g.nz;
     double2* buf = fft_buffer(g, c->scratch);
-    double* cp = (double*)c->stage;
     R* T = (R*)c->T[c->tcur];
     const int nper_axes = g.walls ? g.d - 1 : g.d;
     int64_t nper = g.nx;
@@ -237,7 +299,15 @@ int t_implicit_step(lf_ctx* c, double xi, double T_w)
         if (fft_forward_axis(g, buf, a, s) != cudaSuccess) return LF_ECUDA;
     if (g.walls) {
         const int64_t M = N / (g.d == 2 ? g.ny : g.nz);
-        k_t_thomas<<<(unsigned)((M + 31) / 32), 32, 0, s>>>(g, buf, cp, xi, T_w * (double)nper, g.t_mode);
+        if (!c->tcoef) return LF_EINVAL;     // lf_set_t_solver allocates the tables
+        if (!c->tcoef_valid || c->tcoef_xi != xi || c->tcoef_mode != g.t_mode || c->tcoef_stencil != g.stencil) {
+            k_t_coef<<<(unsigned)((M + 31) / 32), 32, 0, s>>>(g, c->tcoef, xi, g.t_mode);
+            c->tcoef_valid = true;
+            c->tcoef_xi = xi;
+            c->tcoef_mode = g.t_mode;
+            c->tcoef_stencil = g.stencil;
+        }
+        k_t_thomas<<<(unsigned)((M + 31) / 32), 32, 0, s>>>(g, buf, c->tcoef, xi, T_w * (double)nper, g.t_mode);
     } else {
         k_t_divide<<<grid_t(N), 256, 0, s>>>(g, buf, xi);
     }
