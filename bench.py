@@ -143,13 +143,29 @@ def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000, d=2, nz=1, tau=1.0, s
 
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    workload: 256x256 of the 2D quench, 64^3 of the 3D one (same physics and
+    stencils)."""
     rank, world, _ = ranks()
     if rank != 0:
         return 0
+    if args.workload in ("ens96", "sur256"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle times single lattices; the ensemble and "
+                          "surrogate workloads have no CPU reference arm (their baselines are the single-run GPU "
+                          "path, reported in their own lines)"}), flush=True)
+        return 0
     from oracle import oracle as O
 
-    nx = ny = 256
-    cfg = O.make_cfg(nx=nx, ny=ny, xi=1e-3)
+    iso = int(args.stencil == "isotropic")
+    if args.workload == "cube384":
+        d, nx, ny, nz, tau = 3, 64, 64, 64, 0.6
+        full = f"cube384: 3D D3Q19 lamellar quench between cold walls (z), sampled as {nx}x{ny}x{nz} per step"
+    else:
+        d, nx, ny, nz, tau = 2, 256, 256, 1, 1.0
+        full = f"prec1024: 2D D2Q9 lamellar quench between cold walls, sampled as {nx}x{ny} per step"
+    if iso:
+        full += ", isotropic stencils"
+    cfg = O.make_cfg(d=d, nx=nx, ny=ny, nz=nz, xi=args.xi, tau=tau, stencil=iso)
     st = O.init(cfg)
     for _ in range(args.warmup):
         st = O.run(st, 1)
@@ -157,16 +173,16 @@ def run_reference(args):
     for _ in range(args.steps):
         st = O.run(st, 1)
     el = time.perf_counter() - t0
-    value = 1e-6 * nx * ny * args.steps / el
+    sites = nx * ny * nz
+    value = 1e-6 * sites * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "prec1024: 2D D2Q9 lamellar quench between cold walls, sampled as 256x256 per step",
-                   "sites_per_step": nx * ny, "grid": [nx, ny], "xi": 1e-3, "tau": 1.0},
+        "config": {"workload": full, "sites_per_step": sites, "grid": [nx, ny, nz][:d], "xi": args.xi, "tau": tau},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
-                         "sample": f"{args.steps} FP64 oracle steps of a 256x256 lattice (same physics as the "
-                                   f"1024x1024 workload), OpenMP over rows"},
+                         "sample": f"{args.steps} FP64 oracle steps of a {'x'.join(map(str, [nx, ny, nz][:d]))} "
+                                   f"lattice (same physics as the full workload), OpenMP over rows"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
