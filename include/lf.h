@@ -126,7 +126,11 @@ typedef struct {
     double  mom[3];       /* sum n u                                              */
     double  umax;         /* max |u|                                              */
     double  mach;         /* umax / c_s (Sec. 2: must stay < 0.1)                 */
-    double  free_energy;  /* phi part of Eq. fren on the lattice                  */
+    double  free_energy;  /* phi part of Eq. fren on the lattice: sum a phi^2/2 +
+                             b phi^4/4 + c (lap phi)^2/2 (5-/7-point lap) plus
+                             kappa/2 sum over nearest-neighbour links inside the
+                             lattice of (dphi)^2; its phi-derivative is mu of
+                             Eq. chem with the compact stencils                */
     double  grad2[3];     /* sum (d_x phi)^2, (d_y phi)^2, (d_z phi)^2 (central)  */
     double  orient_s;     /* (d <(d_perp phi)^2>/<|grad phi|^2> - 1)/(d - 1)      */
     double  k_peak;       /* first moment of S(k) over shells above S_peak / 2    */
@@ -216,20 +220,27 @@ int lf_structure_factor(lf_ctx* ctx, double* out, int64_t nb);
  * waiting; nothing is allocated and no CUDA allocation routine is called.
  * Scratch: a fixed device array of 162,816 bytes in this library (1216 x 10
  * partial sums and 2 x 4096 layer sums), present on every GPU that loads
- * the library until the process exits; L above 4096, or 2^31 or more sites,
- * is rejected with LF_EINVAL.  The first call on a device resolves that
- * array's device address (cudaGetSymbolAddress); make it before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
- * GPU (different streams, or devices in one context) race and corrupt each
- * other's partial sums -- serialise them.  No state carries over between
- * calls (every partial read is written by the same call). */
+ * the library until the process exits; an extent above 2^24, L above 4096,
+ * or 2^31 or more sites is rejected with LF_EINVAL.  The first call on a
+ * device resolves that array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process; make it before any stream capture,
+ * and do not use this call after the device's primary context has been
+ * reset (cudaDeviceReset), which leaves the kept address stale.  Each device
+ * has its own copy of the array, and all calls on one device share it: calls
+ * on the same device whose work overlaps on the GPU (for instance on two
+ * streams) race and corrupt each other's partial sums -- serialise them.
+ * No state carries over between calls (every partial read is written by the
+ * same call). */
 int lf_diag_sums_noalloc(int d, int64_t nx, int64_t ny, int64_t nz, int walls, int precision,
                          const void* phi, const void* T, const void* moments, double b, double kappa,
                          double c, double Tc, double* out, void* stream);
 
-/* Checkpoint: writes / reads grid, walls, params (except pointers), step and
- * the full state in the context's precision.  lf_load requires a context
- * created with the same grid, walls and precision (LF_EIO otherwise). */
+/* Checkpoint: writes / reads grid, walls, params (except pointers), the
+ * stencil and temperature solver in use, step and the full state in the
+ * context's precision.  lf_load requires a context with the same grid, walls,
+ * precision, stencil (lf_set_stencil) and temperature solver
+ * (lf_set_t_solver), and returns LF_EIO otherwise, so that a resumed run
+ * cannot continue with another scheme; set those before loading. */
 int lf_save(lf_ctx* ctx, const char* path);
 int lf_load(lf_ctx* ctx, const char* path);
 

@@ -17,8 +17,14 @@ below are this project's readings, written out plainly:
   box, averaged over shells of width dk = 2 pi / L_min (bin b = round(|k|/dk),
   b = 1 .. L_min // 2); S_peak = max_b S_b; k_peak = sum k_b S_b / sum S_b over
   the bins with S_b > S_peak / 2, k_b = b dk;
-* free energy (phi part of Eq. fren): sum a phi^2/2 + b phi^4/4 +
-  kappa |grad phi|^2 / 2 + c (nabla^2 phi)^2 / 2.
+* free energy (phi part of Eq. fren) on the lattice: sum_r [a phi^2/2 +
+  b phi^4/4 + c (nabla^2 phi)^2 / 2] + kappa/2 sum_links (phi(r + e) - phi(r))^2,
+  the links joining nearest neighbours (periodic axes wrap; no link crosses a
+  wall) and nabla^2 the 5-/7-point Laplacian with the even wall reflection.
+  This is the lattice functional whose derivative with respect to phi(r) is
+  the chemical potential of Eq. chem as the compact stencils discretise it
+  (-kappa nabla^2 phi is minus the derivative of the link sum), so the pair
+  (free energy, mu) is consistent site by site.
 """
 from __future__ import annotations
 
@@ -100,13 +106,22 @@ def structure_factor(phi: np.ndarray):
     return kb, Sb, k_peak, float(S_peak)
 
 
+def link_squares(phi: np.ndarray, walls: bool) -> float:
+    """sum over nearest-neighbour links of (phi(r + e) - phi(r))^2; along the
+    wall normal (the slowest array axis) only links inside the lattice."""
+    acc = 0.0
+    for ax in range(phi.ndim):
+        dl = np.diff(phi, axis=ax) if (walls and ax == 0) else np.roll(phi, -1, axis=ax) - phi
+        acc += float((dl ** 2).sum())
+    return acc
+
+
 def free_energy(phi: np.ndarray, T: np.ndarray, walls: bool, b: float, kappa: float,
                 c: float, Tc: float) -> float:
     a = (T - Tc) / Tc
-    g = gradients(phi, walls)
     psi = _laplacian(phi, walls, 0)
-    dens = a * phi ** 2 / 2 + b * phi ** 4 / 4 + kappa * sum(x ** 2 for x in g) / 2 + c * psi ** 2 / 2
-    return float(dens.sum())
+    local = a * phi ** 2 / 2 + b * phi ** 4 / 4 + c * psi ** 2 / 2
+    return float(local.sum()) + kappa / 2 * link_squares(phi, walls)
 
 
 def sums(aux: dict, phi: np.ndarray):

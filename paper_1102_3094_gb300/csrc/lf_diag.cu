@@ -71,8 +71,13 @@ __device__ __forceinline__ double at(const R* f, const Geom& g, int x, int y, in
 
 // Central differences and the Laplacian of phi at (x, y, z); along the wall
 // axis the neighbour beyond the last layer is the layer itself (even mirror).
+// With `links` given, also the sum over the site's forward links of
+// (phi(r + e) - phi(r))^2: the mirror neighbour makes the link out of the
+// last layer vanish, so every nearest-neighbour link inside the lattice is
+// counted once.
 template <typename R>
-__device__ void phi_derivs(const R* phi, const Geom& g, int x, int y, int z, double* grad, double* lap)
+__device__ void phi_derivs(const R* phi, const Geom& g, int x, int y, int z, double* grad, double* lap,
+                           double* links = nullptr)
 {
     const int wy = g.walls && g.d == 2, wz = g.walls && g.d == 3;
     const double c = at(phi, g, x, y, z);
@@ -81,13 +86,16 @@ __device__ void phi_derivs(const R* phi, const Geom& g, int x, int y, int z, dou
     grad[0] = 0.5 * (xp - xm);
     grad[1] = 0.5 * (yp - ym);
     double l = xp + xm - 2.0 * c + yp + ym - 2.0 * c;
+    double k2 = (xp - c) * (xp - c) + (yp - c) * (yp - c);
     grad[2] = 0.0;
     if (g.d == 3) {
         const double zp = at(phi, g, x, y, nb_index(z, 1, g.nz, wz)), zm = at(phi, g, x, y, nb_index(z, -1, g.nz, wz));
         grad[2] = 0.5 * (zp - zm);
         l += zp + zm - 2.0 * c;
+        k2 += (zp - c) * (zp - c);
     }
     *lap = l;
+    if (links) *links = k2;
 }
 
 template <int NQ>
@@ -134,12 +142,11 @@ __global__ void __launch_bounds__(kThreads) k_diag_partial(Geom g, const R* __re
         const int y = (int)(row % g.ny), z = (int)(row / g.ny);
         const int64_t site = row * g.pitch + x;
         const double ph = (double)phi[site];
-        double gr[3], lap;
-        phi_derivs(phi, g, x, y, z, gr, &lap);
+        double gr[3], lap, links;
+        phi_derivs(phi, g, x, y, z, gr, &lap, &links);
         const double n = (double)aux[4 * P + site];
         const double ux = (double)aux[5 * P + site], uy = (double)aux[6 * P + site], uz = (double)aux[7 * P + site];
         const double a = ((double)T[site] - Tc) / Tc;
-        const double g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
         v[DQ_MASS] += n;
         v[DQ_PHI] += ph;
         v[DQ_MX] += n * ux;
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_diag_partial(Geom g, const R* __re
         v[DQ_GX] += gr[0] * gr[0];
         v[DQ_GY] += gr[1] * gr[1];
         v[DQ_GZ] += gr[2] * gr[2];
-        v[DQ_FE] += a * ph * ph / 2 + b * ph * ph * ph * ph / 4 + kappa * g2 / 2 + c * lap * lap / 2;
+        v[DQ_FE] += a * ph * ph / 2 + b * ph * ph * ph * ph / 4 + kappa * links / 2 + c * lap * lap / 2;
         v[DQ_U2MAX] = fmax(v[DQ_U2MAX], ux * ux + uy * uy + uz * uz);
     }
     block_reduce_store<DQ_N>(v, part + (int64_t)blockIdx.x * DQ_N, DQ_U2MAX);
@@ -562,7 +569,10 @@ __global__ void k_layers_to_s(const double* __restrict__ sums, int L, int d, dou
 }
 
 // Device address of the scratch array on the current device, resolved once
-// per device (the first call on a device does it; see the header).
+// per device (the first call on a device does it; see the header).  The
+// cached address belongs to the device's primary context: after that context
+// is reset (cudaDeviceReset) the address is stale, so the entry point is not
+// for use across a reset.
 int noalloc_scratch(double** out)
 {
     static std::mutex mu;
@@ -592,6 +602,8 @@ extern "C" int lf_diag_sums_noalloc(int d, int64_t nx, int64_t ny, int64_t nz, i
     using namespace lf;
     if (d != 2 && d != 3) return LF_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1 || (d == 2 && nz != 1)) return LF_EINVAL;
+    // bound each extent before forming the product, which could otherwise wrap
+    if (nx > (1 << 24) || ny > (1 << 24) || nz > (1 << 24)) return LF_EINVAL;
     if (precision != LF_FP64 && precision != LF_FP32) return LF_EINVAL;
     if (!phi || !T || !moments || !out) return LF_EINVAL;
     if (!(Tc > 0)) return LF_EINVAL;

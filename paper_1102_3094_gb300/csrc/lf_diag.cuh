@@ -13,7 +13,7 @@ enum {
     DQ_PHI,        // sum phi
     DQ_MX, DQ_MY, DQ_MZ,   // sum n u
     DQ_GX, DQ_GY, DQ_GZ,   // sum (d_a phi)^2, central differences
-    DQ_FE,         // sum a phi^2/2 + b phi^4/4 + kappa |grad phi|^2/2 + c (nabla^2 phi)^2/2
+    DQ_FE,         // sum a phi^2/2 + b phi^4/4 + c (nabla^2 phi)^2/2, plus kappa/2 sum_links (dphi)^2
     DQ_U2MAX,      // max |u|^2
     DQ_N
 };

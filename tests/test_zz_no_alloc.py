@@ -66,3 +66,6 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert rc == lf.LF_EINVAL
     rc = lf.lf_diag_sums_noalloc(3, 8, 8, 5000, 1, lf.LF_FP32, p, p, p, 1.0, -0.025, 0.02, 1.0, p, 0)
     assert rc == lf.LF_EINVAL
+    # an extent whose product with the others wraps to a small number
+    rc = lf.lf_diag_sums_noalloc(2, (1 << 62) + 1, 4, 1, 1, lf.LF_FP64, p, p, p, 1.0, -0.025, 0.02, 1.0, p, 0)
+    assert rc == lf.LF_EINVAL
