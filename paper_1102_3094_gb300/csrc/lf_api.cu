@@ -687,7 +687,10 @@ struct CkptHeader {
     int64_t nx, ny, nz, step;
     lf_params params;
     double T_w;
+    int32_t stencil, t_solver;   // the scheme the state was advanced with
+    int32_t pad_[2];
 };
+constexpr char kCkptMagic[8] = "LFCKPT2";
 }  // namespace
 
 // The file holds the state exactly as the context stores it: the population
@@ -715,12 +718,14 @@ int lf_save(lf_ctx* c, const char* path)
     if (!c || !path) return LF_EINVAL;
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
-    std::memcpy(h.magic, "LFCKPT1", 8);
-    h.version = 1; h.d = c->g.d; h.precision = c->prec; h.walls = c->g.walls; h.t_mode = c->g.t_mode;
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 2; h.d = c->g.d; h.precision = c->prec; h.walls = c->g.walls; h.t_mode = c->g.t_mode;
     h.Q = c->Q; h.nx = c->g.nx; h.ny = c->g.ny; h.nz = c->g.nz; h.step = c->step;
     h.params = c->params;
     h.params.stream = nullptr; h.params.workspace = nullptr; h.params.workspace_bytes = 0;
     h.T_w = c->walls.T_w;
+    h.stencil = c->g.stencil;
+    h.t_solver = c->t_solver;
     const size_t nf = (size_t)c->N * c->esz;
     unsigned char* buf = (unsigned char*)std::malloc(nf * (c->Q + 2));
     if (!buf) return LF_ENOMEM;
@@ -750,9 +755,12 @@ int lf_load(lf_ctx* c, const char* path)
     if (!fp) return LF_EIO;
     CkptHeader h;
     int rc = LF_OK;
-    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, "LFCKPT1", 8) != 0 || h.d != c->g.d ||
+    // A checkpoint resumes only on the lattice and with the scheme it was
+    // written with: a different stencil or temperature solver would silently
+    // continue the run with another method, so it is refused.
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.d != c->g.d ||
         h.precision != c->prec || h.walls != c->g.walls || h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz ||
-        h.Q != c->Q)
+        h.Q != c->Q || h.stencil != c->g.stencil || h.t_solver != c->t_solver)
         rc = LF_EIO;
     const size_t nf = (size_t)c->N * c->esz;
     unsigned char* buf = nullptr;

@@ -104,3 +104,89 @@ def test_isotropic_runs_in_an_ensemble_equal_single_runs():
             np.testing.assert_array_equal(run.get(name, "fp32"), ref.get(name, "fp32"), err_msg=f"run {r} {name}")
         ref.close()
     ens.close()
+
+
+# ---- every member against the FP64 oracle ----------------------------------
+from oracle import oracle as O  # noqa: E402
+from paper_1102_3094_gb300 import synth  # noqa: E402
+
+ORACLE_MEMBERS = [
+    dict(nx=64, ny=40, xi=0.01, tau=1.0, seed=31),                                  # compact, walls
+    dict(nx=70, ny=37, xi=0.5, tau=0.6, seed=32, t_wall_mode=1),                    # 3 sub-steps, halfway T
+    dict(nx=33, ny=17, xi=math.inf, tau=3.0, seed=33),                              # instantaneous quench
+    dict(nx=41, ny=23, xi=0.2, tau=0.6, seed=34, walls=0),                          # periodic, 2 sub-steps
+    dict(nx=56, ny=30, xi=0.01, tau=3.0, seed=35, stencil="isotropic"),             # isotropic tile item
+    dict(nx=47, ny=29, xi=0.7, tau=0.6, seed=36, stencil="isotropic", walls=0),     # isotropic, periodic, 4 sub-steps
+    dict(nx=120, ny=3, xi=0.01, tau=1.0, seed=37),                                  # thinner than the halo
+]
+
+
+def _oracle_cfg(m):
+    return O.make_cfg(d=2, nx=m["nx"], ny=m["ny"], walls=m.get("walls", 1), t_wall_mode=m.get("t_wall_mode", 0),
+                      xi=m["xi"], tau=m["tau"], seed=m["seed"], stencil=int(m.get("stencil") == "isotropic"))
+
+
+def _to_oracle_f(f_lib):
+    e, _ = lf.lf_lattice(2)
+    eo, _ = O.velocity_set(2)
+    out = np.empty_like(f_lib)
+    for i, v in enumerate(e):
+        out[int(np.where((eo == v).all(1))[0][0])] = f_lib[i]
+    return out
+
+
+def _relerr(got, want):
+    s = np.abs(want).max()
+    return np.abs(got - want).max() / (s if s > 0 else 1.0)
+
+
+@pytest.mark.parametrize("tuned", [False, True])
+def test_ensemble_members_match_oracle_one_step(tuned):
+    """Every member of a mixed ensemble (both stencils, n_sub > 1, xi = inf,
+    periodic and walled, tau = 0.6 .. 3, a lattice thinner than the halo),
+    set to a random state, advanced by one batched step and compared element
+    by element with one FP64 oracle step from the same (FP32-rounded) state:
+    within 2e-6 max-norm relative error on f, phi and T."""
+    ens = lf.Ensemble(ORACLE_MEMBERS)
+    if tuned:
+        ens.tune(reps=2)
+    states = []
+    _, w = lf.lf_lattice(2)
+    for r, m in enumerate(ORACLE_MEMBERS):
+        run = ens.run(r)
+        phi, T, rr = synth.random_state(run.shape, 9, 100 + r, dtype=np.float32)
+        if m.get("walls", 1) and m.get("t_wall_mode", 0) == 0:
+            T[0] = 0.5
+            T[-1] = 0.5
+        f = (w.reshape(-1, 1, 1) * (1 + rr)).astype(np.float32)
+        run.set("phi", phi)
+        run.set("T", T)
+        run.set("pop", f)
+        states.append(O.State(_oracle_cfg(m), _to_oracle_f(run.get("pop")), run.get("phi"), run.get("T")))
+    ens.step(1)
+    for r, m in enumerate(ORACLE_MEMBERS):
+        run = ens.run(r)
+        want = O.step(states[r])
+        for name, got, ref in (("phi", run.get("phi"), want.phi), ("T", run.get("T"), want.T),
+                               ("pop", _to_oracle_f(run.get("pop")), want.f)):
+            assert _relerr(got, ref) < 2e-6, (r, m, name, _relerr(got, ref))
+    ens.close()
+
+
+def test_ensemble_members_match_oracle_many_steps():
+    """The same members from their initial quench, 40 batched steps, against
+    40 FP64 oracle steps from the FP32-rounded initial state; FP32 rounding
+    accumulates over the steps, so the bound is 40 x the one-step 2e-6."""
+    ens = lf.Ensemble(ORACLE_MEMBERS)
+    starts = []
+    for r, m in enumerate(ORACLE_MEMBERS):
+        run = ens.run(r)
+        starts.append(O.State(_oracle_cfg(m), _to_oracle_f(run.get("pop")), run.get("phi"), run.get("T")))
+    ens.step(40)
+    for r, m in enumerate(ORACLE_MEMBERS):
+        run = ens.run(r)
+        want = O.run(starts[r], 40)
+        for name, got, ref in (("phi", run.get("phi"), want.phi), ("T", run.get("T"), want.T),
+                               ("pop", _to_oracle_f(run.get("pop")), want.f)):
+            assert _relerr(got, ref) < 40 * 2e-6, (r, m, name, _relerr(got, ref))
+    ens.close()

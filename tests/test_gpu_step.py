@@ -382,6 +382,36 @@ def test_checkpoint_resume_bit_identical(prec):
     b.close()
 
 
+def test_checkpoint_refuses_another_scheme():
+    """A checkpoint written with one stencil or temperature solver does not
+    load into a context set to the other (LF_EIO, state kept); once the
+    context is set like the writer, it loads and resumes bit for bit."""
+    a = lf.Lattice(nx=40, ny=24, precision="fp32", xi=0.5, stencil="isotropic")
+    a.set_t_solver("implicit")
+    a.step(4)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "iso_impl.lfck")
+        a.save(path)
+        a.step(3)
+        b = lf.Lattice(nx=40, ny=24, precision="fp32", xi=0.5)
+        phi0 = b.get("phi", "fp32")
+        for stencil, solver in (("compact", "explicit"), ("isotropic", "explicit"), ("compact", "implicit")):
+            b.set_stencil(stencil)
+            b.set_t_solver(solver)
+            with pytest.raises(lf.LFError) as ei:
+                b.load(path)
+            assert ei.value.code == lf.LF_EIO, (stencil, solver)
+            np.testing.assert_array_equal(b.get("phi", "fp32"), phi0)
+        b.set_stencil("isotropic")
+        b.set_t_solver("implicit")
+        b.load(path)
+        b.step(3)
+    for name in ("phi", "T", "pop"):
+        np.testing.assert_array_equal(a.get(name, "fp32"), b.get(name, "fp32"))
+    a.close()
+    b.close()
+
+
 def test_bounded_wait_reports_timeout_and_recovers(monkeypatch):
     """A blocking call whose wait for the stream runs out returns LF_ETIMEOUT
     (here: a 1 us limit behind ~100 queued steps) without breaking the context;
