@@ -1,15 +1,18 @@
 #!/usr/bin/env python3
-"""Throughput of the fused hybrid LB/FD step on GB300.
+"""Throughput of the hybrid LB/FD step on GB300.
 
-Workload (default): the precision form of the method, 2D D2Q9 on 1024 x 1024
-sites, FP32 state (populations stored as deviations from w_i n0), walls at
-y = 0 and 1023 (bounce-back, T_w = 0.5), Tc = 1, T0 = 1.1, b = 1,
-kappa = -0.025, c = 0.02, Gamma = 0.05, xi = 1e-3, tau = 1, phi i.i.d. uniform
-in [-0.05, 0.05] (synthetic, seeded).  One benchmark step is one time step of
-the method (one lf_step(ctx, 1) call = one fused kernel launch).  The L2 cache
-(129 MB; the state is 2 x 44 MiB) is flushed by writing a 256 MiB buffer
-before every timed step, and each step is timed alone with CUDA events on the
-library's stream, so that every step reads its inputs from HBM.
+Workload (default, cube384): the 3D form of the method, D3Q19 on 384^3 sites,
+FP32 state (populations stored as deviations from w_i n0), periodic in x and
+y, cold walls at z = 0 and 383 (bounce-back, T_w = 0.5), Tc = 1, T0 = 1.1,
+b = 1, kappa = -0.025, c = 0.02, Gamma = 0.05, xi = 1e-3, tau = 0.6, phi
+i.i.d. uniform in [-0.05, 0.05] (synthetic, seeded).  One benchmark step is
+one time step of the method (one lf_step(ctx, 1) call: the three passes of
+the 3D step).  The state (2 x 9.5 GB) is far larger than the 129 MB L2.
+
+prec1024 is the 2D precision form (D2Q9, 1024 x 1024, xi = 1e-3, tau = 1, one
+fused kernel per step); its state (2 x 44 MiB) fits in L2, so a 256 MiB buffer
+is written (and another read) before every timed step.  Each step is timed
+alone with CUDA events on the library's stream.
 
 Metric: MLUPS = 1e-6 x sites x steps / s (million lattice-site updates per
 second), whole job over all ranks.  --impl reference times the FP64 CPU oracle
@@ -79,10 +82,12 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            import atexit
+            atexit.register(self.__exit__)   # never leave the sampler running
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -95,8 +100,23 @@ class Clocks:
         """keep only the samples taken between t0 and t1 (host clock)."""
         self.lines = [(ts, ln) for ts, ln in self.lines if t0 <= ts <= t1]
 
+    def summary_over(self, timed, run, min_samples=5):
+        """Clock summary of the timed window (t0, t1) when it holds at least
+        `min_samples` samples, else of the whole GPU run (warm-up, timed
+        steps and the end-to-end leg), which short timed regions need."""
+        keep = self.lines
+        self.window(*timed)
+        out = self.summary()
+        out["window"] = "timed steps"
+        if out["samples"] < min_samples:
+            self.lines = [(ts, ln) for ts, ln in keep if run[0] <= ts <= run[1]]
+            out = self.summary()
+            out["window"] = "whole GPU run (warm-up, timed steps, end-to-end leg)"
+        self.lines = keep
+        return out
+
     def __exit__(self, *a):
-        if self.proc:
+        if self.proc and self.proc.poll() is None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -508,6 +528,13 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize(dev)
 
+    # nvidia-smi samples the clocks from before the warm-up to the end of the
+    # end-to-end leg; the line reports the timed window, or the whole run when
+    # the timed window is too short to hold enough samples
+    clk = Clocks(local)
+    clk.__enter__()
+    time.sleep(0.5)                          # let the sampler start
+    t_run0 = time.time()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             l2_flush(1.0)
@@ -515,22 +542,18 @@ def run_ours(args):
     barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clk = Clocks(local)
-    with clk:
-        time.sleep(0.5)                      # let the sampler start
-        t_begin = time.time()
-        with torch.cuda.stream(stream):
-            for k in range(args.steps):
-                if restore > 0 and k % restore == 0:
-                    restore_state()
-                    n_restores += 1
-                l2_flush(float(k))
-                starts[k].record(stream)
-                sim.step(1)
-                ends[k].record(stream)
-        barrier()
-        t_end = time.time()
-    clk.window(t_begin, t_end + 0.15)
+    t_begin = time.time()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            if restore > 0 and k % restore == 0:
+                restore_state()
+                n_restores += 1
+            l2_flush(float(k))
+            starts[k].record(stream)
+            sim.step(1)
+            ends[k].record(stream)
+    barrier()
+    t_end = time.time()
     times_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = max_over_ranks(sum(times_ms) / 1e3, dev)
     dg = sim.diag()
@@ -582,12 +605,16 @@ def run_ours(args):
             lf.lf_step(sim.ctx, 1)
             lf.lf_fields(sim.ctx, lf.FIELDS["phi"], out_h.data_ptr(), out_h.numel() * es, False)
         el = max_over_ranks(time.perf_counter() - t0, dev)
+        torch.cuda.synchronize(dev)
         e2e = {"value": job_rate(N, args.e2e_steps, world, el), "unit": "MLUPS",
                "h2d_bytes_per_step": (sim.Q + 2) * N * es, "d2h_bytes_per_step": N * es,
                "steps": args.e2e_steps,
                "what": "per step: lf_fields_set of f, phi, T from pinned host, lf_step(1), lf_fields of phi to "
                        "pinned host"}
 
+    t_run1 = time.time()
+    clk.__exit__(None, None, None)
+    clocks = clk.summary_over((t_begin, t_end + 0.1), (t_run0, t_run1 + 0.1))
     cpu = None
     if rank == 0 and args.cpu_seconds > 0:
         if d == 3:
@@ -623,7 +650,7 @@ def run_ours(args):
             "restores": ({"every": restore, "count": n_restores, "launches": 3 * n_restores,
                           "what": "lf_fields_set of f, phi, T from a device copy of the initial state, "
                                   "between the timed events"} if restore > 0 else None),
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "diag_after": {"mass": dg["mass"], "mach": dg["mach"], "rc": dg["rc"]},
         }
         print(json.dumps(line), flush=True)
@@ -639,7 +666,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["prec1024", "cube384", "ens96", "sur256"], default="prec1024")
+    ap.add_argument("--workload", choices=["prec1024", "cube384", "ens96", "sur256"], default="cube384")
     ap.add_argument("--sur-runs", type=int, default=32)
     ap.add_argument("--sur-windows", type=int, default=20)
     ap.add_argument("--sur-iters", type=int, default=3000)

@@ -20,8 +20,8 @@ def _run(*extra):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("extra,sites", [((), 256 * 256), (("--workload", "cube384"), 64 ** 3),
-                                         (("--stencil", "isotropic"), 256 * 256)])
+@pytest.mark.parametrize("extra,sites", [((), 64 ** 3), (("--workload", "prec1024"), 256 * 256),
+                                         (("--workload", "prec1024", "--stencil", "isotropic"), 256 * 256)])
 def test_reference_line(extra, sites):
     line = _run(*extra)
     assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
