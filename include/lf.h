@@ -273,6 +273,24 @@ int lf_load(lf_ctx* ctx, const char* path);
 #define LF_VARIANT_SPLIT3 3
 int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
 
+/* Autotuner of the step's mapping to the GPU.  Times every candidate kernel
+ * variant and shape for this lattice -- 2D: CTA width (120 or 56 columns) and
+ * rows per segment of the row marches, and the tile kernel; 3D: tile shape and
+ * planes per segment of the three-pass step's force pass, and the fused plane
+ * march -- `reps` timed steps each (CUDA events) on a scratch context of the
+ * same lattice, stencil, precision, parameters and temperature solver, each
+ * candidate from the same initial state, and sets the fastest on ctx as by
+ * lf_set_kernel_variant.  ctx's state is not touched.  The choice is cached per
+ * (device, lattice sizes, precision, stencil, walls, hydrodynamics) for the
+ * life of the process, so later calls with the same key only set it.  The
+ * scratch context allocates as much device memory as ctx, plus one copy of
+ * its state, for the duration of the call; it waits for ctx's stream.  Any of
+ * variant, param, ms_per_step may be NULL; on success they receive the choice
+ * and its time per step in milliseconds.  The isotropic 2D step has a single
+ * kernel (the tile form), which is then the only candidate.  Returns LF_EINVAL
+ * for reps < 1 or an ensemble member. */
+int lf_tune(lf_ctx* ctx, int reps, int* variant, int* param, double* ms_per_step);
+
 /* Time discretisation of the temperature (d_t T = xi lap T, Sec. 2 after Eq.
  * massdiff):
  *   LF_TSOLVER_EXPLICIT (default): explicit Euler in n_sub = lf_nsub(xi, d)

@@ -93,6 +93,8 @@ def lib():
             L.lf_set_t_solver.restype = C.c_int
             L.lf_set_stencil.argtypes = [vp, C.c_int]
             L.lf_set_stencil.restype = C.c_int
+            L.lf_tune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.lf_tune.restype = C.c_int
             L.lf_step_count.argtypes = [vp]
             L.lf_step_count.restype = i64
             L.lf_destroy.argtypes = [vp]
@@ -188,6 +190,13 @@ def lf_set_kernel_variant(ctx, variant: int, param: int = 0) -> None:
     _ok(lib().lf_set_kernel_variant(ctx, variant, param), "lf_set_kernel_variant")
 
 
+def lf_tune(ctx, reps: int = 5):
+    """Runs the autotuner (include/lf.h); returns (variant, param, ms per step)."""
+    v, p, ms = C.c_int(), C.c_int(), C.c_double()
+    _ok(lib().lf_tune(ctx, reps, C.byref(v), C.byref(p), C.byref(ms)), "lf_tune")
+    return v.value, p.value, ms.value
+
+
 def lf_step_count(ctx) -> int:
     return lib().lf_step_count(ctx)
 
@@ -270,6 +279,10 @@ class Lattice:
         code = {"explicit": 0, "implicit": 1}[solver]
         _ok(lib().lf_set_t_solver(self.ctx, code), "lf_set_t_solver")
 
+    def tune(self, reps: int = 5):
+        """Autotune the kernel variant and shape; returns (variant, param, ms)."""
+        return lf_tune(self.ctx, reps)
+
     def set_stencil(self, stencil: str = "compact"):
         code = {"compact": LF_STENCIL_COMPACT, "isotropic": LF_STENCIL_ISOTROPIC}[stencil]
         _ok(lib().lf_set_stencil(self.ctx, code), "lf_set_stencil")
@@ -333,12 +346,16 @@ def _ens_lib():
                                     C.POINTER(vp)]
         L.lf_ens_tune.argtypes = [vp, C.c_int]
         L.lf_ens_rows.argtypes = [vp, C.c_int]
+        L.lf_ens_param.argtypes = [vp, C.c_int]
+        L.lf_ens_prune.argtypes = [vp, C.POINTER(C.c_int)]
+        L.lf_ens_active.argtypes = [vp, C.c_int]
         L.lf_ens_step.argtypes = [vp, C.c_int64]
         L.lf_ens_run.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.lf_ens_sync.argtypes = [vp]
         L.lf_ens_destroy.argtypes = [vp]
         L.lf_ens_destroy.restype = None
-        for fn in ("lf_ens_create", "lf_ens_tune", "lf_ens_rows", "lf_ens_step", "lf_ens_run", "lf_ens_sync"):
+        for fn in ("lf_ens_create", "lf_ens_tune", "lf_ens_rows", "lf_ens_param", "lf_ens_prune", "lf_ens_active",
+                   "lf_ens_step", "lf_ens_run", "lf_ens_sync"):
             getattr(L, fn).restype = C.c_int
         L._ens_ready = True
     return L
@@ -360,6 +377,20 @@ def lf_ens_tune(ens, reps: int = 5) -> None:
 
 def lf_ens_rows(ens, run: int) -> int:
     return _ok(_ens_lib().lf_ens_rows(ens, run), "lf_ens_rows")
+
+
+def lf_ens_param(ens, run: int) -> int:
+    return _ok(_ens_lib().lf_ens_param(ens, run), "lf_ens_param")
+
+
+def lf_ens_prune(ens) -> int:
+    n = C.c_int()
+    _ok(_ens_lib().lf_ens_prune(ens, C.byref(n)), "lf_ens_prune")
+    return n.value
+
+
+def lf_ens_active(ens, run: int) -> bool:
+    return bool(_ok(_ens_lib().lf_ens_active(ens, run), "lf_ens_active"))
 
 
 def lf_ens_step(ens, nsteps: int) -> None:
@@ -432,6 +463,17 @@ class Ensemble:
 
     def rows(self, run: int) -> int:
         return lf_ens_rows(self.ens, run)
+
+    def prune(self) -> int:
+        """Retire the runs that went non-finite; returns the runs still stepped."""
+        return lf_ens_prune(self.ens)
+
+    def active(self, run: int) -> bool:
+        return lf_ens_active(self.ens, run)
+
+    def param(self, run: int) -> int:
+        """LF_VARIANT_MARCH2 param that reproduces run `run` stepped alone."""
+        return lf_ens_param(self.ens, run)
 
     def run(self, r: int) -> Lattice:
         return _RunView(self.ens, lf_ens_run(self.ens, r), self.shapes[r])
