@@ -30,8 +30,12 @@ using namespace lf;
 
 namespace {
 
-constexpr int kNT = 64, kD = 3;     // 56-column strips: less idle width on 128^2 .. 512^2 lattices
-using MarchCfg = march::March2<kNT, kD>;
+// Strips of 56 columns (64-thread CTAs) leave less idle width on 128^2 ..
+// 512^2 lattices; 120-column strips (128 threads) issue fewer halo columns on
+// wide ones.  The tuner picks per lattice size.
+constexpr int kD = 3;
+template <int NT>
+using MarchCfg = march::March2<NT, kD>;
 constexpr int kTX = 64, kTY = 16, kTNT = 256;   // the FP32 tile of the single-run isotropic step
 using TileCfg = tile::Tile<float, kTX, kTY>;
 
@@ -71,20 +75,24 @@ __global__ void __launch_bounds__(kTNT) k_ens_tile2d_iso(const EnsRun* __restric
     }
 }
 
-__global__ void __launch_bounds__(kNT, 6) k_ens_march2d(const EnsRun* __restrict__ runs,
-                                                       const EnsItem* __restrict__ items, int nitems)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_ens_march2d(const EnsRun* __restrict__ runs,
+                                                         const EnsItem* __restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const EnsItem w = items[it];
         const EnsRun r = runs[w.run];
         if (r.p.hydro)
-            march::march2d_pair<kNT, kD, true>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
+            march::march2d_pair<NT, kD, true>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
         else
-            march::march2d_pair<kNT, kD, false>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
+            march::march2d_pair<NT, kD, false>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
         __syncthreads();   // the next item reuses the shared rings
     }
 }
+// the single-run launcher's instantiations: 64 threads at six CTAs per SM, 128 at three
+constexpr auto kEns64 = k_ens_march2d<64, 6>;
+constexpr auto kEns128 = k_ens_march2d<128, 3>;
 
 // Pairs of segments of a run with H rows per segment (as the single-run
 // launcher counts them, so a run stepped alone with the same H matches).
@@ -135,6 +143,8 @@ struct lf_ens {
     int nruns;
     std::vector<lf_ctx*> runs;
     std::vector<int> rows;          // rows per segment (lane) per run
+    std::vector<int> width;         // threads per march CTA per run: 64 (56 columns) or 128 (120)
+    std::vector<char> active;       // 0 once lf_ens_prune retired the run (non-finite state)
     cudaStream_t stream;
     bool own_stream;
     unsigned char* arena;
@@ -142,8 +152,10 @@ struct lf_ens {
     cudaGraphExec_t gA, gB, gAB;
     int parity;                     // 0: the next step is step A of the cycle, 1: step B
     std::vector<Cursor> base;       // buffer cursors at the start of step A
-    int march_blocks;
+    int march_blocks[2];            // 64- and 128-thread march kernels
     int tile_blocks;
+    int nitems[2];
+    EnsItem* d_items[2];
 };
 
 namespace {
@@ -164,14 +176,17 @@ struct Half {
     std::vector<EnsT*> ts;          // per extra sub-step s = 1 .. max_nsub - 1
 };
 
-int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsItem* items, int nitems, EnsTile* tiles,
+int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsTile* tiles,
             int ntiles, const std::vector<EnsTItem*>& titems, const std::vector<int>& ntitems, cudaGraphExec_t* out)
 {
     cudaGraph_t graph;
     if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LF_ECUDA;
     for (int h : halves) {
-        if (nitems > 0)
-            k_ens_march2d<<<e->march_blocks, kNT, MarchCfg::BYTES, e->stream>>>(H[h].runs, items, nitems);
+        if (e->nitems[0] > 0)
+            kEns64<<<e->march_blocks[0], 64, MarchCfg<64>::BYTES, e->stream>>>(H[h].runs, e->d_items[0], e->nitems[0]);
+        if (e->nitems[1] > 0)
+            kEns128<<<e->march_blocks[1], 128, MarchCfg<128>::BYTES, e->stream>>>(H[h].runs, e->d_items[1],
+                                                                               e->nitems[1]);
         if (ntiles > 0)
             k_ens_tile2d_iso<<<e->tile_blocks, kTNT, TileCfg::BYTES, e->stream>>>(H[h].runs, tiles, ntiles);
         for (size_t s = 0; s < H[h].ts.size(); ++s) {
@@ -235,40 +250,43 @@ int build(lf_ens* e)
             }
         }
     }
-    // work lists: march items sorted by cost (longest lane first), the tiles
-    // of the isotropic runs, T tiles per sub-step
-    std::vector<EnsItem> items;
+    // work lists: march items per CTA width sorted by cost (longest lane
+    // first), the tiles of the isotropic runs, T tiles per sub-step
+    std::vector<EnsItem> items[2];
     std::vector<EnsTile> tiles;
     for (int r = 0; r < R; ++r) {
         const lf_ctx* c = e->runs[r];
+        if (!e->active[r]) continue;
         if (c->g.stencil == LF_STENCIL_ISOTROPIC) {
             for (int by = 0; by < (c->g.ny + kTY - 1) / kTY; ++by)
                 for (int bx = 0; bx < (c->g.nx + kTX - 1) / kTX; ++bx) tiles.push_back({r, bx, by});
             continue;
         }
         const int np = pairs_for(c->g.ny, e->rows[r]);
-        const int strips = (c->g.nx + MarchCfg::U - 1) / MarchCfg::U;
+        const int wi = e->width[r] == 64 ? 0 : 1;
+        const int U = wi == 0 ? MarchCfg<64>::U : MarchCfg<128>::U;
+        const int strips = (c->g.nx + U - 1) / U;
         for (int pr = 0; pr < np; ++pr)
-            for (int st = 0; st < strips; ++st) items.push_back({r, st, pr, np});
+            for (int st = 0; st < strips; ++st) items[wi].push_back({r, st, pr, np});
     }
     auto lane = [&](const EnsItem& w) {
         const int ny = e->runs[w.run]->g.ny;
         return (ny + 2 * w.npairs - 1) / (2 * w.npairs);
     };
-    std::stable_sort(items.begin(), items.end(),
-                     [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
+    for (auto& it : items)
+        std::stable_sort(it.begin(), it.end(), [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
     std::vector<std::vector<EnsTItem>> titems(max_nsub > 1 ? max_nsub - 1 : 0);
     for (int s = 1; s < max_nsub; ++s)
         for (int r = 0; r < R; ++r) {
             const lf_ctx* c = e->runs[r];
-            if (!phys_f(c).t_update || s >= c->nsub) continue;
+            if (!e->active[r] || !phys_f(c).t_update || s >= c->nsub) continue;
             for (int by = 0; by < (c->g.ny + 7) / 8; ++by)
                 for (int bx = 0; bx < (c->g.nx + 31) / 32; ++bx) titems[s - 1].push_back({r, bx, by});
         }
     // one device block for everything
     auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
-    size_t bytes = 2 * a256(sizeof(EnsRun) * R) + a256(sizeof(EnsItem) * items.size()) +
-                   a256(sizeof(EnsTile) * tiles.size());
+    size_t bytes = 2 * a256(sizeof(EnsRun) * R) + a256(sizeof(EnsItem) * items[0].size()) +
+                   a256(sizeof(EnsItem) * items[1].size()) + a256(sizeof(EnsTile) * tiles.size());
     for (int s = 1; s < max_nsub; ++s) bytes += 2 * a256(sizeof(EnsT) * R) + a256(sizeof(EnsTItem) * titems[s - 1].size());
     if (cudaMalloc((void**)&e->tables, bytes) != cudaSuccess) { cudaGetLastError(); return LF_ENOMEM; }
     unsigned char* p = e->tables;
@@ -279,9 +297,12 @@ int build(lf_ens* e)
         copies.push_back({p, {hr[h].data(), sizeof(EnsRun) * R}});
         p += a256(sizeof(EnsRun) * R);
     }
-    EnsItem* d_items = (EnsItem*)p;
-    copies.push_back({p, {items.data(), sizeof(EnsItem) * items.size()}});
-    p += a256(sizeof(EnsItem) * items.size());
+    for (int wi = 0; wi < 2; ++wi) {
+        e->d_items[wi] = (EnsItem*)p;
+        e->nitems[wi] = (int)items[wi].size();
+        copies.push_back({p, {items[wi].data(), sizeof(EnsItem) * items[wi].size()}});
+        p += a256(sizeof(EnsItem) * items[wi].size());
+    }
     EnsTile* d_tiles = (EnsTile*)p;
     copies.push_back({p, {tiles.data(), sizeof(EnsTile) * tiles.size()}});
     p += a256(sizeof(EnsTile) * tiles.size());
@@ -305,33 +326,36 @@ int build(lf_ens* e)
     int rc = wait_stream(e->stream);   // host vectors go out of scope
     if (rc != LF_OK) return rc;
 
-    if (cudaFuncSetAttribute(k_ens_march2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg::BYTES) !=
+    if (cudaFuncSetAttribute(kEns64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<64>::BYTES) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kEns128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<128>::BYTES) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_ens_tile2d_iso, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg::BYTES) !=
             cudaSuccess)
         return LF_ECUDA;
-    int per_sm = 0, per_sm_t = 0, sms = 0, dev = 0;
+    int per_sm[2] = {0, 0}, per_sm_t = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ens_march2d, kNT, MarchCfg::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], kEns64, 64, MarchCfg<64>::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], kEns128, 128, MarchCfg<128>::BYTES);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_ens_tile2d_iso, kTNT, TileCfg::BYTES);
-    e->march_blocks = std::max(1, std::min((int)items.size(), std::max(1, per_sm) * std::max(1, sms)));
+    for (int wi = 0; wi < 2; ++wi)
+        e->march_blocks[wi] = std::max(1, std::min(e->nitems[wi], std::max(1, per_sm[wi]) * std::max(1, sms)));
     e->tile_blocks = std::max(1, std::min((int)tiles.size(), std::max(1, per_sm_t) * std::max(1, sms)));
 
-    const int nitems = (int)items.size(), ntiles = (int)tiles.size();
-    if ((rc = capture(e, {0}, halves, d_items, nitems, d_tiles, ntiles, d_titems, ntitems, &e->gA)) != LF_OK)
-        return rc;
-    if ((rc = capture(e, {1}, halves, d_items, nitems, d_tiles, ntiles, d_titems, ntitems, &e->gB)) != LF_OK)
-        return rc;
-    if ((rc = capture(e, {0, 1}, halves, d_items, nitems, d_tiles, ntiles, d_titems, ntitems, &e->gAB)) != LF_OK)
-        return rc;
+    const int ntiles = (int)tiles.size();
+    if ((rc = capture(e, {0}, halves, d_tiles, ntiles, d_titems, ntitems, &e->gA)) != LF_OK) return rc;
+    if ((rc = capture(e, {1}, halves, d_tiles, ntiles, d_titems, ntitems, &e->gB)) != LF_OK) return rc;
+    if ((rc = capture(e, {0, 1}, halves, d_tiles, ntiles, d_titems, ntitems, &e->gAB)) != LF_OK) return rc;
     e->parity = 0;
     return LF_OK;
 }
 
 void advance_cursors(lf_ens* e, int64_t n)
 {
-    for (lf_ctx* c : e->runs) {
+    for (size_t r = 0; r < e->runs.size(); ++r) {
+        if (!e->active[r]) continue;
+        lf_ctx* c = e->runs[r];
         const bool tu = phys_f(c).t_update;
         const int tflips = tu ? c->nsub : 1;
         if ((n & 1) != 0) {
@@ -395,6 +419,8 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
             c->ens_member = true;
             e->runs.push_back(c);
             e->rows.push_back(c->g.ny / 2 < 16 ? (c->g.ny / 2 > 0 ? c->g.ny / 2 : 1) : 16);
+            e->width.push_back(64);
+            e->active.push_back(1);
         }
     }
     if (rc == LF_OK) rc = build(e);
@@ -411,45 +437,71 @@ int lf_ens_tune(lf_ens* e, int reps)
     if (!e || reps < 1) return LF_EINVAL;
     int rc = wait_stream(e->stream);
     if (rc != LF_OK) return rc;
-    std::map<std::pair<int, int>, int> best;   // (nx, ny) -> rows
-    for (int r = 0; r < e->nruns; ++r) {
-        lf_ctx* c = e->runs[r];
-        if (c->g.stencil == LF_STENCIL_ISOTROPIC) continue;     // tiles: nothing to tune
-        const auto key = std::make_pair(c->g.nx, c->g.ny);
-        if (best.count(key)) continue;
-        lf_params p = c->params;
-        p.workspace = nullptr;
-        p.workspace_bytes = 0;
-        p.stream = e->stream;
-        lf_ctx* tmp = nullptr;
-        if ((rc = lf_create(&c->grid, &c->walls, &p, &tmp)) != LF_OK) return rc;
-        cudaEvent_t t0, t1;
-        cudaEventCreate(&t0);
-        cudaEventCreate(&t1);
-        float best_ms = 1e30f;
-        int best_h = e->rows[r];
-        const int cand[] = {8, 12, 16, 20, 24, 32, 48, 64, 96, 128};
-        for (int h : cand) {
-            if (2 * h > c->g.ny && h != cand[0]) continue;
-            lf_set_kernel_variant(tmp, LF_VARIANT_MARCH2, h);
-            lf_step(tmp, 2);
-            cudaEventRecord(t0, e->stream);
-            lf_step(tmp, reps);
-            cudaEventRecord(t1, e->stream);
-            if ((rc = wait_stream(e->stream)) != LF_OK) break;
-            float ms = 0;
-            cudaEventElapsedTime(&ms, t0, t1);
-            if (ms < best_ms) { best_ms = ms; best_h = h; }
-        }
-        cudaEventDestroy(t0);
-        cudaEventDestroy(t1);
-        lf_destroy(tmp);
-        if (rc != LF_OK) return rc;
-        best[key] = best_h;
+    // A scratch ensemble of the same runs, so that every candidate is timed
+    // as what it is for: the throughput of the whole batch, not the latency
+    // of one run alone (which favours short segments and many CTAs).
+    const int R = e->nruns;
+    std::vector<lf_grid> G(R);
+    std::vector<lf_walls> W(R);
+    std::vector<lf_params> P(R);
+    for (int r = 0; r < R; ++r) {
+        G[r] = e->runs[r]->grid;
+        W[r] = e->runs[r]->walls;
+        P[r] = e->runs[r]->params;
     }
-    for (int r = 0; r < e->nruns; ++r)
-        if (e->runs[r]->g.stencil != LF_STENCIL_ISOTROPIC)
-            e->rows[r] = best[std::make_pair(e->runs[r]->g.nx, e->runs[r]->g.ny)];
+    lf_ens* sc = nullptr;
+    if ((rc = lf_ens_create(R, G.data(), W.data(), P.data(), e->stream, &sc)) != LF_OK) return rc;
+    sc->width = e->width;
+    sc->rows = e->rows;
+    sc->active = e->active;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    // one pass of coordinate descent over the lattice sizes of the compact runs
+    std::vector<std::pair<int, int>> keys;
+    for (int r = 0; r < R; ++r) {
+        const lf_ctx* c = e->runs[r];
+        if (c->g.stencil == LF_STENCIL_ISOTROPIC || !e->active[r]) continue;
+        const auto key = std::make_pair(c->g.nx, c->g.ny);
+        if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    auto set_shape = [&](lf_ens* x, const std::pair<int, int>& key, int w, int h) {
+        for (int r = 0; r < R; ++r)
+            if (e->runs[r]->g.stencil != LF_STENCIL_ISOTROPIC &&
+                std::make_pair(e->runs[r]->g.nx, e->runs[r]->g.ny) == key) {
+                x->width[r] = w;
+                x->rows[r] = h;
+            }
+    };
+    const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
+    for (const auto& key : keys) {
+        float best_ms = 1e30f;
+        std::pair<int, int> best_wh{64, 16};
+        for (int w : {64, 128})
+            for (int h : cand) {
+                if (2 * h > key.second && h != cand[0]) continue;
+                set_shape(sc, key, w, h);
+                if ((rc = build(sc)) != LF_OK) break;
+                if ((rc = lf_ens_step(sc, 2)) != LF_OK) break;
+                cudaEventRecord(t0, sc->stream);
+                if ((rc = lf_ens_step(sc, reps)) != LF_OK) break;
+                cudaEventRecord(t1, sc->stream);
+                if ((rc = wait_stream(sc->stream)) != LF_OK) break;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (ms < best_ms) { best_ms = ms; best_wh = {w, h}; }
+            }
+        if (rc != LF_OK) break;
+        set_shape(sc, key, best_wh.first, best_wh.second);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (rc == LF_OK) {
+        e->width = sc->width;
+        e->rows = sc->rows;
+    }
+    lf_ens_destroy(sc);
+    if (rc != LF_OK) return rc;
     return build(e);
 }
 
@@ -457,6 +509,39 @@ int lf_ens_rows(const lf_ens* e, int run)
 {
     if (!e || run < 0 || run >= e->nruns) return LF_EINVAL;
     return e->rows[run];
+}
+
+int lf_ens_prune(lf_ens* e, int* nactive)
+{
+    if (!e) return LF_EINVAL;
+    int rc = wait_stream(e->stream);
+    if (rc != LF_OK) return rc;
+    bool changed = false;
+    int live = 0;
+    for (int r = 0; r < e->nruns; ++r) {
+        if (e->active[r] && e->runs[r]->flag_host && *e->runs[r]->flag_host) {
+            e->active[r] = 0;
+            changed = true;
+        }
+        live += e->active[r] ? 1 : 0;
+    }
+    // the two-step graphs assume every run starts step A of a cycle: a
+    // rebuild restarts the cycle from the runs' present buffers
+    if (changed && (rc = build(e)) != LF_OK) return rc;
+    if (nactive) *nactive = live;
+    return LF_OK;
+}
+
+int lf_ens_active(const lf_ens* e, int run)
+{
+    if (!e || run < 0 || run >= e->nruns) return LF_EINVAL;
+    return e->active[run] ? 1 : 0;
+}
+
+int lf_ens_param(const lf_ens* e, int run)
+{
+    if (!e || run < 0 || run >= e->nruns) return LF_EINVAL;
+    return (e->width[run] == 64 ? 1 << 16 : 0) | e->rows[run];
 }
 
 int lf_ens_step(lf_ens* e, int64_t nsteps)

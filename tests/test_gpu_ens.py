@@ -26,7 +26,7 @@ MEMBERS = [
 
 
 def _alone(m, phases):
-    """The run advanced alone: phases = [(steps, rows per segment), ...]."""
+    """The run advanced alone: phases = [(steps, march2 param), ...]."""
     kw = {k: v for k, v in m.items()}
     sim = lf.Lattice(precision="fp32", **kw)
     for steps, rows in phases:
@@ -36,11 +36,11 @@ def _alone(m, phases):
 
 
 def _compare(ens, steps, before=None):
-    """before: (steps, rows per run) taken before the current row split."""
+    """before: (steps, shape param per run) taken before the current shapes."""
     for r, m in enumerate(MEMBERS):
-        phases = [(steps, ens.rows(r))]
+        phases = [(steps, ens.param(r))]
         if before is not None:
-            phases = [(before[0], before[1][r]), (steps - before[0], ens.rows(r))]
+            phases = [(before[0], before[1][r]), (steps - before[0], ens.param(r))]
         ref = _alone(m, phases)
         run = ens.run(r)
         for name in ("phi", "T", "pop"):
@@ -62,12 +62,12 @@ def test_ensemble_equals_single_runs():
 def test_ensemble_after_tuning():
     ens = lf.Ensemble(MEMBERS)
     ens.step(3)
-    rows0 = [ens.rows(r) for r in range(len(MEMBERS))]
+    params0 = [ens.param(r) for r in range(len(MEMBERS))]
     ens.tune(reps=3)
     rows = [ens.rows(r) for r in range(len(MEMBERS))]
     assert all(r >= 1 for r in rows)
     ens.step(6)
-    _compare(ens, 9, before=(3, rows0))
+    _compare(ens, 9, before=(3, params0))
     ens.close()
 
 
@@ -97,7 +97,7 @@ def test_isotropic_runs_in_an_ensemble_equal_single_runs():
     ens.step(6)
     for r, m in enumerate(ISO_MEMBERS):
         ref = lf.Lattice(precision="fp32", **m)
-        ref.set_variant("march2", ens.rows(r))
+        ref.set_variant("march2", ens.param(r))
         ref.step(11)
         run = ens.run(r)
         for name in ("phi", "T", "pop"):
@@ -189,4 +189,31 @@ def test_ensemble_members_match_oracle_many_steps():
         for name, got, ref in (("phi", run.get("phi"), want.phi), ("T", run.get("T"), want.T),
                                ("pop", _to_oracle_f(run.get("pop")), want.f)):
             assert _relerr(got, ref) < 40 * 2e-6, (r, m, name, _relerr(got, ref))
+    ens.close()
+
+
+def test_prune_retires_nonfinite_runs():
+    """A run that diverges (tau = 0.6 with an instantaneous quench: the method
+    itself goes non-finite at these parameters) is retired by lf_ens_prune:
+    its step count stops, while the other runs keep stepping and still equal
+    the same runs stepped alone."""
+    members = [dict(nx=64, ny=64, xi=math.inf, tau=0.6, seed=41),
+               dict(nx=70, ny=37, xi=0.01, tau=1.0, seed=42),
+               dict(nx=48, ny=40, xi=0.5, tau=3.0, seed=43, stencil="isotropic")]
+    ens = lf.Ensemble(members)
+    ens.step(600)
+    nonfinite = [bool(ens.run(r).diag()["nonfinite"]) for r in range(len(members))]
+    assert nonfinite[0] and not nonfinite[1] and not nonfinite[2]
+    assert ens.prune() == 2
+    assert [ens.active(r) for r in range(3)] == [False, True, True]
+    ens.step(7)
+    assert ens.run(0).step_count == 600
+    for r in (1, 2):
+        assert ens.run(r).step_count == 607
+        ref = lf.Lattice(precision="fp32", **members[r])
+        ref.set_variant("march2", ens.param(r))
+        ref.step(607)
+        for name in ("phi", "T", "pop"):
+            np.testing.assert_array_equal(ens.run(r).get(name, "fp32"), ref.get(name, "fp32"), err_msg=f"{r} {name}")
+        ref.close()
     ens.close()
