@@ -142,23 +142,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000, d=2, nz=1, tau=1.0, stencil=0):
+def oracle_rate(nx, ny, xi, seconds=10.0, max_steps=10000, d=2, nz=1, tau=1.0, stencil=0, restore=0):
     """The FP64 CPU oracle as it stands on a bounded sample: steps of an
-    nx x ny (x nz) lattice with the workload's physics, for about `seconds`."""
+    nx x ny (x nz) lattice with the workload's physics, for about `seconds`.
+    With `restore` > 0 the initial quench is taken up again every `restore`
+    steps (outside the timed intervals), as the GPU workload does, so that
+    every timed step advances a finite state."""
     from oracle import oracle as O
 
     cfg = O.make_cfg(d=d, nx=nx, ny=ny, nz=nz, xi=xi, tau=tau, stencil=stencil)
-    st = O.init(cfg)
-    st = O.run(st, 1)   # warm: compile/load, first touch
-    steps, t0 = 0, time.perf_counter()
+    st0 = O.init(cfg)
+    st = O.run(st0, 1)   # warm: compile/load, first touch
+    steps, el, since = 0, 0.0, 1
     chunk = 1
-    while time.perf_counter() - t0 < seconds and steps < max_steps:
+    while el < seconds and steps < max_steps:
+        if restore > 0 and since + chunk > restore:
+            st, since = st0.copy(), 0
+            chunk = min(chunk, restore)
+        t0 = time.perf_counter()
         st = O.run(st, chunk)
+        el += time.perf_counter() - t0
         steps += chunk
-        el = time.perf_counter() - t0
+        since += chunk
         if el < seconds / 4:
             chunk *= 2
-    el = time.perf_counter() - t0
     return 1e-6 * nx * ny * nz * steps / el, steps, el, O.threads()
 
 
@@ -229,8 +236,12 @@ def traffic_for(kernel_key: str):
 
 def run_ensemble(args):
     """96 independent runs (mixed sizes, xi, tau): batched (one graph-replayed
-    persistent launch per step) against the same runs stepped one after
-    another by lf_step; identical results, compared at the end."""
+    persistent launch per step, shapes from the ensemble autotuner) against
+    the same runs stepped one after another by lf_step at their own tuned
+    shapes; results equal to FP32 rounding, compared at the end.  Runs whose state goes non-finite (fast
+    quenches at tau = 0.6 diverge for the method itself) are retired every
+    --ens-prune-every steps, in both arms, and only the runs still finite at
+    the end of a block of steps count towards the rate."""
     import numpy as np
     import torch
 
@@ -246,63 +257,112 @@ def run_ensemble(args):
     members = synth.ensemble_members()
     if args.stencil == "isotropic":
         members = [dict(m, stencil="isotropic") for m in members]
-    sites = sum(m["nx"] * m["ny"] for m in members)
+    sites_r = [m["nx"] * m["ny"] for m in members]
+    sites = sum(sites_r)
     with torch.cuda.stream(stream):
         ens = lf.Ensemble(members, stream=stream)
         t0 = time.time()
         ens.tune(reps=5)
         tune_s = time.time() - t0
+        shapes = {}
+        for r, m in enumerate(members):
+            if m.get("stencil") != "isotropic":
+                pr = ens.param(r)
+                shapes[f"{m['nx']}x{m['ny']}"] = {"cta_threads": 64 if pr >> 16 else 128, "rows": pr & 0xFFFF}
+        # the plain single-run path at its own best shapes (lf_tune, cached per lattice size)
         singles = [lf.Lattice(precision="fp32", stream=stream, **m) for m in members]
+        single_shapes = {}
         for r, s_ in enumerate(singles):
-            s_.set_variant("march2", ens.rows(r))   # same kernel and row split as the batch
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            v_, p_, _ = s_.tune(reps=3)
+            single_shapes[f"{members[r]['nx']}x{members[r]['ny']}" + ("-iso" if members[r].get("stencil") else "")] = \
+                {"variant": v_, "param": p_}
         ens.step(args.warmup)
         for s_ in singles:
             s_.step(args.warmup)
         torch.cuda.synchronize(dev)
+        live = [True] * len(members)
+        live_s = [True] * len(members)
+        ens.prune()
+        for r in range(len(members)):
+            live[r] = ens.active(r)
+            live_s[r] = not singles[r].diag()["nonfinite"]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         clk = Clocks(local)
+        t_batch = t_seq = 0.0
+        site_steps = 0
+        left = args.steps
+        block = args.ens_prune_every if args.ens_prune_every > 0 else args.steps
         with clk:
             time.sleep(0.5)
             tb = time.time()
-            ev[0].record(stream)
-            ens.step(args.steps)
-            ev[1].record(stream)
-            ev[2].record(stream)
-            for s_ in singles:
-                s_.step(args.steps)
-            ev[3].record(stream)
-            torch.cuda.synchronize(dev)
+            while left > 0:
+                k = min(block, left)
+                ev[0].record(stream)
+                ens.step(k)
+                ev[1].record(stream)
+                ev[2].record(stream)
+                for r, s_ in enumerate(singles):
+                    if live_s[r]:
+                        s_.step(k)
+                ev[3].record(stream)
+                torch.cuda.synchronize(dev)
+                t_batch += ev[0].elapsed_time(ev[1]) / 1e3
+                t_seq += ev[2].elapsed_time(ev[3]) / 1e3
+                ens.prune()
+                for r in range(len(members)):
+                    live[r] = ens.active(r)
+                    if live_s[r]:
+                        live_s[r] = not singles[r].diag()["nonfinite"]
+                site_steps += k * sum(sr for sr, a in zip(sites_r, live) if a)
+                left -= k
             te = time.time()
         clk.window(tb, te + 0.15)
-        t_batch = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, dev)
-        t_seq = max_over_ranks(ev[2].elapsed_time(ev[3]) / 1e3, dev)
-        identical, nonfinite = True, 0
+        t_batch = max_over_ranks(t_batch, dev)
+        t_seq = max_over_ranks(t_seq, dev)
+        # the two arms split the rows differently (each at its own best shape), so
+        # they agree to FP32 rounding, not bit for bit: compare what the runs are
+        # for, the structure factor peak and the order parameter field
+        sk_err, l2_err = 0.0, 0.0
         for r in range(len(members)):
+            if not (live[r] and live_s[r]):
+                continue
+            da, db = ens.run(r).diag(), singles[r].diag()
+            sk_err = max(sk_err, abs(da["k_peak"] / db["k_peak"] - 1), abs(da["s_peak"] / db["s_peak"] - 1))
             a = ens.run(r).get("phi", "fp32")
             b = singles[r].get("phi", "fp32")
-            identical &= bool(np.array_equal(a, b, equal_nan=True))
-            nonfinite += int(not np.isfinite(a).all())
-    value = job_rate(sites, args.steps, world, t_batch)
+            l2_err = max(l2_err, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        n_live = sum(live)
+        same_retirement = live == live_s
+    value = 1e-6 * site_steps * world / t_batch
     peak, peak_kind = peaks()
-    achieved = 88 * sites * args.steps / t_batch / 1e9
+    achieved = 88 * site_steps / t_batch / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "ens96: 96 independent 2D runs, 24 each of 128^2, 256^2, 384^2, 512^2, xi "
                                "log-uniform in [1e-4, 1], tau in {0.6, 1, 3}, one persistent launch per step "
-                               "replayed from a CUDA graph, tuned segment heights"
+                               "replayed from a CUDA graph, CTA width and segment height from the autotuner"
                                + (", isotropic 9-point stencils (tile items)" if args.stencil == "isotropic" else ""),
-                   "sites_per_step": sites, "l2": "inputs (1 GB of state) larger than L2"},
+                   "sites_per_step_all_runs": sites, "tuned_shapes": shapes,
+                   "sequential_shapes": single_shapes,
+                   "l2": "inputs (1 GB of state) larger than L2",
+                   "rate_counts": "site updates of the runs still finite at the end of each block of "
+                                  f"{block} steps (non-finite runs retired between blocks, outside the timing)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_site": 88,
                      "kernel": ("k_ens_tile2d_iso" if args.stencil == "isotropic" else "k_ens_march2d")
                                + " (+ k_ens_tsub2d for runs with xi/nsub sub-steps)"},
         "batched_vs_sequential": {"t_batched_s": t_batch, "t_sequential_s": t_seq, "speedup": t_seq / t_batch,
-                                  "bit_identical_phi": identical, "tune_s": tune_s,
-                                  "runs_nonfinite": nonfinite,
-                                  "note": "runs with tau = 0.6 and fast quenches (xi above ~0.05) diverge for the "
-                                          "method itself at these parameters (the CPU oracle diverges the same way)"},
+                                  "max_sk_peak_err": sk_err, "max_phi_rel_l2": l2_err, "tune_s": tune_s,
+                                  "what": "time to solution of the same runs and steps: batched against one "
+                                          "after another by lf_step at each run's own tuned shape; S(k) peak "
+                                          "position/height and phi compared at the end over the finite runs",
+                                  "runs_finite_at_end": n_live, "runs_retired": len(members) - n_live,
+                                  "same_runs_retired_in_both_arms": same_retirement,
+                                  "note": "runs with tau = 0.6 and fast quenches diverge for the method itself at "
+                                          "these parameters (the CPU oracle diverges the same way); both arms "
+                                          "retire them at the same block boundaries"},
         "clocks": clk.summary(),
     }
     if world > 1:
@@ -319,11 +379,15 @@ def run_ensemble(args):
 
 
 def run_surrogate(args):
-    """Learned surrogate at 256 x 256: trajectories of the plain solver (an
-    ensemble, xi log-uniform in [1e-4, 1]) -> (state, state K steps later)
-    pairs; training on the tensor-core kernels; then the same number of steps
-    of a fresh run done plain-only and interleaved (surrogate windows checked by
-    plain shadow windows), time-to-solution and S(k) error compared."""
+    """Learned surrogate at 256 x 256.  Trajectories of the plain solver (one
+    ensemble, xi log-uniform in [1e-4, 1]) are kept on the device as states
+    every K steps; consecutive states form the (state, state K steps later)
+    training pairs.  Whole trajectories are held out for the accuracy test,
+    optionally with a learning curve over the amount of training data.  Then a
+    fresh run is advanced plain-only and interleaved 1:1 with the surrogate,
+    every surrogate window checked by a plain shadow window at the 2 %
+    threshold; the time to solution is reported counting a surrogate window as
+    a gain only when its check passed."""
     import numpy as np
     import torch
 
@@ -340,60 +404,42 @@ def run_surrogate(args):
     rng = np.random.default_rng(2011)
     nruns, nwin, warm = args.sur_runs, args.sur_windows, 400
     members = [dict(nx=NX, ny=NY, xi=float(10 ** rng.uniform(-4, 0)), tau=1.0, seed=500 + i) for i in range(nruns)]
+    B = args.sur_batch
     with torch.cuda.stream(stream):
         t0 = time.time()
-        ens = lf.Ensemble(members, stream=stream)
-        ens.step(warm)
-        xs, ys = [], []
-
-        def snap():
-            return [torch.stack([ens.run(r).get(n, "fp32", device=True) for n in ("phi", "T", "ux", "uy")])
-                    for r in range(nruns)]
-        prev = snap()
-        for w in range(nwin):
-            ens.step(K)
-            cur = snap()
-            for r in range(nruns):
-                if torch.isfinite(prev[r]).all() and torch.isfinite(cur[r]).all():
-                    xs.append(prev[r])
-                    ys.append(cur[r])
-            prev = cur
-        X, Y = torch.stack(xs), torch.stack(ys)
-        ens.close()
-        # pairs whose velocity left the LB's low-Mach range are diverging runs
-        # (fast quenches at these parameters): not training material
-        umax = torch.maximum(X[:, 2:].abs().amax(dim=(1, 2, 3)), Y[:, 2:].abs().amax(dim=(1, 2, 3)))
-        good = umax < 0.2
-        n_dropped = int((~good).sum())
-        X, Y = X[good], Y[good]
-        # held-out windows: every 8th pair
-        hold = torch.zeros(X.shape[0], dtype=torch.bool)
-        hold[::8] = True
-        Xv, Yv = X[hold.to(dev)], Y[hold.to(dev)]
-        X, Y = X[~hold.to(dev)], Y[~hold.to(dev)]
-        t_data = time.time() - t0
-        # inputs centred on the data mean; every channel scaled by the spread of
-        # its K-step change, so all four channels weigh alike in the loss
-        offset = X.permute(1, 0, 2, 3).reshape(4, -1).mean(dim=1).cpu().numpy()
-        scale = (Y - X).permute(1, 0, 2, 3).reshape(4, -1).std(dim=1).clamp_min(1e-6).cpu().numpy()
-        B = 8
-        sur = lf.Surrogate(NY, NX, B, scale=scale, offset=offset, seed=7, stream=stream)
-        sur.set_clip(1.0)
-        npairs = X.shape[0]
-        gen = torch.Generator().manual_seed(0)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        losses = []
-        ev[0].record(stream)
-        for it in range(args.sur_iters):
-            lr = args.sur_lr * 0.5 * (1 + math.cos(math.pi * it / args.sur_iters))
-            idx = torch.randint(0, npairs, (B,), generator=gen).to(dev)
-            l = sur.train_step(X[idx].contiguous(), Y[idx].contiguous(), lr)
-            if it % 250 == 0 or it == args.sur_iters - 1:
-                losses.append((it, l))
-        ev[1].record(stream)
+        # states[r, w] = (phi, T, ux, uy) of run r after warm + w K steps
+        S = torch.empty((nruns, nwin + 1, 4, NY, NX), dtype=torch.float32, device=dev)
+        chunk = 128                          # runs per ensemble
+        for c0 in range(0, nruns, chunk):
+            ms = members[c0:c0 + chunk]
+            ens = lf.Ensemble(ms, stream=stream)
+            ens.step(warm)
+            for w in range(nwin + 1):
+                if w:
+                    ens.step(K)
+                for r in range(len(ms)):
+                    ctx = lf.lf_ens_run(ens.ens, r)
+                    for ci, name in enumerate(("phi", "T", "ux", "uy")):
+                        dst = S[c0 + r, w, ci]
+                        lf.lf_fields(ctx, lf.FIELDS[name], dst.data_ptr(), dst.numel() * 4, True)
+            ens.close()
+        # a pair is usable while the run stays finite and at low Mach (|u| < 0.2):
+        # runs with fast quenches diverge for the method itself at these parameters
+        umax = S[:, :, 2:].abs().amax(dim=(2, 3, 4))
+        ok_state = torch.isfinite(S).flatten(2).all(dim=2) & (umax < 0.2)
+        ok_pair = ok_state[:, :-1] & ok_state[:, 1:]
+        held = torch.zeros(nruns, dtype=torch.bool, device=dev)
+        held[7::8] = True                    # whole trajectories held out
+        tr_idx = torch.nonzero(ok_pair & ~held[:, None])
+        ho_idx = torch.nonzero(ok_pair & held[:, None])
+        n_dropped = int((~ok_pair).sum())
         torch.cuda.synchronize(dev)
-        t_train = ev[0].elapsed_time(ev[1]) / 1e3
-        # held-out accuracy against keeping the state unchanged, S(k) by the library
+        t_data = time.time() - t0
+        X0 = S[tr_idx[:, 0], tr_idx[:, 1]]
+        offset = X0.permute(1, 0, 2, 3).reshape(4, -1).mean(dim=1).cpu().numpy()
+        dY = S[tr_idx[:, 0], tr_idx[:, 1] + 1] - X0
+        scale = dY.permute(1, 0, 2, 3).reshape(4, -1).std(dim=1).clamp_min(1e-6).cpu().numpy()
+        del X0, dY
         probe = lf.Lattice(nx=NX, ny=NY, precision="fp32", xi=1e-2, tau=1.0, seed=1, stream=stream, device=dev)
 
         def sk(phi):
@@ -404,17 +450,63 @@ def run_surrogate(args):
         def sk_err(a, b):
             (ka, sa), (kb, sb) = sk(a), sk(b)
             return max(abs(ka / kb - 1), abs(sa / sb - 1))
-        ho = {"pairs": int(Xv.shape[0]), "phi_l2": [], "sk": [], "persist_phi_l2": [], "persist_sk": []}
-        for i in range(Xv.shape[0]):
-            yp = sur.predict(Xv[i:i + 1].contiguous())[0]
-            yt = Yv[i]
-            ho["phi_l2"].append(float((yp[0] - yt[0]).norm() / yt[0].norm()))
-            ho["persist_phi_l2"].append(float((Xv[i, 0] - yt[0]).norm() / yt[0].norm()))
-            ho["sk"].append(sk_err(yp[0].contiguous(), yt[0].contiguous()))
-            ho["persist_sk"].append(sk_err(Xv[i, 0].contiguous(), yt[0].contiguous()))
-        probe.close()
-        heldout = {k: (float(np.mean(v)) if isinstance(v, list) else v) for k, v in ho.items()}
-        heldout.update({k + "_median": float(np.median(v)) for k, v in ho.items() if isinstance(v, list)})
+
+        def train(pairs, iters, seed):
+            """A network trained on the given (run, window) pairs; returns it,
+            the training time and the loss trace."""
+            sur = lf.Surrogate(NY, NX, B, scale=scale, offset=offset, seed=seed, stream=stream)
+            sur.set_clip(1.0)
+            gen = torch.Generator().manual_seed(seed)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            losses = []
+            ev[0].record(stream)
+            for it in range(iters):
+                lr = args.sur_lr * 0.5 * (1 + math.cos(math.pi * it / iters))
+                sel = pairs[torch.randint(0, pairs.shape[0], (B,), generator=gen).to(dev)]
+                x = S[sel[:, 0], sel[:, 1]].contiguous()
+                y = S[sel[:, 0], sel[:, 1] + 1].contiguous()
+                l = sur.train_step(x, y, lr)
+                if it % 500 == 0 or it == iters - 1:
+                    losses.append((it, l))
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            return sur, ev[0].elapsed_time(ev[1]) / 1e3, losses
+
+        def heldout(sur, limit=None):
+            """One-window accuracy on the held-out trajectories against keeping
+            the state unchanged: phi relative L2 error and S(k) peak error."""
+            idx = ho_idx if limit is None else ho_idx[:limit]
+            acc = {"pairs": int(idx.shape[0]), "phi_l2": [], "sk": [], "persist_phi_l2": [], "persist_sk": []}
+            for r_, w_ in idx.tolist():
+                x = S[r_, w_:w_ + 1].contiguous()
+                yt = S[r_, w_ + 1]
+                yp = sur.predict(x)[0]
+                acc["phi_l2"].append(float((yp[0] - yt[0]).norm() / yt[0].norm()))
+                acc["persist_phi_l2"].append(float((x[0, 0] - yt[0]).norm() / yt[0].norm()))
+                acc["sk"].append(sk_err(yp[0].contiguous(), yt[0].contiguous()))
+                acc["persist_sk"].append(sk_err(x[0, 0].contiguous(), yt[0].contiguous()))
+            out = {k: (float(np.mean(v)) if isinstance(v, list) else v) for k, v in acc.items()}
+            out.update({k + "_median": float(np.median(v)) for k, v in acc.items() if isinstance(v, list)})
+            out["within_2pct"] = float(np.mean([max(a, b) <= 0.02 for a, b in zip(acc["phi_l2"], acc["sk"])]))
+            return out
+
+        # learning curve: networks on random subsets of the training pairs, each
+        # trained for as many steps as the main network (the last point)
+        curve = []
+        perm = torch.randperm(tr_idx.shape[0], generator=torch.Generator().manual_seed(3)).to(dev)
+        for frac in [float(v) for v in args.sur_curve.split(",") if v and float(v) < 1.0]:
+            n = max(B, int(frac * tr_idx.shape[0]))
+            net, t_tr, _ = train(tr_idx[perm[:n]], args.sur_iters, 7)
+            h = heldout(net, limit=args.sur_curve_pairs)
+            curve.append({"train_pairs": n, "iters": args.sur_iters, "phi_l2": h["phi_l2"],
+                          "phi_l2_median": h["phi_l2_median"], "sk": h["sk"], "within_2pct": h["within_2pct"]})
+            net.close()
+        sur, t_train, losses = train(tr_idx, args.sur_iters, 7)
+        ho = heldout(sur)
+        if curve:
+            h = heldout(sur, limit=args.sur_curve_pairs)
+            curve.append({"train_pairs": int(tr_idx.shape[0]), "iters": args.sur_iters, "phi_l2": h["phi_l2"],
+                          "phi_l2_median": h["phi_l2_median"], "sk": h["sk"], "within_2pct": h["within_2pct"]})
         # evaluation run: fresh state, same physics, xi in the middle of the range
         ev_kw = dict(nx=NX, ny=NY, precision="fp32", xi=1e-2, tau=1.0, seed=9001, stream=stream, device=dev)
         plain = lf.Lattice(**ev_kw)
@@ -439,23 +531,44 @@ def run_surrogate(args):
         dp, dh = plain.diag(), hyb.diag()
         pp, ph = plain.get("phi", "fp32"), hyb.get("phi", "fp32")
         l2 = float(np.linalg.norm(ph - pp) / np.linalg.norm(pp))
+        probe.close()
     final_sk_err = max(abs(dh["k_peak"] / dp["k_peak"] - 1), abs(dh["s_peak"] / dp["s_peak"] - 1))
+    # time to solution counting only windows known to be within the threshold:
+    # plain windows, the predictions whose check passed, and for every other
+    # surrogate window its prediction and a plain window
+    tts = None
+    if rep and rep.get("shadow_checks"):
+        n_sur = (args.sur_eval_windows + 1) // 2
+        n_plain = args.sur_eval_windows // 2
+        t_pred = rep["t_surrogate_s"] / n_sur
+        t_pw = rep["t_plain_s"] / max(1, n_plain + rep["rejected"])
+        passed = rep["shadow_checks"] - rep["fallbacks"]
+        unknown = n_sur - passed
+        t_known = n_plain * t_pw + passed * t_pred + unknown * (t_pred + t_pw)
+        tts = {"t_s": t_known, "speedup_vs_plain": t_plain / t_known, "windows_passed": passed,
+               "windows_checked": rep["shadow_checks"], "t_prediction_s": t_pred, "t_plain_window_s": t_pw,
+               "what": "plain windows + predictions whose shadow check passed + (prediction + plain window) for "
+                       "every other surrogate window; shadow windows are the verification, not counted"}
     sites = NX * NY
+    value = 1e-6 * sites * nsteps / tts["t_s"] if tts else 0.0
     line = {
-        "metric": METRIC + " (surrogate-interleaved time to solution)", "value": 1e-6 * sites * nsteps / t_hyb,
-        "unit": "MLUPS", "n_gpus": 1, "steps": nsteps, "warmup": warm, "ms_per_step": 1e3 * t_hyb / nsteps,
+        "metric": METRIC + " (surrogate-interleaved time to solution, counting only windows checked within 2 %)",
+        "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": nsteps, "warmup": warm,
+        "ms_per_step": 1e3 * tts["t_s"] / nsteps if tts else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
         "config": {"workload": "sur256: 256x256 lamellar quench, 6-layer 64-channel residual CNN advancing "
-                               f"(phi, T, ux, uy) by K={K} steps, trained on {npairs} pairs from {nruns} solver "
-                               "trajectories (xi log-uniform in [1e-4, 1]); evaluation at xi = 1e-2",
+                               f"(phi, T, ux, uy) by K={K} steps, trained on {int(tr_idx.shape[0])} pairs from "
+                               f"{nruns - nruns // 8} solver trajectories of {warm + nwin * K} steps (xi log-uniform "
+                               f"in [1e-4, 1]; the stated data volume is 2000 trajectories of 20k steps); "
+                               f"{nruns // 8} whole trajectories held out; evaluation at xi = 1e-2",
                    "train_iters": args.sur_iters, "batch": B, "lr": args.sur_lr, "lr_schedule": "cosine",
-                   "grad_clip": 1.0, "pairs_dropped_umax": n_dropped,
+                   "grad_clip": 1.0, "pairs_dropped": n_dropped,
                    "shadow_every": args.sur_shadow_every, "threshold": 0.02},
-        "surrogate": {"t_data_s": t_data, "t_train_s": t_train, "losses": losses, "heldout": heldout,
-                      "report": rep, "run_error": run_error,
+        "surrogate": {"t_data_s": t_data, "t_train_s": t_train, "losses": losses, "heldout": ho,
+                      "learning_curve": curve, "report": rep, "run_error": run_error,
                       "t_plain_only_s": t_plain, "t_interleaved_wall_s": t_hyb,
-                      "speedup_vs_plain": t_plain / t_hyb, "final_phi_rel_l2_vs_plain": l2,
-                      "final_sk_peak_err_vs_plain": final_sk_err},
+                      "time_to_solution_known_good": tts,
+                      "final_phi_rel_l2_vs_plain": l2, "final_sk_peak_err_vs_plain": final_sk_err},
     }
     print(json.dumps(line), flush=True)
     for o in (plain, hyb, sur):
@@ -579,7 +692,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic_for(f"{kname}_{prec}_{nx}"), "peak_kind": peak_kind,
             "algorithmic_bytes_per_site": bps,
-            "kernel": kname + (" (three passes; bytes and time of the whole step)" if passes > 1
+            "kernel": kname + (f" ({passes} passes; bytes and time of the whole step)" if passes > 1
                                else " (fused phi-chain + LB + FD)"),
             "kernel_ms_mean": kernel_ms, "kernel_ms_median": statistics.median(times_ms) / per_kernel}
 
@@ -619,8 +732,8 @@ def run_ours(args):
     if rank == 0 and args.cpu_seconds > 0:
         if d == 3:
             rate, steps, el, cores = oracle_rate(64, 64, args.xi, seconds=args.cpu_seconds, d=3, nz=64, tau=tau,
-                                                 stencil=int(iso))
-            smp = "64x64x64"
+                                                 stencil=int(iso), restore=restore)
+            smp = "64x64x64" + (f", initial quench restored every {restore} steps" if restore > 0 else "")
         else:
             rate, steps, el, cores = oracle_rate(256, 256, args.xi, seconds=args.cpu_seconds, stencil=int(iso))
             smp = "256x256"
@@ -667,12 +780,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["prec1024", "cube384", "ens96", "sur256"], default="cube384")
-    ap.add_argument("--sur-runs", type=int, default=32)
-    ap.add_argument("--sur-windows", type=int, default=20)
-    ap.add_argument("--sur-iters", type=int, default=3000)
+    ap.add_argument("--ens-prune-every", type=int, default=500,
+                    help="ens96: retire non-finite runs every this many steps (0 = never)")
+    ap.add_argument("--sur-runs", type=int, default=512, help="solver trajectories (every 8th held out)")
+    ap.add_argument("--sur-windows", type=int, default=40, help="K-step windows per trajectory after the warm-up")
+    ap.add_argument("--sur-iters", type=int, default=16000)
+    ap.add_argument("--sur-batch", type=int, default=8)
     ap.add_argument("--sur-lr", type=float, default=1e-3)
+    ap.add_argument("--sur-curve", default="", help="comma-separated fractions below 1 of the training pairs "
+                    "for a learning curve (one network each, as many steps as the main network)")
+    ap.add_argument("--sur-curve-pairs", type=int, default=512, help="held-out pairs per learning-curve point")
     ap.add_argument("--sur-eval-windows", type=int, default=40)
-    ap.add_argument("--sur-shadow-every", type=int, default=4)
+    ap.add_argument("--sur-shadow-every", type=int, default=1)
     ap.add_argument("--size", type=int, default=1024, help="2D lattice side (prec1024)")
     ap.add_argument("--size3", type=int, default=384, help="3D lattice side (cube384)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
