@@ -599,15 +599,23 @@ def run_ours(args):
         tau = 1.0
     sim = lf.Lattice(d=d, nx=nx, ny=ny, nz=nz, precision=prec, xi=args.xi, tau=tau, seed=1 + rank, stream=stream,
                      device=dev)
-    variant = args.variant
-    if variant == "auto":
-        variant = "split3" if d == 3 else ("march2" if prec == "fp32" else "march")
-    sim.set_variant(variant, args.tune)
     iso = args.stencil == "isotropic"
     if iso:
         sim.set_stencil("isotropic")        # 2D: the tile kernel; 3D: the variant set (three passes by default)
-        if d == 2:
-            variant = "tile"
+    names = {lf.LF_VARIANT_MARCH: "march", lf.LF_VARIANT_TILE: "tile", lf.LF_VARIANT_MARCH2: "march2",
+             lf.LF_VARIANT_SPLIT3: "split3"}
+    variant = args.variant
+    tuned = None
+    if variant == "auto":
+        # the library's autotuner picks the kernel variant and shape for this lattice
+        v_, p_, ms_ = sim.tune(reps=5)
+        variant, param = names[v_], p_
+        tuned = {"variant": variant, "param": p_, "ms_per_step_in_tuning": ms_}
+    else:
+        param = args.tune
+        sim.set_variant(variant, param)
+    if iso and d == 2:
+        variant = "tile"
     N = nx * ny * nz
     # The compact 3D step at these parameters goes non-finite after about 150
     # steps (the FP64 oracle too), so the 3D workload restores its initial quench
@@ -690,7 +698,8 @@ def run_ours(args):
     if kname == "k_march2d_x2" and prec == "fp64":
         kname = "k_march2d"                 # the packed kernel is FP32 only
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_for(f"{kname}_{prec}_{nx}"), "peak_kind": peak_kind,
+            # ncu DRAM bytes per kernel shape (key suffix _p<param>; no suffix: the default shape)
+            "traffic": traffic_for(f"{kname}_{prec}_{nx}" + (f"_p{param}" if param else "")), "peak_kind": peak_kind,
             "algorithmic_bytes_per_site": bps,
             "kernel": kname + (f" ({passes} passes; bytes and time of the whole step)" if passes > 1
                                else " (fused phi-chain + LB + FD)"),
@@ -740,6 +749,34 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"{steps} FP64 oracle steps of a {smp} lattice with the workload's physics "
                          f"({el:.1f} s)"}
+    # The compact 3D step at tau = 0.6 goes non-finite after about 150 steps (the
+    # oracle too), hence the restores above.  The configuration that runs to its
+    # stated 20k steps at this size is tau = 3 with the isotropic stencils: time
+    # it too, without restores, beside the main line.
+    stable = None
+    if d == 3 and args.stable_run and not iso:
+        sim.close()
+        sim = lf.Lattice(d=3, nx=nx, ny=ny, nz=nz, precision=prec, xi=args.xi, tau=3.0, seed=1 + rank,
+                         stream=stream, device=dev, stencil="isotropic")
+        v_, p_, _ = sim.tune(reps=3)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                sim.step(1)
+        barrier()
+        ts = []
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                starts[k].record(stream)
+                sim.step(1)
+                ends[k].record(stream)
+        barrier()
+        ts = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        tot = max_over_ranks(sum(ts) / 1e3, dev)
+        ach = bps * N * args.steps / tot / 1e9
+        stable = {"what": "tau = 3, isotropic 19-point stencils (runs the 20k steps finite); no restores",
+                  "value": job_rate(N, args.steps, world, tot), "unit": "MLUPS",
+                  "ms_per_step": 1e3 * tot / args.steps, "frac": ach / peak, "achieved_gbs": ach,
+                  "kernel_shape": {"variant": names[v_], "param": p_}, "diag_after": {"rc": sim.diag()["rc"]}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -755,7 +792,8 @@ def run_ours(args):
                                           + (", then a 256 MiB read so no dirty flush lines are written back "
                                              "inside the timed step" if args.flush == "write+read" else "")
                                           + "); each step timed alone with CUDA events on the library stream"),
-                       "parallelism": f"replicas x{world} (one independent lattice per GPU)"},
+                       "parallelism": f"replicas x{world} (one independent lattice per GPU)",
+                       "kernel_shape": tuned if tuned else {"variant": variant, "param": param, "from": "--variant"}},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -765,6 +803,7 @@ def run_ours(args):
                                   "between the timed events"} if restore > 0 else None),
             "clocks": clocks,
             "diag_after": {"mass": dg["mass"], "mach": dg["mach"], "rc": dg["rc"]},
+            "stable_configuration": stable,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -801,12 +840,14 @@ def main():
                     help="restore the initial state every R timed steps, outside the timed events "
                          "(default: 100 in 3D, never in 2D; 0 = never)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--stable-run", type=int, default=1,
+                    help="3D compact workload: also time tau = 3 with the isotropic stencils (1) or not (0)")
     ap.add_argument("--variant", choices=["auto", "march", "tile", "march2", "split3"], default="auto",
-                    help="step kernel variant (all compute the same step); auto = the library's default "
-                         "(2D FP32: march2, 2D FP64: march, 3D: split3)")
+                    help="step kernel variant (all compute the same step); auto = the choice of the library's "
+                         "autotuner (lf_tune) for this lattice")
     ap.add_argument("--flush", choices=["write", "write+read"], default="write+read",
                     help="L2 eviction between timed steps (2D and 3D single-lattice workloads)")
-    ap.add_argument("--tune", type=int, default=0, help="march: rows per CTA segment (0 = automatic)")
+    ap.add_argument("--tune", type=int, default=0, help="param of an explicit --variant (see lf_set_kernel_variant)")
     ap.add_argument("--stencil", choices=["compact", "isotropic"], default="compact",
                     help="finite-difference stencils (isotropic: the 2D tile kernel; in 3D the chosen variant)")
     args = ap.parse_args()

@@ -1,0 +1,95 @@
+"""Runs of the synthetic lamellar-quench configurations to their stated
+lengths, with either stencil, reporting the structure-factor peak, the
+orientation order parameter and the Mach number along the way (Sec. 2 asks for
+Ma < 0.1) and where a run goes non-finite.
+
+    python -m paper_1102_3094_gb300.config_runs [--cube 384] [--square 1024]
+                                                [--quick] [--out FILE]
+
+Configurations (b = 1, kappa = -0.025, c = 0.02, Gamma = 0.05, Tc = 1,
+T0 = 1.1, T_w = 0.5, phi uniform in [-0.05, 0.05]):
+  * 3D, cube^3 D3Q19, FP32, periodic in x and y, cold walls normal to z,
+    xi in {1e-3, 1e-2}, tau in {0.6, 3}, 20k steps;
+  * 2D, square^2 D2Q9, FP32, cold walls normal to y, xi in {1e-3, 1e-1},
+    tau = 1, 50k steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+
+def run(d, n, xi, tau, stencil, steps, reports, seed=1):
+    from paper_1102_3094_gb300 import lf
+
+    shape = dict(d=3, nx=n, ny=n, nz=n) if d == 3 else dict(d=2, nx=n, ny=n)
+    sim = lf.Lattice(precision="fp32", xi=xi, tau=tau, seed=seed, stencil=stencil, **shape)
+    rows, done, diverged = [], 0, None
+    for r in range(1, reports + 1):
+        target = steps * r // reports
+        try:
+            sim.step(target - done)
+        except lf.LFError as ex:              # the state went non-finite inside this stretch
+            diverged = {"after": done, "before": target, "error": str(ex)}
+            break
+        done = target
+        dg = sim.diag()
+        if dg["rc"] != 0:
+            diverged = {"after": rows[-1]["t"] if rows else 0, "before": done, "error": lf.strerror(dg["rc"])}
+            break
+        rows.append({"t": done, "k_peak": dg["k_peak"], "s_peak": dg["s_peak"], "s": dg["orient_s"],
+                     "mach": dg["mach"], "mass": dg["mass"]})
+    sim.close()
+    return {"d": d, "n": n, "xi": xi, "tau": tau, "stencil": stencil, "steps": steps, "series": rows,
+            "diverged": diverged, "finite_to": rows[-1]["t"] if rows else 0}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--cube", type=int, default=384, help="3D lattice side (0: skip the 3D runs)")
+    ap.add_argument("--square", type=int, default=1024, help="2D lattice side (0: skip the 2D runs)")
+    ap.add_argument("--quick", action="store_true", help="a tenth of every run length")
+    ap.add_argument("--reports", type=int, default=10)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    import torch
+
+    torch.cuda.init()
+    div = 10 if args.quick else 1
+    cases = []
+    if args.cube:
+        for stencil in ("compact", "isotropic"):
+            for tau in (0.6, 3.0):
+                for xi in (1e-3, 1e-2):
+                    cases.append((3, args.cube, xi, tau, stencil, 20_000 // div))
+    if args.square:
+        for stencil in ("compact", "isotropic"):
+            for xi in (1e-3, 1e-1):
+                cases.append((2, args.square, xi, 1.0, stencil, 50_000 // div))
+    results = []
+    for c in cases:
+        res = run(*c, reports=args.reports)
+        results.append(res)
+        print(json.dumps(res), flush=True)
+    print("\n| lattice | stencil | tau | xi | finite to (of) | k_peak | S_peak | s | max Ma |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for r in results:
+        last = r["series"][-1] if r["series"] else None
+        ma = max((x["mach"] for x in r["series"]), default=float("nan"))
+        lat = f"{r['n']}^{r['d']}"
+        if last:
+            print(f"| {lat} | {r['stencil']} | {r['tau']:g} | {r['xi']:g} | {r['finite_to']} ({r['steps']}) | "
+                  f"{last['k_peak']:.4f} | {last['s_peak']:.4g} | {last['s']:+.3f} | {ma:.3f} |")
+        else:
+            print(f"| {lat} | {r['stencil']} | {r['tau']:g} | {r['xi']:g} | non-finite before "
+                  f"{r['diverged']['before']} ({r['steps']}) | | | | |")
+    if args.out:
+        with open(args.out, "w") as fh:
+            for r in results:
+                fh.write(json.dumps(r) + "\n")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
