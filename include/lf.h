@@ -261,10 +261,10 @@ int lf_load(lf_ctx* ctx, const char* path);
  *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a
  *     plane march ((param & 0xFFFF) = planes per segment, 0 = automatic; in
  *     FP32 two segments run in the lanes of packed FP32x2 arithmetic unless
- *     (param >> 16) is 1 or 2, which select one lane on 60x4 or 28x12
- *     tiles), then collision and streaming, then the phi and T updates, one
- *     thread per site; mu, F and u pass through the context's derived-field
- *     planes.  For 3D contexts every other variant runs the fused plane
+ *     (param >> 16) & 15 is 1 or 2, which select one lane on 60x4 or 28x12
+ *     tiles), then collision and streaming, then the phi and T updates by a
+ *     column march over (param >> 20) & 255 planes per segment (0 = 16); mu,
+ *     F and u pass through the context's derived-field planes.  For 3D contexts every other variant runs the fused plane
  *     march (param = planes per segment).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
 #define LF_VARIANT_MARCH  0

@@ -45,6 +45,46 @@ def run(d, n, xi, tau, stencil, steps, reports, seed=1):
             "diverged": diverged, "finite_to": rows[-1]["t"] if rows else 0}
 
 
+def precision_pair(n, xi, stencil, seeds, steps, reports):
+    """The precision form against FP64 on the GPU: the same run (lattice,
+    physics, seed) in FP32 (deviation populations) and in FP64, S(k) peak
+    position and height and s at every report time; per report time the seed
+    means of both and their relative (k, S) or absolute (s) differences."""
+    from paper_1102_3094_gb300 import lf
+
+    per = {"fp32": {}, "fp64": {}}
+    for seed in seeds:
+        for prec in ("fp32", "fp64"):
+            sim = lf.Lattice(nx=n, ny=n, precision=prec, xi=xi, tau=1.0, seed=seed, stencil=stencil)
+            rows, done = [], 0
+            for r in range(1, reports + 1):
+                target = steps * r // reports
+                try:
+                    sim.step(target - done)
+                except lf.LFError:               # the run went non-finite in this stretch
+                    break
+                done = target
+                dg = sim.diag()
+                if dg["rc"] != 0:
+                    break
+                rows.append({"t": done, "k_peak": dg["k_peak"], "s_peak": dg["s_peak"], "s": dg["orient_s"]})
+            sim.close()
+            per[prec][seed] = rows
+    table = []
+    for i in range(reports):
+        # seeds whose runs are finite at this report time in both precisions
+        ok = [sd for sd in seeds if len(per["fp32"][sd]) > i and len(per["fp64"][sd]) > i]
+        if not ok:
+            break
+        m = {p_: {k: sum(per[p_][sd][i][k] for sd in ok) / len(ok) for k in ("k_peak", "s_peak", "s")} for p_ in per}
+        table.append({"t": per["fp32"][ok[0]][i]["t"], "seeds": len(ok), "fp32": m["fp32"], "fp64": m["fp64"],
+                      "d_k_peak": abs(m["fp32"]["k_peak"] / m["fp64"]["k_peak"] - 1),
+                      "d_s_peak": abs(m["fp32"]["s_peak"] / m["fp64"]["s_peak"] - 1),
+                      "d_s": abs(m["fp32"]["s"] - m["fp64"]["s"])})
+    return {"n": n, "xi": xi, "stencil": stencil, "seeds": list(seeds), "steps": steps, "table": table,
+            "runs": {p_: {str(k): v for k, v in d.items()} for p_, d in per.items()}}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--cube", type=int, default=384, help="3D lattice side (0: skip the 3D runs)")
@@ -52,7 +92,32 @@ def main(argv=None) -> int:
     ap.add_argument("--quick", action="store_true", help="a tenth of every run length")
     ap.add_argument("--reports", type=int, default=10)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--precision", action="store_true",
+                    help="instead: FP32 against FP64 over 8 seeds at square^2, 50k steps (isotropic stencils "
+                         "at xi = 1e-3 and 0.1, compact at xi = 1e-3)")
     args = ap.parse_args(argv)
+    if args.precision:
+        import torch
+
+        torch.cuda.init()
+        div = 10 if args.quick else 1
+        out = [precision_pair(args.square, xi, st, range(1, 9), 50_000 // div, args.reports)
+               for xi, st in ((1e-3, "isotropic"), (1e-1, "isotropic"), (1e-3, "compact"))]
+        for res in out:
+            print(f"\n{args.square}^2 {res['stencil']} xi = {res['xi']:g}, 8 seeds: seed means, FP32 against FP64")
+            print("| t | seeds | k_peak fp32 / fp64 | S_peak fp32 / fp64 | s fp32 / fp64 | dk | dS | ds |")
+            print("|---|---|---|---|---|---|---|---|")
+            for r in res["table"]:
+                a, b = r["fp32"], r["fp64"]
+                print(f"| {r['t']} | {r['seeds']} | {a['k_peak']:.4f} / {b['k_peak']:.4f} | "
+                      f"{a['s_peak']:.4g} / {b['s_peak']:.4g} | "
+                      f"{a['s']:+.3f} / {b['s']:+.3f} | {100 * r['d_k_peak']:.2f} % | {100 * r['d_s_peak']:.2f} % | "
+                      f"{r['d_s']:.3f} |")
+        if args.out:
+            with open(args.out, "w") as fh:
+                for r in out:
+                    fh.write(json.dumps(r) + "\n")
+        return 0
     import torch
 
     torch.cuda.init()

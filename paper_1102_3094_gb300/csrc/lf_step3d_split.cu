@@ -570,13 +570,13 @@ __global__ void __launch_bounds__(128) k_lb3d(Geom g, Phys<R> p, StepIO<R> io)
 // the in-plane neighbours come through L1.  phi(t+1) from the fluxes
 // g = phi u of the neighbours and lap(mu) (mu even, g_z odd across the
 // walls); the first temperature sub-step with the wall rule of the context.
-constexpr int kZC = 16;
+constexpr int kZC = 16;   // planes per segment of the phi passes unless the variant's param sets them
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
+__global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io, int zc)
 {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
+    const int za = blockIdx.z * zc, zb = min(za + zc, g.nz);
     if (x >= g.nx || y >= g.ny) return;
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
     const int64_t zs = (int64_t)ny * pitch;
@@ -676,14 +676,14 @@ __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io)
 constexpr int kIsoTW = 34, kIsoTA = kIsoTW * 10, kIsoNF = 5;   // tile + 1 (32 x 8 + halo); mu, T, g_x, g_y, g_z
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> io)
+__global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> io, int zc)
 {
     constexpr int TW = kIsoTW, TA = kIsoTA, NF = kIsoNF;
     extern __shared__ __align__(16) unsigned char smem_iso[];
     R (*sm)[NF][TA] = reinterpret_cast<R (*)[NF][TA]>(smem_iso);     // [4 slots][NF][TA]
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
-    const int za = blockIdx.z * kZC, zb = min(za + kZC, g.nz);
+    const int za = blockIdx.z * zc, zb = min(za + zc, g.nz);
     const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
     const int64_t zs = (int64_t)ny * pitch;
     const bool hyd = p.hydro != 0;
@@ -844,8 +844,8 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
     if (iso) {
         e = launch_force<R, 28, 12, true>(g, p, io, s);
     } else if constexpr (sizeof(R) == 4) {
-        // (param >> 16): 0 = two z-lanes in packed FP32x2, 1 / 2 = one lane on 60x4 / 28x12 tiles
-        const int sel = g.tune >> 16;
+        // (param >> 16) & 15: 0 = two z-lanes in packed FP32x2, 1 / 2 = one lane on 60x4 / 28x12 tiles
+        const int sel = (g.tune >> 16) & 15;
         e = sel == 1 ? launch_force<R, 60, 4>(g, p, io, s)
           : sel == 2 ? launch_force<R, 28, 12>(g, p, io, s)
                      : launch_force_x2<28, 12>(g, p, io, s);
@@ -858,14 +858,17 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
         k_lb3d<R><<<grid, 128, 0, s>>>(g, p, io);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kZC - 1) / kZC);
+    // planes per segment of the phi pass: (param >> 20) & 255, 0 = kZC
+    int zc = (g.tune >> 20) & 255;
+    if (zc <= 0) zc = kZC;
+    dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
     if (iso) {
         constexpr size_t bytes = sizeof(R) * 4 * kIsoNF * kIsoTA;
         static unsigned long long attr_done = 0;
         if ((e = raise_smem_limit(k_phi3d_iso<R>, (int)bytes, &attr_done)) != cudaSuccess) return e;
-        k_phi3d_iso<R><<<gc, 256, bytes, s>>>(g, p, io);
+        k_phi3d_iso<R><<<gc, 256, bytes, s>>>(g, p, io, zc);
     } else
-        k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io);
+        k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io, zc);
     return cudaGetLastError();
 }
 

@@ -16,8 +16,12 @@
 // descriptor start moved by dx pixels -- all 9 taps read the same three rows,
 // which are loaded once.  The rows two ahead are prefetched with cp.async.
 // The 9 weight taps stay in shared memory (K-major).  One thread issues the
-// MMAs of row y into one of two TMEM accumulators while all four warps run
-// the epilogue of row y - 1 from the other.
+// MMAs of row y into one of two TMEM accumulators while the warps run the
+// epilogue of row y - 1 from the other.  With 64 output channels the CTA has
+// 512 threads: a warp reads the TMEM lanes of its quarter (warp mod 4, 32
+// pixels) and a quarter of the channels (warp / 4), so sixteen warps share
+// the epilogue's memory latency (132 us against 157 us with four warps for
+// 64 -> 64 at 8 x 256^2); the 16-channel last layer keeps 128 threads.
 #include <cuda_bf16.h>
 
 #include "lf_internal.cuh"
@@ -58,15 +62,21 @@ struct ConvSmem {
     static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;   // two accumulators
 };
 
+template <int COUT>
+constexpr int conv_threads() { return COUT >= 64 ? 512 : 128; }
+
 __device__ __forceinline__ int64_t pix_off(int b, int y, int x, int NY, int NX)
 {
     return ((int64_t)b * (NY + 2) + (y + 1)) * (NX + 2) + (x + 1);   // padded pixel index
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128, 1) k_conv3x3(ConvArgs a, int rows_per_item)
+__global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a, int rows_per_item)
 {
     using S = ConvSmem<CIN, COUT>;
+    constexpr int NT = conv_threads<COUT>();
+    constexpr int PARTS = (NT / 128) < (COUT / 16) ? (NT / 128) : (COUT / 16);   // channel parts of the epilogue
+    constexpr int CPP = COUT / PARTS;                                            // channels per part
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT >= 16 && COUT <= 128, "MMA shape");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem + S::B_OFF;
@@ -88,7 +98,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3(ConvArgs a, int rows_per_ite
         tc::fence_mbar_init();
     }
     // all 9 weight taps into shared memory (K-major core-matrix layout)
-    for (int q = tid; q < 9 * COUT * (CIN / 8); q += 128) {
+    for (int q = tid; q < 9 * COUT * (CIN / 8); q += NT) {
         const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
         const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
         tc::cp_async16(sB + t * S::B_TAP + tc::kmajor_offset(n, 8 * j, CIN), a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
@@ -99,7 +109,9 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3(ConvArgs a, int rows_per_ite
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;   // the warp's TMEM lane quarter
+    const int part = warp >> 2;                                       // its share of the channels
+    const int pix = tid & 127;                                        // pixel of the tile = TMEM lane
     uint32_t ph[2] = {0u, 0u};
     bool ok = true;
 
@@ -108,7 +120,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3(ConvArgs a, int rows_per_ite
     auto load_row = [&](int b, int pr, int x0) {
         unsigned char* dst = sR + (pr % S::NSLOT) * S::ROW_BYTES;
         const __nv_bfloat16* src = a.in + (((int64_t)b * (NY + 2) + pr) * (NX + 2) + x0) * CIN;
-        for (int q = tid; q < S::RP * S::KC; q += 128) {
+        for (int q = tid; q < S::RP * S::KC; q += NT) {
             const int px = q / S::KC, j = q - px * S::KC;
             tc::cp_async16(dst + j * S::LBO_A + px * 16, src + (int64_t)px * CIN + 8 * j);
         }
@@ -132,12 +144,13 @@ __global__ void __launch_bounds__(128, 1) k_conv3x3(ConvArgs a, int rows_per_ite
 
     // epilogue of output row y (TMEM accumulator at column dcol): thread = pixel
     auto epilogue = [&](int b, int y, int x0, uint32_t dcol) {
-        const int x = x0 + tid;
+        if (part >= PARTS) return;
+        const int x = x0 + pix;
         const int64_t po = pix_off(b, y, x, NY, NX);
         const bool halo_hi = (x == 0), halo_lo = (x == NX - 1);   // copies into columns NX + 1 / 0
         const int64_t po_h = halo_hi ? pix_off(b, y, NX, NY, NX) : pix_off(b, y, -1, NY, NX);
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
+        for (int c0 = part * CPP; c0 < (part + 1) * CPP; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tmem + lane_base + dcol + (uint32_t)c0, v);
             if (a.bias)
@@ -262,7 +275,7 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
     if (rpi > a.NY) rpi = a.NY;
     const int nitems = cols * ((a.NY + rpi - 1) / rpi);
     const int blocks = nitems < 152 ? nitems : 152;
-    k_conv3x3<CIN, COUT><<<blocks, 128, S::BYTES, s>>>(a, rpi);
+    k_conv3x3<CIN, COUT><<<blocks, conv_threads<COUT>(), S::BYTES, s>>>(a, rpi);
     return cudaGetLastError();
 }
 

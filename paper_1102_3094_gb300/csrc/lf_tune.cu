@@ -60,16 +60,20 @@ std::vector<std::pair<int, int>> candidates(const lf_ctx* c)
         v.push_back({LF_VARIANT_TILE, 0});
         return v;
     }
-    // 3D: the three-pass step with its force-pass shapes and segment heights,
-    // then the fused plane march
+    // 3D: the three-pass step with its force-pass shapes and segment heights
+    // and the phi pass's segment heights, then the fused plane march
     const int planes[] = {0, 8, 16, 32, 64};
-    if (iso || c->prec == LF_FP64) {
-        for (int h : planes)
-            if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, h});
-    } else {
-        for (int sel = 0; sel < 3; ++sel)            // packed two-lane 28x12, one lane 60x4, one lane 28x12
+    const int phis[] = {0, 32, 64};
+    for (int zc : phis) {
+        if (zc > g.nz) continue;
+        if (iso || c->prec == LF_FP64) {
             for (int h : planes)
-                if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, (sel << 16) | h});
+                if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, (zc << 20) | h});
+        } else {
+            for (int sel = 0; sel < 3; ++sel)        // packed two-lane 28x12, one lane 60x4, one lane 28x12
+                for (int h : planes)
+                    if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, (zc << 20) | (sel << 16) | h});
+        }
     }
     v.push_back({LF_VARIANT_MARCH, 0});
     return v;

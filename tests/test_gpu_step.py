@@ -175,7 +175,8 @@ CASES3 = [
 
 
 VARIANTS3 = {"fused": ("march", 0), "split3": ("split3", 0), "split3-z3": ("split3", 3),
-             "split3-60x4": ("split3", 1 << 16), "split3-scalar-z5": ("split3", (2 << 16) | 5)}
+             "split3-60x4": ("split3", 1 << 16), "split3-scalar-z5": ("split3", (2 << 16) | 5),
+             "split3-phi1": ("split3", 1 << 20), "split3-phi7-z5": ("split3", (7 << 20) | 5)}
 
 
 @pytest.mark.parametrize("variant", list(VARIANTS3))
@@ -187,7 +188,7 @@ def test_aux_and_step_parity_3d(case, prec, variant):
     _check_aux_and_step_3d(sim, st, prec)
 
 
-@pytest.mark.parametrize("variant", ["split3", "split3-z3", "fused"])
+@pytest.mark.parametrize("variant", ["split3", "split3-z3", "split3-phi1", "fused"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
 def test_isotropic_stencil_parity_3d(case, prec, variant):
