@@ -142,20 +142,41 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a,
         }
     };
 
+    // the thread's 16 channels of the bias, for the whole launch
+    static_assert(CPP == 16, "one 16-channel group per thread in the epilogue");
+    float bz[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) bz[i] = (a.bias && part < PARTS) ? a.bias[part * CPP + i] : 0.f;
+    // residual and mask inputs of the thread's pixel in row y, loaded before the
+    // wait for the row's MMAs so that their latency overlaps it
+    auto preload = [&](int b, int y, int x0, uint4* rp, uint4* mp) {
+        if (part >= PARTS) return;
+        const int64_t po = pix_off(b, y, x0 + pix, NY, NX);
+        if (a.resid) {
+            const uint4* rs = reinterpret_cast<const uint4*>(a.resid + po * COUT + part * CPP);
+            rp[0] = rs[0];
+            rp[1] = rs[1];
+        }
+        if (a.mask) {
+            const uint4* ms = reinterpret_cast<const uint4*>(a.mask + po * COUT + part * CPP);
+            mp[0] = ms[0];
+            mp[1] = ms[1];
+        }
+    };
+
     // epilogue of output row y (TMEM accumulator at column dcol): thread = pixel
-    auto epilogue = [&](int b, int y, int x0, uint32_t dcol) {
+    auto epilogue = [&](int b, int y, int x0, uint32_t dcol, const uint4* rp, const uint4* mp) {
         if (part >= PARTS) return;
         const int x = x0 + pix;
         const int64_t po = pix_off(b, y, x, NY, NX);
         const bool halo_hi = (x == 0), halo_lo = (x == NX - 1);   // copies into columns NX + 1 / 0
         const int64_t po_h = halo_hi ? pix_off(b, y, NX, NY, NX) : pix_off(b, y, -1, NY, NX);
-#pragma unroll
-        for (int c0 = part * CPP; c0 < (part + 1) * CPP; c0 += 16) {
+        {
+            const int c0 = part * CPP;
             float v[16];
             tc::tmem_ld16(tmem + lane_base + dcol + (uint32_t)c0, v);
-            if (a.bias)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += a.bias[c0 + i];
+            for (int i = 0; i < 16; ++i) v[i] += bz[i];
             if (a.y4 && c0 == 0) {
                 const int64_t q = (((int64_t)b * NY + y) * NX + x) * 4;
 #pragma unroll
@@ -170,9 +191,8 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a,
                 for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
             if (a.resid) {
                 __align__(16) __nv_bfloat16 r[16];
-                const uint4* rs = reinterpret_cast<const uint4*>(a.resid + po * COUT + c0);
-                reinterpret_cast<uint4*>(r)[0] = rs[0];
-                reinterpret_cast<uint4*>(r)[1] = rs[1];
+                reinterpret_cast<uint4*>(r)[0] = rp[0];
+                reinterpret_cast<uint4*>(r)[1] = rp[1];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] += __bfloat162float(r[i]);
             }
@@ -180,9 +200,8 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a,
             for (int i = 0; i < 16; ++i) ho[i] = __float2bfloat16_rn(v[i]);
             if (a.mask) {
                 __align__(16) __nv_bfloat16 m[16];
-                const uint4* ms = reinterpret_cast<const uint4*>(a.mask + po * COUT + c0);
-                reinterpret_cast<uint4*>(m)[0] = ms[0];
-                reinterpret_cast<uint4*>(m)[1] = ms[1];
+                reinterpret_cast<uint4*>(m)[0] = mp[0];
+                reinterpret_cast<uint4*>(m)[1] = mp[1];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) hm[i] = __bfloat162float(m[i]) > 0.f ? ho[i] : __float2bfloat16_rn(0.f);
             }
@@ -229,6 +248,8 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a,
                 issue_row(y, dcur);
                 tc::mma_commit(&bar[y & 1]);
             }
+            uint4 rp[2] = {}, mp[2] = {};
+            if (y > ya) preload(b, y - 1, x0, rp, mp);
             if (y > ya) {   // MMAs of row y - 1 done: its ring slot and accumulator are free to use
                 const bool w = tc::mbar_wait(&bar[(y - 1) & 1], ph[(y - 1) & 1]);
                 ph[(y - 1) & 1] ^= 1;
@@ -238,16 +259,18 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a,
             // prefetch padded row y + 4 into the slot of padded row y - 1
             if (y + 4 <= yb + 1) load_row(b, y + 4, x0);
             commit();
-            if (y > ya) epilogue(b, y - 1, x0, dprev);
+            if (y > ya) epilogue(b, y - 1, x0, dprev, rp, mp);
         }
         if (!ok) break;
         {   // last row of the item
             const int y = yb - 1;
+            uint4 rp[2] = {}, mp[2] = {};
+            preload(b, y, x0, rp, mp);
             const bool w = tc::mbar_wait(&bar[y & 1], ph[y & 1]);
             ph[y & 1] ^= 1;
             if (__syncthreads_or(!w)) { ok = false; break; }
             tc::fence_after_sync();
-            epilogue(b, y, x0, (uint32_t)((y & 1) * COUT));
+            epilogue(b, y, x0, (uint32_t)((y & 1) * COUT), rp, mp);
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         tc::fence_before_sync();
