@@ -823,8 +823,8 @@ def main():
                     help="ens96: retire non-finite runs every this many steps (0 = never)")
     ap.add_argument("--sur-runs", type=int, default=512, help="solver trajectories (every 8th held out)")
     ap.add_argument("--sur-windows", type=int, default=40, help="K-step windows per trajectory after the warm-up")
-    ap.add_argument("--sur-iters", type=int, default=16000)
-    ap.add_argument("--sur-batch", type=int, default=8)
+    ap.add_argument("--sur-iters", type=int, default=40000)
+    ap.add_argument("--sur-batch", type=int, default=16)
     ap.add_argument("--sur-lr", type=float, default=1e-3)
     ap.add_argument("--sur-curve", default="", help="comma-separated fractions below 1 of the training pairs "
                     "for a learning curve (one network each, as many steps as the main network)")
