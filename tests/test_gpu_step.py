@@ -278,11 +278,15 @@ def test_multistep_fp64_small64():
     sim.close()
 
 
-def test_full_size_one_step_fp32():
+@pytest.mark.parametrize("tuned", [False, True])
+def test_full_size_one_step_fp32(tuned):
     """The 1024 x 1024 FP32 workload, in the launch configuration the benchmark
-    times: one step from the seeded state, every site against the oracle."""
+    times (the autotuner's choice, as the benchmark takes it, and the library's
+    default): one step from the seeded state, every site against the oracle."""
     kw = synth.WORKLOADS["prec1024"]
     sim = lf.Lattice(nx=1024, ny=1024, precision="fp32", xi=kw["xi"])
+    if tuned:
+        sim.tune(reps=5)
     cfg = O.make_cfg(nx=1024, ny=1024, xi=kw["xi"])
     sim.step(3)            # leave the trivial initial populations
     st = O.State(cfg, to_oracle_f(sim.get("pop"), 2), sim.get("phi"), sim.get("T"))
@@ -333,16 +337,35 @@ def _sampled_window_parity(sim, d, okw, centres, half=8):
             assert relerr(got[sel], want[sel]) < 2e-6, (c, name, relerr(got[sel], want[sel]))
 
 
-def test_cube384_sampled_windows_fp32():
+@pytest.mark.parametrize("tuned", [False, True])
+def test_cube384_sampled_windows_fp32(tuned):
     """The 384^3 FP32 workload in the launch configuration the benchmark times
-    (the three-pass step, seed 1): one step, checked on six 8 x 8 columns of all
-    384 planes against the oracle on 16 x 16 x 384 windows."""
+    (the three-pass step with the autotuner's shape, as the benchmark takes it,
+    and with the library's default shape; seed 1): one step, checked on six
+    8 x 8 columns of all 384 planes against the oracle on 16 x 16 x 384 windows."""
     kw = synth.WORKLOADS["cube384"]
     sim = lf.Lattice(d=3, nx=384, ny=384, nz=384, precision="fp32", xi=kw["xi"], tau=kw["tau"], seed=1)
+    if tuned:
+        sim.tune(reps=3)
     sim.step(3)            # leave the trivial initial populations
     rng = np.random.default_rng(21)
     centres = [tuple(int(v) for v in rng.integers(0, 384, 2)) for _ in range(5)] + [(0, 383)]
     _sampled_window_parity(sim, 3, dict(xi=kw["xi"], tau=kw["tau"]), centres)
+    sim.close()
+
+
+def test_cube384_isotropic_tau3_sampled_windows_fp32():
+    """The configuration the benchmark times beside its main line (384^3, tau = 3,
+    isotropic 19-point stencils, the autotuner's shape): one step, checked on six
+    8 x 8 columns of all 384 planes against the oracle on 16 x 16 x 384 windows."""
+    kw = synth.WORKLOADS["cube384"]
+    sim = lf.Lattice(d=3, nx=384, ny=384, nz=384, precision="fp32", xi=kw["xi"], tau=3.0, seed=1,
+                     stencil="isotropic")
+    sim.tune(reps=3)
+    sim.step(3)            # leave the trivial initial populations
+    rng = np.random.default_rng(23)
+    centres = [tuple(int(v) for v in rng.integers(0, 384, 2)) for _ in range(5)] + [(383, 0)]
+    _sampled_window_parity(sim, 3, dict(xi=kw["xi"], tau=3.0, stencil=1), centres)
     sim.close()
 
 
