@@ -302,6 +302,178 @@ __global__ void __launch_bounds__(Force3<R, TX, TY, ISO>::NTH) k_force3d(Geom g,
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
+// Pass A with the isotropic stencils as a column march with sliding sums.
+// Every 19-point operator is split by plane (Plane19 in lf_iso3.cuh): each
+// thread loads the in-plane neighbours of one new plane of phi, psi and P per
+// iteration and keeps the partial sums of the centres still open in
+// registers, so shared memory holds one plane of each field (two with the
+// plane in flight) and each neighbour is loaded once per column rather than
+// once per operator and centre.  Iteration k, after one barrier:
+//   phi plane k (prefetched in iteration k - 1)   -> psi, grad phi at k - 1   (every column, r = 2)
+//   psi plane k - 2 (stored in iteration k - 1)   -> lam, grad psi at k - 3, then mu and P at k - 3 (r = 1)
+//   P plane k - 4 (stored in iteration k - 1)     -> F at k - 5 (the tile)
+// Each stage reads only planes written before the barrier and writes the slot
+// its readers left in the previous iteration, so one barrier per plane
+// orders everything; the march runs z1 - z0 + 8 iterations.
+template <typename R, int TX, int TY>
+struct Force3Iso {
+    static constexpr int CW = TX + 4, CH = TY + 4, NTH = CW * CH;   // threads = columns of the psi region
+    static constexpr int W3 = TX + 6, H3 = TY + 6, A3 = W3 * H3;    // phi (r = 3)
+    static constexpr int A2 = CW * CH;                              // psi, P (r = 2 / r = 1, psi-region indexing)
+    static constexpr int PHI = 0;                                   // [2][A3]
+    static constexpr int PSI = PHI + 2 * A3;                        // [2][A2]
+    static constexpr int PP = PSI + 2 * A2;                         // [2][xx, xy, yy, xz, yz, zz][A2]
+    static constexpr int TOTAL = PP + 12 * A2;
+    static constexpr size_t MAPS = sizeof(R) * TOTAL;
+    static constexpr size_t BYTES = MAPS + sizeof(int) * (W3 + H3);
+};
+
+template <typename R, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso(Geom g, Phys<R> p, StepIO<R> io, int Hz)
+{
+    using P3 = Force3Iso<R, TX, TY>;
+    constexpr int W3 = P3::W3, CW = P3::CW, A3 = P3::A3, A2 = P3::A2, NTH = P3::NTH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    R* sphi = sm + P3::PHI;
+    R* spsi = sm + P3::PSI;
+    R* sP = sm + P3::PP;
+    int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);   // x0 - 3 + i -> storage column
+    int* rowmap = colmap + W3;                                   // y0 - 3 + j -> storage row
+
+    const int t = threadIdx.x;
+    const int cx = t % CW, cy = t / CW;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * Hz, z1 = min(z0 + Hz, nz);
+    const int kbeg = z0 - 3, kphi = z1 + 2, kend = z1 + 4;   // phi planes kbeg .. kphi
+    const R half = R(0.5);
+    const bool in1 = cx >= 1 && cx < CW - 1 && cy >= 1 && cy < P3::CH - 1;
+    const bool in0 = cx >= 2 && cx < CW - 2 && cy >= 2 && cy < P3::CH - 2;
+    const int gx = x0 - 2 + cx, gy = y0 - 2 + cy;
+    const bool own = in0 && gx < nx && gy < ny;
+    const bool hyd = p.hydro != 0;
+    bool bad = false;
+
+    for (int q = t; q < W3 + P3::H3; q += NTH) {
+        if (q < W3) colmap[q] = wrap_s(x0 - 3 + q, nx);
+        else rowmap[q - W3] = wrap_s(y0 - 3 + (q - W3), ny);
+    }
+    __syncthreads();
+    const int col_off = rowmap[cy + 1] * pitch + colmap[cx + 1];
+    const int c3 = (cy + 1) * W3 + cx + 1;
+    const int c2 = t;
+    static_assert(A3 <= 2 * NTH, "at most two phi elements per thread");
+    const int qe = t + NTH;
+    const bool two = qe < A3;
+    const int oe0 = rowmap[t / W3] * pitch + colmap[t % W3];
+    const int oe1 = two ? rowmap[qe / W3] * pitch + colmap[qe % W3] : 0;
+
+    auto fetch = [&](int z) {
+        if (z <= kphi) {
+            const int pz = map_z(z, nz, walls) * zs;
+            R* d = sphi + ((z - kbeg) & 1) * A3;
+            cp_async_s<sizeof(R)>(&d[t], io.phi_in + (pz + oe0));
+            if (two) cp_async_s<sizeof(R)>(&d[qe], io.phi_in + (pz + oe1));
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    Slide19<R> sphi19, spsi19;
+    R ph1 = 0, ph2 = 0, ph3 = 0;                     // own phi(k-1), phi(k-2), phi(k-3)
+    R ps1 = 0, ps2 = 0;                              // own psi(k-2), psi(k-3)
+    R dx1 = 0, dy1 = 0, dz1 = 0, dx2 = 0, dy2 = 0, dz2 = 0;   // grad phi(k-2), grad phi(k-3)
+    R oxz = 0, oyz = 0, ozz = 0;                     // own P_xz, P_yz, P_zz of plane k-4
+    R aFx = 0, aFy = 0, aFz = 0, bFx = 0, bFy = 0, bFz = 0;   // -12 F: open sums of centre k-5, parts of plane k-5 for k-4
+
+    fetch(kbeg);
+    for (int k = kbeg; k <= kend; ++k) {
+        const int z2 = k - 3;                            // mu / P plane of this iteration
+        const bool st2 = in1 && k >= z0 && k <= z1 + 3;
+        R Tc = R(0);
+        if (st2 && z2 >= z0 - 1) Tc = io.T_in[map_z(z2, nz, walls) * zs + col_off];
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        fetch(k + 1);
+
+        // ---- phi plane k: psi and grad phi at k - 1 (every column) ------------------
+        R phk = R(0), psk = R(0), dxk = R(0), dyk = R(0), dzk = R(0);
+        if (k <= kphi) {
+            const R* a = sphi + ((k - kbeg) & 1) * A3;
+            phk = a[c3];
+            sphi19.push(plane19<R, W3>(a, c3, phk), psk, dxk, dyk, dzk);
+            spsi[((k - 1 - kbeg) & 1) * A2 + c2] = psk;
+        }
+
+        // ---- psi plane k - 2: lam, grad psi, mu, P at k - 3 (r = 1) --------------------
+        R nxz = R(0), nyz = R(0), nzz = R(0);
+        if (st2) {
+            const R* b = spsi + ((k - 2 - kbeg) & 1) * A2;
+            R lam, s0, s1, s2;
+            spsi19.push(plane19<R, CW>(b, c2, ps1), lam, s0, s1, s2);
+            if (z2 >= z0 - 1) {
+                const R ph = ph3, psi = ps2;
+                const R av = (Tc - p.Tc) * p.inv_Tc;
+                if (own && z2 >= z0 && z2 < z1) {
+                    const R mu = av * ph + p.b * ph * ph * ph - p.kappa * psi + p.c * lam;
+                    bad |= !isfinite(mu);
+                    io.mu[z2 * zs + gy * pitch + gx] = mu;
+                }
+                if (hyd) {
+                    const R d0 = dx2, d1 = dy2, d2 = dz2;
+                    const R ph2_ = ph * ph;
+                    const R iso = av * ph2_ * half + R(0.75) * p.b * ph2_ * ph2_
+                                - p.kappa * (ph * psi + half * (d0 * d0 + d1 * d1 + d2 * d2))
+                                + p.c * (ph * lam + half * psi * psi + d0 * s0 + d1 * s1 + d2 * s2);
+                    R* P = sP + ((z2 - kbeg) & 1) * 6 * A2;
+                    nxz = p.kappa * d0 * d2 - p.c * (d0 * s2 + d2 * s0);
+                    nyz = p.kappa * d1 * d2 - p.c * (d1 * s2 + d2 * s1);
+                    nzz = iso + p.kappa * d2 * d2 - R(2) * p.c * d2 * s2;
+                    P[0 * A2 + c2] = iso + p.kappa * d0 * d0 - R(2) * p.c * d0 * s0;
+                    P[1 * A2 + c2] = p.kappa * d0 * d1 - p.c * (d0 * s1 + d1 * s0);
+                    P[2 * A2 + c2] = iso + p.kappa * d1 * d1 - R(2) * p.c * d1 * s1;
+                    P[3 * A2 + c2] = nxz;
+                    P[4 * A2 + c2] = nyz;
+                    P[5 * A2 + c2] = nzz;
+                }
+            }
+        }
+
+        // ---- P plane k - 4: F at k - 5 (the tile) --------------------------------------
+        if (hyd && in0 && k >= z0 + 3) {
+            const R* P = sP + ((k - 4 - kbeg) & 1) * 6 * A2;
+            const Plane19<R> xx = plane19<R, CW>(P + 0 * A2, c2, R(0));
+            const Plane19<R> xy = plane19<R, CW>(P + 1 * A2, c2, R(0));
+            const Plane19<R> yy = plane19<R, CW>(P + 2 * A2, c2, R(0));
+            const Plane19<R> xz = plane19<R, CW>(P + 3 * A2, c2, oxz);
+            const Plane19<R> yz = plane19<R, CW>(P + 4 * A2, c2, oyz);
+            const R zc = (P[5 * A2 + c2 + 1] + P[5 * A2 + c2 - 1]) + (P[5 * A2 + c2 + CW] + P[5 * A2 + c2 - CW]);
+            const R szz = R(2) * ozz + zc;
+            // -12 F(m) = O(m) + [A(m - 1) - s(m - 1)] + [A(m + 1) + s(m + 1)], per component
+            const R Ox = xx.gx + xy.gy, Ax = xx.ax + xy.ay;
+            const R Oy = xy.gx + yy.gy, Ay = xy.ax + yy.ay;
+            const R Oz = xz.gx + yz.gy, Az = xz.ax + yz.ay;
+            if (own && k >= z0 + 5) {
+                const int site = (k - 5) * zs + gy * pitch + gx;
+                io.F[0][site] = -(aFx + (Ax + xz.s)) * R(1.0 / 12.0);
+                io.F[1][site] = -(aFy + (Ay + yz.s)) * R(1.0 / 12.0);
+                io.F[2][site] = -(aFz + (Az + szz)) * R(1.0 / 12.0);
+            }
+            aFx = Ox + bFx; aFy = Oy + bFy; aFz = Oz + bFz;
+            bFx = Ax - xz.s; bFy = Ay - yz.s; bFz = Az - szz;
+        }
+
+        // shift the windows
+        ph3 = ph2; ph2 = ph1; ph1 = phk;
+        ps2 = ps1; ps1 = psk;
+        dx2 = dx1; dy2 = dy1; dz2 = dz1; dx1 = dxk; dy1 = dyk; dz1 = dzk;
+        oxz = nxz; oyz = nyz; ozz = nzz;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
 // Pass A on two z-segments at once (FP32): lane .x marches planes
 // [z0, z0 + H), lane .y planes [z0 + H, z0 + 2H) (shorter or empty at the top
 // of the lattice), both with the same lags, and all arithmetic runs on packed
@@ -791,6 +963,122 @@ __global__ void __launch_bounds__(256) k_phi3d_iso(Geom g, Phys<R> p, StepIO<R> 
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
+// Pass C with the isotropic stencils as a column march with sliding sums
+// (Plane19 in lf_iso3.cuh).  A 32 x 8 block stages one plane of mu, T and the
+// fluxes g = phi u on the tile grown by one site in a two-slot shared ring;
+// each thread loads the in-plane neighbours of the new plane k once, keeps the
+// open sums of its column in registers and completes phi(t+1) and the first
+// temperature sub-step at k - 1.  Plane k + 1 is loaded into registers before
+// the arithmetic of plane k and stored into the slot of plane k - 1 after it,
+// so one barrier per plane orders the ring.  A plane beyond a wall holds the
+// wall plane, and its parts enter the sums transformed: mu, g_x and g_y even
+// (unchanged), g_z odd (s negated), T the halfway ghost 2 T_w - T (s -> 12 T_w - s).
+template <typename R>
+__global__ void __launch_bounds__(256) k_phi3d_isoz(Geom g, Phys<R> p, StepIO<R> io, int zc)
+{
+    constexpr int TW = kIsoTW, TA = kIsoTA, NF = kIsoNF;
+    extern __shared__ __align__(16) unsigned char smem_iso[];
+    R (*sm)[NF][TA] = reinterpret_cast<R (*)[NF][TA]>(smem_iso);     // [2 slots][NF][TA]
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const int za = blockIdx.z * zc, zb = min(za + zc, g.nz);
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
+    const int64_t zs = (int64_t)ny * pitch;
+    const bool hyd = p.hydro != 0;
+    const bool halfway = walls && g.t_mode == LF_TWALL_HALFWAY;
+    const R* __restrict__ mu = io.mu;
+    const R* __restrict__ ph = io.phi_in;
+    const R* __restrict__ T = io.T_in;
+    const R* __restrict__ ux = io.u[0];
+    const R* __restrict__ uy = io.u[1];
+    const R* __restrict__ uz = io.u[2];
+    auto zmap = [&](int zl) -> int64_t {
+        int z = zl;
+        if (walls) z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
+        else z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        return (int64_t)z * zs;
+    };
+    int64_t off[2];
+    bool has[2];
+    for (int i = 0; i < 2; ++i) {
+        const int q = t + 256 * i;
+        has[i] = q < TA;
+        const int ly = has[i] ? q / TW : 0, lx = has[i] ? q - ly * TW : 0;
+        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        off[i] = (int64_t)gy * pitch + gx;
+    }
+    R v[2][NF];
+    auto fetch = [&](int zl) {
+        const int64_t pz = zmap(zl);
+        for (int i = 0; i < 2; ++i) {
+            if (!has[i]) continue;
+            const int64_t o = pz + off[i];
+            v[i][0] = mu[o];
+            v[i][1] = T[o];
+            const R f = ph[o];
+            v[i][2] = hyd ? f * ux[o] : R(0);
+            v[i][3] = hyd ? f * uy[o] : R(0);
+            v[i][4] = hyd ? f * uz[o] : R(0);
+        }
+    };
+    auto put = [&](int zl) {
+        const int sl = (zl - za + 1) & 1;
+        for (int i = 0; i < 2; ++i)
+            if (has[i])
+                for (int f = 0; f < NF; ++f) sm[sl][f][t + 256 * i] = v[i][f];
+    };
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const int c = (ty + 1) * TW + tx + 1;
+    const int64_t col = (int64_t)y * pitch + x;
+    Slide19<R> smu, sT, sgx, sgy, sgz;
+    R Tc1 = R(0);                                           // own T of plane k - 1
+    bool bad = false;
+    fetch(za - 1);
+    put(za - 1);
+    for (int k = za - 1; k <= zb; ++k) {
+        __syncthreads();                                    // plane k is in its slot
+        if (k < zb) fetch(k + 1);                           // in flight during the arithmetic below
+        const int s0 = (k - za + 1) & 1;
+        const bool ghost = walls && (k < 0 || k >= nz);
+        const R Tck = sm[s0][1][c];
+        Plane19<R> qm = plane19<R, TW>(sm[s0][0], c, sm[s0][0][c]);
+        Plane19<R> qT = plane19<R, TW>(sm[s0][1], c, Tck);
+        Plane19<R> qx = plane19<R, TW>(sm[s0][2], c, R(0));
+        Plane19<R> qy = plane19<R, TW>(sm[s0][3], c, R(0));
+        Plane19<R> qz = plane19<R, TW>(sm[s0][4], c, sm[s0][4][c]);
+        if (ghost) {
+            qz.s = -qz.s;
+            if (halfway) qT.s = R(12) * p.T_w - qT.s;
+        }
+        R lapmu, lapT, dgx, dgy, dgz, u0, u1, u2;
+        smu.push(qm, lapmu, u0, u1, u2);
+        sT.push(qT, lapT, u0, u1, u2);
+        sgx.push(qx, u0, dgx, u1, u2);
+        sgy.push(qy, u0, u1, dgy, u2);
+        sgz.push(qz, u0, u1, u2, dgz);
+        const int m = k - 1;                                // the plane completed by plane k
+        if (act && k > za) {
+            const int64_t site = (int64_t)m * zs + col;
+            const R div = hyd ? (dgx + dgy) + dgz : R(0);
+            const R phn = ph[site] - div + p.Gamma * lapmu;
+            io.phi_out[site] = phn;
+            R Tn = Tc1;
+            if (p.t_update) {
+                if (walls && g.t_mode == LF_TWALL_LAYERS && (m == 0 || m == nz - 1)) Tn = p.T_w;
+                else Tn = Tc1 + p.dxi * lapT;
+            }
+            io.T_out[site] = Tn;
+            bad |= !isfinite(phn) || !isfinite(Tn);
+        }
+        Tc1 = Tck;
+        if (k < zb) put(k + 1);                             // slot of plane k - 1, read by nobody now
+    }
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
 template <typename R, int TX, int TY, bool ISO = false>
 cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
@@ -803,6 +1091,27 @@ cudaError_t launch_force(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
     int Hz = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;
     if (Hz <= 0) {   // about eight waves of two CTAs per SM, segments of at least 16 planes
         const int want = (8 * 2 * 152 + tiles - 1) / tiles;
+        Hz = (g.nz + want - 1) / want;
+        if (Hz < 16) Hz = 16;
+    }
+    if (Hz > g.nz) Hz = g.nz;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + Hz - 1) / Hz);
+    kern<<<grid, P3::NTH, P3::BYTES, s>>>(g, p, io, Hz);
+    return cudaGetLastError();
+}
+
+template <typename R, int TX, int TY, int MINB>
+cudaError_t launch_force_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
+{
+    using P3 = Force3Iso<R, TX, TY>;
+    auto kern = k_force3d_iso<R, TX, TY, MINB>;
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    const cudaError_t e = raise_smem_limit(kern, (int)P3::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    int Hz = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;
+    if (Hz <= 0) {   // about eight waves of the resident CTAs, segments of at least 16 planes
+        const int want = (8 * MINB * 152 + tiles - 1) / tiles;
         Hz = (g.nz + want - 1) / want;
         if (Hz < 16) Hz = 16;
     }
@@ -842,7 +1151,19 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
     cudaError_t e;
     const bool iso = g.stencil == LF_STENCIL_ISOTROPIC;
     if (iso) {
-        e = launch_force<R, 28, 12, true>(g, p, io, s);
+        // (param >> 16) & 15: 0 = sliding sums on 28x12 tiles (FP32: two CTAs per SM),
+        // 1 = on 28x28 tiles, 3 = on 28x12 tiles at one CTA per SM (FP32 only; FP64
+        // takes 0), 2 = the three-plane form (each operator from its own shared loads)
+        const int sel = (g.tune >> 16) & 15;
+        if (sel == 2) {
+            e = launch_force<R, 28, 12, true>(g, p, io, s);
+        } else if constexpr (sizeof(R) == 4) {
+            e = sel == 1 ? launch_force_iso<R, 28, 28, 1>(g, p, io, s)
+              : sel == 3 ? launch_force_iso<R, 28, 12, 1>(g, p, io, s)
+                         : launch_force_iso<R, 28, 12, 2>(g, p, io, s);
+        } else {
+            e = launch_force_iso<R, 28, 12, 1>(g, p, io, s);
+        }
     } else if constexpr (sizeof(R) == 4) {
         // (param >> 16) & 15: 0 = two z-lanes in packed FP32x2, 1 / 2 = one lane on 60x4 / 28x12 tiles
         const int sel = (g.tune >> 16) & 15;
@@ -862,11 +1183,16 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
     int zc = (g.tune >> 20) & 255;
     if (zc <= 0) zc = kZC;
     dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
-    if (iso) {
+    if (iso && (g.tune >> 28) & 1) {                      // param bit 28: the three-plane phi pass
         constexpr size_t bytes = sizeof(R) * 4 * kIsoNF * kIsoTA;
         static unsigned long long attr_done = 0;
         if ((e = raise_smem_limit(k_phi3d_iso<R>, (int)bytes, &attr_done)) != cudaSuccess) return e;
         k_phi3d_iso<R><<<gc, 256, bytes, s>>>(g, p, io, zc);
+    } else if (iso) {
+        constexpr size_t bytes = sizeof(R) * 2 * kIsoNF * kIsoTA;
+        static unsigned long long attr_done = 0;
+        if ((e = raise_smem_limit(k_phi3d_isoz<R>, (int)bytes, &attr_done)) != cudaSuccess) return e;
+        k_phi3d_isoz<R><<<gc, 256, bytes, s>>>(g, p, io, zc);
     } else
         k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io, zc);
     return cudaGetLastError();

@@ -188,14 +188,24 @@ def test_aux_and_step_parity_3d(case, prec, variant):
     _check_aux_and_step_3d(sim, st, prec)
 
 
-@pytest.mark.parametrize("variant", ["split3", "split3-z3", "split3-phi1", "fused"])
+# force-pass forms of the isotropic three-pass step ((param >> 16) & 15)
+VARIANTS3_ISO = {"split3": ("split3", 0), "split3-z3": ("split3", 3), "split3-phi1": ("split3", 1 << 20),
+                 "split3-28x28": ("split3", 1 << 16), "split3-28x28-z5": ("split3", (1 << 16) | 5),
+                 "split3-3plane": ("split3", 2 << 16), "split3-1cta-z5": ("split3", (3 << 16) | 5),
+                 "split3-phi3plane": ("split3", 1 << 28), "split3-phi5": ("split3", 5 << 20),
+                 "fused": ("march", 0)}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS3_ISO))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
 def test_isotropic_stencil_parity_3d(case, prec, variant):
-    """Isotropic 19-point stencils: the three-pass step (with segments of 3
-    planes as well) and the fused plane march."""
+    """Isotropic 19-point stencils: the three-pass step with each force-pass
+    form (sliding sums on 28x12 and 28x28 tiles, the three-plane form; segments
+    of 3 and 5 planes as well), both phi-pass forms (sliding sums with segments
+    of 16, 5 and 1 planes; the three-plane form) and the fused plane march."""
     sim, cfg, st = make_pair(case, prec, stencil="isotropic")
-    sim.set_variant(*VARIANTS3[variant])
+    sim.set_variant(*VARIANTS3_ISO[variant])
     _check_aux_and_step_3d(sim, st, prec)
 
 
