@@ -26,6 +26,8 @@
 #include "lf_march2d_x2.cuh"      // packed FP32x2 helpers
 #include "lf_iso3.cuh"
 
+#include <type_traits>
+
 namespace lf {
 
 namespace {
@@ -349,8 +351,8 @@ __global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso
     const int z0 = blockIdx.z * Hz, z1 = min(z0 + Hz, nz);
     const int kbeg = z0 - 3, kphi = z1 + 2, kend = z1 + 4;   // phi planes kbeg .. kphi
     const R half = R(0.5);
-    const bool in1 = cx >= 1 && cx < CW - 1 && cy >= 1 && cy < P3::CH - 1;
     const bool in0 = cx >= 2 && cx < CW - 2 && cy >= 2 && cy < P3::CH - 2;
+    const bool row1 = cy >= 1 && cy < P3::CH - 1, row0 = cy >= 2 && cy < P3::CH - 2;
     const int gx = x0 - 2 + cx, gy = y0 - 2 + cy;
     const bool own = in0 && gx < nx && gy < ny;
     const bool hyd = p.hydro != 0;
@@ -370,10 +372,10 @@ __global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso
     const int oe0 = rowmap[t / W3] * pitch + colmap[t % W3];
     const int oe1 = two ? rowmap[qe / W3] * pitch + colmap[qe % W3] : 0;
 
-    auto fetch = [&](int z) {
+    auto fetch = [&](int z, int slot) {
         if (z <= kphi) {
             const int pz = map_z(z, nz, walls) * zs;
-            R* d = sphi + ((z - kbeg) & 1) * A3;
+            R* d = sphi + slot * A3;
             cp_async_s<sizeof(R)>(&d[t], io.phi_in + (pz + oe0));
             if (two) cp_async_s<sizeof(R)>(&d[qe], io.phi_in + (pz + oe1));
         }
@@ -387,29 +389,34 @@ __global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso
     R oxz = 0, oyz = 0, ozz = 0;                     // own P_xz, P_yz, P_zz of plane k-4
     R aFx = 0, aFy = 0, aFz = 0, bFx = 0, bFy = 0, bFz = 0;   // -12 F: open sums of centre k-5, parts of plane k-5 for k-4
 
-    fetch(kbeg);
-    for (int k = kbeg; k <= kend; ++k) {
+    // iteration k; PAR = (k - kbeg) & 1 selects the ring slots.  The stage
+    // predicates depend on the row of the column only (a warp is one row of
+    // the psi region): the halo lanes of a row run the stage too, on
+    // neighbours that stay inside the shared allocation, and neither their
+    // mu nor their F is stored (their P lands in columns nobody reads).
+    auto iter = [&](int k, auto par_c) {
+        constexpr int PAR = decltype(par_c)::value;
         const int z2 = k - 3;                            // mu / P plane of this iteration
-        const bool st2 = in1 && k >= z0 && k <= z1 + 3;
+        const bool st2 = row1 && k >= z0 && k <= z1 + 3;
         R Tc = R(0);
         if (st2 && z2 >= z0 - 1) Tc = io.T_in[map_z(z2, nz, walls) * zs + col_off];
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        fetch(k + 1);
+        fetch(k + 1, PAR ^ 1);
 
         // ---- phi plane k: psi and grad phi at k - 1 (every column) ------------------
         R phk = R(0), psk = R(0), dxk = R(0), dyk = R(0), dzk = R(0);
         if (k <= kphi) {
-            const R* a = sphi + ((k - kbeg) & 1) * A3;
+            const R* a = sphi + PAR * A3;
             phk = a[c3];
             sphi19.push(plane19<R, W3>(a, c3, phk), psk, dxk, dyk, dzk);
-            spsi[((k - 1 - kbeg) & 1) * A2 + c2] = psk;
+            spsi[(PAR ^ 1) * A2 + c2] = psk;             // slot of psi(k - 1)
         }
 
         // ---- psi plane k - 2: lam, grad psi, mu, P at k - 3 (r = 1) --------------------
         R nxz = R(0), nyz = R(0), nzz = R(0);
         if (st2) {
-            const R* b = spsi + ((k - 2 - kbeg) & 1) * A2;
+            const R* b = spsi + PAR * A2;                // psi(k - 2)
             R lam, s0, s1, s2;
             spsi19.push(plane19<R, CW>(b, c2, ps1), lam, s0, s1, s2);
             if (z2 >= z0 - 1) {
@@ -426,7 +433,7 @@ __global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso
                     const R iso = av * ph2_ * half + R(0.75) * p.b * ph2_ * ph2_
                                 - p.kappa * (ph * psi + half * (d0 * d0 + d1 * d1 + d2 * d2))
                                 + p.c * (ph * lam + half * psi * psi + d0 * s0 + d1 * s1 + d2 * s2);
-                    R* P = sP + ((z2 - kbeg) & 1) * 6 * A2;
+                    R* P = sP + (PAR ^ 1) * 6 * A2;          // slot of P(k - 3)
                     nxz = p.kappa * d0 * d2 - p.c * (d0 * s2 + d2 * s0);
                     nyz = p.kappa * d1 * d2 - p.c * (d1 * s2 + d2 * s1);
                     nzz = iso + p.kappa * d2 * d2 - R(2) * p.c * d2 * s2;
@@ -441,8 +448,8 @@ __global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso
         }
 
         // ---- P plane k - 4: F at k - 5 (the tile) --------------------------------------
-        if (hyd && in0 && k >= z0 + 3) {
-            const R* P = sP + ((k - 4 - kbeg) & 1) * 6 * A2;
+        if (hyd && row0 && k >= z0 + 3 && k <= kend) {
+            const R* P = sP + PAR * 6 * A2;              // P(k - 4)
             const Plane19<R> xx = plane19<R, CW>(P + 0 * A2, c2, R(0));
             const Plane19<R> xy = plane19<R, CW>(P + 1 * A2, c2, R(0));
             const Plane19<R> yy = plane19<R, CW>(P + 2 * A2, c2, R(0));
@@ -469,6 +476,15 @@ __global__ void __launch_bounds__(Force3Iso<R, TX, TY>::NTH, MINB) k_force3d_iso
         ps2 = ps1; ps1 = psk;
         dx2 = dx1; dy2 = dy1; dz2 = dz1; dx1 = dxk; dy1 = dyk; dz1 = dzk;
         oxz = nxz; oyz = nyz; ozz = nzz;
+    };
+
+    fetch(kbeg, 0);
+    // two iterations per trip, so that slots and window shifts are fixed in
+    // each copy; an odd count ends with one more iteration whose stages are all
+    // out of range (only its barrier runs)
+    for (int k = kbeg; k <= kend; k += 2) {
+        iter(k, std::integral_constant<int, 0>{});
+        iter(k + 1, std::integral_constant<int, 1>{});
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
@@ -666,6 +682,236 @@ __global__ void __launch_bounds__(Force3x2<TX, TY>::NTH, 2) k_force3d_x2(Geom g,
         iter(j + 1, std::integral_constant<int, 1>{});
         iter(j + 2, std::integral_constant<int, 2>{});
         iter(j + 3, std::integral_constant<int, 3>{});
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
+// The sliding-sum isotropic pass A on two z-segments at once (FP32): lane .x
+// marches planes [z0, z0 + H), lane .y planes [z0 + H, z0 + 2H) (shorter or
+// empty at the top of the lattice), with the stages and lags of
+// k_force3d_iso, float2 shared planes (one 64-bit load brings a neighbour of
+// both lanes) and packed FP32x2 arithmetic throughout.
+template <int TX, int TY>
+struct Force3IsoX2 {
+    static constexpr int CW = TX + 4, CH = TY + 4, NTH = CW * CH;
+    static constexpr int W3 = TX + 6, H3 = TY + 6, A3 = W3 * H3;
+    static constexpr int A2 = CW * CH;
+    static constexpr int PHI = 0;                                   // [2][A3] float2
+    static constexpr int PSI = PHI + 2 * A3;                        // [2][A2]
+    static constexpr int PP = PSI + 2 * A2;                         // [2][6][A2]
+    static constexpr int TOTAL = PP + 12 * A2;
+    static constexpr size_t MAPS = sizeof(float2) * TOTAL;
+    static constexpr size_t BYTES = MAPS + sizeof(int) * (W3 + H3);
+};
+
+namespace iso2 {
+using namespace march;
+struct Plane {
+    float2 s, l, gx, gy, ax, ay;
+};
+template <int W>
+__device__ __forceinline__ Plane plane(const float2* a, int c, float2 ac)
+{
+    const float2 e = a[c + 1], w = a[c - 1], n = a[c + W], so = a[c - W];
+    const float2 ne = a[c + W + 1], nw = a[c + W - 1], se = a[c - W + 1], sw = a[c - W - 1];
+    const float2 cross = add2(add2(e, w), add2(n, so));
+    Plane r;
+    r.s = fma2(v2(2.f), ac, cross);
+    r.l = fma2(v2(-24.f), ac, fma2(v2(2.f), cross, add2(add2(ne, nw), add2(se, sw))));
+    r.ax = sub2(e, w);
+    r.ay = sub2(n, so);
+    r.gx = fma2(v2(2.f), r.ax, add2(sub2(ne, nw), sub2(se, sw)));
+    r.gy = fma2(v2(2.f), r.ay, add2(sub2(ne, se), sub2(nw, sw)));
+    return r;
+}
+struct Slide {
+    float2 l = v2(0.f), gx = v2(0.f), gy = v2(0.f), s_prev = v2(0.f), s = v2(0.f), ax = v2(0.f), ay = v2(0.f);
+    __device__ __forceinline__ void push(const Plane& q, float2& lap, float2& dx, float2& dy, float2& dz)
+    {
+        lap = mul2(add2(l, q.s), v2(1.f / 6.f));
+        dx = mul2(add2(gx, q.ax), v2(1.f / 12.f));
+        dy = mul2(add2(gy, q.ay), v2(1.f / 12.f));
+        dz = mul2(sub2(q.s, s_prev), v2(1.f / 12.f));
+        l = add2(q.l, s);
+        gx = add2(q.gx, ax);
+        gy = add2(q.gy, ay);
+        s_prev = s;
+        s = q.s;
+        ax = q.ax;
+        ay = q.ay;
+    }
+};
+}  // namespace iso2
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(Geom g, Phys<float> p, StepIO<float> io, int H)
+{
+    using namespace march;
+    using P3 = Force3IsoX2<TX, TY>;
+    constexpr int W3 = P3::W3, CW = P3::CW, A3 = P3::A3, A2 = P3::A2, NTH = P3::NTH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    float2* sphi = sm + P3::PHI;
+    float2* spsi = sm + P3::PSI;
+    float2* sP = sm + P3::PP;
+    int* colmap = reinterpret_cast<int*>(smem_raw + P3::MAPS);
+    int* rowmap = colmap + W3;
+
+    const int t = threadIdx.x;
+    const int cx = t % CW, cy = t / CW;
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
+    const int zs = ny * pitch;                   // 32-bit offsets: Q * padded sites < 2^31 (checked at creation)
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int za0 = blockIdx.z * 2 * H, zb0 = za0 + H;                    // first plane of each lane
+    const int ha = min(H, nz - za0), hb = max(0, min(H, nz - zb0));     // planes per lane
+    const int hmax = ha > hb ? ha : hb;
+    // relative plane j of lane L is plane z0_L + j; phi planes j = -3 .. hmax + 2,
+    // iterations j = -3 .. hmax + 4
+    const int jphi = hmax + 2, jend = hmax + 4;
+    const bool in0 = cx >= 2 && cx < CW - 2 && cy >= 2 && cy < P3::CH - 2;
+    const bool row1 = cy >= 1 && cy < P3::CH - 1, row0 = cy >= 2 && cy < P3::CH - 2;
+    const int gx = x0 - 2 + cx, gy = y0 - 2 + cy;
+    const bool own = in0 && gx < nx && gy < ny;
+    const int own_off = gy * pitch + gx;
+    const bool hyd = p.hydro != 0;
+    bool bad = false;
+
+    for (int q = t; q < W3 + P3::H3; q += NTH) {
+        if (q < W3) colmap[q] = wrap_s(x0 - 3 + q, nx);
+        else rowmap[q - W3] = wrap_s(y0 - 3 + (q - W3), ny);
+    }
+    __syncthreads();
+    const int col_off = rowmap[cy + 1] * pitch + colmap[cx + 1];
+    const int c3 = (cy + 1) * W3 + cx + 1;
+    const int c2 = t;
+    static_assert(A3 <= 2 * NTH, "at most two phi elements per thread");
+    const int qe = t + NTH;
+    const bool two = qe < A3;
+    const int oe0 = rowmap[t / W3] * pitch + colmap[t % W3];
+    const int oe1 = two ? rowmap[qe / W3] * pitch + colmap[qe % W3] : 0;
+
+    auto fetch = [&](int j, int slot) {
+        if (j <= jphi) {
+            const int pa = map_z(za0 + j, nz, walls) * zs, pb = map_z(zb0 + j, nz, walls) * zs;
+            float* d = reinterpret_cast<float*>(sphi + slot * A3);
+            cp_async_s<4>(d + 2 * t, io.phi_in + (pa + oe0));
+            cp_async_s<4>(d + 2 * t + 1, io.phi_in + (pb + oe0));
+            if (two) {
+                cp_async_s<4>(d + 2 * qe, io.phi_in + (pa + oe1));
+                cp_async_s<4>(d + 2 * qe + 1, io.phi_in + (pb + oe1));
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    iso2::Slide sphi19, spsi19;
+    float2 ph1 = v2(0.f), ph2 = v2(0.f), ph3 = v2(0.f);        // own phi(j-1), phi(j-2), phi(j-3)
+    float2 ps1 = v2(0.f), ps2 = v2(0.f);                       // own psi(j-2), psi(j-3)
+    float2 dx1 = v2(0.f), dy1 = v2(0.f), dz1 = v2(0.f), dx2 = v2(0.f), dy2 = v2(0.f), dz2 = v2(0.f);
+    float2 oxz = v2(0.f), oyz = v2(0.f), ozz = v2(0.f);        // own P_xz, P_yz, P_zz of plane j-4
+    float2 aFx = v2(0.f), aFy = v2(0.f), aFz = v2(0.f), bFx = v2(0.f), bFy = v2(0.f), bFz = v2(0.f);
+    const float2 half = v2(0.5f), k_ = v2(p.kappa), mc = v2(-p.c), m2c = v2(-2.f * p.c);
+
+    auto iter = [&](int j, auto par_c) {
+        constexpr int PAR = decltype(par_c)::value;        // (j + 3) & 1
+        const int r2 = j - 3;                               // mu / P plane of this iteration
+        const bool st2 = row1 && j >= 0 && j <= hmax + 3;
+        float2 Tc = v2(0.f);
+        if (st2 && r2 >= -1)
+            Tc = make_float2(io.T_in[map_z(za0 + r2, nz, walls) * zs + col_off],
+                             io.T_in[map_z(zb0 + r2, nz, walls) * zs + col_off]);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        fetch(j + 1, PAR ^ 1);
+
+        // phi plane j: psi and grad phi at j - 1 (every column)
+        float2 phk = v2(0.f), psk = v2(0.f), dxk = v2(0.f), dyk = v2(0.f), dzk = v2(0.f);
+        if (j <= jphi) {
+            const float2* a = sphi + PAR * A3;
+            phk = a[c3];
+            sphi19.push(iso2::plane<W3>(a, c3, phk), psk, dxk, dyk, dzk);
+            spsi[(PAR ^ 1) * A2 + c2] = psk;
+        }
+
+        // psi plane j - 2: lam, grad psi, mu, P at j - 3 (rows of the r = 1 region)
+        float2 nxz = v2(0.f), nyz = v2(0.f), nzz = v2(0.f);
+        if (st2) {
+            float2 lam, s0, s1, s2;
+            spsi19.push(iso2::plane<CW>(spsi + PAR * A2, c2, ps1), lam, s0, s1, s2);
+            if (r2 >= -1) {
+                const float2 ph = ph3, psi = ps2;
+                const float2 av = mul2(sub2(Tc, v2(p.Tc)), v2(p.inv_Tc));
+                const float2 phsq = mul2(ph, ph);
+                if (own && r2 >= 0) {
+                    const float2 mu = fma2(v2(p.c), lam, fma2(v2(-p.kappa), psi, mul2(ph, fma2(v2(p.b), phsq, av))));
+                    if (r2 < ha) { bad |= !isfinite(mu.x); io.mu[(za0 + r2) * zs + own_off] = mu.x; }
+                    if (r2 < hb) { bad |= !isfinite(mu.y); io.mu[(zb0 + r2) * zs + own_off] = mu.y; }
+                }
+                if (hyd) {
+                    const float2 d0 = dx2, d1 = dy2, d2 = dz2;
+                    const float2 gp2 = fma2(d0, d0, fma2(d1, d1, mul2(d2, d2)));
+                    const float2 gpgs = fma2(d0, s0, fma2(d1, s1, mul2(d2, s2)));
+                    float2 iso = mul2(phsq, fma2(v2(0.75f * p.b), phsq, mul2(half, av)));
+                    iso = fma2(v2(-p.kappa), fma2(half, gp2, mul2(ph, psi)), iso);
+                    iso = fma2(v2(p.c), add2(fma2(ph, lam, mul2(half, mul2(psi, psi))), gpgs), iso);
+                    float2* P = sP + (PAR ^ 1) * 6 * A2;
+                    nxz = fma2(k_, mul2(d0, d2), mul2(mc, fma2(d0, s2, mul2(d2, s0))));
+                    nyz = fma2(k_, mul2(d1, d2), mul2(mc, fma2(d1, s2, mul2(d2, s1))));
+                    nzz = fma2(k_, mul2(d2, d2), fma2(m2c, mul2(d2, s2), iso));
+                    P[0 * A2 + c2] = fma2(k_, mul2(d0, d0), fma2(m2c, mul2(d0, s0), iso));
+                    P[1 * A2 + c2] = fma2(k_, mul2(d0, d1), mul2(mc, fma2(d0, s1, mul2(d1, s0))));
+                    P[2 * A2 + c2] = fma2(k_, mul2(d1, d1), fma2(m2c, mul2(d1, s1), iso));
+                    P[3 * A2 + c2] = nxz;
+                    P[4 * A2 + c2] = nyz;
+                    P[5 * A2 + c2] = nzz;
+                }
+            }
+        }
+
+        // P plane j - 4: F at j - 5 (rows of the tile)
+        if (hyd && row0 && j >= 3 && j <= jend) {
+            const float2* P = sP + PAR * 6 * A2;
+            const iso2::Plane xx = iso2::plane<CW>(P + 0 * A2, c2, v2(0.f));
+            const iso2::Plane xy = iso2::plane<CW>(P + 1 * A2, c2, v2(0.f));
+            const iso2::Plane yy = iso2::plane<CW>(P + 2 * A2, c2, v2(0.f));
+            const iso2::Plane xz = iso2::plane<CW>(P + 3 * A2, c2, oxz);
+            const iso2::Plane yz = iso2::plane<CW>(P + 4 * A2, c2, oyz);
+            const float2* pz = P + 5 * A2;
+            const float2 szz = fma2(v2(2.f), ozz, add2(add2(pz[c2 + 1], pz[c2 - 1]), add2(pz[c2 + CW], pz[c2 - CW])));
+            const float2 Ox = add2(xx.gx, xy.gy), Ax = add2(xx.ax, xy.ay);
+            const float2 Oy = add2(xy.gx, yy.gy), Ay = add2(xy.ax, yy.ay);
+            const float2 Oz = add2(xz.gx, yz.gy), Az = add2(xz.ax, yz.ay);
+            const int r5 = j - 5;
+            if (own && r5 >= 0) {
+                const float2 m12 = v2(-1.f / 12.f);
+                const float2 Fx = mul2(add2(aFx, add2(Ax, xz.s)), m12);
+                const float2 Fy = mul2(add2(aFy, add2(Ay, yz.s)), m12);
+                const float2 Fz = mul2(add2(aFz, add2(Az, szz)), m12);
+                if (r5 < ha) {
+                    const int site = (za0 + r5) * zs + own_off;
+                    io.F[0][site] = Fx.x; io.F[1][site] = Fy.x; io.F[2][site] = Fz.x;
+                }
+                if (r5 < hb) {
+                    const int site = (zb0 + r5) * zs + own_off;
+                    io.F[0][site] = Fx.y; io.F[1][site] = Fy.y; io.F[2][site] = Fz.y;
+                }
+            }
+            aFx = add2(Ox, bFx); aFy = add2(Oy, bFy); aFz = add2(Oz, bFz);
+            bFx = sub2(Ax, xz.s); bFy = sub2(Ay, yz.s); bFz = sub2(Az, szz);
+        }
+
+        ph3 = ph2; ph2 = ph1; ph1 = phk;
+        ps2 = ps1; ps1 = psk;
+        dx2 = dx1; dy2 = dy1; dz2 = dz1; dx1 = dxk; dy1 = dyk; dz1 = dzk;
+        oxz = nxz; oyz = nyz; ozz = nzz;
+    };
+
+    fetch(-3, 0);
+#pragma unroll 1
+    for (int j = -3; j <= jend; j += 2) {
+        iter(j, std::integral_constant<int, 0>{});
+        iter(j + 1, std::integral_constant<int, 1>{});
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
@@ -1122,6 +1368,27 @@ cudaError_t launch_force_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& i
 }
 
 template <int TX, int TY>
+cudaError_t launch_force_iso_x2(const Geom& g, const Phys<float>& p, const StepIO<float>& io, cudaStream_t s)
+{
+    using P3 = Force3IsoX2<TX, TY>;
+    auto kern = k_force3d_iso_x2<TX, TY>;
+    static unsigned long long attr_done = 0;      // per instantiation and device
+    const cudaError_t e = raise_smem_limit(kern, (int)P3::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    int H = (g.tune & 0xFFFF) > 0 ? (g.tune & 0xFFFF) : 0;     // planes per lane
+    if (H <= 0) {   // about eight waves of one CTA per SM, lanes of at least 16 planes
+        const int want = (8 * 152 + tiles - 1) / tiles;
+        H = (g.nz + 2 * want - 1) / (2 * want);
+        if (H < 16) H = 16;
+    }
+    if (H > g.nz) H = g.nz;
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + 2 * H - 1) / (2 * H));
+    kern<<<grid, P3::NTH, P3::BYTES, s>>>(g, p, io, H);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY>
 cudaError_t launch_force_x2(const Geom& g, const Phys<float>& p, const StepIO<float>& io, cudaStream_t s)
 {
     using P3 = Force3x2<TX, TY>;
@@ -1152,14 +1419,16 @@ cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io,
     const bool iso = g.stencil == LF_STENCIL_ISOTROPIC;
     if (iso) {
         // (param >> 16) & 15: 0 = sliding sums on 28x12 tiles (FP32: two CTAs per SM),
-        // 1 = on 28x28 tiles, 3 = on 28x12 tiles at one CTA per SM (FP32 only; FP64
-        // takes 0), 2 = the three-plane form (each operator from its own shared loads)
+        // 1 = on 28x28 tiles, 3 = on 28x12 tiles at one CTA per SM, 4 = two z-lanes
+        // in packed FP32x2 on 28x12 tiles (FP32 only; FP64 takes 0), 2 = the
+        // three-plane form (each operator from its own shared loads)
         const int sel = (g.tune >> 16) & 15;
         if (sel == 2) {
             e = launch_force<R, 28, 12, true>(g, p, io, s);
         } else if constexpr (sizeof(R) == 4) {
             e = sel == 1 ? launch_force_iso<R, 28, 28, 1>(g, p, io, s)
               : sel == 3 ? launch_force_iso<R, 28, 12, 1>(g, p, io, s)
+              : sel == 4 ? launch_force_iso_x2<28, 12>(g, p, io, s)
                          : launch_force_iso<R, 28, 12, 2>(g, p, io, s);
         } else {
             e = launch_force_iso<R, 28, 12, 1>(g, p, io, s);

@@ -66,10 +66,10 @@ std::vector<std::pair<int, int>> candidates(const lf_ctx* c)
     const int phis[] = {0, 32, 64};
     for (int zc : phis) {
         if (zc > g.nz) continue;
-        if (iso) {                                   // sliding-sum force pass: 28x12 (two or one CTA per SM), 28x28; three-plane form
-            const int sels32[] = {0, 1, 3, 2}, sels64[] = {0, 2};
+        if (iso) {                                   // sliding-sum force pass: two packed z-lanes, 28x12 (two or one CTA per SM), 28x28; three-plane form
+            const int sels32[] = {4, 0, 1, 3, 2}, sels64[] = {0, 2};
             const int* sels = c->prec == LF_FP32 ? sels32 : sels64;
-            const int nsel = c->prec == LF_FP32 ? 4 : 2;
+            const int nsel = c->prec == LF_FP32 ? 5 : 2;
             for (int i = 0; i < nsel; ++i)
                 for (int h : planes)
                     if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, (zc << 20) | (sels[i] << 16) | h});

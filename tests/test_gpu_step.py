@@ -193,6 +193,7 @@ VARIANTS3_ISO = {"split3": ("split3", 0), "split3-z3": ("split3", 3), "split3-ph
                  "split3-28x28": ("split3", 1 << 16), "split3-28x28-z5": ("split3", (1 << 16) | 5),
                  "split3-3plane": ("split3", 2 << 16), "split3-1cta-z5": ("split3", (3 << 16) | 5),
                  "split3-phi3plane": ("split3", 1 << 28), "split3-phi5": ("split3", 5 << 20),
+                 "split3-x2": ("split3", 4 << 16), "split3-x2-z3": ("split3", (4 << 16) | 3),
                  "fused": ("march", 0)}
 
 
@@ -201,7 +202,8 @@ VARIANTS3_ISO = {"split3": ("split3", 0), "split3-z3": ("split3", 3), "split3-ph
 @pytest.mark.parametrize("case", CASES3, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny", "nz")) + str(c))
 def test_isotropic_stencil_parity_3d(case, prec, variant):
     """Isotropic 19-point stencils: the three-pass step with each force-pass
-    form (sliding sums on 28x12 and 28x28 tiles, the three-plane form; segments
+    form (sliding sums on 28x12 and 28x28 tiles, on two z-lanes in packed FP32x2
+    (one lane in FP64), the three-plane form; segments
     of 3 and 5 planes as well), both phi-pass forms (sliding sums with segments
     of 16, 5 and 1 planes; the three-plane form) and the fused plane march."""
     sim, cfg, st = make_pair(case, prec, stencil="isotropic")
