@@ -791,19 +791,25 @@ __global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(
     const int oe0 = rowmap[t / W3] * pitch + colmap[t % W3];
     const int oe1 = two ? rowmap[qe / W3] * pitch + colmap[qe % W3] : 0;
 
-    auto fetch = [&](int j, int slot) {
-        if (j <= jphi) {
-            const int pa = map_z(za0 + j, nz, walls) * zs, pb = map_z(zb0 + j, nz, walls) * zs;
-            float* d = reinterpret_cast<float*>(sphi + slot * A3);
-            cp_async_s<4>(d + 2 * t, io.phi_in + (pa + oe0));
-            cp_async_s<4>(d + 2 * t + 1, io.phi_in + (pb + oe0));
-            if (two) {
-                cp_async_s<4>(d + 2 * qe, io.phi_in + (pa + oe1));
-                cp_async_s<4>(d + 2 * qe + 1, io.phi_in + (pb + oe1));
-            }
+    // storage offsets pa, pb of the planes to fetch into ring slot `slot`
+    auto fetch_at = [&](int pa, int pb, int slot) {
+        float* d = reinterpret_cast<float*>(sphi + slot * A3);
+        cp_async_s<4>(d + 2 * t, io.phi_in + (pa + oe0));
+        cp_async_s<4>(d + 2 * t + 1, io.phi_in + (pb + oe0));
+        if (two) {
+            cp_async_s<4>(d + 2 * qe, io.phi_in + (pa + oe1));
+            cp_async_s<4>(d + 2 * qe + 1, io.phi_in + (pb + oe1));
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
+    auto fetch = [&](int j, int slot) {
+        if (j <= jphi) {
+            fetch_at(map_z(za0 + j, nz, walls) * zs, map_z(zb0 + j, nz, walls) * zs, slot);
+            return;
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    const int zs3 = 3 * zs, zs5 = 5 * zs;
 
     iso2::Slide sphi19, spsi19;
     float2 ph1 = v2(0.f), ph2 = v2(0.f), ph3 = v2(0.f);        // own phi(j-1), phi(j-2), phi(j-3)
@@ -813,25 +819,39 @@ __global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(
     float2 aFx = v2(0.f), aFy = v2(0.f), aFz = v2(0.f), bFx = v2(0.f), bFy = v2(0.f), bFz = v2(0.f);
     const float2 half = v2(0.5f), k_ = v2(p.kappa), mc = v2(-p.c), m2c = v2(-2.f * p.c);
 
-    auto iter = [&](int j, auto par_c) {
-        constexpr int PAR = decltype(par_c)::value;        // (j + 3) & 1
+    // iteration j; PAR = (j + 3) & 1 selects the ring slots.  FULL: an
+    // iteration of the steady state (j in [5, hmin - 2]), in which every stage
+    // runs, every plane it touches lies inside both lanes' ranges and inside
+    // the lattice, and all its outputs are stored: no range checks, no plane
+    // mapping.
+    const int hmin = ha < hb ? ha : hb;
+    auto iter = [&](int j, auto par_c, auto full_c) {
+        constexpr int PAR = decltype(par_c)::value;
+        constexpr bool FULL = decltype(full_c)::value;
         const int r2 = j - 3;                               // mu / P plane of this iteration
-        const bool st2 = row1 && j >= 0 && j <= hmax + 3;
+        const int ba = (za0 + j) * zs, bb = (zb0 + j) * zs; // plane j of each lane (FULL only)
+        const bool st2 = FULL ? row1 : row1 && j >= 0 && j <= hmax + 3;
         float2 Tc = v2(0.f);
-        if (st2 && r2 >= -1)
+        if constexpr (FULL) {
+            if (row1) Tc = make_float2(io.T_in[ba - zs3 + col_off], io.T_in[bb - zs3 + col_off]);
+        } else if (st2 && r2 >= -1) {
             Tc = make_float2(io.T_in[map_z(za0 + r2, nz, walls) * zs + col_off],
                              io.T_in[map_z(zb0 + r2, nz, walls) * zs + col_off]);
+        }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        fetch(j + 1, PAR ^ 1);
+        if constexpr (FULL) fetch_at(ba + zs, bb + zs, PAR ^ 1);
+        else fetch(j + 1, PAR ^ 1);
 
         // phi plane j: psi and grad phi at j - 1 (every column)
-        float2 phk = v2(0.f), psk = v2(0.f), dxk = v2(0.f), dyk = v2(0.f), dzk = v2(0.f);
-        if (j <= jphi) {
+        float2 phk, psk, dxk, dyk, dzk;
+        if (FULL || j <= jphi) {
             const float2* a = sphi + PAR * A3;
             phk = a[c3];
             sphi19.push(iso2::plane<W3>(a, c3, phk), psk, dxk, dyk, dzk);
             spsi[(PAR ^ 1) * A2 + c2] = psk;
+        } else {
+            phk = psk = dxk = dyk = dzk = v2(0.f);
         }
 
         // psi plane j - 2: lam, grad psi, mu, P at j - 3 (rows of the r = 1 region)
@@ -839,14 +859,20 @@ __global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(
         if (st2) {
             float2 lam, s0, s1, s2;
             spsi19.push(iso2::plane<CW>(spsi + PAR * A2, c2, ps1), lam, s0, s1, s2);
-            if (r2 >= -1) {
+            if (FULL || r2 >= -1) {
                 const float2 ph = ph3, psi = ps2;
                 const float2 av = mul2(sub2(Tc, v2(p.Tc)), v2(p.inv_Tc));
                 const float2 phsq = mul2(ph, ph);
-                if (own && r2 >= 0) {
+                if (own && (FULL || r2 >= 0)) {
                     const float2 mu = fma2(v2(p.c), lam, fma2(v2(-p.kappa), psi, mul2(ph, fma2(v2(p.b), phsq, av))));
-                    if (r2 < ha) { bad |= !isfinite(mu.x); io.mu[(za0 + r2) * zs + own_off] = mu.x; }
-                    if (r2 < hb) { bad |= !isfinite(mu.y); io.mu[(zb0 + r2) * zs + own_off] = mu.y; }
+                    if constexpr (FULL) {
+                        bad |= !isfinite(mu.x) || !isfinite(mu.y);
+                        io.mu[ba - zs3 + own_off] = mu.x;
+                        io.mu[bb - zs3 + own_off] = mu.y;
+                    } else {
+                        if (r2 < ha) { bad |= !isfinite(mu.x); io.mu[(za0 + r2) * zs + own_off] = mu.x; }
+                        if (r2 < hb) { bad |= !isfinite(mu.y); io.mu[(zb0 + r2) * zs + own_off] = mu.y; }
+                    }
                 }
                 if (hyd) {
                     const float2 d0 = dx2, d1 = dy2, d2 = dz2;
@@ -870,7 +896,7 @@ __global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(
         }
 
         // P plane j - 4: F at j - 5 (rows of the tile)
-        if (hyd && row0 && j >= 3 && j <= jend) {
+        if (hyd && row0 && (FULL || (j >= 3 && j <= jend))) {
             const float2* P = sP + PAR * 6 * A2;
             const iso2::Plane xx = iso2::plane<CW>(P + 0 * A2, c2, v2(0.f));
             const iso2::Plane xy = iso2::plane<CW>(P + 1 * A2, c2, v2(0.f));
@@ -883,17 +909,17 @@ __global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(
             const float2 Oy = add2(xy.gx, yy.gy), Ay = add2(xy.ax, yy.ay);
             const float2 Oz = add2(xz.gx, yz.gy), Az = add2(xz.ax, yz.ay);
             const int r5 = j - 5;
-            if (own && r5 >= 0) {
+            if (own && (FULL || r5 >= 0)) {
                 const float2 m12 = v2(-1.f / 12.f);
                 const float2 Fx = mul2(add2(aFx, add2(Ax, xz.s)), m12);
                 const float2 Fy = mul2(add2(aFy, add2(Ay, yz.s)), m12);
                 const float2 Fz = mul2(add2(aFz, add2(Az, szz)), m12);
-                if (r5 < ha) {
-                    const int site = (za0 + r5) * zs + own_off;
+                if (FULL || r5 < ha) {
+                    const int site = (FULL ? ba - zs5 : (za0 + r5) * zs) + own_off;
                     io.F[0][site] = Fx.x; io.F[1][site] = Fy.x; io.F[2][site] = Fz.x;
                 }
-                if (r5 < hb) {
-                    const int site = (zb0 + r5) * zs + own_off;
+                if (FULL || r5 < hb) {
+                    const int site = (FULL ? bb - zs5 : (zb0 + r5) * zs) + own_off;
                     io.F[0][site] = Fx.y; io.F[1][site] = Fy.y; io.F[2][site] = Fz.y;
                 }
             }
@@ -906,12 +932,29 @@ __global__ void __launch_bounds__(Force3IsoX2<TX, TY>::NTH, 1) k_force3d_iso_x2(
         dx2 = dx1; dy2 = dy1; dz2 = dz1; dx1 = dxk; dy1 = dyk; dz1 = dzk;
         oxz = nxz; oyz = nyz; ozz = nzz;
     };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using GEN = std::false_type;
+    using STEADY = std::true_type;
 
     fetch(-3, 0);
+    int j = -3;
+    // warm-up iterations -3 .. 4, the steady state in pairs, then the rest
+    // (an odd count ends with one iteration whose stages are all out of range)
 #pragma unroll 1
-    for (int j = -3; j <= jend; j += 2) {
-        iter(j, std::integral_constant<int, 0>{});
-        iter(j + 1, std::integral_constant<int, 1>{});
+    for (; j < 5; j += 2) {
+        iter(j, I0{}, GEN{});
+        iter(j + 1, I1{}, GEN{});
+    }
+#pragma unroll 1
+    for (; j + 1 <= hmin - 2; j += 2) {
+        iter(j, I0{}, STEADY{});
+        iter(j + 1, I1{}, STEADY{});
+    }
+#pragma unroll 1
+    for (; j <= jend; j += 2) {
+        iter(j, I0{}, GEN{});
+        iter(j + 1, I1{}, GEN{});
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
