@@ -265,13 +265,12 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     u pass through the context's derived-field planes.  (param >> 16) & 15
  *     selects the force pass's form: with the compact stencils, in FP32, 0 =
  *     two segments in the lanes of packed FP32x2 arithmetic, 1 / 2 = one lane
- *     on 60x4 / 28x12 tiles; with the isotropic stencils, 0 = sliding plane
- *     sums on 28x12 tiles (FP32: two CTAs per SM), 1 = on 28x28 tiles, 3 = on
- *     28x12 tiles at one CTA per SM, 4 = two segments in packed FP32x2 lanes
- *     (1, 3 and 4 in FP32 only; FP64 takes 0), 2 = the three-plane form.
- *     With the isotropic stencils bit 28 selects the three-plane phi pass
- *     instead of the sliding-sum one.  For 3D contexts every other variant
- *     runs the fused plane march (param = planes per segment).
+ *     on 60x4 / 28x12 tiles; with the isotropic stencils (both passes as
+ *     column marches with sliding plane sums), 0 = one lane on 28x12 tiles
+ *     (FP32: two CTAs per SM), 1 = on 28x28 tiles, 3 = on 28x12 tiles at one
+ *     CTA per SM, 4 = two segments in packed FP32x2 lanes (1, 3 and 4 in FP32
+ *     only; FP64 takes 0).  For 3D contexts every other variant runs the
+ *     fused plane march (param = planes per segment).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
 #define LF_VARIANT_MARCH  0
 #define LF_VARIANT_TILE   1

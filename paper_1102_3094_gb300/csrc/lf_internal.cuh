@@ -112,6 +112,11 @@ cudaError_t launch_step3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, 
                           cudaStream_t s);
 template <typename R>
 cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);
+// passes A and C of the three-pass step with the isotropic stencils (lf_step3d_iso.cu)
+template <typename R>
+cudaError_t launch_force3d_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);
+template <typename R>
+cudaError_t launch_phi3d_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, int zc, cudaStream_t s);
 template <typename R>
 cudaError_t launch_tsub3d(const Geom& g, const Phys<R>& p, const R* Tin, R* Tout, cudaStream_t s);
 template <typename R>

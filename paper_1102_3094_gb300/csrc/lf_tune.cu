@@ -66,10 +66,10 @@ std::vector<std::pair<int, int>> candidates(const lf_ctx* c)
     const int phis[] = {0, 32, 64};
     for (int zc : phis) {
         if (zc > g.nz) continue;
-        if (iso) {                                   // sliding-sum force pass: two packed z-lanes, 28x12 (two or one CTA per SM), 28x28; three-plane form
-            const int sels32[] = {4, 0, 1, 3, 2}, sels64[] = {0, 2};
+        if (iso) {                                   // sliding-sum force pass: two packed z-lanes, one lane on 28x12 (two or one CTA per SM) or 28x28
+            const int sels32[] = {4, 0, 1, 3}, sels64[] = {0};
             const int* sels = c->prec == LF_FP32 ? sels32 : sels64;
-            const int nsel = c->prec == LF_FP32 ? 5 : 2;
+            const int nsel = c->prec == LF_FP32 ? 4 : 1;
             const int lanes[] = {0, 48, 64, 96, 128, 192};   // planes per lane of the packed form
             for (int i = 0; i < nsel; ++i) {
                 if (sels[i] == 4) {

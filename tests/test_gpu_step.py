@@ -191,8 +191,7 @@ def test_aux_and_step_parity_3d(case, prec, variant):
 # force-pass forms of the isotropic three-pass step ((param >> 16) & 15)
 VARIANTS3_ISO = {"split3": ("split3", 0), "split3-z3": ("split3", 3), "split3-phi1": ("split3", 1 << 20),
                  "split3-28x28": ("split3", 1 << 16), "split3-28x28-z5": ("split3", (1 << 16) | 5),
-                 "split3-3plane": ("split3", 2 << 16), "split3-1cta-z5": ("split3", (3 << 16) | 5),
-                 "split3-phi3plane": ("split3", 1 << 28), "split3-phi5": ("split3", 5 << 20),
+                 "split3-1cta-z5": ("split3", (3 << 16) | 5), "split3-phi5": ("split3", 5 << 20),
                  "split3-x2": ("split3", 4 << 16), "split3-x2-z3": ("split3", (4 << 16) | 3),
                  "split3-x2-z8": ("split3", (4 << 16) | 8),
                  "fused": ("march", 0)}
@@ -204,9 +203,8 @@ VARIANTS3_ISO = {"split3": ("split3", 0), "split3-z3": ("split3", 3), "split3-ph
 def test_isotropic_stencil_parity_3d(case, prec, variant):
     """Isotropic 19-point stencils: the three-pass step with each force-pass
     form (sliding sums on 28x12 and 28x28 tiles, on two z-lanes in packed FP32x2
-    (one lane in FP64), the three-plane form; segments
-    of 3 and 5 planes as well), both phi-pass forms (sliding sums with segments
-    of 16, 5 and 1 planes; the three-plane form) and the fused plane march."""
+    (one lane in FP64); segments of 3, 5 and 8 planes as well), the phi pass
+    with segments of 16, 5 and 1 planes, and the fused plane march."""
     sim, cfg, st = make_pair(case, prec, stencil="isotropic")
     sim.set_variant(*VARIANTS3_ISO[variant])
     _check_aux_and_step_3d(sim, st, prec)
