@@ -776,6 +776,7 @@ def run_ours(args):
         stable = {"what": "tau = 3, isotropic 19-point stencils (runs the 20k steps finite); no restores",
                   "value": job_rate(N, args.steps, world, tot), "unit": "MLUPS",
                   "ms_per_step": 1e3 * tot / args.steps, "frac": ach / peak, "achieved_gbs": ach,
+                  "traffic": traffic_for(f"k_force3d+k_lb3d+k_phi3d_iso_{prec}_{nx}_p{p_}") if v_ == 3 else None,
                   "kernel_shape": {"variant": names[v_], "param": p_}, "diag_after": {"rc": sim.diag()["rc"]}}
     if rank == 0:
         line = {
