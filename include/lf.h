@@ -250,6 +250,8 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     marches down a segment of (param & 0xFFFF) rows (0 = chosen from the
  *     lattice size), inputs prefetched with cp.async; (param >> 16) == 1
  *     selects CTAs of 64 threads (56 columns) instead of 128 (120 columns);
+ *     with the isotropic stencils both march variants run this one-lane
+ *     march, with sliding row sums;
  *   LF_VARIANT_TILE: one CTA per 2D tile, each stage of the step on the whole
  *     tile in shared memory (`param` ignored);
  *   LF_VARIANT_MARCH2 (default for 2D FP32; FP64 contexts run LF_VARIANT_MARCH
@@ -291,8 +293,8 @@ int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
  * scratch context allocates as much device memory as ctx, plus one copy of
  * its state, for the duration of the call; it waits for ctx's stream.  Any of
  * variant, param, ms_per_step may be NULL; on success they receive the choice
- * and its time per step in milliseconds.  The isotropic 2D step has a single
- * kernel (the tile form), which is then the only candidate.  Returns LF_EINVAL
+ * and its time per step in milliseconds.  For the isotropic 2D step the
+ * candidates are the one-lane row march and the tile kernel.  Returns LF_EINVAL
  * for reps < 1 or an ensemble member. */
 int lf_tune(lf_ctx* ctx, int reps, int* variant, int* param, double* ms_per_step);
 
@@ -328,15 +330,17 @@ int lf_set_t_solver(lf_ctx* ctx, int solver);
  *     second order with an isotropic leading error (Thampi et al., J. Comput.
  *     Phys. 234 (2013) 1).  Applies to psi, lam, grad phi, grad psi, F, the
  *     flux divergence, lap mu and lap T; the wall images are those of the
- *     compact stencils, applied to the diagonal neighbours too.  In 2D it
- *     runs the LF_VARIANT_TILE kernel whatever variant is set; in 3D the
- *     variant set (three passes by default, or the fused plane march).  Its
+ *     compact stencils, applied to the diagonal neighbours too.  In 2D the
+ *     march variants run a row march whose 9-point operators are split into
+ *     sliding row sums, LF_VARIANT_TILE the tile kernel; in 3D the variant
+ *     set (three passes by default, or the fused plane march).  Its
  *     largest Laplacian eigenvalue is 16/3 in 2D and 3D (8 and 12 for the
  *     compact stencils), which the stability check of lf_create uses.
  * Returns LF_EINVAL for an unknown stencil or an ensemble member (an
  * ensemble's runs take their stencil from params at lf_ens_create), and
  * LF_EUNSTABLE if the context's parameters are unstable with the new stencil
- * (the context keeps its stencil then).  lf_load does not restore it. */
+ * (the context keeps its stencil then).  lf_load refuses a checkpoint
+ * written with another stencil. */
 #define LF_STENCIL_COMPACT   0
 #define LF_STENCIL_ISOTROPIC 1
 int lf_set_stencil(lf_ctx* ctx, int stencil);

@@ -26,6 +26,10 @@
 // one odd quantity, the wall-normal flux g_y, is reflected with a sign flip
 // in the last stage.  Populations are stored as deviations f_i - w_i n0.
 //
+// With the isotropic stencils the march variants run the row march of
+// lf_march2d_iso.cuh (sliding row sums); the tile kernel below serves
+// LF_VARIANT_TILE and the derived fields.
+//
 // With ISO set, every derivative takes the isotropic 9-point form instead:
 // lap A = [4 (nearest) + (diagonal) - 20 A]/6 and d_x A = [4 (E - W) + (NE - NW)
 // + (SE - SW)]/12 (the D2Q9 weights: d_a = 3 sum w_i e_ia A(r + e_i), lap = 6
@@ -34,6 +38,7 @@
 // of the halfway temperature ghost are applied to whole rows.
 #include "lf_internal.cuh"
 #include "lf_march2d.cuh"
+#include "lf_march2d_iso.cuh"
 #include "lf_march2d_x2.cuh"
 #include "lf_tile2d.cuh"
 
@@ -55,6 +60,14 @@ __global__ void __launch_bounds__(NT) k_march2d(Geom g, Phys<R> p, StepIO<R> io,
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     march::march2d_segment<R, NT, D>(g, p, io, blockIdx.x, blockIdx.y, H, smem_raw);
+}
+
+// The row march with the isotropic 9-point stencils: see lf_march2d_iso.cuh.
+template <typename R, int NT, int D>
+__global__ void __launch_bounds__(NT) k_march2d_iso(Geom g, Phys<R> p, StepIO<R> io, int H)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    march::march2d_segment_iso<R, NT, D>(g, p, io, blockIdx.x, blockIdx.y, H, smem_raw);
 }
 
 // Two segments per CTA in the lanes of float2 (packed FP32x2 arithmetic).
@@ -88,6 +101,22 @@ cudaError_t launch_march(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
 {
     using M = march::March<R, NT, D>;
     auto kern = k_march2d<R, NT, D>;
+    static unsigned long long attr_done = 0;
+    cudaError_t e = raise_smem_limit(kern, (int)M::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = device_sms(&sms)) != cudaSuccess) return e;
+    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
+    dim3 grid((g.nx + M::U - 1) / M::U, (g.ny + H - 1) / H);
+    kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
+    return cudaGetLastError();
+}
+
+template <typename R, int NT, int D>
+cudaError_t launch_march_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
+{
+    using M = march::MarchIso<R, NT, D>;
+    auto kern = k_march2d_iso<R, NT, D>;
     static unsigned long long attr_done = 0;
     cudaError_t e = raise_smem_limit(kern, (int)M::BYTES, &attr_done);
     if (e != cudaSuccess) return e;
@@ -139,7 +168,9 @@ __global__ void k_tsub2d_iso(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __
 template <typename R>
 cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
-    if (g.stencil == LF_STENCIL_ISOTROPIC) {           // tile kernel only
+    if (g.stencil == LF_STENCIL_ISOTROPIC) {           // the row march (both march variants) or the tile kernel
+        if (!aux && (g.variant == LF_VARIANT_MARCH || g.variant == LF_VARIANT_MARCH2) && g.ny >= 2)
+            return (g.tune >> 16) == 1 ? launch_march_iso<R, 64, 3>(g, p, io, s) : launch_march_iso<R, 128, 3>(g, p, io, s);
         if constexpr (sizeof(R) == 4)
             return aux ? launch_cfg<R, 64, 16, 256, true, true>(g, p, io, s)
                        : launch_cfg<R, 64, 16, 256, false, true>(g, p, io, s);

@@ -45,7 +45,7 @@ def to_oracle_f(f_lib, d):
 
 VARIANTS = {"march": ("march", 0), "march-h5": ("march", 5), "tile": ("tile", 0),
             "march2": ("march2", 0), "march2-h5": ("march2", 5), "march2-h1": ("march2", 1),
-            "march2-n64": ("march2", 1 << 16)}
+            "march2-n64": ("march2", 1 << 16), "march-h1": ("march", 1), "march-n64-h3": ("march", (1 << 16) | 3)}
 
 
 def make_pair(case, prec, seed=11, variant="march", stencil="compact"):
@@ -96,21 +96,25 @@ def test_aux_and_step_parity(case, prec, variant):
     _check_aux_and_step(sim, st, prec)
 
 
-@pytest.mark.parametrize("variant", ["march2", "tile"])
+@pytest.mark.parametrize("variant", ["march", "march-h5", "march-h1", "march-n64-h3", "march2", "tile"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny")) + str(c))
 def test_isotropic_stencil_parity(case, prec, variant):
-    """Isotropic 9-point stencils (runs the tile kernel whatever the variant)."""
+    """Isotropic 9-point stencils: the row march with sliding row sums
+    (LF_VARIANT_MARCH, segments of the model's height and of 5, 1 and 3 rows,
+    128- and 64-thread strips) and the tile kernel (the other variants)."""
     sim, cfg, st = make_pair(case, prec, variant=variant, stencil="isotropic")
     _check_aux_and_step(sim, st, prec)
 
 
-def test_isotropic_multistep_fp64():
+@pytest.mark.parametrize("variant", ["march", "tile"])
+def test_isotropic_multistep_fp64(variant):
     """200 coupled steps with the isotropic stencils: walls with the halfway T
     ghost and nsub = 2, then a fully periodic lattice."""
     for kw in (dict(nx=64, ny=48, t_wall_mode=1, xi=0.3), dict(nx=40, ny=36, walls=0, xi=0.01)):
         sim = lf.Lattice(precision="fp64", **kw)
         sim.set_stencil("isotropic")
+        sim.set_variant(*VARIANTS[variant])
         st = O.init(O.make_cfg(stencil=1, **kw))
         sim.step(200)
         ref = O.run(st, 200)
