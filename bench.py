@@ -266,9 +266,9 @@ def run_ensemble(args):
         tune_s = time.time() - t0
         shapes = {}
         for r, m in enumerate(members):
-            if m.get("stencil") != "isotropic":
-                pr = ens.param(r)
-                shapes[f"{m['nx']}x{m['ny']}"] = {"cta_threads": 64 if pr >> 16 else 128, "rows": pr & 0xFFFF}
+            pr = ens.param(r)
+            shapes[f"{m['nx']}x{m['ny']}" + ("-iso" if m.get("stencil") == "isotropic" else "")] = \
+                {"cta_threads": 64 if pr >> 16 else 128, "rows": pr & 0xFFFF}
         # the plain single-run path at its own best shapes (lf_tune, cached per lattice size)
         singles = [lf.Lattice(precision="fp32", stream=stream, **m) for m in members]
         single_shapes = {}
@@ -343,7 +343,7 @@ def run_ensemble(args):
         "config": {"workload": "ens96: 96 independent 2D runs, 24 each of 128^2, 256^2, 384^2, 512^2, xi "
                                "log-uniform in [1e-4, 1], tau in {0.6, 1, 3}, one persistent launch per step "
                                "replayed from a CUDA graph, CTA width and segment height from the autotuner"
-                               + (", isotropic 9-point stencils (tile items)" if args.stencil == "isotropic" else ""),
+                               + (", isotropic 9-point stencils (one-lane row-march items)" if args.stencil == "isotropic" else ""),
                    "sites_per_step_all_runs": sites, "tuned_shapes": shapes,
                    "sequential_shapes": single_shapes,
                    "l2": "inputs (1 GB of state) larger than L2",
@@ -351,7 +351,7 @@ def run_ensemble(args):
                                   f"{block} steps (non-finite runs retired between blocks, outside the timing)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_site": 88,
-                     "kernel": ("k_ens_tile2d_iso" if args.stencil == "isotropic" else "k_ens_march2d")
+                     "kernel": ("k_ens_march2d_iso" if args.stencil == "isotropic" else "k_ens_march2d")
                                + " (+ k_ens_tsub2d for runs with xi/nsub sub-steps)"},
         "batched_vs_sequential": {"t_batched_s": t_batch, "t_sequential_s": t_seq, "speedup": t_seq / t_batch,
                                   "max_sk_peak_err": sk_err, "max_phi_rel_l2": l2_err, "tune_s": tune_s,
@@ -601,7 +601,7 @@ def run_ours(args):
                      device=dev)
     iso = args.stencil == "isotropic"
     if iso:
-        sim.set_stencil("isotropic")        # 2D: the tile kernel; 3D: the variant set (three passes by default)
+        sim.set_stencil("isotropic")        # 2D: the isotropic row march; 3D: the variant set (three passes by default)
     names = {lf.LF_VARIANT_MARCH: "march", lf.LF_VARIANT_TILE: "tile", lf.LF_VARIANT_MARCH2: "march2",
              lf.LF_VARIANT_SPLIT3: "split3"}
     variant = args.variant

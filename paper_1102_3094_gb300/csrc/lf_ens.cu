@@ -6,9 +6,10 @@
 // two-lane row-marching step of lf_march2d_x2.cuh (two segments of a strip
 // marching away from their common row) -- followed, when some runs need extra
 // temperature sub-steps, by one launch per sub-step over the tiles of those
-// runs.  Runs with the isotropic stencils are (run, tile) items of a second
-// persistent kernel that runs the tile form of the step (lf_tile2d.cuh), the
-// code a single isotropic run uses.  Every run returns to its starting buffers
+// runs.  Runs with the isotropic stencils are (run, strip, segment) items of a
+// second persistent kernel that runs the one-lane isotropic row march
+// (lf_march2d_iso.cuh), the code a single isotropic run uses.  Every run
+// returns to its starting buffers
 // after two steps (f and phi flip once per step, T flips nsub times), so two
 // steps are captured in one CUDA graph and replayed; single-step graphs handle
 // odd counts.
@@ -17,12 +18,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <new>
 #include <utility>
 #include <vector>
 
 #include "lf_ctx.cuh"
 #include "lf_ens.h"
+#include "lf_march2d_iso.cuh"
 #include "lf_march2d_x2.cuh"
 #include "lf_tile2d.cuh"
 
@@ -36,8 +39,8 @@ namespace {
 constexpr int kD = 3;
 template <int NT>
 using MarchCfg = march::March2<NT, kD>;
-constexpr int kTX = 64, kTY = 16, kTNT = 256;   // the FP32 tile of the single-run isotropic step
-using TileCfg = tile::Tile<float, kTX, kTY>;
+template <int NT>
+using IsoCfg = march::MarchIso<float, NT, kD>;
 
 struct EnsRun {
     Geom g;
@@ -60,20 +63,23 @@ struct EnsTItem {
     int run, bx, by;
 };
 
-// (run, tile) items of the isotropic runs, in the same struct as the T tiles.
-using EnsTile = EnsTItem;
-
-__global__ void __launch_bounds__(kTNT) k_ens_tile2d_iso(const EnsRun* __restrict__ runs,
-                                                        const EnsTile* __restrict__ items, int nitems)
+// Isotropic runs: items (run, strip, segment, rows per segment) in the
+// fields (run, strip, pair, npairs) of EnsItem; the launch bounds of the
+// single-run kernel, so both compile the same step.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ens_march2d_iso(const EnsRun* __restrict__ runs,
+                                                       const EnsItem* __restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const EnsTile w = items[it];
+        const EnsItem w = items[it];
         const EnsRun r = runs[w.run];
-        tile::step2d_tile<float, kTX, kTY, kTNT, false, true>(r.g, r.p, r.io, w.bx, w.by, smem_raw);
-        __syncthreads();   // the next item reuses the tile
+        march::march2d_segment_iso<float, NT, kD>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
+        __syncthreads();   // the next item reuses the shared rings
     }
 }
+constexpr auto kIso64 = k_ens_march2d_iso<64>;
+constexpr auto kIso128 = k_ens_march2d_iso<128>;
 
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_ens_march2d(const EnsRun* __restrict__ runs,
@@ -152,10 +158,9 @@ struct lf_ens {
     cudaGraphExec_t gA, gB, gAB;
     int parity;                     // 0: the next step is step A of the cycle, 1: step B
     std::vector<Cursor> base;       // buffer cursors at the start of step A
-    int march_blocks[2];            // 64- and 128-thread march kernels
-    int tile_blocks;
-    int nitems[2];
-    EnsItem* d_items[2];
+    int march_blocks[4];            // 64- and 128-thread march kernels, compact then isotropic
+    int nitems[4];
+    EnsItem* d_items[4];
 };
 
 namespace {
@@ -176,8 +181,8 @@ struct Half {
     std::vector<EnsT*> ts;          // per extra sub-step s = 1 .. max_nsub - 1
 };
 
-int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsTile* tiles,
-            int ntiles, const std::vector<EnsTItem*>& titems, const std::vector<int>& ntitems, cudaGraphExec_t* out)
+int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, const std::vector<EnsTItem*>& titems,
+            const std::vector<int>& ntitems, cudaGraphExec_t* out)
 {
     cudaGraph_t graph;
     if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LF_ECUDA;
@@ -187,8 +192,11 @@ int capture(lf_ens* e, const std::vector<int>& halves, const Half* H, EnsTile* t
         if (e->nitems[1] > 0)
             kEns128<<<e->march_blocks[1], 128, MarchCfg<128>::BYTES, e->stream>>>(H[h].runs, e->d_items[1],
                                                                                e->nitems[1]);
-        if (ntiles > 0)
-            k_ens_tile2d_iso<<<e->tile_blocks, kTNT, TileCfg::BYTES, e->stream>>>(H[h].runs, tiles, ntiles);
+        if (e->nitems[2] > 0)
+            kIso64<<<e->march_blocks[2], 64, IsoCfg<64>::BYTES, e->stream>>>(H[h].runs, e->d_items[2], e->nitems[2]);
+        if (e->nitems[3] > 0)
+            kIso128<<<e->march_blocks[3], 128, IsoCfg<128>::BYTES, e->stream>>>(H[h].runs, e->d_items[3],
+                                                                              e->nitems[3]);
         for (size_t s = 0; s < H[h].ts.size(); ++s) {
             if (ntitems[s] == 0) continue;
             const int blocks = std::min(ntitems[s], 152 * 8);
@@ -250,16 +258,20 @@ int build(lf_ens* e)
             }
         }
     }
-    // work lists: march items per CTA width sorted by cost (longest lane
-    // first), the tiles of the isotropic runs, T tiles per sub-step
-    std::vector<EnsItem> items[2];
-    std::vector<EnsTile> tiles;
+    // work lists: march items per kind and CTA width (compact 64, 128,
+    // isotropic 64, 128) sorted by cost (longest segment first), T tiles per
+    // sub-step
+    std::vector<EnsItem> items[4];
     for (int r = 0; r < R; ++r) {
         const lf_ctx* c = e->runs[r];
         if (!e->active[r]) continue;
         if (c->g.stencil == LF_STENCIL_ISOTROPIC) {
-            for (int by = 0; by < (c->g.ny + kTY - 1) / kTY; ++by)
-                for (int bx = 0; bx < (c->g.nx + kTX - 1) / kTX; ++bx) tiles.push_back({r, bx, by});
+            const int wi = e->width[r] == 64 ? 2 : 3;
+            const int U = wi == 2 ? IsoCfg<64>::U : IsoCfg<128>::U;
+            const int H = std::min(e->rows[r], c->g.ny);      // as the single-run launcher sets it
+            const int strips = (c->g.nx + U - 1) / U;
+            for (int sg = 0; sg < (c->g.ny + H - 1) / H; ++sg)
+                for (int st = 0; st < strips; ++st) items[wi].push_back({r, st, sg, H});
             continue;
         }
         const int np = pairs_for(c->g.ny, e->rows[r]);
@@ -273,8 +285,12 @@ int build(lf_ens* e)
         const int ny = e->runs[w.run]->g.ny;
         return (ny + 2 * w.npairs - 1) / (2 * w.npairs);
     };
-    for (auto& it : items)
-        std::stable_sort(it.begin(), it.end(), [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
+    for (int k = 0; k < 2; ++k)
+        std::stable_sort(items[k].begin(), items[k].end(),
+                         [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
+    for (int k = 2; k < 4; ++k)
+        std::stable_sort(items[k].begin(), items[k].end(),
+                         [&](const EnsItem& a, const EnsItem& b) { return a.npairs > b.npairs; });
     std::vector<std::vector<EnsTItem>> titems(max_nsub > 1 ? max_nsub - 1 : 0);
     for (int s = 1; s < max_nsub; ++s)
         for (int r = 0; r < R; ++r) {
@@ -285,8 +301,8 @@ int build(lf_ens* e)
         }
     // one device block for everything
     auto a256 = [](size_t v) { return (v + 255) / 256 * 256; };
-    size_t bytes = 2 * a256(sizeof(EnsRun) * R) + a256(sizeof(EnsItem) * items[0].size()) +
-                   a256(sizeof(EnsItem) * items[1].size()) + a256(sizeof(EnsTile) * tiles.size());
+    size_t bytes = 2 * a256(sizeof(EnsRun) * R);
+    for (const auto& it : items) bytes += a256(sizeof(EnsItem) * it.size());
     for (int s = 1; s < max_nsub; ++s) bytes += 2 * a256(sizeof(EnsT) * R) + a256(sizeof(EnsTItem) * titems[s - 1].size());
     if (cudaMalloc((void**)&e->tables, bytes) != cudaSuccess) { cudaGetLastError(); return LF_ENOMEM; }
     unsigned char* p = e->tables;
@@ -297,15 +313,12 @@ int build(lf_ens* e)
         copies.push_back({p, {hr[h].data(), sizeof(EnsRun) * R}});
         p += a256(sizeof(EnsRun) * R);
     }
-    for (int wi = 0; wi < 2; ++wi) {
+    for (int wi = 0; wi < 4; ++wi) {
         e->d_items[wi] = (EnsItem*)p;
         e->nitems[wi] = (int)items[wi].size();
         copies.push_back({p, {items[wi].data(), sizeof(EnsItem) * items[wi].size()}});
         p += a256(sizeof(EnsItem) * items[wi].size());
     }
-    EnsTile* d_tiles = (EnsTile*)p;
-    copies.push_back({p, {tiles.data(), sizeof(EnsTile) * tiles.size()}});
-    p += a256(sizeof(EnsTile) * tiles.size());
     std::vector<EnsTItem*> d_titems;
     std::vector<int> ntitems;
     for (int s = 1; s < max_nsub; ++s) {
@@ -330,23 +343,24 @@ int build(lf_ens* e)
             cudaSuccess ||
         cudaFuncSetAttribute(kEns128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MarchCfg<128>::BYTES) !=
             cudaSuccess ||
-        cudaFuncSetAttribute(k_ens_tile2d_iso, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TileCfg::BYTES) !=
+        cudaFuncSetAttribute(kIso64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IsoCfg<64>::BYTES) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(kIso128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IsoCfg<128>::BYTES) !=
             cudaSuccess)
         return LF_ECUDA;
-    int per_sm[2] = {0, 0}, per_sm_t = 0, sms = 0, dev = 0;
+    int per_sm[4] = {0, 0, 0, 0}, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], kEns64, 64, MarchCfg<64>::BYTES);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], kEns128, 128, MarchCfg<128>::BYTES);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, k_ens_tile2d_iso, kTNT, TileCfg::BYTES);
-    for (int wi = 0; wi < 2; ++wi)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], kIso64, 64, IsoCfg<64>::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[3], kIso128, 128, IsoCfg<128>::BYTES);
+    for (int wi = 0; wi < 4; ++wi)
         e->march_blocks[wi] = std::max(1, std::min(e->nitems[wi], std::max(1, per_sm[wi]) * std::max(1, sms)));
-    e->tile_blocks = std::max(1, std::min((int)tiles.size(), std::max(1, per_sm_t) * std::max(1, sms)));
 
-    const int ntiles = (int)tiles.size();
-    if ((rc = capture(e, {0}, halves, d_tiles, ntiles, d_titems, ntitems, &e->gA)) != LF_OK) return rc;
-    if ((rc = capture(e, {1}, halves, d_tiles, ntiles, d_titems, ntitems, &e->gB)) != LF_OK) return rc;
-    if ((rc = capture(e, {0, 1}, halves, d_tiles, ntiles, d_titems, ntitems, &e->gAB)) != LF_OK) return rc;
+    if ((rc = capture(e, {0}, halves, d_titems, ntitems, &e->gA)) != LF_OK) return rc;
+    if ((rc = capture(e, {1}, halves, d_titems, ntitems, &e->gB)) != LF_OK) return rc;
+    if ((rc = capture(e, {0, 1}, halves, d_titems, ntitems, &e->gAB)) != LF_OK) return rc;
     e->parity = 0;
     return LF_OK;
 }
@@ -457,29 +471,33 @@ int lf_ens_tune(lf_ens* e, int reps)
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    // one pass of coordinate descent over the lattice sizes of the compact runs
-    std::vector<std::pair<int, int>> keys;
+    // one pass of coordinate descent over the (lattice size, stencil) classes
+    // of the runs
+    using Key = std::tuple<int, int, int>;
+    std::vector<Key> keys;
+    auto key_of = [&](const lf_ctx* c) { return Key{c->g.nx, c->g.ny, c->g.stencil}; };
     for (int r = 0; r < R; ++r) {
-        const lf_ctx* c = e->runs[r];
-        if (c->g.stencil == LF_STENCIL_ISOTROPIC || !e->active[r]) continue;
-        const auto key = std::make_pair(c->g.nx, c->g.ny);
+        if (!e->active[r]) continue;
+        const Key key = key_of(e->runs[r]);
         if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
     }
-    auto set_shape = [&](lf_ens* x, const std::pair<int, int>& key, int w, int h) {
+    auto set_shape = [&](lf_ens* x, const Key& key, int w, int h) {
         for (int r = 0; r < R; ++r)
-            if (e->runs[r]->g.stencil != LF_STENCIL_ISOTROPIC &&
-                std::make_pair(e->runs[r]->g.nx, e->runs[r]->g.ny) == key) {
+            if (key_of(e->runs[r]) == key) {
                 x->width[r] = w;
                 x->rows[r] = h;
             }
     };
     const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
     for (const auto& key : keys) {
+        const int ny = std::get<1>(key);
+        const bool iso = std::get<2>(key) == LF_STENCIL_ISOTROPIC;
         float best_ms = 1e30f;
         std::pair<int, int> best_wh{64, 16};
         for (int w : {64, 128})
             for (int h : cand) {
-                if (2 * h > key.second && h != cand[0]) continue;
+                // the packed march keeps two segments of h rows per CTA, the isotropic one one
+                if ((iso ? h > ny : 2 * h > ny) && h != cand[0]) continue;
                 set_shape(sc, key, w, h);
                 if ((rc = build(sc)) != LF_OK) break;
                 if ((rc = lf_ens_step(sc, 2)) != LF_OK) break;

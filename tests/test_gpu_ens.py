@@ -84,15 +84,16 @@ ISO_MEMBERS = [
     dict(nx=64, ny=64, xi=0.01, tau=1.0, seed=21, stencil="isotropic"),
     dict(nx=96, ny=80, xi=0.5, tau=0.6, seed=22, stencil="isotropic", t_wall_mode=1),   # 3 sub-steps, halfway T
     dict(nx=130, ny=70, xi=1e-3, tau=3.0, seed=23),                                    # compact, in the same launch
-    dict(nx=33, ny=17, xi=0.2, tau=0.8, seed=24, walls=0, stencil="isotropic"),         # periodic, ragged tiles
+    dict(nx=33, ny=17, xi=0.2, tau=0.8, seed=24, walls=0, stencil="isotropic"),         # periodic, ragged strips
 ]
 
 
 def test_isotropic_runs_in_an_ensemble_equal_single_runs():
-    """Runs with the isotropic stencils (tile items) and a compact run (march
-    items) in one ensemble, each equal bit for bit to the run stepped alone."""
+    """Runs with the isotropic stencils (one-lane row-march items) and a
+    compact run (packed march items) in one ensemble, each equal bit for bit
+    to the run stepped alone with the ensemble's shape."""
     ens = lf.Ensemble(ISO_MEMBERS)
-    ens.tune(reps=2)                     # skips the isotropic runs
+    ens.tune(reps=2)                     # shapes of every (lattice, stencil) class
     ens.step(5)
     ens.step(6)
     for r, m in enumerate(ISO_MEMBERS):
@@ -115,7 +116,7 @@ ORACLE_MEMBERS = [
     dict(nx=70, ny=37, xi=0.5, tau=0.6, seed=32, t_wall_mode=1),                    # 3 sub-steps, halfway T
     dict(nx=33, ny=17, xi=math.inf, tau=3.0, seed=33),                              # instantaneous quench
     dict(nx=41, ny=23, xi=0.2, tau=0.6, seed=34, walls=0),                          # periodic, 2 sub-steps
-    dict(nx=56, ny=30, xi=0.01, tau=3.0, seed=35, stencil="isotropic"),             # isotropic tile item
+    dict(nx=56, ny=30, xi=0.01, tau=3.0, seed=35, stencil="isotropic"),             # isotropic row-march items
     dict(nx=47, ny=29, xi=0.7, tau=0.6, seed=36, stencil="isotropic", walls=0),     # isotropic, periodic, 4 sub-steps
     dict(nx=120, ny=3, xi=0.01, tau=1.0, seed=37),                                  # thinner than the halo
 ]
