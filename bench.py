@@ -343,7 +343,7 @@ def run_ensemble(args):
         "config": {"workload": "ens96: 96 independent 2D runs, 24 each of 128^2, 256^2, 384^2, 512^2, xi "
                                "log-uniform in [1e-4, 1], tau in {0.6, 1, 3}, one persistent launch per step "
                                "replayed from a CUDA graph, CTA width and segment height from the autotuner"
-                               + (", isotropic 9-point stencils (one-lane row-march items)" if args.stencil == "isotropic" else ""),
+                               + (", isotropic 9-point stencils (two-lane isotropic march items)" if args.stencil == "isotropic" else ""),
                    "sites_per_step_all_runs": sites, "tuned_shapes": shapes,
                    "sequential_shapes": single_shapes,
                    "l2": "inputs (1 GB of state) larger than L2",

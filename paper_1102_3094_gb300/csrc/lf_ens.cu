@@ -6,10 +6,10 @@
 // two-lane row-marching step of lf_march2d_x2.cuh (two segments of a strip
 // marching away from their common row) -- followed, when some runs need extra
 // temperature sub-steps, by one launch per sub-step over the tiles of those
-// runs.  Runs with the isotropic stencils are (run, strip, segment) items of a
-// second persistent kernel that runs the one-lane isotropic row march
-// (lf_march2d_iso.cuh), the code a single isotropic run uses.  Every run
-// returns to its starting buffers
+// runs.  Runs with the isotropic stencils are (run, strip, pair) items of a
+// second persistent kernel that runs the two-lane isotropic row march
+// (lf_march2d_iso.cuh), the code a single isotropic FP32 run uses by default.
+// Every run returns to its starting buffers
 // after two steps (f and phi flip once per step, T flips nsub times), so two
 // steps are captured in one CUDA graph and replayed; single-step graphs handle
 // odd counts.
@@ -40,7 +40,7 @@ constexpr int kD = 3;
 template <int NT>
 using MarchCfg = march::March2<NT, kD>;
 template <int NT>
-using IsoCfg = march::MarchIso<float, NT, kD>;
+using IsoCfg = march::MarchIso2<NT, kD>;
 
 struct EnsRun {
     Geom g;
@@ -63,23 +63,26 @@ struct EnsTItem {
     int run, bx, by;
 };
 
-// Isotropic runs: items (run, strip, segment, rows per segment) in the
-// fields (run, strip, pair, npairs) of EnsItem; the launch bounds of the
-// single-run kernel, so both compile the same step.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ens_march2d_iso(const EnsRun* __restrict__ runs,
-                                                       const EnsItem* __restrict__ items, int nitems)
+// Isotropic runs: (run, strip, pair) items of the two-lane isotropic march,
+// with the launch bounds of the single-run kernel, so both compile the same
+// step.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_ens_march2d_iso(const EnsRun* __restrict__ runs,
+                                                             const EnsItem* __restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const EnsItem w = items[it];
         const EnsRun r = runs[w.run];
-        march::march2d_segment_iso<float, NT, kD>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
+        if (r.p.hydro)
+            march::march2d_pair_iso<NT, kD, true>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
+        else
+            march::march2d_pair_iso<NT, kD, false>(r.g, r.p, r.io, w.strip, w.pair, w.npairs, smem_raw);
         __syncthreads();   // the next item reuses the shared rings
     }
 }
-constexpr auto kIso64 = k_ens_march2d_iso<64>;
-constexpr auto kIso128 = k_ens_march2d_iso<128>;
+constexpr auto kIso64 = k_ens_march2d_iso<64, 6>;
+constexpr auto kIso128 = k_ens_march2d_iso<128, 3>;
 
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_ens_march2d(const EnsRun* __restrict__ runs,
@@ -259,24 +262,16 @@ int build(lf_ens* e)
         }
     }
     // work lists: march items per kind and CTA width (compact 64, 128,
-    // isotropic 64, 128) sorted by cost (longest segment first), T tiles per
+    // isotropic 64, 128) sorted by cost (longest lane first), T tiles per
     // sub-step
     std::vector<EnsItem> items[4];
     for (int r = 0; r < R; ++r) {
         const lf_ctx* c = e->runs[r];
         if (!e->active[r]) continue;
-        if (c->g.stencil == LF_STENCIL_ISOTROPIC) {
-            const int wi = e->width[r] == 64 ? 2 : 3;
-            const int U = wi == 2 ? IsoCfg<64>::U : IsoCfg<128>::U;
-            const int H = std::min(e->rows[r], c->g.ny);      // as the single-run launcher sets it
-            const int strips = (c->g.nx + U - 1) / U;
-            for (int sg = 0; sg < (c->g.ny + H - 1) / H; ++sg)
-                for (int st = 0; st < strips; ++st) items[wi].push_back({r, st, sg, H});
-            continue;
-        }
+        const bool iso = c->g.stencil == LF_STENCIL_ISOTROPIC;
         const int np = pairs_for(c->g.ny, e->rows[r]);
-        const int wi = e->width[r] == 64 ? 0 : 1;
-        const int U = wi == 0 ? MarchCfg<64>::U : MarchCfg<128>::U;
+        const int wi = (e->width[r] == 64 ? 0 : 1) + (iso ? 2 : 0);
+        const int U = (wi & 1) == 0 ? MarchCfg<64>::U : MarchCfg<128>::U;   // 56 or 120 columns for both kinds
         const int strips = (c->g.nx + U - 1) / U;
         for (int pr = 0; pr < np; ++pr)
             for (int st = 0; st < strips; ++st) items[wi].push_back({r, st, pr, np});
@@ -285,12 +280,8 @@ int build(lf_ens* e)
         const int ny = e->runs[w.run]->g.ny;
         return (ny + 2 * w.npairs - 1) / (2 * w.npairs);
     };
-    for (int k = 0; k < 2; ++k)
-        std::stable_sort(items[k].begin(), items[k].end(),
-                         [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
-    for (int k = 2; k < 4; ++k)
-        std::stable_sort(items[k].begin(), items[k].end(),
-                         [&](const EnsItem& a, const EnsItem& b) { return a.npairs > b.npairs; });
+    for (auto& it : items)
+        std::stable_sort(it.begin(), it.end(), [&](const EnsItem& a, const EnsItem& b) { return lane(a) > lane(b); });
     std::vector<std::vector<EnsTItem>> titems(max_nsub > 1 ? max_nsub - 1 : 0);
     for (int s = 1; s < max_nsub; ++s)
         for (int r = 0; r < R; ++r) {
@@ -491,13 +482,11 @@ int lf_ens_tune(lf_ens* e, int reps)
     const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128};
     for (const auto& key : keys) {
         const int ny = std::get<1>(key);
-        const bool iso = std::get<2>(key) == LF_STENCIL_ISOTROPIC;
         float best_ms = 1e30f;
         std::pair<int, int> best_wh{64, 16};
         for (int w : {64, 128})
             for (int h : cand) {
-                // the packed march keeps two segments of h rows per CTA, the isotropic one one
-                if ((iso ? h > ny : 2 * h > ny) && h != cand[0]) continue;
+                if (2 * h > ny && h != cand[0]) continue;     // two segments of h rows per CTA
                 set_shape(sc, key, w, h);
                 if ((rc = build(sc)) != LF_OK) break;
                 if ((rc = lf_ens_step(sc, 2)) != LF_OK) break;

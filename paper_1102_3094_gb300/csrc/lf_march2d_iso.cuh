@@ -35,6 +35,7 @@
 #pragma once
 
 #include "lf_march2d.cuh"
+#include "lf_march2d_x2.cuh"      // packed FP32x2 helpers, pair_rows
 
 namespace lf {
 namespace march {
@@ -328,6 +329,354 @@ __device__ __forceinline__ void march2d_segment_iso(const Geom& g, const Phys<R>
         }
 
         // ---- shift the windows ---------------------------------------------------------
+        ph7 = ph6; ph6 = ph5; ph5 = ph4; ph4 = ph3; ph3 = ph2; ph2 = ph1; ph1 = phk;
+        T3 = T2; T2 = T1; T1 = Tk;
+        ps2 = ps1; ps1 = psk;
+        dx2 = dx1; dy2 = dy1; dx1 = dxk; dy1 = dyk;
+        mu1 = muk;
+        pxy1 = pxyk; pyy1 = pyyk;
+        gy1 = gyk;
+        lm2 = lm1; lm1 = lmk;
+        sk = (sk + 1 == M::SIN) ? 0 : sk + 1;
+    }
+    cp_wait<0>();
+    if (__any_sync(0xffffffffu, !isfinite(probe)) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
+}  // namespace march
+}  // namespace lf
+
+// ===========================================================================
+// The same march on two segments of a strip at once (FP32): lane .x covers
+// the rows [ya, ya + ha), lane .y the rows [yb, yb + hb) just above them
+// (the two halves of a pair of segments, as pair_rows splits them), both
+// marching upwards in lockstep with their own halo rows, every field in the
+// lanes of float2 values and the arithmetic on packed FP32x2 instructions.
+// The wall rules and the output ranges are applied per lane.
+// ===========================================================================
+namespace lf {
+namespace march {
+
+template <int NT, int D>
+struct MarchIso2 {
+    static constexpr int U = NT - 8;
+    static constexpr int SIN = D + 1;
+    static constexpr int SF = D + 1;
+    static constexpr int PHI = 0;
+    static constexpr int TT = PHI + SIN * NT;
+    static constexpr int F = TT + SIN * NT;
+    static constexpr int PSI = F + SF * 9 * NT;
+    static constexpr int MU = PSI + 2 * NT;
+    static constexpr int PXX = MU + 2 * NT;
+    static constexpr int PXY = PXX + 2 * NT;
+    static constexpr int PYY = PXY + 2 * NT;
+    static constexpr int GX = PYY + 2 * NT;
+    static constexpr int GY = GX + 2 * NT;
+    static constexpr int TOTAL = GY + 2 * NT;          // float2 elements
+    static constexpr size_t BYTES = sizeof(float2) * TOTAL;
+};
+
+struct Row9x2 {
+    float2 s, l, ax;
+};
+
+__device__ __forceinline__ Row9x2 row9x2(float2 w, float2 c, float2 e)
+{
+    const float2 ew = add2(e, w);
+    Row9x2 q;
+    q.s = fma2(v2(4.f), c, ew);
+    q.l = fma2(v2(-20.f), c, mul2(v2(4.f), ew));
+    q.ax = sub2(e, w);
+    return q;
+}
+
+struct Slide9x2 {
+    float2 l = v2(0.f), gx = v2(0.f), s_prev = v2(0.f), s = v2(0.f), ax = v2(0.f);
+    __device__ __forceinline__ void push(const Row9x2& q, float2& lap, float2& dx, float2& dy)
+    {
+        lap = mul2(add2(l, q.s), v2(1.f / 6.f));
+        dx = mul2(add2(gx, q.ax), v2(1.f / 12.f));
+        dy = mul2(sub2(q.s, s_prev), v2(1.f / 12.f));
+        l = add2(q.l, s);
+        gx = fma2(v2(4.f), q.ax, ax);
+        s_prev = s;
+        s = q.s;
+        ax = q.ax;
+    }
+};
+
+template <int NT, int D, bool HYDRO>
+__device__ __forceinline__ void march2d_pair_iso(const Geom& g, const Phys<float>& p, const StepIO<float>& io,
+                                                 int strip, int pair, int npairs, unsigned char* smem_raw)
+{
+    using L = D2Q9;
+    using M = MarchIso2<NT, D>;
+    static_assert(M::SF == 4, "population ring indexed with & 3");
+    float2* sm = reinterpret_cast<float2*>(smem_raw);
+    float2* sphi = sm + M::PHI;
+    float2* sT = sm + M::TT;
+    float2* sf = sm + M::F;
+    float2* spsi = sm + M::PSI;
+    float2* smu = sm + M::MU;
+    float2* sPxx = sm + M::PXX;
+    float2* sPxy = sm + M::PXY;
+    float2* sPyy = sm + M::PYY;
+    float2* sgx = sm + M::GX;
+    float2* sgy = sm + M::GY;
+
+    const int t = threadIdx.x;
+    const int nx = g.nx, ny = g.ny, pitch = g.pitch, walls = g.walls;
+    const int plane = (int)g.plane;
+    const int x0 = strip * M::U;
+    int mid, ha, hb;
+    pair_rows(ny, npairs, pair, mid, ha, hb);      // rows [mid - ha, mid) and [mid, mid + hb)
+    const int ya = mid - ha, yb = mid;             // first row of lane .x / .y
+    const int hmax = ha > hb ? ha : hb;
+    const int cx = x0 - 4 + t;
+    const int gx = wrap_any(cx, nx);
+    const int gxm = wrap_any(cx - 1, nx), gxp = wrap_any(cx + 1, nx);
+    const bool own = t >= 4 && t < NT - 4 && cx < nx;
+    const bool r3 = t >= 1 && t < NT - 1;
+    const bool r2 = t >= 2 && t < NT - 2;
+    const bool has_u = t >= 3 && t < NT - 3;
+    const float2 half = v2(0.5f);
+    const float omega = p.inv_tau, keep = 1.f - p.inv_tau;
+    const bool t_half = walls && g.t_mode == LF_TWALL_HALFWAY;
+    const bool t_lay = walls && g.t_mode == LF_TWALL_LAYERS;
+    const int jphi = hmax + 3, jend = hmax + 6;   // relative rows j of both lanes: row ya + j / yb + j
+
+    Slide9x2 sl_phi, sl_T, sl_psi, sl_mu, sl_gx, sl_gy;
+    float2 ph1 = v2(0.f), ph2 = v2(0.f), ph3 = v2(0.f), ph4 = v2(0.f), ph5 = v2(0.f), ph6 = v2(0.f), ph7 = v2(0.f);
+    float2 T1 = v2(0.f), T2 = v2(0.f), T3 = v2(0.f);
+    float2 ps1 = v2(0.f), ps2 = v2(0.f);
+    float2 dx1 = v2(0.f), dy1 = v2(0.f), dx2 = v2(0.f), dy2 = v2(0.f);
+    float2 mu1 = v2(0.f), pxy1 = v2(0.f), pyy1 = v2(0.f), gy1 = v2(0.f);
+    float2 lm1 = v2(0.f), lm2 = v2(0.f);
+    float2 aFx = v2(0.f), aFy = v2(0.f), bFx = v2(0.f), bFy = v2(0.f);
+    float probe = 0.f;
+
+    int s_issue = 0;
+    auto issue = [&](int jj) {
+        const int q = jj + D;                        // phi / T row
+        if (q <= jphi) {
+            const int oa = map_row(ya + q, ny, walls) * pitch + gx, ob = map_row(yb + q, ny, walls) * pitch + gx;
+            float* d = reinterpret_cast<float*>(&sphi[s_issue * NT + t]);
+            float* e = reinterpret_cast<float*>(&sT[s_issue * NT + t]);
+            cp_async<4>(d, io.phi_in + oa);
+            cp_async<4>(d + 1, io.phi_in + ob);
+            cp_async<4>(e, io.T_in + oa);
+            cp_async<4>(e + 1, io.T_in + ob);
+        }
+        s_issue = (s_issue + 1 == M::SIN) ? 0 : s_issue + 1;
+        const int qf = jj + D - 5;                   // population row
+        if (HYDRO && has_u && qf >= -1 && qf <= hmax) {
+            float* dst = reinterpret_cast<float*>(sf + ((qf + 4) & 3) * L::Q * NT + t);
+            const int ra = ya + qf, rb = yb + qf;
+            if (qf <= ha && !(walls && (ra < 0 || ra >= ny))) {
+                const float* src = io.f_in + ((walls ? ra : map_row(ra, ny, 0)) * pitch + gx);
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) cp_async<4>(dst + 2 * i * NT, src + i * plane);
+            }
+            if (qf <= hb && !(walls && (rb < 0 || rb >= ny))) {
+                const float* src = io.f_in + ((walls ? rb : map_row(rb, ny, 0)) * pitch + gx);
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) cp_async<4>(dst + 2 * i * NT + 1, src + i * plane);
+            }
+        }
+        cp_commit();
+    };
+
+    for (int jj = -4 - D; jj < -4; ++jj) issue(jj);
+
+    int sk = 0;
+#pragma unroll 1
+    for (int j = -4; j <= jend; ++j) {
+        cp_wait<D - 1>();
+        __syncthreads();
+        issue(j);
+        const int par = (j + 4) & 1;
+
+        // ---- phi, T of row j: psi, grad phi, T(t+1) at j - 1 -------------------------
+        float2 phk = v2(0.f), psk = v2(0.f), dxk = v2(0.f), dyk = v2(0.f), Tk = v2(0.f);
+        if (j <= jphi) {
+            phk = sphi[sk * NT + t];
+            Tk = sT[sk * NT + t];
+            if (r3) {
+                sl_phi.push(row9x2(sphi[sk * NT + t - 1], phk, sphi[sk * NT + t + 1]), psk, dxk, dyk);
+                spsi[(par ^ 1) * NT + t] = psk;
+            }
+            if (own) {
+                Row9x2 qT = row9x2(sT[sk * NT + t - 1], Tk, sT[sk * NT + t + 1]);
+                if (t_half) {
+                    const float tw12 = 12.f * p.T_w;
+                    if (ya + j == 0) sl_T.s.x = tw12 - qT.s.x;      // the row below is the halfway ghost
+                    if (yb + j == 0) sl_T.s.y = tw12 - qT.s.y;
+                    if (ya + j == ny) qT.s.x = tw12 - sl_T.s.x;     // the row above is the halfway ghost
+                    if (yb + j == ny) qT.s.y = tw12 - sl_T.s.y;
+                }
+                float2 lapT, u0, u1;
+                sl_T.push(qT, lapT, u0, u1);
+                const int m = j - 1;
+                float2 Tn = T1;
+                if (p.t_update) {
+                    Tn = fma2(v2(p.dxi), lapT, T1);
+                    if (t_lay && (ya + m == 0 || ya + m == ny - 1)) Tn.x = p.T_w;
+                    if (t_lay && (yb + m == 0 || yb + m == ny - 1)) Tn.y = p.T_w;
+                }
+                if (m >= 0 && m < ha) { probe += Tn.x; io.T_out[(ya + m) * pitch + gx] = Tn.x; }
+                if (m >= 0 && m < hb) { probe += Tn.y; io.T_out[(yb + m) * pitch + gx] = Tn.y; }
+            }
+        }
+
+        // ---- psi of row j - 2: lam, grad psi, mu, P of row j - 3 ---------------------
+        float2 muk = v2(0.f), pxyk = v2(0.f), pyyk = v2(0.f);
+        if (r2 && j >= -1 && j <= hmax + 4) {
+            float2 lam, dsx, dsy;
+            sl_psi.push(row9x2(spsi[par * NT + t - 1], ps1, spsi[par * NT + t + 1]), lam, dsx, dsy);
+            if (j >= 1) {
+                const float2 ph = ph3, ps = ps2;
+                const float2 av = mul2(sub2(T3, v2(p.Tc)), v2(p.inv_Tc));
+                const float2 phsq = mul2(ph, ph);
+                muk = fma2(v2(p.c), lam, fma2(v2(-p.kappa), ps, mul2(ph, fma2(v2(p.b), phsq, av))));
+                smu[(par ^ 1) * NT + t] = muk;
+                if constexpr (HYDRO) {
+                    const float2 dpx = dx2, dpy = dy2;
+                    const float2 gp2 = fma2(dpx, dpx, mul2(dpy, dpy));
+                    const float2 gpgs = fma2(dpx, dsx, mul2(dpy, dsy));
+                    float2 iso = mul2(phsq, fma2(v2(0.75f * p.b), phsq, mul2(half, av)));
+                    iso = fma2(v2(-p.kappa), fma2(half, gp2, mul2(ph, ps)), iso);
+                    iso = fma2(v2(p.c), add2(fma2(ph, lam, mul2(half, mul2(ps, ps))), gpgs), iso);
+                    const float2 c2 = v2(-2.f * p.c);
+                    pxyk = fma2(v2(p.kappa), mul2(dpx, dpy), mul2(v2(-p.c), fma2(dpx, dsy, mul2(dpy, dsx))));
+                    pyyk = fma2(v2(p.kappa), mul2(dpy, dpy), fma2(c2, mul2(dpy, dsy), iso));
+                    sPxx[(par ^ 1) * NT + t] = fma2(v2(p.kappa), mul2(dpx, dpx), fma2(c2, mul2(dpx, dsx), iso));
+                    sPxy[(par ^ 1) * NT + t] = pxyk;
+                    sPyy[(par ^ 1) * NT + t] = pyyk;
+                }
+            }
+        }
+
+        // ---- P of row j - 4: F at j - 5; n, u, g; collide and push row j - 5 -----------
+        float2 gyk = v2(0.f);
+        if (HYDRO && has_u && j >= 2 && j <= hmax + 5) {
+            const int q = par * NT + t;
+            const float2 axx = sub2(sPxx[q + 1], sPxx[q - 1]);
+            const float2 axy = sub2(sPxy[q + 1], sPxy[q - 1]);
+            const float2 sxy = fma2(v2(4.f), pxy1, add2(sPxy[q + 1], sPxy[q - 1]));
+            const float2 syy = fma2(v2(4.f), pyy1, add2(sPyy[q + 1], sPyy[q - 1]));
+            const float2 m12 = v2(-1.f / 12.f);
+            const float2 Fx = mul2(add2(aFx, add2(axx, sxy)), m12);
+            const float2 Fy = mul2(add2(aFy, add2(axy, syy)), m12);
+            aFx = fma2(v2(4.f), axx, bFx);
+            aFy = fma2(v2(4.f), axy, bFy);
+            bFx = sub2(axx, sxy);
+            bFy = sub2(axy, syy);
+            const int m = j - 5;
+            float2 gxv = v2(0.f);
+            if (j >= 4) {
+                const int ma = ya + m, mb = yb + m;
+                const bool gha = walls && (ma < 0 || ma >= ny), ghb = walls && (mb < 0 || mb >= ny);
+                const float2* fr = sf + ((m + 4) & 3) * L::Q * NT + t;
+                float2 df[L::Q];
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i) {
+                    df[i] = fr[i * NT];
+                    if (gha) df[i].x = 0.f;
+                    if (ghb) df[i].y = 0.f;
+                }
+                const float2 dn = add2(add2(add2(df[0], df[1]), add2(df[2], df[3])),
+                                       add2(add2(df[4], df[5]), add2(add2(df[6], df[7]), df[8])));
+                const float2 jx = add2(add2(sub2(df[1], df[3]), sub2(df[5], df[6])), sub2(df[8], df[7]));
+                const float2 jy = add2(add2(sub2(df[2], df[4]), sub2(df[5], df[8])), sub2(df[6], df[7]));
+                const float2 n = add2(v2(p.n0), dn);
+                const float2 inv_n = make_float2(__frcp_rn(n.x), __frcp_rn(n.y));
+                const float2 vx = mul2(fma2(half, Fx, jx), inv_n), vy = mul2(fma2(half, Fy, jy), inv_n);
+                gxv = mul2(ph5, vx);
+                gyk = mul2(ph5, vy);
+                if (gha) { gxv.x = 0.f; gyk.x = 0.f; }
+                if (ghb) { gxv.y = 0.f; gyk.y = 0.f; }
+                const bool col_a = own && m >= 0 && m < ha, col_b = own && m >= 0 && m < hb;
+                if (col_a || col_b) {
+                    const float2 on = mul2(v2(omega), n);
+                    const float2 uu = fma2(vx, vx, mul2(vy, vy));
+                    const float2 uF = fma2(vx, Fx, mul2(vy, Fy));
+                    const float2 C0 = fma2(v2(-3.f * p.guo), uF, fma2(mul2(v2(-1.5f), on), uu, mul2(v2(omega), dn)));
+                    const float2 a3 = mul2(v2(3.f), on), a45 = mul2(v2(4.5f), on);
+                    const float2 g3 = v2(3.f * p.guo), g9 = v2(9.f * p.guo);
+                    const float2 kp = v2(keep);
+                    float2 post[L::Q];
+                    post[0] = fma2(kp, df[0], mul2(v2((float)L::w(0)), C0));
+                    auto pair_ = [&](int i, int jq, float2 sv, float2 ev) {
+                        const float2 sym = fma2(sv, fma2(a45, sv, mul2(g9, ev)), C0);
+                        const float2 anti = fma2(a3, sv, mul2(g3, ev));
+                        const float2 wi = v2((float)L::w(i));
+                        post[i] = fma2(kp, df[i], mul2(wi, add2(sym, anti)));
+                        post[jq] = fma2(kp, df[jq], mul2(wi, sub2(sym, anti)));
+                    };
+                    pair_(1, 3, vx, Fx);
+                    pair_(2, 4, vy, Fy);
+                    pair_(5, 7, add2(vx, vy), add2(Fx, Fy));
+                    pair_(6, 8, sub2(vy, vx), sub2(Fy, Fx));
+                    float* out = io.f_out;
+                    auto push = [&](auto lane_tag, int r) {
+                        constexpr int LN = decltype(lane_tag)::value;
+                        auto pv = [&](int i) { return LN == 0 ? post[i].x : post[i].y; };
+                        probe += LN == 0 ? n.x : n.y;
+                        const int site = r * pitch + gx;
+                        const int up = ((r + 1 == ny) ? 0 : r + 1) * pitch;
+                        const int dn_ = ((r == 0) ? ny - 1 : r - 1) * pitch;
+                        const int mid_ = r * pitch;
+                        const bool wall_lo = walls && r == 0, wall_hi = walls && r == ny - 1;
+                        out[site] = pv(0);
+                        auto st = [&](int i, int jq, int off_i, int off_j, bool bb_i, bool bb_j) {
+                            if (bb_i) out[jq * plane + site] = pv(i); else out[i * plane + off_i] = pv(i);
+                            if (bb_j) out[i * plane + site] = pv(jq); else out[jq * plane + off_j] = pv(jq);
+                        };
+                        st(1, 3, mid_ + gxp, mid_ + gxm, false, false);
+                        st(2, 4, up + gx, dn_ + gx, wall_hi, wall_lo);
+                        st(5, 7, up + gxp, dn_ + gxm, wall_hi, wall_lo);
+                        st(6, 8, up + gxm, dn_ + gxp, wall_hi, wall_lo);
+                    };
+                    if (col_a) push(std::integral_constant<int, 0>{}, ma);
+                    if (col_b) push(std::integral_constant<int, 1>{}, mb);
+                }
+            }
+            sgx[(par ^ 1) * NT + t] = gxv;
+            sgy[(par ^ 1) * NT + t] = gyk;
+        }
+
+        // ---- mu of row j - 4, g of row j - 6: phi(t+1) of row j - 7 -------------------
+        float2 lmk = v2(0.f);
+        if (own && j >= 3 && j <= jend) {
+            float2 u0, u1;
+            if (j <= hmax + 4) sl_mu.push(row9x2(smu[par * NT + t - 1], mu1, smu[par * NT + t + 1]), lmk, u0, u1);
+            float2 div = v2(0.f);
+            if (HYDRO && j >= 5) {
+                const int r = j - 6;
+                const int q = par * NT + t;
+                Row9x2 qx = row9x2(sgx[q - 1], v2(0.f), sgx[q + 1]);
+                Row9x2 qy = row9x2(sgy[q - 1], gy1, sgy[q + 1]);
+                if (walls) {
+                    // the row below the wall row is its image (g_x even, g_y odd)
+                    if (ya + r == 0) { sl_gx.ax.x = qx.ax.x; sl_gy.s.x = -qy.s.x; }
+                    if (yb + r == 0) { sl_gx.ax.y = qx.ax.y; sl_gy.s.y = -qy.s.y; }
+                    // the row above row ny - 1 is the image of row ny - 1
+                    if (ya + r == ny) { qx.ax.x = sl_gx.ax.x; qy.s.x = -sl_gy.s.x; }
+                    if (yb + r == ny) { qx.ax.y = sl_gx.ax.y; qy.s.y = -sl_gy.s.y; }
+                }
+                float2 dgx, dgy;
+                sl_gx.push(qx, u0, dgx, u1);
+                sl_gy.push(qy, u0, u1, dgy);
+                div = add2(dgx, dgy);
+            }
+            const int m = j - 7;
+            if ((HYDRO ? j >= 5 : true) && m >= 0) {
+                const float2 phn = fma2(v2(p.Gamma), lm2, sub2(ph7, div));
+                if (m < ha) { probe += phn.x; io.phi_out[(ya + m) * pitch + gx] = phn.x; }
+                if (m < hb) { probe += phn.y; io.phi_out[(yb + m) * pitch + gx] = phn.y; }
+            }
+        }
+
         ph7 = ph6; ph6 = ph5; ph5 = ph4; ph4 = ph3; ph3 = ph2; ph2 = ph1; ph1 = phk;
         T3 = T2; T2 = T1; T1 = Tk;
         ps2 = ps1; ps1 = psk;

@@ -70,6 +70,14 @@ __global__ void __launch_bounds__(NT) k_march2d_iso(Geom g, Phys<R> p, StepIO<R>
     march::march2d_segment_iso<R, NT, D>(g, p, io, blockIdx.x, blockIdx.y, H, smem_raw);
 }
 
+// The isotropic row march on two segments per CTA (packed FP32x2 lanes).
+template <int NT, int D, bool HYDRO, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_march2d_iso_x2(Geom g, Phys<float> p, StepIO<float> io, int npairs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    march::march2d_pair_iso<NT, D, HYDRO>(g, p, io, blockIdx.x, blockIdx.y, npairs, smem_raw);
+}
+
 // Two segments per CTA in the lanes of float2 (packed FP32x2 arithmetic).
 template <int NT, int D, bool HYDRO, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_march2d_x2(Geom g, Phys<float> p, StepIO<float> io, int npairs)
@@ -109,6 +117,24 @@ cudaError_t launch_march(const Geom& g, const Phys<R>& p, const StepIO<R>& io, c
     const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
     dim3 grid((g.nx + M::U - 1) / M::U, (g.ny + H - 1) / H);
     kern<<<grid, NT, M::BYTES, s>>>(g, p, io, H);
+    return cudaGetLastError();
+}
+
+template <int NT, int D, bool HYDRO, int MINB>
+cudaError_t launch_march_iso_x2(const Geom& g, const Phys<float>& p, const StepIO<float>& io, cudaStream_t s)
+{
+    using M = march::MarchIso2<NT, D>;
+    auto kern = k_march2d_iso_x2<NT, D, HYDRO, MINB>;
+    static unsigned long long attr_done = 0;
+    cudaError_t e = raise_smem_limit(kern, (int)M::BYTES, &attr_done);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    if ((e = device_sms(&sms)) != cudaSuccess) return e;
+    const int H = march::march2_rows_for(g.nx, g.ny, M::U, g.tune & 0xFFFF, sms);
+    int npairs = (g.ny + 2 * H - 1) / (2 * H);
+    if (npairs > g.ny / 2) npairs = g.ny / 2;       // every lane keeps at least one row
+    dim3 grid((g.nx + M::U - 1) / M::U, npairs);
+    kern<<<grid, NT, M::BYTES, s>>>(g, p, io, npairs);
     return cudaGetLastError();
 }
 
@@ -168,7 +194,16 @@ __global__ void k_tsub2d_iso(Geom g, Phys<R> p, const R* __restrict__ Tin, R* __
 template <typename R>
 cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
 {
-    if (g.stencil == LF_STENCIL_ISOTROPIC) {           // the row march (both march variants) or the tile kernel
+    if (g.stencil == LF_STENCIL_ISOTROPIC) {           // the row marches or the tile kernel
+        if constexpr (sizeof(R) == 4) {
+            if (!aux && g.variant == LF_VARIANT_MARCH2 && g.ny >= 2) {
+                if ((g.tune >> 16) == 1)
+                    return p.hydro ? launch_march_iso_x2<64, 3, true, 6>(g, p, io, s)
+                                   : launch_march_iso_x2<64, 3, false, 6>(g, p, io, s);
+                return p.hydro ? launch_march_iso_x2<128, 3, true, 3>(g, p, io, s)
+                               : launch_march_iso_x2<128, 3, false, 3>(g, p, io, s);
+            }
+        }
         if (!aux && (g.variant == LF_VARIANT_MARCH || g.variant == LF_VARIANT_MARCH2) && g.ny >= 2)
             return (g.tune >> 16) == 1 ? launch_march_iso<R, 64, 3>(g, p, io, s) : launch_march_iso<R, 128, 3>(g, p, io, s);
         if constexpr (sizeof(R) == 4)

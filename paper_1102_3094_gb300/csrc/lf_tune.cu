@@ -43,11 +43,13 @@ std::vector<std::pair<int, int>> candidates(const lf_ctx* c)
     const lf::Geom& g = c->g;
     const bool iso = g.stencil == LF_STENCIL_ISOTROPIC;
     if (g.d == 2) {
-        if (iso) {                                   // the isotropic row march (128- or 64-thread strips), the tile kernel
+        if (iso) {                                   // the isotropic row marches (two lanes in FP32, one), the tile kernel
             const int heights[] = {0, 4, 8, 12, 16, 24, 32, 48, 64};
             for (int w = 0; w < 2; ++w)
-                for (int h : heights)
+                for (int h : heights) {
+                    if (c->prec == LF_FP32 && (h == 0 || 2 * h <= g.ny)) v.push_back({LF_VARIANT_MARCH2, (w << 16) | h});
                     if (h <= g.ny) v.push_back({LF_VARIANT_MARCH, (w << 16) | h});
+                }
             v.push_back({LF_VARIANT_TILE, 0});
             return v;
         }

@@ -89,7 +89,7 @@ ISO_MEMBERS = [
 
 
 def test_isotropic_runs_in_an_ensemble_equal_single_runs():
-    """Runs with the isotropic stencils (one-lane row-march items) and a
+    """Runs with the isotropic stencils (two-lane isotropic march items) and a
     compact run (packed march items) in one ensemble, each equal bit for bit
     to the run stepped alone with the ensemble's shape."""
     ens = lf.Ensemble(ISO_MEMBERS)

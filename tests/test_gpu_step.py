@@ -96,13 +96,15 @@ def test_aux_and_step_parity(case, prec, variant):
     _check_aux_and_step(sim, st, prec)
 
 
-@pytest.mark.parametrize("variant", ["march", "march-h5", "march-h1", "march-n64-h3", "march2", "tile"])
+@pytest.mark.parametrize("variant", ["march", "march-h5", "march-h1", "march-n64-h3", "march2", "march2-h5", "march2-h1",
+                                     "march2-n64", "tile"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(str(c[k]) for k in ("nx", "ny")) + str(c))
 def test_isotropic_stencil_parity(case, prec, variant):
-    """Isotropic 9-point stencils: the row march with sliding row sums
-    (LF_VARIANT_MARCH, segments of the model's height and of 5, 1 and 3 rows,
-    128- and 64-thread strips) and the tile kernel (the other variants)."""
+    """Isotropic 9-point stencils: the row march with sliding row sums, one
+    lane (LF_VARIANT_MARCH) and, in FP32, two packed lanes (LF_VARIANT_MARCH2;
+    FP64 runs the one-lane march), segments of the model's height and of 5, 1
+    and 3 rows, 128- and 64-thread strips; and the tile kernel."""
     sim, cfg, st = make_pair(case, prec, variant=variant, stencil="isotropic")
     _check_aux_and_step(sim, st, prec)
 
