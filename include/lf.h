@@ -250,8 +250,8 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     marches down a segment of (param & 0xFFFF) rows (0 = chosen from the
  *     lattice size), inputs prefetched with cp.async; (param >> 16) == 1
  *     selects CTAs of 64 threads (56 columns) instead of 128 (120 columns);
- *     with the isotropic stencils both march variants run this one-lane
- *     march, with sliding row sums;
+ *     with the isotropic stencils this one-lane march runs with sliding row
+ *     sums;
  *   LF_VARIANT_TILE: one CTA per 2D tile, each stage of the step on the whole
  *     tile in shared memory (`param` ignored);
  *   LF_VARIANT_MARCH2 (default for 2D FP32; FP64 contexts run LF_VARIANT_MARCH
@@ -259,7 +259,9 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     march away from their common row, carried in the two lanes of packed
  *     FP32x2 arithmetic; (param & 0xFFFF) = rows per segment (0 = chosen from
  *     the lattice size and the SM count), (param >> 16) == 1 selects CTAs of
- *     64 threads (56 columns) instead of 128 (120 columns);
+ *     64 threads (56 columns) instead of 128 (120 columns); with the
+ *     isotropic stencils the two segments are the lower and upper halves of a
+ *     pair, both marching upwards, with sliding row sums;
  *   LF_VARIANT_SPLIT3 (3D default): three passes per step -- mu and F by a
  *     plane march ((param & 0xFFFF) = planes per segment, 0 = automatic),
  *     then collision and streaming, then the phi and T updates by a column
@@ -294,7 +296,8 @@ int lf_set_kernel_variant(lf_ctx* ctx, int variant, int param);
  * its state, for the duration of the call; it waits for ctx's stream.  Any of
  * variant, param, ms_per_step may be NULL; on success they receive the choice
  * and its time per step in milliseconds.  For the isotropic 2D step the
- * candidates are the one-lane row march and the tile kernel.  Returns LF_EINVAL
+ * candidates are the two-lane (FP32) and one-lane row marches and the tile
+ * kernel.  Returns LF_EINVAL
  * for reps < 1 or an ensemble member. */
 int lf_tune(lf_ctx* ctx, int reps, int* variant, int* param, double* ms_per_step);
 
