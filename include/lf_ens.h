@@ -11,9 +11,10 @@
  * graph.  Results are bit-identical to stepping every run alone with lf_step
  * under LF_VARIANT_MARCH2 with param = lf_ens_param(e, r) (the per-site
  * arithmetic is the same code and the rows are split the same way).  Runs
- * created with params.stencil = LF_STENCIL_ISOTROPIC are (run, 64 x 16 tile)
- * items of a second persistent kernel, the tile form a single isotropic 2D run
- * uses, and are bit-identical to that run stepped alone.
+ * created with params.stencil = LF_STENCIL_ISOTROPIC are (run, strip, segment
+ * pair) items of a second persistent kernel, the two-lane isotropic march a
+ * single isotropic FP32 run takes under LF_VARIANT_MARCH2, and are
+ * bit-identical to that run stepped alone with the same param.
  *
  * Restrictions: every run is two-dimensional (d = 2), LF_FP32, ny >= 2.
  * Conventions (return codes, layouts, ownership) are those of lf.h.
