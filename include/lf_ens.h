@@ -46,13 +46,13 @@ int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const 
  * threads = 120-column strips) and segment height (1 .. 128 rows, at most
  * ny / 2), reps timed steps each (CUDA events), and keeps the shape of the
  * fastest batch.  The objective is the ensemble's throughput, not one run's
- * latency.  The runs' states are not touched.  Isotropic runs are 64 x 16
- * tile items, the one shape of their kernel, and are not tuned.  Rebuilds the
- * work lists and the graphs. */
+ * latency.  The runs' states are not touched.  Compact and isotropic runs of
+ * one lattice size are separate classes, tuned one after the other.
+ * Rebuilds the work lists and the graphs. */
 int lf_ens_tune(lf_ens* e, int reps);
 
 /* Rows per segment the work list uses for run r (after tuning, or the
- * default min(16, ny / 2)); not used by isotropic runs. */
+ * default min(16, ny / 2)). */
 int lf_ens_rows(const lf_ens* e, int run);
 
 /* The LF_VARIANT_MARCH2 param of run r's shape: (1 << 16 for 64-thread CTAs,
