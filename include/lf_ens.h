@@ -39,16 +39,15 @@ typedef struct lf_ens lf_ens;
 int lf_ens_create(int nruns, const lf_grid* grids, const lf_walls* walls, const lf_params* params,
                   void* stream, lf_ens** out);
 
-/* Autotuner: for every distinct lattice size of the compact runs in turn,
+/* Autotuner: for every distinct (lattice size, stencil) class of the runs in turn,
  * times the whole batch -- a scratch ensemble of the same runs, which holds
  * as much device memory as this one for the duration of the call -- with that
  * size's runs set to every CTA width (64 threads = 56-column strips, 128
  * threads = 120-column strips) and segment height (1 .. 128 rows, at most
  * ny / 2), reps timed steps each (CUDA events), and keeps the shape of the
  * fastest batch.  The objective is the ensemble's throughput, not one run's
- * latency.  The runs' states are not touched.  Compact and isotropic runs of
- * one lattice size are separate classes, tuned one after the other.
- * Rebuilds the work lists and the graphs. */
+ * latency.  The runs' states are not touched.  Rebuilds the work lists and
+ * the graphs. */
 int lf_ens_tune(lf_ens* e, int reps);
 
 /* Rows per segment the work list uses for run r (after tuning, or the
