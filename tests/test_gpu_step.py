@@ -315,6 +315,27 @@ def test_full_size_one_step_fp32(tuned):
     sim.close()
 
 
+@pytest.mark.parametrize("tuned", [False, True])
+@pytest.mark.parametrize("xi", [1e-3, 0.1])
+def test_full_size_one_step_isotropic_fp32(tuned, xi):
+    """The same 1024 x 1024 workload with the isotropic 9-point stencils (the
+    two 2D configurations that run their 50k steps), in the library's default
+    configuration (the packed isotropic march) and the autotuner's choice:
+    one step from the seeded state, every site against the oracle."""
+    sim = lf.Lattice(nx=1024, ny=1024, precision="fp32", xi=xi, stencil="isotropic")
+    if tuned:
+        sim.tune(reps=5)
+    cfg = O.make_cfg(nx=1024, ny=1024, xi=xi, stencil=1)
+    sim.step(3)
+    st = O.State(cfg, to_oracle_f(sim.get("pop"), 2), sim.get("phi"), sim.get("T"))
+    sim.step(1)
+    ref = O.step(st)
+    for name, got, want in (("phi", sim.get("phi"), ref.phi), ("T", sim.get("T"), ref.T),
+                            ("f", to_oracle_f(sim.get("pop"), 2), ref.f)):
+        assert relerr(got, want) < 2e-6, (name, relerr(got, want))
+    sim.close()
+
+
 def _sampled_window_parity(sim, d, okw, centres, half=8):
     """One step of `sim` checked on sub-lattices: around each sampled centre
     (x0 in 2D, (x0, y0) in 3D) the oracle steps a 2*half-wide window, periodic
