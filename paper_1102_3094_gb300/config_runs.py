@@ -45,17 +45,18 @@ def run(d, n, xi, tau, stencil, steps, reports, seed=1):
             "diverged": diverged, "finite_to": rows[-1]["t"] if rows else 0}
 
 
-def precision_pair(n, xi, stencil, seeds, steps, reports):
+def precision_pair(n, xi, stencil, seeds, steps, reports, d=2, tau=1.0):
     """The precision form against FP64 on the GPU: the same run (lattice,
     physics, seed) in FP32 (deviation populations) and in FP64, S(k) peak
     position and height and s at every report time; per report time the seed
     means of both and their relative (k, S) or absolute (s) differences."""
     from paper_1102_3094_gb300 import lf
 
+    shape = dict(d=3, nx=n, ny=n, nz=n) if d == 3 else dict(d=2, nx=n, ny=n)
     per = {"fp32": {}, "fp64": {}}
     for seed in seeds:
         for prec in ("fp32", "fp64"):
-            sim = lf.Lattice(nx=n, ny=n, precision=prec, xi=xi, tau=1.0, seed=seed, stencil=stencil)
+            sim = lf.Lattice(precision=prec, xi=xi, tau=tau, seed=seed, stencil=stencil, **shape)
             rows, done = [], 0
             for r in range(1, reports + 1):
                 target = steps * r // reports
@@ -81,7 +82,8 @@ def precision_pair(n, xi, stencil, seeds, steps, reports):
                       "d_k_peak": abs(m["fp32"]["k_peak"] / m["fp64"]["k_peak"] - 1),
                       "d_s_peak": abs(m["fp32"]["s_peak"] / m["fp64"]["s_peak"] - 1),
                       "d_s": abs(m["fp32"]["s"] - m["fp64"]["s"])})
-    return {"n": n, "xi": xi, "stencil": stencil, "seeds": list(seeds), "steps": steps, "table": table,
+    return {"d": d, "n": n, "xi": xi, "tau": tau, "stencil": stencil, "seeds": list(seeds), "steps": steps,
+            "table": table,
             "runs": {p_: {str(k): v for k, v in d.items()} for p_, d in per.items()}}
 
 
@@ -95,16 +97,25 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", action="store_true",
                     help="instead: FP32 against FP64 over 8 seeds at square^2, 50k steps (isotropic stencils "
                          "at xi = 1e-3 and 0.1, compact at xi = 1e-3)")
+    ap.add_argument("--precision3d", type=int, default=0, metavar="N",
+                    help="instead: FP32 against FP64 over 8 seeds at N^3, 20k steps (isotropic stencils, "
+                         "tau = 3, xi = 1e-3: the 3D configuration that runs its length)")
     args = ap.parse_args(argv)
-    if args.precision:
+    if args.precision or args.precision3d:
         import torch
 
         torch.cuda.init()
         div = 10 if args.quick else 1
-        out = [precision_pair(args.square, xi, st, range(1, 9), 50_000 // div, args.reports)
-               for xi, st in ((1e-3, "isotropic"), (1e-1, "isotropic"), (1e-3, "compact"))]
+        if args.precision3d:
+            out = [precision_pair(args.precision3d, 1e-3, "isotropic", range(1, 9), 20_000 // div, args.reports,
+                                  d=3, tau=3.0)]
+        else:
+            out = [precision_pair(args.square, xi, st, range(1, 9), 50_000 // div, args.reports)
+                   for xi, st in ((1e-3, "isotropic"), (1e-1, "isotropic"), (1e-3, "compact"))]
         for res in out:
-            print(f"\n{args.square}^2 {res['stencil']} xi = {res['xi']:g}, 8 seeds: seed means, FP32 against FP64")
+            lat = f"{res['n']}^{res['d']}"
+            print(f"\n{lat} {res['stencil']} xi = {res['xi']:g}, tau = {res['tau']:g}, 8 seeds: seed means, "
+                  "FP32 against FP64")
             print("| t | seeds | k_peak fp32 / fp64 | S_peak fp32 / fp64 | s fp32 / fp64 | dk | dS | ds |")
             print("|---|---|---|---|---|---|---|---|")
             for r in res["table"]:
