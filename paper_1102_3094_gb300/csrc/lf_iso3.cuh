@@ -1,7 +1,7 @@
 // lf_iso3.cuh -- the isotropic 19-point operators (D3Q19 weights) on three
-// shared-memory planes, used by the fused plane march (lf_step3d.cu) and the
-// three-pass step (lf_step3d_split.cu) when the context's stencil is
-// LF_STENCIL_ISOTROPIC:
+// shared-memory planes, used by the fused plane march (lf_step3d.cu), and the
+// same operators split by plane for the column marches of the three-pass step
+// (lf_step3d_iso.cu), when the context's stencil is LF_STENCIL_ISOTROPIC:
 //   d_a A = 3 sum_i w_i e_ia A(r + e_i) = [2 (nearest difference) + (edge differences)] / 12,
 //   lap A = 6 sum_i w_i [A(r + e_i) - A(r)] = [2 (6 nearest) + (12 edges) - 24 A] / 6.
 #pragma once
