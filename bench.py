@@ -614,8 +614,6 @@ def run_ours(args):
     else:
         param = args.tune
         sim.set_variant(variant, param)
-    if iso and d == 2:
-        variant = "tile"
     N = nx * ny * nz
     # The compact 3D step at these parameters goes non-finite after about 150
     # steps (the FP64 oracle too), so the 3D workload restores its initial quench
@@ -690,13 +688,13 @@ def run_ours(args):
     kernel_ms = statistics.mean(times_ms) / per_kernel
     achieved = bps * N / (kernel_ms * 1e-3) / 1e9
     if d == 3:
-        kname = "k_force3d+k_lb3d+k_phi3d" if variant == "split3" else "k_march3d"
+        kname = ("k_force3d+k_lb3d+k_phi3d" if variant == "split3" else "k_march3d") + ("_iso" if iso else "")
+    elif iso:
+        kname = {"march": "k_march2d_iso", "march2": "k_march2d_iso_x2", "tile": "k_step2d_iso"}[variant]
     else:
         kname = {"march": "k_march2d", "march2": "k_march2d_x2", "tile": "k_step2d"}[variant]
-    if iso:
-        kname += "_iso"                     # the ISO instantiation of the tile / fused kernel
-    if kname == "k_march2d_x2" and prec == "fp64":
-        kname = "k_march2d"                 # the packed kernel is FP32 only
+    if kname.startswith("k_march2d") and kname.endswith("x2") and prec == "fp64":
+        kname = kname[:-3]                  # the packed kernels are FP32 only
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             # ncu DRAM bytes per kernel shape (key suffix _p<param>; no suffix: the default shape)
             "traffic": traffic_for(f"{kname}_{prec}_{nx}" + (f"_p{param}" if param else "")), "peak_kind": peak_kind,
@@ -704,6 +702,49 @@ def run_ours(args):
             "kernel": kname + (f" ({passes} passes; bytes and time of the whole step)" if passes > 1
                                else " (fused phi-chain + LB + FD)"),
             "kernel_ms_mean": kernel_ms, "kernel_ms_median": statistics.median(times_ms) / per_kernel}
+
+    # ---- the three passes of the 3D step, timed one by one ------------------
+    # (CUDA events at the pass boundaries, recorded by the library on its
+    # stream; a short sequence after the timed steps, L2 flushed before each
+    # step as above)
+    def pass_breakdown(sim_, iso_, param_, restore_fn):
+        sel = (param_ >> 16) & 15
+        if iso_:
+            force = "k_force3d_iso_x2" if (sel == 4 and prec == "fp32") else "k_force3d_iso"
+            phi_k = "k_phi3d_isoz"
+        else:
+            force = "k_force3d_x2" if (sel == 0 and prec == "fp32") else "k_force3d"
+            phi_k = "k_phi3d"
+        esz = 4 if prec == "fp32" else 8
+        per_site = [6 * esz, 44 * esz, 8 * esz]      # A: phi, T in, mu, F out; B: f in/out, F, u; C: phi, u, mu, T in, phi, T out
+        acc, cnt = [0.0, 0.0, 0.0], 0
+        sim_.set_pass_timing(True)
+        with torch.cuda.stream(stream):
+            if restore_fn:
+                restore_fn()
+            for k in range(min(args.steps, 30)):
+                l2_flush(float(k))
+                sim_.step(1)
+                ms_ = sim_.pass_times()
+                if len(ms_) == 3:
+                    acc = [a + b for a, b in zip(acc, ms_)]
+                    cnt += 1
+        sim_.set_pass_timing(False)
+        if cnt == 0:
+            return None
+        out = []
+        for name, b, t in zip((force, "k_lb3d", phi_k), per_site, acc):
+            ms_ = t / cnt
+            gbs = b * N / (ms_ * 1e-3) / 1e9
+            out.append({"kernel": name, "ms": ms_, "algorithmic_bytes_per_site": b, "achieved_gbs": gbs,
+                        "frac": gbs / peak})
+        dom = max(out, key=lambda x: x["ms"])
+        return {"steps": cnt, "passes": out,
+                "dominant": {"kernel": dom["kernel"], "achieved_gbs": dom["achieved_gbs"], "frac": dom["frac"],
+                             "share_of_step": dom["ms"] / sum(x["ms"] for x in out)}}
+
+    if d == 3 and variant == "split3":
+        roof["per_pass"] = pass_breakdown(sim, iso, param, restore_state if restore > 0 else None)
 
     # ---- end to end through the C ABI with host buffers ---------------------
     e2e = None
@@ -777,6 +818,7 @@ def run_ours(args):
                   "value": job_rate(N, args.steps, world, tot), "unit": "MLUPS",
                   "ms_per_step": 1e3 * tot / args.steps, "frac": ach / peak, "achieved_gbs": ach,
                   "traffic": traffic_for(f"k_force3d+k_lb3d+k_phi3d_iso_{prec}_{nx}_p{p_}") if v_ == 3 else None,
+                  "per_pass": pass_breakdown(sim, True, p_, None) if v_ == 3 else None,
                   "kernel_shape": {"variant": names[v_], "param": p_}, "diag_after": {"rc": sim.diag()["rc"]}}
     if rank == 0:
         line = {

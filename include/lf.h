@@ -351,6 +351,22 @@ int lf_set_stencil(lf_ctx* ctx, int stencil);
 /* Current step counter. */
 int64_t lf_step_count(const lf_ctx* ctx);
 
+/* Timing of the passes of the three-pass 3D step (LF_VARIANT_SPLIT3, Sec. 2:
+ * pass A mu and F, Eqs. chem and ff; pass B collision and streaming, Eqs.
+ * moment, evoleqn, latticeforceterm; pass C phi(t+1), Eq. massdiff, and the
+ * first temperature sub-step).  With enable != 0, every later lf_step of such
+ * a context records CUDA events on its stream before pass A and after each
+ * pass (it creates four events on the first call; lf_destroy releases them).
+ * lf_pass_times waits for the context's stream and writes the durations in
+ * milliseconds of the passes of the last step taken, in launch order, into
+ * ms[0 .. min(n, 3) - 1], and their count into *npasses (may be NULL): 3, or
+ * 0 when that step recorded none (timing off, 2D, another variant).  Further
+ * temperature sub-steps are not part of the passes.  LF_EINVAL for a NULL
+ * context, an ensemble member, n < 0 or ms NULL with n > 0; the bounded
+ * stream wait's LF_ETIMEOUT / LF_ECUDA. */
+int lf_set_pass_timing(lf_ctx* ctx, int enable);
+int lf_pass_times(lf_ctx* ctx, float* ms, int n, int* npasses);
+
 /* Frees the context's own allocations (not a caller workspace).  NULL is a no-op. */
 void lf_destroy(lf_ctx* ctx);
 

@@ -171,9 +171,11 @@ StepIO<R> io_of(lf_ctx* c, bool aux)
 }
 
 template <typename R>
-cudaError_t launch_step_any(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s)
+cudaError_t launch_step_any(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux, cudaStream_t s,
+                            cudaEvent_t* ev = nullptr)
 {
     if (g.d == 2) return launch_step2d<R>(g, p, io, aux, s);
+    if (!aux && g.variant == LF_VARIANT_SPLIT3) return launch_split3d<R>(g, p, io, s, ev);
     return launch_step3d<R>(g, p, io, aux, s);
 }
 
@@ -183,7 +185,10 @@ int do_steps(lf_ctx* c, int64_t n)
     const Phys<R> ph = phys_of<R>(c);
     for (int64_t k = 0; k < n; ++k) {
         StepIO<R> io = io_of<R>(c, true);      // the three-pass 3D step passes mu, F, u through aux
-        if (launch_step_any<R>(c->g, ph, io, false, c->stream) != cudaSuccess) return LF_ECUDA;
+        const bool timed = c->pass_timing && c->g.d == 3 && c->g.variant == LF_VARIANT_SPLIT3;
+        if (launch_step_any<R>(c->g, ph, io, false, c->stream, timed ? c->pass_ev : nullptr) != cudaSuccess)
+            return LF_ECUDA;
+        c->pass_recorded = timed;
         if (c->params.hydro) c->fcur ^= 1;
         c->pcur ^= 1;
         c->tcur ^= 1;
@@ -638,6 +643,40 @@ int lf_structure_factor(lf_ctx* c, double* out, int64_t nb)
 
 int64_t lf_step_count(const lf_ctx* c) { return c ? c->step : -1; }
 
+int lf_set_pass_timing(lf_ctx* c, int enable)
+{
+    if (!c || c->ens_member) return LF_EINVAL;
+    if (enable && !c->pass_ev[0]) {
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&c->pass_ev[i]) != cudaSuccess) {
+                for (int j = 0; j < i; ++j) {
+                    cudaEventDestroy(c->pass_ev[j]);
+                    c->pass_ev[j] = nullptr;
+                }
+                cudaGetLastError();
+                return LF_ECUDA;
+            }
+    }
+    c->pass_timing = enable != 0;
+    c->pass_recorded = false;
+    return LF_OK;
+}
+
+int lf_pass_times(lf_ctx* c, float* ms, int n, int* npasses)
+{
+    if (!c || n < 0 || (n > 0 && !ms)) return LF_EINVAL;
+    int np = 0;
+    if (c->pass_recorded) {
+        const int rc = wait_stream(c->stream);
+        if (rc != LF_OK) return rc;
+        np = 3;
+        for (int i = 0; i < np && i < n; ++i)
+            if (cudaEventElapsedTime(&ms[i], c->pass_ev[i], c->pass_ev[i + 1]) != cudaSuccess) return LF_ECUDA;
+    }
+    if (npasses) *npasses = np;
+    return LF_OK;
+}
+
 int lf_set_t_solver(lf_ctx* c, int solver)
 {
     if (!c || (solver != LF_TSOLVER_EXPLICIT && solver != LF_TSOLVER_IMPLICIT) || c->ens_member) return LF_EINVAL;
@@ -788,6 +827,8 @@ void lf_destroy(lf_ctx* c)
     wait_stream(c->stream);
     if (c->own && c->base) cudaFree(c->base);
     if (c->tcoef) cudaFree(c->tcoef);
+    for (cudaEvent_t ev : c->pass_ev)
+        if (ev) cudaEventDestroy(ev);
     if (c->flag_host) cudaFreeHost(const_cast<int*>(c->flag_host));
     cudaGetLastError();
     delete c;

@@ -42,6 +42,11 @@ struct lf_ctx {
     bool tcoef_valid;
     double tcoef_xi;
     int tcoef_mode, tcoef_stencil;
+    // pass timing (lf_set_pass_timing): events before and after the passes of
+    // the last three-pass step, and whether that step recorded them
+    cudaEvent_t pass_ev[4];
+    bool pass_timing;
+    bool pass_recorded;
 };
 
 namespace lf {

@@ -110,8 +110,18 @@ cudaError_t launch_step2d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, 
 template <typename R>
 cudaError_t launch_step3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, bool aux,
                           cudaStream_t s);
+// the three-pass 3D step (lf_step3d_passes.cu); ev: nullptr, or four events
+// recorded before pass A and after passes A, B and C
 template <typename R>
-cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);
+cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s,
+                           cudaEvent_t* ev = nullptr);
+// its passes with the compact stencils (lf_step3d_split.cu)
+template <typename R>
+cudaError_t launch_force3d_compact(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);
+template <typename R>
+cudaError_t launch_lb3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);
+template <typename R>
+cudaError_t launch_phi3d_compact(const Geom& g, const Phys<R>& p, const StepIO<R>& io, int zc, cudaStream_t s);
 // passes A and C of the three-pass step with the isotropic stencils (lf_step3d_iso.cu)
 template <typename R>
 cudaError_t launch_force3d_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s);

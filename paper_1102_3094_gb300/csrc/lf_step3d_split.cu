@@ -17,7 +17,8 @@
 // tile, against + 3 / + 2 / + 1 in the fused kernel, and no population is
 // read outside its own site.
 //
-// With the isotropic stencils passes A and C are those of lf_step3d_iso.cu.
+// lf_step3d_passes.cu launches the three passes in order; with the isotropic
+// stencils passes A and C are those of lf_step3d_iso.cu.
 #include "lf_step3d_common.cuh"
 #include "lf_march2d_x2.cuh"      // packed FP32x2 helpers
 
@@ -467,7 +468,6 @@ __global__ void __launch_bounds__(128) k_lb3d(Geom g, Phys<R> p, StepIO<R> io)
 // the in-plane neighbours come through L1.  phi(t+1) from the fluxes
 // g = phi u of the neighbours and lap(mu) (mu even, g_z odd across the
 // walls); the first temperature sub-step with the wall rule of the context.
-constexpr int kZC = 16;   // planes per segment of the phi passes unless the variant's param sets them
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_phi3d(Geom g, Phys<R> p, StepIO<R> io, int zc)
@@ -607,38 +607,44 @@ cudaError_t launch_force_x2(const Geom& g, const Phys<float>& p, const StepIO<fl
 
 }  // namespace
 
+// The compact passes, one launcher each (the three-pass step, with the pass
+// boundaries, is put together by lf_step3d_passes.cu).
 template <typename R>
-cudaError_t launch_split3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
+cudaError_t launch_force3d_compact(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
-    cudaError_t e;
-    const bool iso = g.stencil == LF_STENCIL_ISOTROPIC;
-    if (iso) {
-        e = launch_force3d_iso<R>(g, p, io, s);
-    } else if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4) {
         // (param >> 16) & 15: 0 = two z-lanes in packed FP32x2, 1 / 2 = one lane on 60x4 / 28x12 tiles
         const int sel = (g.tune >> 16) & 15;
-        e = sel == 1 ? launch_force<R, 60, 4>(g, p, io, s)
-          : sel == 2 ? launch_force<R, 28, 12>(g, p, io, s)
-                     : launch_force_x2<28, 12>(g, p, io, s);
+        return sel == 1 ? launch_force<R, 60, 4>(g, p, io, s)
+             : sel == 2 ? launch_force<R, 28, 12>(g, p, io, s)
+                        : launch_force_x2<28, 12>(g, p, io, s);
     } else {
-        e = launch_force<R, 28, 12>(g, p, io, s);
+        return launch_force<R, 28, 12>(g, p, io, s);
     }
-    if (e != cudaSuccess) return e;
-    if (p.hydro) {
-        dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
-        k_lb3d<R><<<grid, 128, 0, s>>>(g, p, io);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    // planes per segment of the phi pass: (param >> 20) & 255, 0 = kZC
-    int zc = (g.tune >> 20) & 255;
-    if (zc <= 0) zc = kZC;
-    if (iso) return launch_phi3d_iso<R>(g, p, io, zc, s);
+}
+
+template <typename R>
+cudaError_t launch_lb3d(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
+{
+    dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
+    k_lb3d<R><<<grid, 128, 0, s>>>(g, p, io);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_phi3d_compact(const Geom& g, const Phys<R>& p, const StepIO<R>& io, int zc, cudaStream_t s)
+{
     dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
     k_phi3d<R><<<gc, 256, 0, s>>>(g, p, io, zc);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_split3d<float>(const Geom&, const Phys<float>&, const StepIO<float>&, cudaStream_t);
-template cudaError_t launch_split3d<double>(const Geom&, const Phys<double>&, const StepIO<double>&, cudaStream_t);
+#define LF_INST(R)                                                                                              \
+    template cudaError_t launch_force3d_compact<R>(const Geom&, const Phys<R>&, const StepIO<R>&, cudaStream_t); \
+    template cudaError_t launch_lb3d<R>(const Geom&, const Phys<R>&, const StepIO<R>&, cudaStream_t);           \
+    template cudaError_t launch_phi3d_compact<R>(const Geom&, const Phys<R>&, const StepIO<R>&, int, cudaStream_t);
+LF_INST(float)
+LF_INST(double)
+#undef LF_INST
 
 }  // namespace lf

@@ -97,6 +97,10 @@ def lib():
             L.lf_tune.restype = C.c_int
             L.lf_step_count.argtypes = [vp]
             L.lf_step_count.restype = i64
+            L.lf_set_pass_timing.argtypes = [vp, C.c_int]
+            L.lf_set_pass_timing.restype = C.c_int
+            L.lf_pass_times.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
+            L.lf_pass_times.restype = C.c_int
             L.lf_destroy.argtypes = [vp]
             L.lf_destroy.restype = None
             L.lf_strerror.argtypes = [C.c_int]
@@ -199,6 +203,18 @@ def lf_tune(ctx, reps: int = 5):
 
 def lf_step_count(ctx) -> int:
     return lib().lf_step_count(ctx)
+
+
+def lf_set_pass_timing(ctx, enable: bool) -> int:
+    return lib().lf_set_pass_timing(ctx, int(bool(enable)))
+
+
+def lf_pass_times(ctx):
+    """(rc, [ms of the passes of the last step])."""
+    ms = (C.c_float * 3)()
+    n = C.c_int(0)
+    rc = lib().lf_pass_times(ctx, ms, 3, C.byref(n))
+    return rc, [float(ms[i]) for i in range(n.value)]
 
 
 def lf_destroy(ctx) -> None:
@@ -308,6 +324,16 @@ class Lattice:
     @property
     def step_count(self):
         return lf_step_count(self.ctx)
+
+    def set_pass_timing(self, enable: bool = True):
+        """CUDA events at the pass boundaries of every later three-pass 3D step."""
+        _ok(lf_set_pass_timing(self.ctx, enable), "lf_set_pass_timing")
+
+    def pass_times(self):
+        """Milliseconds of the passes (A, B, C) of the last step, [] if it recorded none."""
+        rc, ms = lf_pass_times(self.ctx)
+        _ok(rc, "lf_pass_times")
+        return ms
 
     def close(self):
         if getattr(self, "ctx", None) is not None and self.ctx.value:

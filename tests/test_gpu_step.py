@@ -702,3 +702,33 @@ def test_conservation_3d(prec, stencil, steps):
     assert abs(d1["phi_sum"] - d0["phi_sum"]) < (1e-10 if prec == "fp64" else 5e-3)
     assert d1["mach"] < 0.1
     sim.close()
+
+
+def test_pass_times_of_the_three_pass_step():
+    """lf_set_pass_timing / lf_pass_times: three positive pass durations for a
+    three-pass 3D step, none with the timing off, for a 2D step or for the
+    fused variant; the step's result is that of the untimed step."""
+    kw = dict(d=3, nx=40, ny=12, nz=20, xi=0.01)
+    a = lf.Lattice(precision="fp32", **kw)
+    b = lf.Lattice(precision="fp32", **kw)
+    a.set_pass_timing(True)
+    a.step(2)
+    b.step(2)
+    ms = a.pass_times()
+    assert len(ms) == 3 and all(t > 0 for t in ms), ms
+    for name in ("phi", "T", "pop"):
+        np.testing.assert_array_equal(a.get(name, "fp32"), b.get(name, "fp32"))
+    a.set_pass_timing(False)
+    a.step(1)
+    assert a.pass_times() == []
+    a.set_pass_timing(True)
+    a.set_variant("march", 0)                # the fused plane march: one kernel
+    a.step(1)
+    assert a.pass_times() == []
+    a.close()
+    b.close()
+    c = lf.Lattice(nx=64, ny=32, precision="fp32", xi=0.01)
+    c.set_pass_timing(True)
+    c.step(1)
+    assert c.pass_times() == []
+    c.close()
