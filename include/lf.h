@@ -273,8 +273,9 @@ int lf_load(lf_ctx* ctx, const char* path);
  *     column marches with sliding plane sums), 0 = one lane on 28x12 tiles
  *     (FP32: two CTAs per SM), 1 = on 28x28 tiles, 3 = on 28x12 tiles at one
  *     CTA per SM, 4 = two segments in packed FP32x2 lanes (1, 3 and 4 in FP32
- *     only; FP64 takes 0).  For 3D contexts every other variant runs the
- *     fused plane march (param = planes per segment).
+ *     only; FP64 takes 0); with the isotropic stencils bit 28 selects the
+ *     phi pass that stages its raw fields by cp.async.  For 3D contexts every
+ *     other variant runs the fused plane march (param = planes per segment).
  * Returns LF_EINVAL for an unknown variant or a negative param. */
 #define LF_VARIANT_MARCH  0
 #define LF_VARIANT_TILE   1

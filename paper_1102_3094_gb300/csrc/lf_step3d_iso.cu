@@ -6,7 +6,8 @@
 //   A  mu and F = -d_a P_ab (Eqs. chem, ff): k_force3d_iso (one lane, FP32
 //      and FP64) or k_force3d_iso_x2 (two z-lanes in packed FP32x2);
 //   C  phi(t+1) = phi - div(phi u) + Gamma lap(mu) (Eq. massdiff) and the
-//      first temperature sub-step: k_phi3d_isoz.
+//      first temperature sub-step: k_phi3d_isoz (fields staged through
+//      registers) or k_phi3d_isoa (raw fields staged by cp.async).
 // Pass B (collision and streaming) is the same for both stencils.  The wall
 // rules are those of the compact passes: phi, T and every derived scalar
 // even about the half-way planes, the wall-normal flux odd, T with its
@@ -598,6 +599,124 @@ __global__ void __launch_bounds__(256) k_phi3d_isoz(Geom g, Phys<R> p, StepIO<R>
     if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
 }
 
+// Pass C with the raw fields staged by cp.async: mu, T, phi, u_x, u_y, u_z of
+// the tile grown by one site go straight from global to a three-slot shared
+// ring, two planes ahead of their use, and the fluxes g = phi u are formed
+// where they are read.  The sums and wall rules are those of k_phi3d_isoz.
+constexpr int kIsoNR = 6;   // mu, T, phi, u_x, u_y, u_z
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_phi3d_isoa(Geom g, Phys<R> p, StepIO<R> io, int zc)
+{
+    constexpr int TW = kIsoTW, TA = kIsoTA, NF = kIsoNR;
+    extern __shared__ __align__(16) unsigned char smem_iso[];
+    R (*sm)[NF][TA] = reinterpret_cast<R (*)[NF][TA]>(smem_iso);     // [3 slots][NF][TA]
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const int za = blockIdx.z * zc, zb = min(za + zc, g.nz);
+    const int nx = g.nx, ny = g.ny, nz = g.nz, pitch = g.pitch, walls = g.walls;
+    const int64_t zs = (int64_t)ny * pitch;
+    const bool hyd = p.hydro != 0;
+    const bool halfway = walls && g.t_mode == LF_TWALL_HALFWAY;
+    auto zmap = [&](int zl) -> int64_t {
+        int z = zl;
+        if (walls) z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
+        else z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        return (int64_t)z * zs;
+    };
+    int64_t off[2];
+    bool has[2];
+    for (int i = 0; i < 2; ++i) {
+        const int q = t + 256 * i;
+        has[i] = q < TA;
+        const int ly = has[i] ? q / TW : 0, lx = has[i] ? q - ly * TW : 0;
+        int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        off[i] = (int64_t)gy * pitch + gx;
+    }
+    const R* src[NF] = {io.mu, io.T_in, io.phi_in, io.u[0], io.u[1], io.u[2]};
+    const int nf = hyd ? NF : 2;
+    // plane zl (za - 1 .. zb) into slot (zl - za + 1) mod 3; one commit group per call
+    auto fetch = [&](int zl) {
+        if (zl <= zb) {
+            const int sl = (zl - za + 1) % 3;
+            const int64_t pz = zmap(zl);
+            for (int i = 0; i < 2; ++i)
+                if (has[i])
+                    for (int f = 0; f < nf; ++f) cp_async_s<sizeof(R)>(&sm[sl][f][t + 256 * i], src[f] + (pz + off[i]));
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const int c = (ty + 1) * TW + tx + 1;
+    const int64_t col = (int64_t)y * pitch + x;
+    Slide19<R> smu, sT, sgx, sgy, sgz;
+    R Tc1 = R(0);
+    bool bad = false;
+    fetch(za - 1);
+    fetch(za);
+    for (int k = za - 1; k <= zb; ++k) {
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // plane k has landed (k + 1 may be in flight)
+        __syncthreads();
+        fetch(k + 2);                                       // into the slot of plane k - 1
+        const int s0 = (k - za + 1) % 3;
+        const bool ghost = walls && (k < 0 || k >= nz);
+        const R* M = sm[s0][0];
+        const R* TT = sm[s0][1];
+        const R Tck = TT[c];
+        Plane19<R> qm = plane19<R, TW>(M, c, M[c]);
+        Plane19<R> qT = plane19<R, TW>(TT, c, Tck);
+        Plane19<R> qx{}, qy{}, qz{};
+        if (hyd) {
+            const R* F = sm[s0][2];
+            const R* UX = sm[s0][3];
+            const R* UY = sm[s0][4];
+            const R* UZ = sm[s0][5];
+            auto gxa = [&](int o) { return F[c + o] * UX[c + o]; };
+            auto gya = [&](int o) { return F[c + o] * UY[c + o]; };
+            auto gza = [&](int o) { return F[c + o] * UZ[c + o]; };
+            const R xe = gxa(1), xw = gxa(-1), xne = gxa(TW + 1), xnw = gxa(TW - 1), xse = gxa(-TW + 1),
+                    xsw = gxa(-TW - 1);
+            qx.ax = xe - xw;
+            qx.gx = R(2) * qx.ax + (xne - xnw) + (xse - xsw);
+            const R yn = gya(TW), ys = gya(-TW), yne = gya(TW + 1), ynw = gya(TW - 1), yse = gya(-TW + 1),
+                    ysw = gya(-TW - 1);
+            qy.ay = yn - ys;
+            qy.gy = R(2) * qy.ay + (yne - yse) + (ynw - ysw);
+            qz.s = R(2) * gza(0) + ((gza(1) + gza(-1)) + (gza(TW) + gza(-TW)));
+        }
+        if (ghost) {
+            qz.s = -qz.s;
+            if (halfway) qT.s = R(12) * p.T_w - qT.s;
+        }
+        R lapmu, lapT, dgx, dgy, dgz, u0, u1, u2;
+        smu.push(qm, lapmu, u0, u1, u2);
+        sT.push(qT, lapT, u0, u1, u2);
+        sgx.push(qx, u0, dgx, u1, u2);
+        sgy.push(qy, u0, u1, dgy, u2);
+        sgz.push(qz, u0, u1, u2, dgz);
+        const int m = k - 1;
+        if (act && k > za) {
+            const int64_t site = (int64_t)m * zs + col;
+            const R div = hyd ? (dgx + dgy) + dgz : R(0);
+            const R phn = io.phi_in[site] - div + p.Gamma * lapmu;
+            io.phi_out[site] = phn;
+            R Tn = Tc1;
+            if (p.t_update) {
+                if (walls && g.t_mode == LF_TWALL_LAYERS && (m == 0 || m == nz - 1)) Tn = p.T_w;
+                else Tn = Tc1 + p.dxi * lapT;
+            }
+            io.T_out[site] = Tn;
+            bad |= !isfinite(phn) || !isfinite(Tn);
+        }
+        Tc1 = Tck;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) *reinterpret_cast<volatile int*>(io.flag) = 1;
+}
+
 template <typename R, int TX, int TY, int MINB>
 cudaError_t launch_force_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, cudaStream_t s)
 {
@@ -662,11 +781,19 @@ cudaError_t launch_force3d_iso(const Geom& g, const Phys<R>& p, const StepIO<R>&
 template <typename R>
 cudaError_t launch_phi3d_iso(const Geom& g, const Phys<R>& p, const StepIO<R>& io, int zc, cudaStream_t s)
 {
+    dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
+    if ((g.tune >> 28) & 1) {                           // param bit 28: the raw fields staged by cp.async
+        constexpr size_t bytes = sizeof(R) * 3 * kIsoNR * kIsoTA;
+        static unsigned long long attr_done = 0;
+        const cudaError_t e = raise_smem_limit(k_phi3d_isoa<R>, (int)bytes, &attr_done);
+        if (e != cudaSuccess) return e;
+        k_phi3d_isoa<R><<<gc, 256, bytes, s>>>(g, p, io, zc);
+        return cudaGetLastError();
+    }
     constexpr size_t bytes = sizeof(R) * 2 * kIsoNF * kIsoTA;
     static unsigned long long attr_done = 0;
     const cudaError_t e = raise_smem_limit(k_phi3d_isoz<R>, (int)bytes, &attr_done);
     if (e != cudaSuccess) return e;
-    dim3 gc((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + zc - 1) / zc);
     k_phi3d_isoz<R><<<gc, 256, bytes, s>>>(g, p, io, zc);
     return cudaGetLastError();
 }

@@ -77,15 +77,17 @@ std::vector<std::pair<int, int>> candidates(const lf_ctx* c)
             const int* sels = c->prec == LF_FP32 ? sels32 : sels64;
             const int nsel = c->prec == LF_FP32 ? 4 : 1;
             const int lanes[] = {0, 48, 64, 96, 128, 192};   // planes per lane of the packed form
-            for (int i = 0; i < nsel; ++i) {
-                if (sels[i] == 4) {
-                    for (int h : lanes)
-                        if (2 * h <= g.nz + 1 || h == 0) v.push_back({LF_VARIANT_SPLIT3, (zc << 20) | (4 << 16) | h});
-                    continue;
+            for (int phi_form = 0; phi_form < 2; ++phi_form)  // phi pass: register-staged, cp.async-staged (bit 28)
+                for (int i = 0; i < nsel; ++i) {
+                    const int base = (phi_form << 28) | (zc << 20) | (sels[i] << 16);
+                    if (sels[i] == 4) {
+                        for (int h : lanes)
+                            if (2 * h <= g.nz + 1 || h == 0) v.push_back({LF_VARIANT_SPLIT3, base | h});
+                        continue;
+                    }
+                    for (int h : planes)
+                        if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, base | h});
                 }
-                for (int h : planes)
-                    if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, (zc << 20) | (sels[i] << 16) | h});
-            }
         } else if (c->prec == LF_FP64) {
             for (int h : planes)
                 if (h <= g.nz) v.push_back({LF_VARIANT_SPLIT3, (zc << 20) | h});

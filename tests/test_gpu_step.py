@@ -200,6 +200,7 @@ VARIANTS3_ISO = {"split3": ("split3", 0), "split3-z3": ("split3", 3), "split3-ph
                  "split3-1cta-z5": ("split3", (3 << 16) | 5), "split3-phi5": ("split3", 5 << 20),
                  "split3-x2": ("split3", 4 << 16), "split3-x2-z3": ("split3", (4 << 16) | 3),
                  "split3-x2-z8": ("split3", (4 << 16) | 8),
+                 "split3-phiasync": ("split3", 1 << 28), "split3-phiasync-z1": ("split3", (1 << 28) | (1 << 20)),
                  "fused": ("march", 0)}
 
 
