@@ -123,3 +123,16 @@ def test_fp32_runs_against_oracle_3d():
         got_s = np.mean([runs[s][i][1]["s"] for s in seeds])
         assert abs(got_k / want_k - 1) < 0.02, (i, got_k, want_k)
         assert abs(got_s - want_s) < 0.01, (i, got_s, want_s)
+
+
+def test_precision_pair_3d_runs():
+    """config_runs.precision_pair on a small 3D case (the script behind the
+    96^3 x 20k-step table): both precisions run, every report time has both
+    seeds, and FP32 stays on the FP64 trajectory (non-chaotic at tau = 3)."""
+    from paper_1102_3094_gb300 import config_runs as C
+
+    res = C.precision_pair(16, 1e-3, "isotropic", [1, 2], 400, 4, d=3, tau=3.0)
+    assert res["d"] == 3 and len(res["table"]) == 4
+    for row in res["table"]:
+        assert row["seeds"] == 2
+        assert row["d_k_peak"] < 1e-3 and row["d_s_peak"] < 1e-3 and row["d_s"] < 1e-3, row
