@@ -425,6 +425,23 @@ def test_largest_2d_lattice_fp32():
     sim.close()
 
 
+@pytest.mark.parametrize("tuned", [False, True])
+def test_isotropic_4096_sampled_windows_fp32(tuned):
+    """The 2D isotropic step at 4096^2 (the size of the benchmark's isotropic
+    4096^2 line), in the default packed isotropic march (lanes of about 158 rows:
+    longer than any smaller case) and the autotuner's choice: one step checked on
+    sampled 16-column windows of all rows, the wrap at x = 0 among them."""
+    n = 4096
+    sim = lf.Lattice(nx=n, ny=n, precision="fp32", xi=1e-3, stencil="isotropic")
+    if tuned:
+        sim.tune(reps=3)
+    sim.step(3)
+    rng = np.random.default_rng(41)
+    centres = [(int(v),) for v in rng.integers(0, n, 3)] + [(0,), (n - 3,)]
+    _sampled_window_parity(sim, 2, dict(xi=1e-3, stencil=1), centres)
+    sim.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_checkpoint_resume_bit_identical(prec):
     a = lf.Lattice(nx=70, ny=37, precision=prec)
