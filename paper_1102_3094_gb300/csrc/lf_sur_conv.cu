@@ -8,20 +8,27 @@
 // boundary rule of the lattice (x periodic: the halo columns copy the
 // opposite edge; y walls: the halo rows are zero).
 //
-// A persistent CTA owns a 128-pixel column block and a run of image rows and
-// marches down them.  Input rows (130 pixels with the halo) sit in a 5-slot
-// shared-memory ring in a pixel-major core-matrix layout ([k core][pixel][8
-// channels], 16 bytes per pixel and core): the 8 pixels of a core matrix are
-// contiguous, so the A operand of tap (dy, dx) is the ring row of dy with its
-// descriptor start moved by dx pixels -- all 9 taps read the same three rows,
-// which are loaded once.  The rows two ahead are prefetched with cp.async.
-// The 9 weight taps stay in shared memory (K-major).  One thread issues the
-// MMAs of row y into one of two TMEM accumulators while the warps run the
-// epilogue of row y - 1 from the other.  With 64 output channels the CTA has
-// 512 threads: a warp reads the TMEM lanes of its quarter (warp mod 4, 32
-// pixels) and a quarter of the channels (warp / 4), so sixteen warps share
-// the epilogue's memory latency (132 us against 157 us with four warps for
-// 64 -> 64 at 8 x 256^2); the 16-channel last layer keeps 128 threads.
+// One persistent CTA per SM takes an equal contiguous share of the output
+// rows (ordered image, 128-pixel column block, row) and marches down them.
+// Input rows (130 pixels with the halo) sit in an 8-slot shared-memory ring in
+// a pixel-major core-matrix layout ([k core][pixel][8 channels], 16 bytes per
+// pixel and core): the 8 pixels of a core matrix are contiguous, so the A
+// operand of tap (dy, dx) is the ring row of dy with its descriptor start
+// moved by dx pixels -- all 9 taps read the same three rows, which are loaded
+// once.  The 9 weight taps stay in shared memory (K-major).  The warps have
+// fixed roles that hand work over through mbarriers:
+//   * a producer warp loads each row by TMA (one 8-channel x 130-pixel box
+//     per k core) as soon as its ring slot is free;
+//   * an MMA warp issues the 9 x CIN / 16 MMAs of a row into one of four TMEM
+//     accumulators once its three rows have landed and the accumulator has
+//     been read, and commits the accumulator and the row slot it no longer
+//     needs;
+//   * the epilogue warps (a TMEM lane quarter and 16 channels each: sixteen
+//     warps for 64 output channels, four for 16) read an accumulator, release
+//     it, and add bias, activation, residual and mask on the way out.
+// So the loads of the rows ahead, the MMAs of the next rows and the epilogue
+// of the current one overlap, with up to four rows between MMA and epilogue.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "lf_internal.cuh"
@@ -51,57 +58,99 @@ template <int CIN, int COUT>
 struct ConvSmem {
     static constexpr int RP = 130;                   // ring row: pixels x0 - 1 .. x0 + 128
     static constexpr int KC = CIN / 8;               // 16-byte channel groups (k cores)
-    static constexpr int LBO_A = RP * 16;            // next k core of the A operand
+    static constexpr int LBO_A = 2176;               // next k core: 130 pixels x 16 bytes, padded to 128 bytes
+    static constexpr int TX_BYTES = KC * RP * 16;    // bytes one row's TMA copies bring
     static constexpr int ROW_BYTES = KC * LBO_A;
-    static constexpr int NSLOT = 5;                  // rows y - 1 .. y + 3
+    static constexpr int NSLOT = 8;                  // ring of input rows
+    static constexpr int NACC = 8;                   // TMEM accumulator slots of COUT columns (output rows)
     static constexpr int B_TAP = COUT * CIN * 2;
     static constexpr int B_OFF = 0;
     static constexpr int R_OFF = 9 * B_TAP;
     static constexpr int BAR_OFF = R_OFF + NSLOT * ROW_BYTES;
-    static constexpr int BYTES = BAR_OFF + 64;
-    static constexpr int TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;   // two accumulators
+    static constexpr int NBAR = 2 * NSLOT + 2 * NACC + 1;   // full, empty, acc full, acc empty, done
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int TMEM_COLS = NACC * COUT < 32 ? 32 : NACC * COUT;
+    static_assert(R_OFF % 128 == 0 && LBO_A % 128 == 0 && LBO_A >= RP * 16, "TMA destinations 128-byte aligned");
+    static_assert((TMEM_COLS & (TMEM_COLS - 1)) == 0 && TMEM_COLS <= 512, "TMEM allocation");
 };
 
+// warps: the epilogue warps (one TMEM lane quarter and 16 channels each),
+// then one TMA producer warp and one MMA warp
 template <int COUT>
-constexpr int conv_threads() { return COUT >= 64 ? 512 : 128; }
+constexpr int conv_epi_warps() { return COUT >= 64 ? 16 : 4; }
+template <int COUT>
+constexpr int conv_threads() { return 32 * (conv_epi_warps<COUT>() + 2); }
 
 __device__ __forceinline__ int64_t pix_off(int b, int y, int x, int NY, int NX)
 {
     return ((int64_t)b * (NY + 2) + (y + 1)) * (NX + 2) + (x + 1);   // padded pixel index
 }
 
+// The CTA's rows are a contiguous share [r0, r1) of all B * (NX / 128) * NY
+// output rows, ordered (image, column block, row); a segment is a maximal run
+// of them in one (image, column block).
+struct ConvSeg {
+    int b, x0, ya, yb;
+};
+__device__ __forceinline__ ConvSeg conv_segment(int64_t q, int64_t r1, int NY, int ncb)
+{
+    const int64_t col = q / NY;
+    ConvSeg g;
+    g.ya = (int)(q - col * NY);
+    g.yb = (int)min((int64_t)NY, (int64_t)g.ya + (r1 - q));
+    g.b = (int)(col / ncb);
+    g.x0 = (int)(col - (int64_t)g.b * ncb) * 128;
+    return g;
+}
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a, int rows_per_item)
+__global__ void __launch_bounds__(conv_threads<COUT>(), 1)
+    k_conv3x3(const __grid_constant__ CUtensorMap tin, ConvArgs a)
 {
     using S = ConvSmem<CIN, COUT>;
+    constexpr int EW = conv_epi_warps<COUT>();
     constexpr int NT = conv_threads<COUT>();
-    constexpr int PARTS = (NT / 128) < (COUT / 16) ? (NT / 128) : (COUT / 16);   // channel parts of the epilogue
-    constexpr int CPP = COUT / PARTS;                                            // channels per part
+    constexpr int PARTS = (EW / 4) < (COUT / 16) ? (EW / 4) : (COUT / 16);   // channel parts of the epilogue
+    constexpr int CPP = COUT / PARTS;                                          // channels per part
     static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT >= 16 && COUT <= 128, "MMA shape");
+    static_assert(CPP == 16, "one 16-channel group per thread in the epilogue");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem + S::B_OFF;
     unsigned char* sR = smem + S::R_OFF;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 16);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int NY = a.NY, NX = a.NX;
-    const int ncb = NX / 128;
-    const int nch = (NY + rows_per_item - 1) / rows_per_item;
-    const int nitems = a.B * ncb * nch;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
-    constexpr uint32_t SBO_B = (CIN / 8) * 128;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);   // ring slot loaded
+    uint64_t* empty = full + S::NSLOT;                                   // ring slot read by its last MMA
+    uint64_t* accf = empty + S::NSLOT;                                   // accumulator complete
+    uint64_t* acce = accf + S::NACC;                                     // accumulator read by the epilogue
+    uint64_t* done = acce + S::NACC;                                     // every MMA of the CTA complete
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NY = a.NY, NX = a.NX, ncb = NX / 128;
+    const int64_t R = (int64_t)a.B * ncb * NY;
+    const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
 
     if (warp == 0) tc::tmem_alloc(tslot, S::TMEM_COLS);
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int i = 0; i < S::NSLOT; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < S::NACC; ++i) {
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], EW);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = (tc::smem_u32(smem) & 127) ? 1 : 0;   // TMA destinations need 128-byte alignment
         tc::fence_mbar_init();
     }
-    // all 9 weight taps into shared memory (K-major core-matrix layout)
+    // all 9 weight taps into shared memory (K-major core-matrix layout), tap
+    // (dy, dx) at position 3 dx + dy: for each dx the three dy taps form one
+    // B operand of 3 COUT rows
     for (int q = tid; q < 9 * COUT * (CIN / 8); q += NT) {
         const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
         const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
-        tc::cp_async16(sB + t * S::B_TAP + tc::kmajor_offset(n, 8 * j, CIN), a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
+        const int pos = 3 * (t % 3) + t / 3;
+        tc::cp_async16(sB + pos * S::B_TAP + tc::kmajor_offset(n, 8 * j, CIN), a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
     }
     tc::cp_async_commit_wait_all();
     tc::fence_proxy_async();
@@ -109,179 +158,204 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1) k_conv3x3(ConvArgs a,
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;   // the warp's TMEM lane quarter
-    const int part = warp >> 2;                                       // its share of the channels
-    const int pix = tid & 127;                                        // pixel of the tile = TMEM lane
-    uint32_t ph[2] = {0u, 0u};
-    bool ok = true;
+    const bool start = *abort_flag == 0;
 
-    // padded row pr (image row pr - 1) of image b, pixels x0 - 1 .. x0 + 128,
-    // into ring slot pr mod 5; one 16-byte channel group per copy
-    auto load_row = [&](int b, int pr, int x0) {
-        unsigned char* dst = sR + (pr % S::NSLOT) * S::ROW_BYTES;
-        const __nv_bfloat16* src = a.in + (((int64_t)b * (NY + 2) + pr) * (NX + 2) + x0) * CIN;
-        for (int q = tid; q < S::RP * S::KC; q += NT) {
-            const int px = q / S::KC, j = q - px * S::KC;
-            tc::cp_async16(dst + j * S::LBO_A + px * 16, src + (int64_t)px * CIN + 8 * j);
-        }
-    };
-    auto commit = [] { asm volatile("cp.async.commit_group;\n" ::: "memory"); };
-
-    // MMAs of output row y: taps (dy, dx) read padded rows y + dy + 1 at pixel shift dx
-    auto issue_row = [&](int y, uint32_t dcol) {
-        const uint32_t ring = tc::smem_u32(sR), bbase = tc::smem_u32(sB);
+    if (warp == EW) {
+        // TMA producer: padded rows ya .. yb + 1 of each segment into the ring,
+        // one box (130 pixels x 8 channels) per k core
+        if (lane == 0 && start) {
+            uint32_t ld = 0;
+            bool ok = true;
+            for (int64_t q = r0; q < r1 && ok;) {
+                const ConvSeg g = conv_segment(q, r1, NY, ncb);
+                for (int pr = g.ya; pr <= g.yb + 1; ++pr, ++ld) {
+                    const uint32_t s = ld % S::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&empty[s], ((ld / S::NSLOT) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    tc::mbar_arrive_expect_tx(&full[s], S::TX_BYTES);
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int dy = t / 3 - 1, dx = t % 3 - 1;
-            const uint32_t abase = ring + (uint32_t)(((y + dy + 1) % S::NSLOT) * S::ROW_BYTES + (dx + 1) * 16);
-#pragma unroll
-            for (int s = 0; s < CIN / 16; ++s)
-                tc::mma_bf16(tmem + dcol, tc::smem_desc(abase + 2 * s * S::LBO_A, S::LBO_A, 128),
-                             tc::smem_desc(bbase + t * S::B_TAP + 256 * s, 128, SBO_B), idesc,
-                             (t > 0 || s > 0) ? 1u : 0u);
-        }
-    };
-
-    // the thread's 16 channels of the bias, for the whole launch
-    static_assert(CPP == 16, "one 16-channel group per thread in the epilogue");
-    float bz[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) bz[i] = (a.bias && part < PARTS) ? a.bias[part * CPP + i] : 0.f;
-    // residual and mask inputs of the thread's pixel in row y, loaded before the
-    // wait for the row's MMAs so that their latency overlaps it
-    auto preload = [&](int b, int y, int x0, uint4* rp, uint4* mp) {
-        if (part >= PARTS) return;
-        const int64_t po = pix_off(b, y, x0 + pix, NY, NX);
-        if (a.resid) {
-            const uint4* rs = reinterpret_cast<const uint4*>(a.resid + po * COUT + part * CPP);
-            rp[0] = rs[0];
-            rp[1] = rs[1];
-        }
-        if (a.mask) {
-            const uint4* ms = reinterpret_cast<const uint4*>(a.mask + po * COUT + part * CPP);
-            mp[0] = ms[0];
-            mp[1] = ms[1];
-        }
-    };
-
-    // epilogue of output row y (TMEM accumulator at column dcol): thread = pixel
-    auto epilogue = [&](int b, int y, int x0, uint32_t dcol, const uint4* rp, const uint4* mp) {
-        if (part >= PARTS) return;
-        const int x = x0 + pix;
-        const int64_t po = pix_off(b, y, x, NY, NX);
-        const bool halo_hi = (x == 0), halo_lo = (x == NX - 1);   // copies into columns NX + 1 / 0
-        const int64_t po_h = halo_hi ? pix_off(b, y, NX, NY, NX) : pix_off(b, y, -1, NY, NX);
-        {
-            const int c0 = part * CPP;
-            float v[16];
-            tc::tmem_ld16(tmem + lane_base + dcol + (uint32_t)c0, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += bz[i];
-            if (a.y4 && c0 == 0) {
-                const int64_t q = (((int64_t)b * NY + y) * NX + x) * 4;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) a.y4[q + i] = a.x4[q + i] + v[i];
-            }
-            __align__(16) __nv_bfloat16 hz[16], ho[16], hm[16];
-            if (a.zout)
-#pragma unroll
-                for (int i = 0; i < 16; ++i) hz[i] = __float2bfloat16_rn(v[i]);
-            if (a.relu)
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-            if (a.resid) {
-                __align__(16) __nv_bfloat16 r[16];
-                reinterpret_cast<uint4*>(r)[0] = rp[0];
-                reinterpret_cast<uint4*>(r)[1] = rp[1];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += __bfloat162float(r[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i) ho[i] = __float2bfloat16_rn(v[i]);
-            if (a.mask) {
-                __align__(16) __nv_bfloat16 m[16];
-                reinterpret_cast<uint4*>(m)[0] = mp[0];
-                reinterpret_cast<uint4*>(m)[1] = mp[1];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) hm[i] = __bfloat162float(m[i]) > 0.f ? ho[i] : __float2bfloat16_rn(0.f);
-            }
-            auto store = [&](__nv_bfloat16* base, const __nv_bfloat16* h) {
-                if (!base) return;
-                const uint4* hv = reinterpret_cast<const uint4*>(h);
-                uint4* d = reinterpret_cast<uint4*>(base + po * COUT + c0);
-                d[0] = hv[0];
-                d[1] = hv[1];
-                if (halo_hi || halo_lo) {
-                    uint4* dh = reinterpret_cast<uint4*>(base + po_h * COUT + c0);
-                    dh[0] = hv[0];
-                    dh[1] = hv[1];
+                    for (int j = 0; j < S::KC; ++j)
+                        tc::tma_load_3d(sR + s * S::ROW_BYTES + j * S::LBO_A, &tin, 8 * j, g.x0, g.b * (NY + 2) + pr,
+                                        &full[s]);
                 }
-            };
-            store(a.zout, hz);
-            store(a.out, ho);
-            if (a.mask) store(a.out2, hm);
-        }
-    };
-
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-        const int ch = item % nch, rest = item / nch;
-        const int cb = rest % ncb, b = rest / ncb;
-        const int x0 = cb * 128;
-        const int ya = ch * rows_per_item, yb = min(ya + rows_per_item, NY);
-        // prologue: padded rows ya .. ya + 2 (image rows ya - 1 .. ya + 1), then ya + 3
-        load_row(b, ya, x0);
-        load_row(b, ya + 1, x0);
-        load_row(b, ya + 2, x0);
-        commit();
-        if (ya + 3 <= yb + 1) load_row(b, ya + 3, x0);
-        commit();
-        for (int y = ya; y < yb; ++y) {
-            const uint32_t dcur = (uint32_t)((y & 1) * COUT), dprev = (uint32_t)(((y - 1) & 1) * COUT);
-            // padded rows y .. y + 2 have landed; the epilogue of row y - 2 has
-            // read accumulator y & 1
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (tid == 0) {
-                issue_row(y, dcur);
-                tc::mma_commit(&bar[y & 1]);
+                q += g.yb - g.ya;
             }
-            uint4 rp[2] = {}, mp[2] = {};
-            if (y > ya) preload(b, y - 1, x0, rp, mp);
-            if (y > ya) {   // MMAs of row y - 1 done: its ring slot and accumulator are free to use
-                const bool w = tc::mbar_wait(&bar[(y - 1) & 1], ph[(y - 1) & 1]);
-                ph[(y - 1) & 1] ^= 1;
-                if (__syncthreads_or(!w)) { ok = false; break; }
+            // leave no copy in flight: the newest load of every slot has landed
+            for (uint32_t k = ld > (uint32_t)S::NSLOT ? ld - S::NSLOT : 0u; k < ld; ++k)
+                tc::mbar_wait(&full[k % S::NSLOT], (k / S::NSLOT) & 1);
+        }
+    } else if (warp == EW + 1) {
+        // MMA issue, one input row at a time: padded row p of a segment feeds
+        // output rows p, p - 1, p - 2 through taps dy = 0, 1, 2.  Output row r
+        // (CTA count) accumulates in TMEM slot (-r) mod NACC, so the three rows
+        // an input row feeds sit in consecutive slots and one MMA with
+        // N = 3 COUT (the dy taps of one dx stacked) covers them; where the
+        // slots wrap around the end of TMEM the MMA is split in two.
+        if (lane == 0 && start) {
+            constexpr uint32_t SBO_B = (CIN / 8) * 128;
+            const uint32_t ring = tc::smem_u32(sR);
+            const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(sB), 128, SBO_B);
+            auto slot = [](uint32_t r) { return (0u - r) % (uint32_t)S::NACC; };
+            uint32_t ld0 = 0, rs = 0;   // the segment's first load and first output row
+            bool ok = true, issued = false;
+            for (int64_t q = r0; q < r1 && ok;) {
+                const ConvSeg g = conv_segment(q, r1, NY, ncb);
+                const int n = g.yb - g.ya;
+                for (int i = 0; i < n + 2; ++i) {   // padded row p = ya + i, load ld0 + i
+                    const uint32_t k = ld0 + i;
+                    const int dlo = i - (n - 1) > 0 ? i - (n - 1) : 0;   // taps whose output row is in the segment
+                    const int dhi = i < 2 ? i : 2;
+                    if (i < n)   // output row p starts: its slot must have been read
+                        ok = tc::mbar_wait_or_abort(&acce[slot(rs + i)], (((rs + i) / S::NACC) & 1) ^ 1, abort_flag);
+                    if (ok) ok = tc::mbar_wait_or_abort(&full[k % S::NSLOT], (k / S::NSLOT) & 1, abort_flag);
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    const uint64_t adesc = tc::smem_desc(ring + (k % S::NSLOT) * S::ROW_BYTES, S::LBO_A, 128);
+                    // taps d0 .. d1 of tap column dx, K step s, into slots slot(rs + i - d0) ...
+                    auto issue = [&](int dx, int s, int d0, int d1, uint32_t accumulate) {
+                        const uint64_t ad = adesc + (uint64_t)((dx * 16 + 2 * s * S::LBO_A) >> 4);
+                        const uint32_t c = slot(rs + i - d0);
+                        const int m = d1 - d0 + 1;
+                        const int m1 = (int)c + m <= S::NACC ? m : S::NACC - (int)c;
+                        tc::mma_bf16(tmem + c * COUT, ad, bdesc0 + (uint64_t)(((3 * dx + d0) * S::B_TAP + 256 * s) >> 4),
+                                     tc::idesc_bf16_f32(128, m1 * COUT), accumulate);
+                        if (m1 < m)
+                            tc::mma_bf16(tmem, ad, bdesc0 + (uint64_t)(((3 * dx + d0 + m1) * S::B_TAP + 256 * s) >> 4),
+                                         tc::idesc_bf16_f32(128, (m - m1) * COUT), accumulate);
+                    };
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int s = 0; s < CIN / 16; ++s) {
+                            if (dx == 0 && s == 0 && dlo == 0) {   // the new accumulator of row p starts from zero
+                                issue(0, 0, 0, 0, 0u);
+                                if (dhi > 0) issue(0, 0, 1, dhi, 1u);
+                            } else {
+                                issue(dx, s, dlo, dhi, 1u);
+                            }
+                        }
+                    issued = true;
+                    tc::mma_commit(&empty[k % S::NSLOT]);                       // the row's last reader
+                    if (dhi == 2) tc::mma_commit(&accf[slot(rs + i - 2)]);      // output row p - 2 is complete
+                }
+                ld0 += n + 2;
+                rs += n;
+                q += n;
+            }
+            if (issued) {   // leave no MMA in flight
+                tc::mma_commit(done);
+                tc::mbar_wait(done, 0);
+            }
+        }
+    } else if (start) {
+        // epilogue: thread = pixel (TMEM lane) x 16 channels
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const int part = warp >> 2;
+        const int pix = tid & 127;
+        const int c0 = part * CPP;
+        float bz[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bz[i] = (a.bias && part < PARTS) ? a.bias[c0 + i] : 0.f;
+        uint32_t r = 0;
+        bool ok = true;
+        for (int64_t q = r0; q < r1 && ok;) {
+            const ConvSeg g = conv_segment(q, r1, NY, ncb);
+            for (int y = g.ya; y < g.yb; ++y, ++r) {
+                const int x = g.x0 + pix;
+                const int64_t po = pix_off(g.b, y, x, NY, NX);
+                // residual and mask loads issued before the wait for the row's MMAs
+                uint4 rp[2] = {}, mp[2] = {};
+                if (a.resid) {
+                    const uint4* rs = reinterpret_cast<const uint4*>(a.resid + po * COUT + c0);
+                    rp[0] = rs[0];
+                    rp[1] = rs[1];
+                }
+                if (a.mask) {
+                    const uint4* ms = reinterpret_cast<const uint4*>(a.mask + po * COUT + c0);
+                    mp[0] = ms[0];
+                    mp[1] = ms[1];
+                }
+                const uint32_t acc = (0u - r) % (uint32_t)S::NACC;   // the row's TMEM slot
+                const bool w = tc::mbar_wait_or_abort(&accf[acc], (r / S::NACC) & 1, abort_flag);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 tc::fence_after_sync();
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + acc * COUT + (uint32_t)c0, v);
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acce[acc]);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += bz[i];
+                if (a.y4 && c0 == 0) {
+                    const int64_t q4 = (((int64_t)g.b * NY + y) * NX + x) * 4;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a.y4[q4 + i] = a.x4[q4 + i] + v[i];
+                }
+                __align__(16) __nv_bfloat16 hz[16], ho[16], hm[16];
+                if (a.zout)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) hz[i] = __float2bfloat16_rn(v[i]);
+                if (a.relu)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+                if (a.resid) {
+                    __align__(16) __nv_bfloat16 rr[16];
+                    reinterpret_cast<uint4*>(rr)[0] = rp[0];
+                    reinterpret_cast<uint4*>(rr)[1] = rp[1];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += __bfloat162float(rr[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) ho[i] = __float2bfloat16_rn(v[i]);
+                if (a.mask) {
+                    __align__(16) __nv_bfloat16 m[16];
+                    reinterpret_cast<uint4*>(m)[0] = mp[0];
+                    reinterpret_cast<uint4*>(m)[1] = mp[1];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) hm[i] = __bfloat162float(m[i]) > 0.f ? ho[i] : __float2bfloat16_rn(0.f);
+                }
+                const bool halo_hi = (x == 0), halo_lo = (x == NX - 1);   // copies into columns NX + 1 / 0
+                const int64_t po_h = halo_hi ? pix_off(g.b, y, NX, NY, NX) : pix_off(g.b, y, -1, NY, NX);
+                auto store = [&](__nv_bfloat16* base, const __nv_bfloat16* h) {
+                    if (!base) return;
+                    const uint4* hv = reinterpret_cast<const uint4*>(h);
+                    uint4* d = reinterpret_cast<uint4*>(base + po * COUT + c0);
+                    d[0] = hv[0];
+                    d[1] = hv[1];
+                    if (halo_hi || halo_lo) {
+                        uint4* dh = reinterpret_cast<uint4*>(base + po_h * COUT + c0);
+                        dh[0] = hv[0];
+                        dh[1] = hv[1];
+                    }
+                };
+                store(a.zout, hz);
+                store(a.out, ho);
+                if (a.mask) store(a.out2, hm);
             }
-            // prefetch padded row y + 4 into the slot of padded row y - 1
-            if (y + 4 <= yb + 1) load_row(b, y + 4, x0);
-            commit();
-            if (y > ya) epilogue(b, y - 1, x0, dprev, rp, mp);
+            q += g.yb - g.ya;
         }
-        if (!ok) break;
-        {   // last row of the item
-            const int y = yb - 1;
-            uint4 rp[2] = {}, mp[2] = {};
-            preload(b, y, x0, rp, mp);
-            const bool w = tc::mbar_wait(&bar[y & 1], ph[y & 1]);
-            ph[y & 1] ^= 1;
-            if (__syncthreads_or(!w)) { ok = false; break; }
-            tc::fence_after_sync();
-            epilogue(b, y, x0, (uint32_t)((y & 1) * COUT), rp, mp);
-        }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        tc::fence_before_sync();
-        __syncthreads();   // accumulators read and ring idle before the next item
-        tc::fence_after_sync();
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (!ok && tid == 0) atomicExch(a.err, 1);
     tc::fence_before_sync();
     __syncthreads();
+    if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
     if (warp == 0) tc::tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+// cuTensorMapEncodeTiled from the driver, found once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
 }
 
 template <int CIN, int COUT>
@@ -290,15 +364,23 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
     using S = ConvSmem<CIN, COUT>;
     static unsigned long long attr_done = 0;      // per instantiation and device
     if (cudaError_t e = raise_smem_limit(k_conv3x3<CIN, COUT>, (int)S::BYTES, &attr_done); e != cudaSuccess) return e;
-    // rows per item: at least ~4 rows (prologue of 4 loaded rows) and about
-    // two items per SM over the whole launch
-    const int cols = a.B * (a.NX / 128);
-    int rpi = (int)(((int64_t)cols * a.NY + 2 * 152 - 1) / (2 * 152));
-    if (rpi < 4) rpi = 4;
-    if (rpi > a.NY) rpi = a.NY;
-    const int nitems = cols * ((a.NY + rpi - 1) / rpi);
-    const int blocks = nitems < 152 ? nitems : 152;
-    k_conv3x3<CIN, COUT><<<blocks, conv_threads<COUT>(), S::BYTES, s>>>(a, rpi);
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // the padded input as [B (NY + 2)][NX + 2][CIN]; a box is 8 channels x 130 pixels of one row
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {(cuuint64_t)CIN, (cuuint64_t)a.NX + 2, (cuuint64_t)a.B * (a.NY + 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)CIN * 2, (cuuint64_t)(a.NX + 2) * CIN * 2};
+    const cuuint32_t box[3] = {8, (cuuint32_t)S::RP, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(a.in), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    int sms = 0;
+    if (cudaError_t e = device_sms(&sms); e != cudaSuccess) return e;
+    const int64_t rows = (int64_t)a.B * (a.NX / 128) * a.NY;
+    const int blocks = (int)(rows < sms ? rows : sms);
+    k_conv3x3<CIN, COUT><<<blocks, conv_threads<COUT>(), S::BYTES, s>>>(m, a);
     return cudaGetLastError();
 }
 

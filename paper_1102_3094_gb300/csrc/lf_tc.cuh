@@ -1,7 +1,8 @@
 // lf_tc.cuh -- Blackwell (sm_103a) tensor-core building blocks written as
 // inline PTX: tensor-memory (TMEM) allocation, shared-memory matrix and
 // instruction descriptors for tcgen05.mma kind::f16 (BF16 inputs, FP32
-// accumulation), MMA issue / commit, TMEM loads, mbarriers with bounded waits.
+// accumulation), MMA issue / commit, TMEM loads, mbarriers with bounded waits,
+// tiled TMA loads.
 //
 // Shared-memory operand layout (SWIZZLE_NONE, K-major): a matrix of R rows x
 // K columns (BF16) is stored as 8x8 "core matrices" of 128 contiguous bytes
@@ -101,6 +102,49 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, uint32
         if (done) return true;
     }
     return false;
+}
+
+// The same wait for a pipeline of several warp roles: it also gives up when
+// another role has raised the CTA's abort flag, and raises it itself when its
+// own poll limit runs out, so that every role winds down.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* mbar, uint32_t phase, volatile int* abort_flag,
+                                                   uint32_t limit = (1u << 22))
+{
+    const uint32_t a = smem_u32(mbar);
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(phase) : "memory");
+        if (done) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Arrives once and adds `bytes` to the transaction count the phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Tiled TMA load of one box of a rank-3 tensor map (a __grid_constant__
+// kernel parameter) into shared memory; completes `bytes` on the mbarrier.
+// The innermost coordinate c0 times the element size must be a multiple of
+// 16 bytes and dst 128-byte aligned.
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2, uint64_t* mbar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3, %4}], [%5];\n"
+                 ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(mbar))
+                 : "memory");
 }
 
 // 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: warp
