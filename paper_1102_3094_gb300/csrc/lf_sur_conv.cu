@@ -58,19 +58,25 @@ template <int CIN, int COUT>
 struct ConvSmem {
     static constexpr int RP = 130;                   // ring row: pixels x0 - 1 .. x0 + 128
     static constexpr int KC = CIN / 8;               // 16-byte channel groups (k cores)
-    static constexpr int LBO_A = 2176;               // next k core: 130 pixels x 16 bytes, padded to 128 bytes
+    // 64 input channels: a ring row is 130 pixel rows of 128 bytes in the
+    // 128-byte swizzled K-major layout (16-byte chunk c of pixel p at chunk
+    // c ^ (p mod 8)), one TMA box per row; fewer channels: core-matrix
+    // interleaved rows ([k core][pixel][8 channels]), one box per k core
+    static constexpr bool SW = CIN == 64;
+    static constexpr int LBO_A = 2176;               // interleaved: next k core, 130 x 16 bytes padded to 128
     static constexpr int TX_BYTES = KC * RP * 16;    // bytes one row's TMA copies bring
-    static constexpr int ROW_BYTES = KC * LBO_A;
+    static constexpr int ROW_BYTES = SW ? 17 * 1024 : KC * LBO_A;
     static constexpr int NSLOT = 8;                  // ring of input rows
     static constexpr int NACC = 8;                   // TMEM accumulator slots of COUT columns (output rows)
     static constexpr int B_TAP = COUT * CIN * 2;
     static constexpr int B_OFF = 0;
     static constexpr int R_OFF = 9 * B_TAP;
     static constexpr int BAR_OFF = R_OFF + NSLOT * ROW_BYTES;
-    static constexpr int NBAR = 2 * NSLOT + 2 * NACC + 1;   // full, empty, acc full, acc empty, done
+    static constexpr int NBAR = 2 * NSLOT + 2 * NACC + 2;   // full, empty, acc full, acc empty, done, weights
     static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
     static constexpr int TMEM_COLS = NACC * COUT < 32 ? 32 : NACC * COUT;
-    static_assert(R_OFF % 128 == 0 && LBO_A % 128 == 0 && LBO_A >= RP * 16, "TMA destinations 128-byte aligned");
+    static_assert(R_OFF % 1024 == 0 && (!SW || ROW_BYTES % 1024 == 0) && LBO_A % 128 == 0 && LBO_A >= RP * 16,
+                  "TMA destinations 1024-byte aligned (swizzle pattern) and 128-byte aligned");
     static_assert((TMEM_COLS & (TMEM_COLS - 1)) == 0 && TMEM_COLS <= 512, "TMEM allocation");
 };
 
@@ -122,38 +128,35 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
     uint64_t* accf = empty + S::NSLOT;                                   // accumulator complete
     uint64_t* acce = accf + S::NACC;                                     // accumulator read by the epilogue
     uint64_t* done = acce + S::NACC;                                     // every MMA of the CTA complete
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* wbar = done + 1;                                           // weights in shared memory
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NY = a.NY, NX = a.NX, ncb = NX / 128;
     const int64_t R = (int64_t)a.B * ncb * NY;
     const int64_t r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+    // a residual that is the layer's own input is read from the input ring (the
+    // output row y's residual is padded row y + 1, pixels 1 .. 128 of its slot);
+    // a slot is then free once its MMAs and that read are done
+    const bool ring_res = CIN == COUT && a.resid != nullptr &&
+                          (const void*)a.resid == (const void*)a.in;
 
     if (warp == 0) tc::tmem_alloc(tslot, S::TMEM_COLS);
     if (tid == 0) {
         for (int i = 0; i < S::NSLOT; ++i) {
             tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&empty[i], 1);
+            tc::mbar_init(&empty[i], ring_res ? 1 + EW : 1);
         }
         for (int i = 0; i < S::NACC; ++i) {
             tc::mbar_init(&accf[i], 1);
             tc::mbar_init(&acce[i], EW);
         }
         tc::mbar_init(done, 1);
-        *abort_flag = (tc::smem_u32(smem) & 127) ? 1 : 0;   // TMA destinations need 128-byte alignment
+        tc::mbar_init(wbar, EW);
+        // TMA destinations: 128-byte aligned, 1024 for the swizzle pattern
+        *abort_flag = (tc::smem_u32(smem) & (S::SW ? 1023u : 127u)) ? 1 : 0;
         tc::fence_mbar_init();
     }
-    // all 9 weight taps into shared memory (K-major core-matrix layout), tap
-    // (dy, dx) at position 3 dx + dy: for each dx the three dy taps form one
-    // B operand of 3 COUT rows
-    for (int q = tid; q < 9 * COUT * (CIN / 8); q += NT) {
-        const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
-        const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
-        const int pos = 3 * (t % 3) + t / 3;
-        tc::cp_async16(sB + pos * S::B_TAP + tc::kmajor_offset(n, 8 * j, CIN), a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
-    }
-    tc::cp_async_commit_wait_all();
-    tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -172,10 +175,13 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
                     const uint32_t s = ld % S::NSLOT;
                     if (!tc::mbar_wait_or_abort(&empty[s], ((ld / S::NSLOT) & 1) ^ 1, abort_flag)) { ok = false; break; }
                     tc::mbar_arrive_expect_tx(&full[s], S::TX_BYTES);
+                    if (S::SW)
+                        tc::tma_load_3d(sR + s * S::ROW_BYTES, &tin, 0, g.x0, g.b * (NY + 2) + pr, &full[s]);
+                    else
 #pragma unroll
-                    for (int j = 0; j < S::KC; ++j)
-                        tc::tma_load_3d(sR + s * S::ROW_BYTES + j * S::LBO_A, &tin, 8 * j, g.x0, g.b * (NY + 2) + pr,
-                                        &full[s]);
+                        for (int j = 0; j < S::KC; ++j)
+                            tc::tma_load_3d(sR + s * S::ROW_BYTES + j * S::LBO_A, &tin, 8 * j, g.x0,
+                                            g.b * (NY + 2) + pr, &full[s]);
                 }
                 q += g.yb - g.ya;
             }
@@ -193,10 +199,11 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
         if (lane == 0 && start) {
             constexpr uint32_t SBO_B = (CIN / 8) * 128;
             const uint32_t ring = tc::smem_u32(sR);
-            const uint64_t bdesc0 = tc::smem_desc(tc::smem_u32(sB), 128, SBO_B);
+            const uint32_t bbase = tc::smem_u32(sB);
+            const uint64_t bdesc0 = tc::smem_desc(bbase, 128, SBO_B);
             auto slot = [](uint32_t r) { return (0u - r) % (uint32_t)S::NACC; };
             uint32_t ld0 = 0, rs = 0;   // the segment's first load and first output row
-            bool ok = true, issued = false;
+            bool ok = tc::mbar_wait_or_abort(wbar, 0, abort_flag), issued = false;
             for (int64_t q = r0; q < r1 && ok;) {
                 const ConvSeg g = conv_segment(q, r1, NY, ncb);
                 const int n = g.yb - g.ya;
@@ -209,32 +216,50 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
                     if (ok) ok = tc::mbar_wait_or_abort(&full[k % S::NSLOT], (k / S::NSLOT) & 1, abort_flag);
                     if (!ok) break;
                     tc::fence_after_sync();
-                    const uint64_t adesc = tc::smem_desc(ring + (k % S::NSLOT) * S::ROW_BYTES, S::LBO_A, 128);
-                    // taps d0 .. d1 of tap column dx, K step s, into slots slot(rs + i - d0) ...
-                    auto issue = [&](int dx, int s, int d0, int d1, uint32_t accumulate) {
-                        const uint64_t ad = adesc + (uint64_t)((dx * 16 + 2 * s * S::LBO_A) >> 4);
-                        const uint32_t c = slot(rs + i - d0);
-                        const int m = d1 - d0 + 1;
-                        const int m1 = (int)c + m <= S::NACC ? m : S::NACC - (int)c;
-                        tc::mma_bf16(tmem + c * COUT, ad, bdesc0 + (uint64_t)(((3 * dx + d0) * S::B_TAP + 256 * s) >> 4),
-                                     tc::idesc_bf16_f32(128, m1 * COUT), accumulate);
-                        if (m1 < m)
-                            tc::mma_bf16(tmem, ad, bdesc0 + (uint64_t)(((3 * dx + d0 + m1) * S::B_TAP + 256 * s) >> 4),
-                                         tc::idesc_bf16_f32(128, (m - m1) * COUT), accumulate);
-                    };
+                    // descriptors at the row's start (A) and at tap position 0 (B); an
+                    // offset within shared memory adds (bytes >> 4) to the start-address
+                    // field, so the (dx, s) offsets below are constants
+                    const uint32_t abase = ring + (k % S::NSLOT) * S::ROW_BYTES;
+                    const uint64_t a0 = S::SW ? tc::smem_desc_sw128(abase) : tc::smem_desc(abase, S::LBO_A, 128);
+                    const uint64_t b0 = S::SW ? tc::smem_desc_sw128(bbase) : bdesc0;
+                    // the taps dlo .. dhi go to slots slot(rs + i - dlo) onwards: one piece,
+                    // or two where the slots wrap around the end of TMEM
+                    const uint32_t c = slot(rs + i - dlo);
+                    const int m = dhi - dlo + 1;
+                    const int m1 = (int)c + m <= S::NACC ? m : S::NACC - (int)c, m2 = m - m1;
+                    const uint32_t d1 = tmem + c * COUT, id1 = tc::idesc_bf16_f32(128, m1 * COUT);
+                    const uint32_t id2 = tc::idesc_bf16_f32(128, (m2 > 0 ? m2 : 1) * COUT);
+                    const uint64_t b1 = b0 + (uint64_t)((dlo * S::B_TAP) >> 4), b2 = b1 + (uint64_t)((m1 * S::B_TAP) >> 4);
+                    constexpr int AS = S::SW ? 32 : 2 * S::LBO_A, AX = S::SW ? 128 : 16;   // A: K step, pixel
+                    constexpr int BS = S::SW ? 32 : 256;                                   // B: K step
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                         for (int s = 0; s < CIN / 16; ++s) {
-                            if (dx == 0 && s == 0 && dlo == 0) {   // the new accumulator of row p starts from zero
-                                issue(0, 0, 0, 0, 0u);
-                                if (dhi > 0) issue(0, 0, 1, dhi, 1u);
+                            const uint64_t ad = a0 + (uint64_t)((dx * AX + s * AS) >> 4);
+                            const uint64_t bo = (uint64_t)((3 * dx * S::B_TAP + s * BS) >> 4);
+                            if (dx == 0 && s == 0 && dlo == 0) {
+                                // the new accumulator of row p (tap dy = 0, slot c) starts from
+                                // zero; the taps dy = 1 .. dhi of the other rows accumulate
+                                tc::mma_bf16(d1, ad, b0, tc::idesc_bf16_f32(128, COUT), 0u);
+                                if (dhi > 0) {
+                                    const uint32_t c1 = (c + 1) % (uint32_t)S::NACC;
+                                    const int n1 = (int)c1 + dhi <= S::NACC ? dhi : S::NACC - (int)c1;
+                                    tc::mma_bf16(tmem + c1 * COUT, ad, b0 + (uint64_t)(S::B_TAP >> 4),
+                                                 tc::idesc_bf16_f32(128, n1 * COUT), 1u);
+                                    if (n1 < dhi)
+                                        tc::mma_bf16(tmem, ad, b0 + (uint64_t)(((1 + n1) * S::B_TAP) >> 4),
+                                                     tc::idesc_bf16_f32(128, (dhi - n1) * COUT), 1u);
+                                }
                             } else {
-                                issue(dx, s, dlo, dhi, 1u);
+                                tc::mma_bf16(d1, ad, b1 + bo, id1, 1u);
+                                if (m2 > 0) tc::mma_bf16(tmem, ad, b2 + bo, id2, 1u);
                             }
                         }
                     issued = true;
-                    tc::mma_commit(&empty[k % S::NSLOT]);                       // the row's last reader
+                    tc::mma_commit(&empty[k % S::NSLOT]);                       // the row's last MMA
+                    if (ring_res && (i == 0 || i == n + 1))   // no residual read of this row follows
+                        tc::mbar_arrive_cnt(&empty[k % S::NSLOT], EW);
                     if (dhi == 2) tc::mma_commit(&accf[slot(rs + i - 2)]);      // output row p - 2 is complete
                 }
                 ld0 += n + 2;
@@ -247,6 +272,21 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
             }
         }
     } else if (start) {
+        // the epilogue warps bring the 9 weight taps into shared memory (K-major
+        // core-matrix layout), tap (dy, dx) at position 3 dx + dy: for each dx
+        // the three dy taps form one B operand of 3 COUT rows
+        for (int q = tid; q < 9 * COUT * (CIN / 8); q += 32 * EW) {
+            const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
+            const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
+            const int pos = 3 * (t % 3) + t / 3;
+            const uint32_t off = S::SW ? (uint32_t)(n * 128 + ((j ^ (n & 7)) * 16))   // swizzled rows of 64 channels
+                                       : tc::kmajor_offset(n, 8 * j, CIN);
+            tc::cp_async16(sB + pos * S::B_TAP + off, a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
+        }
+        tc::cp_async_commit_wait_all();
+        tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(wbar);
         // epilogue: thread = pixel (TMEM lane) x 16 channels
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const int part = warp >> 2;
@@ -255,16 +295,17 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
         float bz[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) bz[i] = (a.bias && part < PARTS) ? a.bias[c0 + i] : 0.f;
-        uint32_t r = 0;
+        uint32_t r = 0, ld0 = 0;
         bool ok = true;
         for (int64_t q = r0; q < r1 && ok;) {
             const ConvSeg g = conv_segment(q, r1, NY, ncb);
             for (int y = g.ya; y < g.yb; ++y, ++r) {
+                const uint32_t kr = ld0 + (uint32_t)(y - g.ya) + 1;   // load of padded row y + 1
                 const int x = g.x0 + pix;
                 const int64_t po = pix_off(g.b, y, x, NY, NX);
                 // residual and mask loads issued before the wait for the row's MMAs
                 uint4 rp[2] = {}, mp[2] = {};
-                if (a.resid) {
+                if (a.resid && !ring_res) {
                     const uint4* rs = reinterpret_cast<const uint4*>(a.resid + po * COUT + c0);
                     rp[0] = rs[0];
                     rp[1] = rs[1];
@@ -283,6 +324,22 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[acc]);
+                if (ring_res) {   // the residual from the ring slot of padded row y + 1
+                    const uint32_t sl = kr % S::NSLOT;
+                    const bool wr = tc::mbar_wait_or_abort(&full[sl], (kr / S::NSLOT) & 1, abort_flag);
+                    if (!__all_sync(0xffffffffu, wr)) { ok = false; break; }
+                    const unsigned char* row = sR + sl * S::ROW_BYTES;
+                    const int px = pix + 1;
+                    if (S::SW) {   // swizzled pixel row
+                        rp[0] = *reinterpret_cast<const uint4*>(row + px * 128 + (((c0 / 8) ^ (px & 7)) * 16));
+                        rp[1] = *reinterpret_cast<const uint4*>(row + px * 128 + (((c0 / 8 + 1) ^ (px & 7)) * 16));
+                    } else {
+                        rp[0] = *reinterpret_cast<const uint4*>(row + (c0 / 8) * S::LBO_A + px * 16);
+                        rp[1] = *reinterpret_cast<const uint4*>(row + (c0 / 8 + 1) * S::LBO_A + px * 16);
+                    }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&empty[sl]);
+                }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] += bz[i];
                 if (a.y4 && c0 == 0) {
@@ -331,6 +388,7 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
                 store(a.out, ho);
                 if (a.mask) store(a.out2, hm);
             }
+            ld0 += (uint32_t)(g.yb - g.ya) + 2;
             q += g.yb - g.ya;
         }
     }
@@ -366,14 +424,16 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
     if (cudaError_t e = raise_smem_limit(k_conv3x3<CIN, COUT>, (int)S::BYTES, &attr_done); e != cudaSuccess) return e;
     const EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
-    // the padded input as [B (NY + 2)][NX + 2][CIN]; a box is 8 channels x 130 pixels of one row
+    // the padded input as [B (NY + 2)][NX + 2][CIN]; a box is 130 pixels of one row, all 64 channels
+    // (128-byte swizzle) or 8 channels
     CUtensorMap m;
     const cuuint64_t dims[3] = {(cuuint64_t)CIN, (cuuint64_t)a.NX + 2, (cuuint64_t)a.B * (a.NY + 2)};
     const cuuint64_t strides[2] = {(cuuint64_t)CIN * 2, (cuuint64_t)(a.NX + 2) * CIN * 2};
-    const cuuint32_t box[3] = {8, (cuuint32_t)S::RP, 1};
+    const cuuint32_t box[3] = {S::SW ? (cuuint32_t)CIN : 8u, (cuuint32_t)S::RP, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(a.in), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, S::SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     int sms = 0;

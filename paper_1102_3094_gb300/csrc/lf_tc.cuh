@@ -37,6 +37,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                            // base offset 0, layout type 0 = no swizzle
 }
 
+// Descriptor of a K-major operand in the 128-byte swizzled layout (rows of
+// 128 bytes, eight-row groups 1024 bytes apart, 16-byte chunk c of row r at
+// chunk c ^ (r mod 8) of a 1024-byte aligned pattern, as a TMA copy with
+// 128-byte swizzle writes it).  The start address may sit inside a pattern
+// (a row offset, or a K offset of 32 bytes per K = 16 step): the swizzle
+// follows the address bits, so the base-offset field stays 0 (measured: a
+// base offset of (address / 128) mod 8 reads the wrong chunks).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                          // leading byte offset: unused for this layout
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next eight-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version of this architecture
+    d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D in FP32, A and B in
 // BF16, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
@@ -126,6 +144,11 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* mbar, uint32_t phas
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t* mbar, uint32_t count)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
 // Arrives once and adds `bytes` to the transaction count the phase waits for.

@@ -25,6 +25,10 @@ def _rand(shape, scale, g):
     (16, 64, 1, False, (2, 5, 256)), (64, 64, 1, True, (2, 5, 256)), (64, 16, 0, False, (2, 5, 256)),
     (64, 64, 1, True, (3, 121, 256)),     # more row runs than SMs: CTAs march over several
     (16, 64, 1, False, (1, 1, 128)),      # one row: prologue and drain only
+    # the residual is the layer's own input (the surrogate's residual layers):
+    # it is read from the input rows already in shared memory
+    (64, 64, 1, "self", (2, 5, 256)), (64, 64, 1, "self", (3, 121, 256)), (64, 64, 0, "self", (1, 1, 128)),
+    (64, 64, 1, "self", (2, 2, 128)),
 ])
 def test_conv3x3_forward(cin, cout, relu, use_resid, shape):
     g = torch.Generator().manual_seed(cin * 100 + cout)
@@ -32,12 +36,12 @@ def test_conv3x3_forward(cin, cout, relu, use_resid, shape):
     h = _rand((B, NY, NX, cin), 1.0, g)
     W = _rand((9, cout, cin), 0.1, g)
     bias = (0.1 * torch.randn(cout, generator=g)).float()
-    resid = _rand((B, NY, NX, cout), 1.0, g) if use_resid else None
+    resid = h if use_resid == "self" else _rand((B, NY, NX, cout), 1.0, g) if use_resid else None
     dev = "cuda"
     inp = lf.pad_nhwc(h).to(dev)
     out = torch.zeros((B, NY + 2, NX + 2, cout), dtype=BF, device=dev)
     zout = torch.zeros_like(out)
-    res_d = lf.pad_nhwc(resid).to(dev) if use_resid else None
+    res_d = inp if use_resid == "self" else lf.pad_nhwc(resid).to(dev) if use_resid else None
     x4 = torch.randn((B, NY, NX, 4), generator=g).float().to(dev) if cout == 16 else None
     y4 = torch.zeros((B, NY, NX, 4), dtype=torch.float32, device=dev) if cout == 16 else None
     err = torch.zeros(1, dtype=torch.int32, device=dev)
