@@ -549,6 +549,7 @@ def run_surrogate(args):
                "windows_checked": rep["shadow_checks"], "t_prediction_s": t_pred, "t_plain_window_s": t_pw,
                "what": "plain windows + predictions whose shadow check passed + (prediction + plain window) for "
                        "every other surrogate window; shadow windows are the verification, not counted"}
+    conv = conv_kernel_times(lf, torch, dev, stream)
     sites = NX * NY
     value = 1e-6 * sites * nsteps / tts["t_s"] if tts else 0.0
     line = {
@@ -567,13 +568,61 @@ def run_surrogate(args):
         "surrogate": {"t_data_s": t_data, "t_train_s": t_train, "losses": losses, "heldout": ho,
                       "learning_curve": curve, "report": rep, "run_error": run_error,
                       "t_plain_only_s": t_plain, "t_interleaved_wall_s": t_hyb,
-                      "time_to_solution_known_good": tts,
+                      "time_to_solution_known_good": tts, "conv_kernels": conv,
                       "final_phi_rel_l2_vs_plain": l2, "final_sk_peak_err_vs_plain": final_sk_err},
     }
     print(json.dumps(line), flush=True)
     for o in (plain, hyb, sur):
         o.close()
     return 0
+
+
+def conv_kernel_times(lf, torch, dev, stream, B=8, NY=256, NX=256, reps=30):
+    """Device time of single tensor-core convolutions (the surrogate's layer shapes at
+    batch B): each launch after a 256 MB L2 flush and a sleep kernel, so that the stream
+    is busy when the start event is recorded; CUDA events on the launching stream."""
+    bf = torch.bfloat16
+    g = torch.Generator(device=dev).manual_seed(7)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {}
+    cases = [("64->64 no residual", 64, 64, False, False), ("64->64 residual = input", 64, 64, True, False),
+             ("64->64 residual = input, pre-activation out", 64, 64, True, True),
+             ("16->64", 16, 64, False, False), ("64->16", 64, 16, False, False)]
+    with torch.cuda.stream(stream):
+        for name, cin, cout, res, zo in cases:
+            inp = torch.randn((B, NY + 2, NX + 2, cin), device=dev, generator=g).to(bf)
+            w = (0.1 * torch.randn((9, cout, cin), device=dev, generator=g)).to(bf).contiguous()
+            bias = torch.randn(cout, device=dev, generator=g)
+            o = torch.zeros((B, NY + 2, NX + 2, cout), dtype=bf, device=dev)
+            z = torch.zeros_like(o) if zo else None
+            x4 = torch.zeros((B, NY, NX, 4), device=dev) if cout == 16 else None
+            y4 = torch.zeros_like(x4) if cout == 16 else None
+
+            def call():
+                lf.lf_sur_conv3x3(B, NY, NX, cin, cout, inp, w, bias, 1, inp if res else None, None, o, None, z,
+                                  x4, y4, err, stream=stream)
+            for _ in range(3):
+                call()
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                torch.cuda._sleep(2_000_000)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call()
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            us = 1e3 * tot / reps
+            flop = 2 * 9 * cin * cout * B * NY * NX
+            out[name] = {"us": us, "tflops": flop / us / 1e6}
+        torch.cuda.synchronize()
+        if int(err.item()) != 0:
+            raise RuntimeError("convolution kernel reported an error")
+    out["shape"] = f"batch {B}, {NY}x{NX}, BF16 in, FP32 accumulate"
+    return out
 
 
 def run_ours(args):

@@ -279,16 +279,18 @@ int refresh_bf16(lf_sur* s, int do_update, float lr)
     return cudaGetLastError() == cudaSuccess ? LF_OK : LF_ECUDA;
 }
 
-int forward(lf_sur* s, const float* raw, int B)
+// keep_z: store each layer's pre-activation values for the backward pass
+// (training); a prediction does not need them
+int forward(lf_sur* s, const float* raw, int B, bool keep_z)
 {
     const int NY = s->NY, NX = s->NX;
     const int64_t N = (int64_t)B * NY * NX;
     k_norm_in<<<blocks_for(N), 256, 0, s->stream>>>(raw, B, NY, NX, s->norm, s->x16, s->x4);
     int rc = lf_sur_conv3x3(B, NY, NX, 16, 64, s->x16, s->wbf[0], s->b[0], 1, nullptr, nullptr, s->h[0], nullptr,
-                            s->z[0], nullptr, nullptr, s->err, s->stream);
+                            keep_z ? s->z[0] : nullptr, nullptr, nullptr, s->err, s->stream);
     for (int l = 1; l < 5 && rc == LF_OK; ++l)
         rc = lf_sur_conv3x3(B, NY, NX, 64, 64, s->h[l - 1], s->wbf[l], s->b[l], 1, s->h[l - 1], nullptr, s->h[l],
-                            nullptr, s->z[l], nullptr, nullptr, s->err, s->stream);
+                            nullptr, keep_z ? s->z[l] : nullptr, nullptr, nullptr, s->err, s->stream);
     if (rc == LF_OK)
         rc = lf_sur_conv3x3(B, NY, NX, 64, 16, s->h[4], s->wbf[5], s->b[5], 0, nullptr, nullptr, nullptr, nullptr,
                             nullptr, s->x4, s->y4, s->err, s->stream);
@@ -300,7 +302,7 @@ int loss_and_grads(lf_sur* s, const float* x, const float* y, int B, double* los
 {
     const int NY = s->NY, NX = s->NX;
     const int64_t N = (int64_t)B * NY * NX;
-    int rc = forward(s, x, B);
+    int rc = forward(s, x, B, grads);
     if (rc != LF_OK) return rc;
     k_norm_target<<<blocks_for(N), 256, 0, s->stream>>>(y, B, NY, NX, s->norm, s->t4);
     const unsigned mb = blocks_for(N);
@@ -502,7 +504,7 @@ int lf_sur_predict(lf_sur* s, const float* x, float* y, int B)
 {
     lf::NvtxRange nvtx_range("lf_sur_predict");
     if (!s || !x || !y || B < 1 || B > s->maxB) return LF_EINVAL;
-    int rc = forward(s, x, B);
+    int rc = forward(s, x, B, false);
     if (rc != LF_OK) return rc;
     k_denorm<<<blocks_for((int64_t)B * s->NY * s->NX), 256, 0, s->stream>>>(s->y4, B, s->NY, s->NX, s->norm, y);
     return cudaGetLastError() == cudaSuccess ? LF_OK : LF_ECUDA;

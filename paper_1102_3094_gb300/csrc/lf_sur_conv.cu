@@ -10,24 +10,30 @@
 //
 // One persistent CTA per SM takes an equal contiguous share of the output
 // rows (ordered image, 128-pixel column block, row) and marches down them.
-// Input rows (130 pixels with the halo) sit in an 8-slot shared-memory ring in
-// a pixel-major core-matrix layout ([k core][pixel][8 channels], 16 bytes per
-// pixel and core): the 8 pixels of a core matrix are contiguous, so the A
-// operand of tap (dy, dx) is the ring row of dy with its descriptor start
-// moved by dx pixels -- all 9 taps read the same three rows, which are loaded
-// once.  The 9 weight taps stay in shared memory (K-major).  The warps have
-// fixed roles that hand work over through mbarriers:
-//   * a producer warp loads each row by TMA (one 8-channel x 130-pixel box
-//     per k core) as soon as its ring slot is free;
-//   * an MMA warp issues the 9 x CIN / 16 MMAs of a row into one of four TMEM
-//     accumulators once its three rows have landed and the accumulator has
-//     been read, and commits the accumulator and the row slot it no longer
-//     needs;
+// Input rows (130 pixels with the halo) sit in an 8-slot shared-memory ring,
+// K-major: with 64 channels each pixel is a 128-byte row of the 128-byte
+// swizzled layout; with 16, the interleaved core-matrix layout ([k core]
+// [pixel][8 channels]).  Either way the A operand of tap (dy, dx) is the ring
+// row of dy with its descriptor start moved by dx pixels -- all 9 taps read
+// the same three rows, which are loaded once.  The 9 weight taps stay in
+// shared memory in the same K-major layouts.  A residual that is the layer's
+// own input is read from the ring as well.  The warps have fixed roles that
+// hand work over through mbarriers:
+//   * a producer warp loads the weights and then each row by TMA as soon as
+//     its ring slot is free (64 channels: one box of 130 pixels in the
+//     128-byte swizzled layout; 16: one 8-channel box per k core);
+//   * an MMA warp issues an input row's MMAs once it has landed and the
+//     accumulator slot of the output row it starts has been read, and commits
+//     the output row it completes and the input row it no longer needs;
 //   * the epilogue warps (a TMEM lane quarter and 16 channels each: sixteen
 //     warps for 64 output channels, four for 16) read an accumulator, release
 //     it, and add bias, activation, residual and mask on the way out.
+// Each input row feeds the three output rows it touches: the dy taps of one
+// tap column dx are stacked along N (one MMA with N = 3 COUT per dx and K
+// step), and output rows accumulate in eight TMEM slots of COUT columns
+// (slot (-r) mod 8 for the CTA's r-th row, so the three rows are adjacent).
 // So the loads of the rows ahead, the MMAs of the next rows and the epilogue
-// of the current one overlap, with up to four rows between MMA and epilogue.
+// of the current one overlap, with up to five rows between MMA and epilogue.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -111,7 +117,7 @@ __device__ __forceinline__ ConvSeg conv_segment(int64_t q, int64_t r1, int NY, i
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
-    k_conv3x3(const __grid_constant__ CUtensorMap tin, ConvArgs a)
+    k_conv3x3(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tw, ConvArgs a)
 {
     using S = ConvSmem<CIN, COUT>;
     constexpr int EW = conv_epi_warps<COUT>();
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
             tc::mbar_init(&acce[i], EW);
         }
         tc::mbar_init(done, 1);
-        tc::mbar_init(wbar, EW);
+        tc::mbar_init(wbar, S::SW ? 1 : EW);
         // TMA destinations: 128-byte aligned, 1024 for the swizzle pattern
         *abort_flag = (tc::smem_u32(smem) & (S::SW ? 1023u : 127u)) ? 1 : 0;
         tc::fence_mbar_init();
@@ -167,6 +173,11 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
         // TMA producer: padded rows ya .. yb + 1 of each segment into the ring,
         // one box (130 pixels x 8 channels) per k core
         if (lane == 0 && start) {
+            if (S::SW) {   // the 9 weight taps, one swizzled box of COUT rows x 64 channels each
+                tc::mbar_arrive_expect_tx(wbar, 9 * S::B_TAP);
+                for (int t = 0; t < 9; ++t)
+                    tc::tma_load_3d(sB + (3 * (t % 3) + t / 3) * S::B_TAP, &tw, 0, 0, t, wbar);
+            }
             uint32_t ld = 0;
             bool ok = true;
             for (int64_t q = r0; q < r1 && ok;) {
@@ -272,21 +283,23 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
             }
         }
     } else if (start) {
-        // the epilogue warps bring the 9 weight taps into shared memory (K-major
-        // core-matrix layout), tap (dy, dx) at position 3 dx + dy: for each dx
-        // the three dy taps form one B operand of 3 COUT rows
-        for (int q = tid; q < 9 * COUT * (CIN / 8); q += 32 * EW) {
-            const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
-            const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
-            const int pos = 3 * (t % 3) + t / 3;
-            const uint32_t off = S::SW ? (uint32_t)(n * 128 + ((j ^ (n & 7)) * 16))   // swizzled rows of 64 channels
-                                       : tc::kmajor_offset(n, 8 * j, CIN);
-            tc::cp_async16(sB + pos * S::B_TAP + off, a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
+        // the 9 weight taps, tap (dy, dx) at position 3 dx + dy, so that for each
+        // dx the three dy taps form one B operand of 3 COUT rows: 64 input
+        // channels come by TMA in the producer (swizzled rows); fewer, from the
+        // epilogue warps in the interleaved K-major core-matrix layout
+        if (!S::SW) {
+            for (int q = tid; q < 9 * COUT * (CIN / 8); q += 32 * EW) {
+                const int t = q / (COUT * (CIN / 8)), rem = q - t * (COUT * (CIN / 8));
+                const int n = rem / (CIN / 8), j = rem - n * (CIN / 8);
+                const int pos = 3 * (t % 3) + t / 3;
+                tc::cp_async16(sB + pos * S::B_TAP + tc::kmajor_offset(n, 8 * j, CIN),
+                               a.w + ((int64_t)t * COUT + n) * CIN + 8 * j);
+            }
+            tc::cp_async_commit_wait_all();
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(wbar);
         }
-        tc::cp_async_commit_wait_all();
-        tc::fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(wbar);
         // epilogue: thread = pixel (TMEM lane) x 16 channels
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
         const int part = warp >> 2;
@@ -436,11 +449,20 @@ cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s)
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+    // the weights as [9][COUT][CIN]; a box is one tap (used with 64 input channels)
+    CUtensorMap mw;
+    const cuuint64_t wdims[3] = {(cuuint64_t)CIN, (cuuint64_t)COUT, 9};
+    const cuuint64_t wstrides[2] = {(cuuint64_t)CIN * 2, (cuuint64_t)COUT * CIN * 2};
+    const cuuint32_t wbox[3] = {(cuuint32_t)CIN, (cuuint32_t)COUT, 1};
+    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(a.w), wdims, wstrides, wbox, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, S::SW ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     int sms = 0;
     if (cudaError_t e = device_sms(&sms); e != cudaSuccess) return e;
     const int64_t rows = (int64_t)a.B * (a.NX / 128) * a.NY;
     const int blocks = (int)(rows < sms ? rows : sms);
-    k_conv3x3<CIN, COUT><<<blocks, conv_threads<COUT>(), S::BYTES, s>>>(m, a);
+    k_conv3x3<CIN, COUT><<<blocks, conv_threads<COUT>(), S::BYTES, s>>>(m, mw, a);
     return cudaGetLastError();
 }
 
