@@ -578,7 +578,7 @@ def run_surrogate(args):
 
 
 def conv_kernel_times(lf, torch, dev, stream, B=8, NY=256, NX=256, reps=30):
-    """Device time of single tensor-core convolutions (the surrogate's layer shapes at
+    """Device time of single tensor-core convolutions and weight gradients (the surrogate's layer shapes at
     batch B): each launch after a 256 MB L2 flush and a sleep kernel, so that the stream
     is busy when the start event is recorded; CUDA events on the launching stream."""
     bf = torch.bfloat16
@@ -618,6 +618,25 @@ def conv_kernel_times(lf, torch, dev, stream, B=8, NY=256, NX=256, reps=30):
             us = 1e3 * tot / reps
             flop = 2 * 9 * cin * cout * B * NY * NX
             out[name] = {"us": us, "tflops": flop / us / 1e6}
+        for cin, cout in ((64, 64), (16, 64), (64, 16)):   # weight gradients
+            h = torch.randn((B, NY + 2, NX + 2, cin), device=dev, generator=g).to(bf)
+            gr = torch.randn((B, NY + 2, NX + 2, cout), device=dev, generator=g).to(bf)
+            dW = torch.zeros((9, cout, cin), device=dev)
+            for _ in range(3):
+                lf.lf_sur_conv3x3_wgrad(B, NY, NX, cin, cout, h, gr, dW, err, stream=stream)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                torch.cuda._sleep(2_000_000)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                lf.lf_sur_conv3x3_wgrad(B, NY, NX, cin, cout, h, gr, dW, err, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            us = 1e3 * tot / reps
+            out[f"weight gradient {cin}->{cout}"] = {"us": us, "tflops": 2 * 9 * cin * cout * B * NY * NX / us / 1e6}
         torch.cuda.synchronize()
         if int(err.item()) != 0:
             raise RuntimeError("convolution kernel reported an error")

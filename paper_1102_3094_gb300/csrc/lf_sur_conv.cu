@@ -682,6 +682,201 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict
     dW[idx] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of the 64 -> 64 convolution as a warp pipeline.  The items
+// and the partial layout are those of k_conv_wgrad<64, 64> (three tap groups
+// by dy, each over a slice of the row tiles); per row tile the producer warp
+// brings g (128 pixels) and the h row of the group's dy (130 pixels) by TMA in
+// the 128-byte swizzled layout, which is MN-major for this GEMM (a pixel is a
+// K row of 64 channels).  The MMA warp takes M = 64 from g (output channel o)
+// and N = 192 from h: the three dx taps stacked as the three 64-channel atoms
+// of the B operand, one pixel (128 bytes) apart, so one MMA per 16 pixels
+// covers the group's three taps.  Two TMEM accumulators of 192 columns let
+// the epilogue warps write one item's partial while the next accumulates.
+// ---------------------------------------------------------------------------
+struct Wg64 {
+    static constexpr int NSLOT = 6;
+    static constexpr int G_BYTES = 128 * 128, H_BYTES = 17 * 1024;   // 128 / 130 pixel rows of 128 bytes
+    static constexpr int SLOT = G_BYTES + H_BYTES;
+    static constexpr int BAR_OFF = NSLOT * SLOT;
+    static constexpr int NBAR = 2 * NSLOT + 2 + 2 + 1;                // full, empty, acc full, acc empty, done
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int THREADS = 6 * 32;                            // 4 epilogue warps, producer, MMA
+    static_assert(SLOT % 1024 == 0 && G_BYTES % 1024 == 0, "swizzle patterns 1024-byte aligned");
+};
+
+__global__ void __launch_bounds__(Wg64::THREADS, 1)
+    k_wgrad64(const __grid_constant__ CUtensorMap tg, const __grid_constant__ CUtensorMap th, WgArgs a)
+{
+    using S = WgCfg<64, 64>;
+    using P = Wg64;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + P::BAR_OFF);
+    uint64_t* empty = full + P::NSLOT;
+    uint64_t* accf = empty + P::NSLOT;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NY = a.NY, NX = a.NX, ncb = NX / 128;
+    const int64_t R = (int64_t)a.B * ncb * NY;
+    constexpr int NITEM = S::NG * S::SLICES;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (tid == 0) {
+        for (int i = 0; i < P::NSLOT; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], 4);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = (tc::smem_u32(smem) & 1023u) ? 1 : 0;
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const bool start = *abort_flag == 0;
+    // the rows of item `it`: [r0, r1) of the row tiles ordered (image, column block, row)
+    auto item_rows = [&](int it, int64_t& r0, int64_t& r1) {
+        const int sl = it % S::SLICES;
+        r0 = R * sl / S::SLICES;
+        r1 = R * (sl + 1) / S::SLICES;
+    };
+
+    if (warp == 4) {   // producer
+        if (lane == 0 && start) {
+            uint32_t ld = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
+                const int gi = it / S::SLICES;          // padded h row y + gi: dy = gi - 1
+                int64_t r0, r1;
+                item_rows(it, r0, r1);
+                for (int64_t r = r0; r < r1; ++r, ++ld) {
+                    const int64_t col = r / NY;
+                    const int y = (int)(r - col * NY), b = (int)(col / ncb), x0 = (int)(col - (int64_t)b * ncb) * 128;
+                    const uint32_t sl = ld % P::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&empty[sl], ((ld / P::NSLOT) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    unsigned char* dst = smem + sl * P::SLOT;
+                    tc::mbar_arrive_expect_tx(&full[sl], 128 * 128 + 130 * 128);
+                    tc::tma_load_3d(dst, &tg, 0, x0 + 1, b * (NY + 2) + y + 1, &full[sl]);
+                    tc::tma_load_3d(dst + P::G_BYTES, &th, 0, x0, b * (NY + 2) + y + gi, &full[sl]);
+                }
+            }
+            for (uint32_t k = ld > (uint32_t)P::NSLOT ? ld - P::NSLOT : 0u; k < ld; ++k)
+                tc::mbar_wait(&full[k % P::NSLOT], (k / P::NSLOT) & 1);
+        }
+    } else if (warp == 5) {   // MMA issue
+        if (lane == 0 && start) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(64, 192) | (1u << 15) | (1u << 16);   // both MN-major
+            const uint32_t base = tc::smem_u32(smem);
+            uint32_t ld = 0, u = 0;
+            bool ok = true, issued = false;
+            for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
+                int64_t r0, r1;
+                item_rows(it, r0, r1);
+                if (r1 <= r0) continue;
+                const uint32_t buf = u & 1, dcol = tmem + buf * 192;
+                if (!tc::mbar_wait_or_abort(&acce[buf], ((u >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                tc::fence_after_sync();
+                for (int64_t r = r0; r < r1; ++r, ++ld) {
+                    const uint32_t sl = ld % P::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&full[sl], (ld / P::NSLOT) & 1, abort_flag)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t gb = base + sl * P::SLOT, hb = gb + P::G_BYTES;
+#pragma unroll
+                    for (int s = 0; s < 8; ++s)   // 16 pixels per MMA
+                        tc::mma_bf16(dcol, tc::smem_desc_sw128_mn(gb + s * 2048, 1024, 1024),
+                                     tc::smem_desc_sw128_mn(hb + s * 2048, 128, 1024), idesc,
+                                     (r == r0 && s == 0) ? 0u : 1u);
+                    issued = true;
+                    tc::mma_commit(&empty[sl]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&accf[buf]);
+                ++u;
+            }
+            if (issued) {
+                tc::mma_commit(done);
+                tc::mbar_wait(done, 0);
+            }
+        }
+    } else if (start) {   // epilogue: M = 64 rows 16 w + l sit in lanes 32 w + l, l < 16
+        uint32_t u = 0;
+        const int m = 16 * warp + lane;   // output channel o
+        for (int it = blockIdx.x; it < NITEM; it += gridDim.x) {
+            int64_t r0, r1;
+            item_rows(it, r0, r1);
+            float* dst = a.part + (size_t)it * 3 * 64 * 64;   // [tap j][i][o] as k_wgrad_reduce<64, 64> reads it
+            if (r1 <= r0) {
+                for (int q = lane; q < 3 * 64 * 16; q += 32) {   // this warp's 16 output channels
+                    const int j = q / (64 * 16), rem = q - j * 64 * 16;
+                    dst[((size_t)j * 64 + rem / 16) * 64 + 16 * warp + rem % 16] = 0.f;
+                }
+                continue;
+            }
+            const uint32_t buf = u & 1;
+            const bool w = tc::mbar_wait_or_abort(&accf[buf], (u >> 1) & 1, abort_flag);
+            if (!__all_sync(0xffffffffu, w)) break;
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int j = 0; j < 3; ++j)
+#pragma unroll 1
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + buf * 192 + (uint32_t)(j * 64 + c0), v);
+                    if (lane < 16)
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) dst[((size_t)j * 64 + c0 + q) * 64 + m] = v[q];
+                }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[buf]);
+            ++u;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+cudaError_t launch_wgrad64(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
+                           size_t part_floats, float* dW, int* err, cudaStream_t s)
+{
+    using S = WgCfg<64, 64>;
+    static unsigned long long attr_done = 0;
+    if (cudaError_t e = raise_smem_limit(k_wgrad64, (int)Wg64::BYTES, &attr_done); e != cudaSuccess) return e;
+    if (part_floats < S::PART) return cudaErrorInvalidValue;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // g and h as [B (NY + 2)][NX + 2][64], boxes of 128 / 130 pixels x 64 channels, 128-byte swizzle
+    CUtensorMap mg, mh;
+    const cuuint64_t dims[3] = {64, (cuuint64_t)NX + 2, (cuuint64_t)B * (NY + 2)};
+    const cuuint64_t strides[2] = {128, (cuuint64_t)(NX + 2) * 128};
+    const cuuint32_t boxg[3] = {64, 128, 1}, boxh[3] = {64, 130, 1}, estr[3] = {1, 1, 1};
+    if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(g), dims, strides, boxg, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(h), dims, strides, boxh, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    int sms = 0;
+    if (cudaError_t e = device_sms(&sms); e != cudaSuccess) return e;
+    constexpr int NITEM = S::NG * S::SLICES;
+    WgArgs a{h, g, part, B, NY, NX, err};
+    k_wgrad64<<<NITEM < sms ? NITEM : sms, Wg64::THREADS, Wg64::BYTES, s>>>(mg, mh, a);
+    const int n = 9 * 64 * 64;
+    k_wgrad_reduce<64, 64><<<(n + 255) / 256, 256, 0, s>>>(part, dW);
+    return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
                          size_t part_floats, float* dW, int* err, cudaStream_t s)
@@ -702,7 +897,7 @@ cudaError_t conv3x3_wgrad(int cin, int cout, const __nv_bfloat16* h, const __nv_
                           float* part, size_t part_floats, float* dW, int* err, cudaStream_t s)
 {
     if (cin == 16 && cout == 64) return launch_wgrad<16, 64>(h, g, B, NY, NX, part, part_floats, dW, err, s);
-    if (cin == 64 && cout == 64) return launch_wgrad<64, 64>(h, g, B, NY, NX, part, part_floats, dW, err, s);
+    if (cin == 64 && cout == 64) return launch_wgrad64(h, g, B, NY, NX, part, part_floats, dW, err, s);
     if (cin == 64 && cout == 16) return launch_wgrad<64, 16>(h, g, B, NY, NX, part, part_floats, dW, err, s);
     return cudaErrorInvalidValue;
 }
