@@ -109,8 +109,14 @@ void lf_sur_destroy(lf_sur* s);
  *   v += resid;  out = v;  out2 = v * (mask > 0);
  *   y4[0..3] = x4[0..3] + (sum + bias)[0..3]  (FP32, unpadded [B][NY][NX][4]).
  * Every non-null BF16 output is written in the padded layout, halo included.
- * err (device int) is set to 1 if a bounded wait inside the kernel gave up.
- * Enqueued on stream; pointers 16-byte aligned. */
+ * The outputs must not overlap the inputs (other CTAs still read rows that a
+ * CTA writes).  resid may be the input itself (resid == in, cin == cout):
+ * it is then read from the input rows the kernel already holds in shared
+ * memory.  The input rows and the weights are read by TMA (tensor maps
+ * encoded per call through the driver's cuTensorMapEncodeTiled; LF_ECUDA if
+ * the driver lacks it).  err (device int) is set to 1 if a bounded wait
+ * inside the kernel gave up or the shared-memory window is not aligned for
+ * the swizzled layouts.  Enqueued on stream; pointers 16-byte aligned. */
 int lf_sur_conv3x3(int B, int NY, int NX, int cin, int cout, const void* in, const void* w,
                    const float* bias, int relu, const void* resid, const void* mask, void* out,
                    void* out2, void* zout, const float* x4, float* y4, int* err, void* stream);
@@ -119,7 +125,8 @@ int lf_sur_conv3x3(int B, int NY, int NX, int cin, int cout, const void* in, con
  * h[p + off_t][i] g[p][o] (FP32 [9][cout][cin]), h in the padded NHWC layout
  * with cin channels, g with cout channels (halo of g unused).  `part` is FP32
  * device scratch of at least lf_sur_wgrad_scratch_floats(cin, cout) floats
- * for the per-CTA partial sums (tensor cores), reduced in a second kernel. */
+ * for the per-CTA partial sums (tensor cores), reduced in a second kernel.
+ * For (64, 64) the rows of h and g are read by TMA (as above). */
 int lf_sur_conv3x3_wgrad(int B, int NY, int NX, int cin, int cout, const void* h, const void* g,
                          float* part, size_t part_floats, float* dW, int* err, void* stream);
 size_t lf_sur_wgrad_scratch_floats(int cin, int cout);
