@@ -877,6 +877,191 @@ cudaError_t launch_wgrad64(const __nv_bfloat16* h, const __nv_bfloat16* g, int B
     return cudaGetLastError();
 }
 
+// The 16 -> 64 weight gradient in the same form: h has 16 channels (32-byte
+// rows, 32-byte swizzle), so a row tile's three h rows (dy = -1, 0, 1) come
+// with its g row, and per 16 pixels one M = 64 x N = 48 MMA per dy covers the
+// three dx taps (B atoms of 16 channels one pixel apart).  An item is a slice
+// of row tiles with all nine taps (columns 16 t + i of a 144-column
+// accumulator), the partial layout of k_conv_wgrad<16, 64>.
+struct Wg16 {
+    static constexpr int NSLOT = 6;
+    static constexpr int G_BYTES = 128 * 128, H_ROW = 5 * 1024;       // g: 128 x 128 B; h: 130 x 32 B, padded
+    static constexpr int SLOT = G_BYTES + 3 * H_ROW;
+    static constexpr int TX = G_BYTES + 3 * 130 * 32;
+    static constexpr int BAR_OFF = NSLOT * SLOT;
+    static constexpr int NBAR = 2 * NSLOT + 2 + 2 + 1;
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int THREADS = 6 * 32;
+    static_assert(SLOT % 1024 == 0 && G_BYTES % 1024 == 0 && H_ROW % 1024 == 0, "swizzle patterns aligned");
+};
+
+__global__ void __launch_bounds__(Wg16::THREADS, 1)
+    k_wgrad16(const __grid_constant__ CUtensorMap tg, const __grid_constant__ CUtensorMap th, WgArgs a)
+{
+    using S = WgCfg<16, 64>;
+    using P = Wg16;
+    static_assert(S::NG == 1 && S::TG == 9 && S::NB == 16, "partial layout of k_conv_wgrad<16, 64>");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + P::BAR_OFF);
+    uint64_t* empty = full + P::NSLOT;
+    uint64_t* accf = empty + P::NSLOT;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NY = a.NY, NX = a.NX, ncb = NX / 128;
+    const int64_t R = (int64_t)a.B * ncb * NY;
+    constexpr int NITEM = S::SLICES;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (tid == 0) {
+        for (int i = 0; i < P::NSLOT; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], 4);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = (tc::smem_u32(smem) & 1023u) ? 1 : 0;
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const bool start = *abort_flag == 0;
+
+    if (warp == 4) {   // producer
+        if (lane == 0 && start) {
+            uint32_t ld = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
+                const int64_t r0 = R * it / NITEM, r1 = R * (it + 1) / NITEM;
+                for (int64_t r = r0; r < r1; ++r, ++ld) {
+                    const int64_t col = r / NY;
+                    const int y = (int)(r - col * NY), b = (int)(col / ncb), x0 = (int)(col - (int64_t)b * ncb) * 128;
+                    const uint32_t sl = ld % P::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&empty[sl], ((ld / P::NSLOT) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    unsigned char* dst = smem + sl * P::SLOT;
+                    tc::mbar_arrive_expect_tx(&full[sl], P::TX);
+                    tc::tma_load_3d(dst, &tg, 0, x0 + 1, b * (NY + 2) + y + 1, &full[sl]);
+                    for (int d = 0; d < 3; ++d)   // padded h rows y, y + 1, y + 2 (dy = d - 1)
+                        tc::tma_load_3d(dst + P::G_BYTES + d * P::H_ROW, &th, 0, x0, b * (NY + 2) + y + d, &full[sl]);
+                }
+            }
+            for (uint32_t k = ld > (uint32_t)P::NSLOT ? ld - P::NSLOT : 0u; k < ld; ++k)
+                tc::mbar_wait(&full[k % P::NSLOT], (k / P::NSLOT) & 1);
+        }
+    } else if (warp == 5) {   // MMA issue
+        if (lane == 0 && start) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(64, 48) | (1u << 15) | (1u << 16);   // both MN-major
+            const uint32_t base = tc::smem_u32(smem);
+            uint32_t ld = 0, u = 0;
+            bool ok = true, issued = false;
+            for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
+                const int64_t r0 = R * it / NITEM, r1 = R * (it + 1) / NITEM;
+                if (r1 <= r0) continue;
+                const uint32_t buf = u & 1, dcol = tmem + buf * 144;
+                if (!tc::mbar_wait_or_abort(&acce[buf], ((u >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                tc::fence_after_sync();
+                for (int64_t r = r0; r < r1; ++r, ++ld) {
+                    const uint32_t sl = ld % P::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&full[sl], (ld / P::NSLOT) & 1, abort_flag)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t gb = base + sl * P::SLOT, hb = gb + P::G_BYTES;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int s = 0; s < 8; ++s)   // 16 pixels per MMA
+                            tc::mma_bf16(dcol + 48 * d, tc::smem_desc_sw128_mn(gb + s * 2048, 1024, 1024),
+                                         tc::smem_desc_sw32_mn(hb + d * P::H_ROW + s * 512, 32, 256), idesc,
+                                         (r == r0 && s == 0) ? 0u : 1u);
+                    issued = true;
+                    tc::mma_commit(&empty[sl]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&accf[buf]);
+                ++u;
+            }
+            if (issued) {
+                tc::mma_commit(done);
+                tc::mbar_wait(done, 0);
+            }
+        }
+    } else if (start) {   // epilogue: M = 64 rows 16 w + l sit in lanes 32 w + l, l < 16
+        uint32_t u = 0;
+        const int o = 16 * warp + lane;
+        for (int it = blockIdx.x; it < NITEM; it += gridDim.x) {
+            const int64_t r0 = R * it / NITEM, r1 = R * (it + 1) / NITEM;
+            float* dst = a.part + (size_t)it * 9 * 64 * 16;   // [tap][o][i]
+            if (r1 <= r0) {
+                for (int q = lane; q < 9 * 16 * 16; q += 32) {   // this warp's 16 output channels
+                    const int t = q / 256, rem = q - t * 256;
+                    dst[((size_t)t * 64 + 16 * warp + rem / 16) * 16 + rem % 16] = 0.f;
+                }
+                continue;
+            }
+            const uint32_t buf = u & 1;
+            const bool w = tc::mbar_wait_or_abort(&accf[buf], (u >> 1) & 1, abort_flag);
+            if (!__all_sync(0xffffffffu, w)) break;
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + buf * 144 + (uint32_t)(16 * t), v);
+                if (lane < 16) {
+                    float4* d4 = reinterpret_cast<float4*>(dst + ((size_t)t * 64 + o) * 16);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[buf]);
+            ++u;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+cudaError_t launch_wgrad16(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
+                           size_t part_floats, float* dW, int* err, cudaStream_t s)
+{
+    using S = WgCfg<16, 64>;
+    static unsigned long long attr_done = 0;
+    if (cudaError_t e = raise_smem_limit(k_wgrad16, (int)Wg16::BYTES, &attr_done); e != cudaSuccess) return e;
+    if (part_floats < S::PART) return cudaErrorInvalidValue;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // g as [B (NY + 2)][NX + 2][64] (boxes of 128 pixels, 128-byte swizzle); h with 16 channels (130 pixels, 32-byte)
+    CUtensorMap mg, mh;
+    const cuuint64_t gdims[3] = {64, (cuuint64_t)NX + 2, (cuuint64_t)B * (NY + 2)};
+    const cuuint64_t gstr[2] = {128, (cuuint64_t)(NX + 2) * 128};
+    const cuuint64_t hdims[3] = {16, (cuuint64_t)NX + 2, (cuuint64_t)B * (NY + 2)};
+    const cuuint64_t hstr[2] = {32, (cuuint64_t)(NX + 2) * 32};
+    const cuuint32_t boxg[3] = {64, 128, 1}, boxh[3] = {16, 130, 1}, estr[3] = {1, 1, 1};
+    if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(g), gdims, gstr, boxg, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(h), hdims, hstr, boxh, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    int sms = 0;
+    if (cudaError_t e = device_sms(&sms); e != cudaSuccess) return e;
+    WgArgs a{h, g, part, B, NY, NX, err};
+    k_wgrad16<<<S::SLICES < sms ? S::SLICES : sms, Wg16::THREADS, Wg16::BYTES, s>>>(mg, mh, a);
+    const int n = 9 * 64 * 16;
+    k_wgrad_reduce<16, 64><<<(n + 255) / 256, 256, 0, s>>>(part, dW);
+    return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
                          size_t part_floats, float* dW, int* err, cudaStream_t s)
@@ -896,7 +1081,7 @@ cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, 
 cudaError_t conv3x3_wgrad(int cin, int cout, const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX,
                           float* part, size_t part_floats, float* dW, int* err, cudaStream_t s)
 {
-    if (cin == 16 && cout == 64) return launch_wgrad<16, 64>(h, g, B, NY, NX, part, part_floats, dW, err, s);
+    if (cin == 16 && cout == 64) return launch_wgrad16(h, g, B, NY, NX, part, part_floats, dW, err, s);
     if (cin == 64 && cout == 64) return launch_wgrad64(h, g, B, NY, NX, part, part_floats, dW, err, s);
     if (cin == 64 && cout == 16) return launch_wgrad<64, 16>(h, g, B, NY, NX, part, part_floats, dW, err, s);
     return cudaErrorInvalidValue;

@@ -69,6 +69,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw128_mn(uint32_t saddr, uint32_t 
     return d;
 }
 
+// MN-major operand in the 32-byte swizzled layout (atoms of 16 elements x 8 K
+// rows of 32 bytes, 256-byte patterns): lbo between 16-element atoms along M
+// or N, sbo between groups of eight K rows.
+__device__ __forceinline__ uint64_t smem_desc_sw32_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;                          // layout: 32-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D in FP32, A and B in
 // BF16, both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
