@@ -477,36 +477,23 @@ cudaError_t conv3x3(int cin, int cout, const ConvArgs& a, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // Weight gradient of a 3x3 convolution on the tensor cores:
 //   dW[t][o][i] = sum_p h[p + off_t][i] g[p][o]
-// For each tap a GEMM D_t = A B^T with K = pixels, M = 64 (the 64-channel
-// side: i for CIN = 64, else o) and N = the other side.  Both operands are
-// read MN-major straight from rows staged in the pixel-major core-matrix
-// layout of the forward kernel ([channel group][pixel][8 channels]): a core
-// matrix is 8 consecutive pixels (K) of 8 channels (MN), so the tap shift dx
-// is a 16-byte move of the descriptor start and nothing is transposed.  A
-// work item is a run of row tiles (128 pixels of one image row) for one
-// group of taps; it accumulates all of its rows in TMEM (one M = 64
-// accumulator per tap) and writes one FP32 partial, summed by
-// k_wgrad_reduce.  For 64 -> 64 the taps are split in three groups by dy
-// (TMEM holds 3 x 64 columns); otherwise one group holds all nine.
+// a GEMM over pixels (K) per tap, with the 64-channel side as M = 64 (i for
+// CIN = 64, else o) and the other as N.  A work item is a slice of the row
+// tiles (128 pixels of one image row) for one group of taps; it accumulates
+// all of its rows in TMEM and writes one FP32 partial [tap][M][N], summed over
+// the items by k_wgrad_reduce.  For 64 -> 64 the taps are split in three
+// groups by dy; otherwise one group holds all nine.  The kernels below
+// (k_wgrad64, k_wgrad16, k_wgrad_o16) stream the rows by TMA in swizzled
+// MN-major layouts, where the tap shift dx is a 128- or 32-byte move of a
+// descriptor start or of an M / N atom.
 // ---------------------------------------------------------------------------
-// threads of the weight-gradient kernel (its time goes to the chain of
-// M = 64 MMAs of each row, not to the staging copies: 256 threads measured
-// the same, 214 us against 208 us for 64 -> 64 at 8 x 256^2)
-constexpr int kWgThreads = 128;
-
 template <int CIN, int COUT>
 struct WgCfg {
-    static constexpr bool HA = CIN == 64;                  // h is the M = 64 operand
-    static constexpr int NB = HA ? COUT : CIN;             // N of the GEMM
+    static constexpr bool HA = CIN == 64;                  // h is the M = 64 operand of the partial
+    static constexpr int NB = HA ? COUT : CIN;             // N of the partial
     static constexpr int NG = (CIN == 64 && COUT == 64) ? 3 : 1;
     static constexpr int TG = 9 / NG;                      // taps per group
     static constexpr int SLICES = (2 * 152) / NG;          // items per group
-    static constexpr int RH = 130, RG = 128;               // pixels per staged h / g row
-    static constexpr int HROW = (CIN / 8) * RH * 16, GROW = (COUT / 8) * RG * 16;
-    static constexpr int NSH = NG == 3 ? 4 : 6, NSG = 4;
-    static constexpr int H_OFF = 0, G_OFF = NSH * HROW, BAR_OFF = G_OFF + NSG * GROW;
-    static constexpr int BYTES = BAR_OFF + 64;
-    static constexpr int TCOLS = TG * NB <= 32 ? 32 : (TG * NB <= 64 ? 64 : (TG * NB <= 128 ? 128 : 256));
     static constexpr size_t PART = (size_t)NG * SLICES * TG * 64 * NB;   // floats
 };
 
@@ -517,153 +504,6 @@ struct WgArgs {
     int B, NY, NX;
     int* err;
 };
-
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(kWgThreads, 1) k_conv_wgrad(WgArgs a)
-{
-    using S = WgCfg<CIN, COUT>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sH = smem + S::H_OFF;
-    unsigned char* sG = smem + S::G_OFF;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);      // one per g slot
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + 48);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NY = a.NY, NX = a.NX;
-    const int ncb = NX / 128;
-    const int64_t R = (int64_t)a.B * ncb * NY;                 // row tiles, ordered (b, cb, y)
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(64, S::NB) | (1u << 15) | (1u << 16);   // both MN-major
-
-    if (warp == 0) tc::tmem_alloc(tslot, S::TCOLS);
-    if (tid == 0) {
-        for (int k = 0; k < S::NSG; ++k) tc::mbar_init(&bar[k], 1);
-        tc::fence_mbar_init();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = *tslot;
-    uint32_t ph[S::NSG] = {};
-    bool ok = true;
-
-    auto commit = [] { asm volatile("cp.async.commit_group;\n" ::: "memory"); };
-    // padded h row pr, pixels x0 - 1 .. x0 + 128, into h slot pr mod NSH
-    auto load_h = [&](int b, int pr, int x0) {
-        unsigned char* dst = sH + (pr % S::NSH) * S::HROW;
-        const __nv_bfloat16* src = a.h + (((int64_t)b * (NY + 2) + pr) * (NX + 2) + x0) * CIN;
-        for (int q = tid; q < S::RH * (CIN / 8); q += kWgThreads) {
-            const int px = q / (CIN / 8), j = q - px * (CIN / 8);
-            tc::cp_async16(dst + j * (S::RH * 16) + px * 16, src + (int64_t)px * CIN + 8 * j);
-        }
-    };
-    // g row y, pixels x0 .. x0 + 127, into g slot y mod NSG
-    auto load_g = [&](int b, int y, int x0) {
-        unsigned char* dst = sG + (y % S::NSG) * S::GROW;
-        const __nv_bfloat16* src = a.g + (((int64_t)b * (NY + 2) + y + 1) * (NX + 2) + x0 + 1) * COUT;
-        for (int q = tid; q < S::RG * (COUT / 8); q += kWgThreads) {
-            const int px = q / (COUT / 8), j = q - px * (COUT / 8);
-            tc::cp_async16(dst + j * (S::RG * 16) + px * 16, src + (int64_t)px * COUT + 8 * j);
-        }
-    };
-    // everything output row y of this group reads that is not already staged
-    // by earlier rows: g row y and the newest h row(s)
-    auto load_rows_for = [&](int b, int y, int x0, int gi, bool first) {
-        load_g(b, y, x0);
-        if (S::NG == 3) {
-            load_h(b, y + gi, x0);                 // padded row y + dy + 1, dy = gi - 1
-        } else if (first) {
-            load_h(b, y, x0); load_h(b, y + 1, x0); load_h(b, y + 2, x0);
-        } else {
-            load_h(b, y + 2, x0);
-        }
-    };
-
-    for (int item = blockIdx.x; item < S::NG * S::SLICES && ok; item += gridDim.x) {
-        const int gi = item / S::SLICES, sl = item - gi * S::SLICES;
-        const int64_t r0 = R * sl / S::SLICES, r1 = R * (sl + 1) / S::SLICES;
-        const int t0 = gi * S::TG;
-        bool first_row = true;
-        for (int64_t r = r0; r < r1 && ok;) {
-            // one run of consecutive rows of one (image, column block)
-            const int64_t bc = r / NY;
-            const int ya = (int)(r - bc * NY);
-            const int64_t rend = min(r1, (bc + 1) * NY);
-            const int yb = ya + (int)(rend - r);
-            const int cb = (int)(bc % ncb), b = (int)(bc / ncb);
-            const int x0 = cb * 128;
-            load_rows_for(b, ya, x0, gi, true);
-            commit();
-            if (ya + 1 < yb) load_rows_for(b, ya + 1, x0, gi, false);
-            commit();
-            for (int y = ya; y < yb; ++y) {
-                asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // rows of output row y landed
-                tc::fence_proxy_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (tid == 0) {
-                    const uint32_t gb = tc::smem_u32(sG + (y % S::NSG) * S::GROW);
-#pragma unroll
-                    for (int j = 0; j < S::TG; ++j) {
-                        const int t = t0 + j, dy = t / 3 - 1, dx = t % 3 - 1;
-                        const uint32_t hb = tc::smem_u32(sH + ((y + dy + 1) % S::NSH) * S::HROW) + (dx + 1) * 16;
-#pragma unroll
-                        for (int s = 0; s < 8; ++s) {            // 16 pixels per MMA
-                            const uint64_t hd = tc::smem_desc(hb + 256 * s, 128, S::RH * 16);
-                            const uint64_t gd = tc::smem_desc(gb + 256 * s, 128, S::RG * 16);
-                            tc::mma_bf16(tmem + (uint32_t)(j * S::NB), S::HA ? hd : gd, S::HA ? gd : hd, idesc,
-                                         (first_row && s == 0) ? 0u : 1u);
-                        }
-                    }
-                    tc::mma_commit(&bar[y % S::NSG]);
-                }
-                first_row = false;
-                if (y >= ya + 2) {   // MMAs of row y - 2 done: its slots may be refilled
-                    const int k = (y - 2) % S::NSG;
-                    const bool w = tc::mbar_wait(&bar[k], ph[k]);
-                    ph[k] ^= 1;
-                    if (__syncthreads_or(!w)) { ok = false; break; }
-                }
-                if (y + 2 < yb) load_rows_for(b, y + 2, x0, gi, false);
-                commit();
-            }
-            if (!ok) break;
-            for (int y = max(ya, yb - 2); y < yb; ++y) {   // the last two rows' MMAs
-                const int k = y % S::NSG;
-                const bool w = tc::mbar_wait(&bar[k], ph[k]);
-                ph[k] ^= 1;
-                if (__syncthreads_or(!w)) { ok = false; break; }
-            }
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            r = rend;
-        }
-        if (!ok) break;
-        // partial of this item: M = 64 accumulator rows 16 w + l sit in lanes 32 w + l, l < 16
-        // (warps 0..3, one TMEM lane quarter each)
-        float* dst = a.part + ((size_t)item * S::TG) * 64 * S::NB;
-        const int m = 16 * warp + lane;
-#pragma unroll
-        for (int j = 0; j < (warp < 4 ? S::TG : 0); ++j)
-#pragma unroll
-            for (int c0 = 0; c0 < S::NB; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * S::NB + c0), v);
-                if (lane < 16)
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) dst[((size_t)j * 64 + m) * S::NB + c0 + i] = first_row ? 0.f : v[i];
-            }
-        tc::fence_before_sync();
-        __syncthreads();   // accumulators read before the next item's first MMA
-        tc::fence_after_sync();
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (!ok && tid == 0) atomicExch(a.err, 1);
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, S::TCOLS);
-}
 
 // dW[t][o][i] = sum over the group's items of part[item][t - t0][m][n]
 template <int CIN, int COUT>
@@ -683,9 +523,9 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient of the 64 -> 64 convolution as a warp pipeline.  The items
-// and the partial layout are those of k_conv_wgrad<64, 64> (three tap groups
-// by dy, each over a slice of the row tiles); per row tile the producer warp
+// Weight gradient of the 64 -> 64 convolution as a warp pipeline over the
+// items of WgCfg<64, 64> (three tap groups by dy, each over a slice of the row
+// tiles, partials [tap][i][o]); per row tile the producer warp
 // brings g (128 pixels) and the h row of the group's dy (130 pixels) by TMA in
 // the 128-byte swizzled layout, which is MN-major for this GEMM (a pixel is a
 // K row of 64 channels).  The MMA warp takes M = 64 from g (output channel o)
@@ -812,7 +652,7 @@ __global__ void __launch_bounds__(Wg64::THREADS, 1)
         for (int it = blockIdx.x; it < NITEM; it += gridDim.x) {
             int64_t r0, r1;
             item_rows(it, r0, r1);
-            float* dst = a.part + (size_t)it * 3 * 64 * 64;   // [tap j][i][o] as k_wgrad_reduce<64, 64> reads it
+            float* dst = a.part + (size_t)it * 3 * 64 * 64;   // [tap j][i][o]
             if (r1 <= r0) {
                 for (int q = lane; q < 3 * 64 * 16; q += 32) {   // this warp's 16 output channels
                     const int j = q / (64 * 16), rem = q - j * 64 * 16;
@@ -882,7 +722,7 @@ cudaError_t launch_wgrad64(const __nv_bfloat16* h, const __nv_bfloat16* g, int B
 // with its g row, and per 16 pixels one M = 64 x N = 48 MMA per dy covers the
 // three dx taps (B atoms of 16 channels one pixel apart).  An item is a slice
 // of row tiles with all nine taps (columns 16 t + i of a 144-column
-// accumulator), the partial layout of k_conv_wgrad<16, 64>.
+// accumulator), partials [tap][o][i].
 struct Wg16 {
     static constexpr int NSLOT = 6;
     static constexpr int G_BYTES = 128 * 128, H_ROW = 5 * 1024;       // g: 128 x 128 B; h: 130 x 32 B, padded
@@ -900,7 +740,7 @@ __global__ void __launch_bounds__(Wg16::THREADS, 1)
 {
     using S = WgCfg<16, 64>;
     using P = Wg16;
-    static_assert(S::NG == 1 && S::TG == 9 && S::NB == 16, "partial layout of k_conv_wgrad<16, 64>");
+    static_assert(S::NG == 1 && S::TG == 9 && S::NB == 16, "one item group of nine taps, 16 columns each");
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + P::BAR_OFF);
     uint64_t* empty = full + P::NSLOT;
@@ -1062,19 +902,194 @@ cudaError_t launch_wgrad16(const __nv_bfloat16* h, const __nv_bfloat16* g, int B
     return cudaGetLastError();
 }
 
-template <int CIN, int COUT>
-cudaError_t launch_wgrad(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
-                         size_t part_floats, float* dW, int* err, cudaStream_t s)
+// The 64 -> 16 weight gradient in the same form: here the shifted operand h
+// (64 channels) is the M side, so per dy group and 16 pixels the taps
+// dx = -1, 0 go into one M = 128 MMA (two M atoms one pixel apart; TMEM lanes
+// 0-63 and 64-127) and dx = +1 into one M = 64 MMA, N = 16 output channels
+// from g (32-byte swizzle).  A row tile's three h rows come with its g row;
+// partials [tap][i][o].
+struct WgO16 {
+    static constexpr int NSLOT = 3;
+    static constexpr int G_BYTES = 4096, H_ROW = 17 * 1024;           // g: 128 x 32 B; h: 130 x 128 B, padded
+    static constexpr int SLOT = G_BYTES + 3 * H_ROW;
+    static constexpr int TX = 128 * 32 + 3 * 130 * 128;
+    static constexpr int BAR_OFF = NSLOT * SLOT;
+    static constexpr int NBAR = 2 * NSLOT + 2 + 2 + 1;
+    static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
+    static constexpr int THREADS = 6 * 32;
+    static_assert(SLOT % 1024 == 0 && G_BYTES % 1024 == 0 && H_ROW % 1024 == 0, "swizzle patterns aligned");
+};
+
+__global__ void __launch_bounds__(WgO16::THREADS, 1)
+    k_wgrad_o16(const __grid_constant__ CUtensorMap tg, const __grid_constant__ CUtensorMap th, WgArgs a)
 {
-    using S = WgCfg<CIN, COUT>;
-    static unsigned long long attr_done = 0;      // per instantiation and device
-    if (cudaError_t e = raise_smem_limit(k_conv_wgrad<CIN, COUT>, (int)S::BYTES, &attr_done); e != cudaSuccess)
-        return e;
+    using S = WgCfg<64, 16>;
+    using P = WgO16;
+    static_assert(S::NG == 1 && S::TG == 9 && S::NB == 16 && S::HA, "one item group of nine taps, [i][o] partials");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + P::BAR_OFF);
+    uint64_t* empty = full + P::NSLOT;
+    uint64_t* accf = empty + P::NSLOT;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NY = a.NY, NX = a.NX, ncb = NX / 128;
+    const int64_t R = (int64_t)a.B * ncb * NY;
+    constexpr int NITEM = S::SLICES;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    if (tid == 0) {
+        for (int i = 0; i < P::NSLOT; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], 4);
+        }
+        tc::mbar_init(done, 1);
+        *abort_flag = (tc::smem_u32(smem) & 1023u) ? 1 : 0;
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const bool start = *abort_flag == 0;
+
+    if (warp == 4) {   // producer
+        if (lane == 0 && start) {
+            uint32_t ld = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
+                const int64_t r0 = R * it / NITEM, r1 = R * (it + 1) / NITEM;
+                for (int64_t r = r0; r < r1; ++r, ++ld) {
+                    const int64_t col = r / NY;
+                    const int y = (int)(r - col * NY), b = (int)(col / ncb), x0 = (int)(col - (int64_t)b * ncb) * 128;
+                    const uint32_t sl = ld % P::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&empty[sl], ((ld / P::NSLOT) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                    unsigned char* dst = smem + sl * P::SLOT;
+                    tc::mbar_arrive_expect_tx(&full[sl], P::TX);
+                    tc::tma_load_3d(dst, &tg, 0, x0 + 1, b * (NY + 2) + y + 1, &full[sl]);
+                    for (int d = 0; d < 3; ++d)   // padded h rows y, y + 1, y + 2 (dy = d - 1)
+                        tc::tma_load_3d(dst + P::G_BYTES + d * P::H_ROW, &th, 0, x0, b * (NY + 2) + y + d, &full[sl]);
+                }
+            }
+            for (uint32_t k = ld > (uint32_t)P::NSLOT ? ld - P::NSLOT : 0u; k < ld; ++k)
+                tc::mbar_wait(&full[k % P::NSLOT], (k / P::NSLOT) & 1);
+        }
+    } else if (warp == 5) {   // MMA issue
+        if (lane == 0 && start) {
+            constexpr uint32_t id128 = tc::idesc_bf16_f32(128, 16) | (1u << 15) | (1u << 16);   // both MN-major
+            constexpr uint32_t id64 = tc::idesc_bf16_f32(64, 16) | (1u << 15) | (1u << 16);
+            const uint32_t base = tc::smem_u32(smem);
+            uint32_t ld = 0, u = 0;
+            bool ok = true, issued = false;
+            for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
+                const int64_t r0 = R * it / NITEM, r1 = R * (it + 1) / NITEM;
+                if (r1 <= r0) continue;
+                const uint32_t buf = u & 1, dcol = tmem + buf * 96;
+                if (!tc::mbar_wait_or_abort(&acce[buf], ((u >> 1) & 1) ^ 1, abort_flag)) { ok = false; break; }
+                tc::fence_after_sync();
+                for (int64_t r = r0; r < r1; ++r, ++ld) {
+                    const uint32_t sl = ld % P::NSLOT;
+                    if (!tc::mbar_wait_or_abort(&full[sl], (ld / P::NSLOT) & 1, abort_flag)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t gb = base + sl * P::SLOT, hb = gb + P::G_BYTES;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) {   // 16 pixels per MMA
+                            const uint64_t bd = tc::smem_desc_sw32_mn(gb + s * 512, 32, 256);
+                            const uint32_t ha = hb + d * P::H_ROW + s * 2048;
+                            const uint32_t acc = (r == r0 && s == 0) ? 0u : 1u;
+                            tc::mma_bf16(dcol + 32 * d, tc::smem_desc_sw128_mn(ha, 128, 1024), bd, id128, acc);
+                            tc::mma_bf16(dcol + 32 * d + 16, tc::smem_desc_sw128_mn(ha + 256, 1024, 1024), bd, id64, acc);
+                        }
+                    issued = true;
+                    tc::mma_commit(&empty[sl]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&accf[buf]);
+                ++u;
+            }
+            if (issued) {
+                tc::mma_commit(done);
+                tc::mbar_wait(done, 0);
+            }
+        }
+    } else if (start) {   // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31
+        uint32_t u = 0;
+        for (int it = blockIdx.x; it < NITEM; it += gridDim.x) {
+            const int64_t r0 = R * it / NITEM, r1 = R * (it + 1) / NITEM;
+            float* dst = a.part + (size_t)it * 9 * 64 * 16;   // [tap][i][o]
+            if (r1 <= r0) {
+                for (int q = tid; q < 9 * 64 * 16; q += 128) dst[q] = 0.f;
+                continue;
+            }
+            const uint32_t buf = u & 1;
+            const bool w = tc::mbar_wait_or_abort(&accf[buf], (u >> 1) & 1, abort_flag);
+            if (!__all_sync(0xffffffffu, w)) break;
+            tc::fence_after_sync();
+            auto put = [&](int t, int i, const float* v) {
+                float4* d4 = reinterpret_cast<float4*>(dst + ((size_t)t * 64 + i) * 16);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            };
+#pragma unroll 1
+            for (int d = 0; d < 3; ++d) {
+                float v[16];
+                // M = 128: row m = lane 32 w + l is tap dx = m / 64 - 1 of channel i = m mod 64
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + buf * 96 + (uint32_t)(32 * d), v);
+                const int m = 32 * warp + lane;
+                put(3 * d + m / 64, m % 64, v);
+                // M = 64 (tap dx = +1): row m = 16 w + l sits in lane 32 w + l, l < 16
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + buf * 96 + (uint32_t)(32 * d + 16), v);
+                if (lane < 16) put(3 * d + 2, 16 * warp + lane, v);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[buf]);
+            ++u;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+cudaError_t launch_wgrad_o16(const __nv_bfloat16* h, const __nv_bfloat16* g, int B, int NY, int NX, float* part,
+                             size_t part_floats, float* dW, int* err, cudaStream_t s)
+{
+    using S = WgCfg<64, 16>;
+    static unsigned long long attr_done = 0;
+    if (cudaError_t e = raise_smem_limit(k_wgrad_o16, (int)WgO16::BYTES, &attr_done); e != cudaSuccess) return e;
     if (part_floats < S::PART) return cudaErrorInvalidValue;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    // g with 16 channels (boxes of 128 pixels, 32-byte swizzle); h with 64 (130 pixels, 128-byte)
+    CUtensorMap mg, mh;
+    const cuuint64_t gdims[3] = {16, (cuuint64_t)NX + 2, (cuuint64_t)B * (NY + 2)};
+    const cuuint64_t gstr[2] = {32, (cuuint64_t)(NX + 2) * 32};
+    const cuuint64_t hdims[3] = {64, (cuuint64_t)NX + 2, (cuuint64_t)B * (NY + 2)};
+    const cuuint64_t hstr[2] = {128, (cuuint64_t)(NX + 2) * 128};
+    const cuuint32_t boxg[3] = {16, 128, 1}, boxh[3] = {64, 130, 1}, estr[3] = {1, 1, 1};
+    if (enc(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(g), gdims, gstr, boxg, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&mh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(h), hdims, hstr, boxh, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    int sms = 0;
+    if (cudaError_t e = device_sms(&sms); e != cudaSuccess) return e;
     WgArgs a{h, g, part, B, NY, NX, err};
-    k_conv_wgrad<CIN, COUT><<<152, kWgThreads, S::BYTES, s>>>(a);
-    const int n = 9 * COUT * CIN;
-    k_wgrad_reduce<CIN, COUT><<<(n + 255) / 256, 256, 0, s>>>(part, dW);
+    k_wgrad_o16<<<S::SLICES < sms ? S::SLICES : sms, WgO16::THREADS, WgO16::BYTES, s>>>(mg, mh, a);
+    const int n = 9 * 16 * 64;
+    k_wgrad_reduce<64, 16><<<(n + 255) / 256, 256, 0, s>>>(part, dW);
     return cudaGetLastError();
 }
 
@@ -1083,7 +1098,7 @@ cudaError_t conv3x3_wgrad(int cin, int cout, const __nv_bfloat16* h, const __nv_
 {
     if (cin == 16 && cout == 64) return launch_wgrad16(h, g, B, NY, NX, part, part_floats, dW, err, s);
     if (cin == 64 && cout == 64) return launch_wgrad64(h, g, B, NY, NX, part, part_floats, dW, err, s);
-    if (cin == 64 && cout == 16) return launch_wgrad<64, 16>(h, g, B, NY, NX, part, part_floats, dW, err, s);
+    if (cin == 64 && cout == 16) return launch_wgrad_o16(h, g, B, NY, NX, part, part_floats, dW, err, s);
     return cudaErrorInvalidValue;
 }
 
