@@ -562,6 +562,7 @@ __global__ void __launch_bounds__(Wg64::THREADS, 1)
     const int NY = a.NY, NX = a.NX, ncb = NX / 128;
     const int64_t R = (int64_t)a.B * ncb * NY;
     constexpr int NITEM = S::NG * S::SLICES;
+    static_assert(S::NG == 3 && S::TG == 3, "three tap groups by dy");
 
     if (warp == 0) tc::tmem_alloc(tslot, 512);
     if (tid == 0) {
@@ -582,9 +583,12 @@ __global__ void __launch_bounds__(Wg64::THREADS, 1)
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
     const bool start = *abort_flag == 0;
-    // the rows of item `it`: [r0, r1) of the row tiles ordered (image, column block, row)
+    // item `it` is tap group it mod 3 of slice it / 3, so that the three groups
+    // of a slice run on neighbouring CTAs at the same time and share their g and
+    // h rows in L2; its rows are [r0, r1) of the row tiles ordered (image,
+    // column block, row), its partial sits at group * SLICES + slice
     auto item_rows = [&](int it, int64_t& r0, int64_t& r1) {
-        const int sl = it % S::SLICES;
+        const int sl = it / 3;
         r0 = R * sl / S::SLICES;
         r1 = R * (sl + 1) / S::SLICES;
     };
@@ -594,7 +598,7 @@ __global__ void __launch_bounds__(Wg64::THREADS, 1)
             uint32_t ld = 0;
             bool ok = true;
             for (int it = blockIdx.x; it < NITEM && ok; it += gridDim.x) {
-                const int gi = it / S::SLICES;          // padded h row y + gi: dy = gi - 1
+                const int gi = it % 3;                  // padded h row y + gi: dy = gi - 1
                 int64_t r0, r1;
                 item_rows(it, r0, r1);
                 for (int64_t r = r0; r < r1; ++r, ++ld) {
@@ -652,7 +656,7 @@ __global__ void __launch_bounds__(Wg64::THREADS, 1)
         for (int it = blockIdx.x; it < NITEM; it += gridDim.x) {
             int64_t r0, r1;
             item_rows(it, r0, r1);
-            float* dst = a.part + (size_t)it * 3 * 64 * 64;   // [tap j][i][o]
+            float* dst = a.part + (size_t)((it % 3) * S::SLICES + it / 3) * 3 * 64 * 64;   // [tap j][i][o]
             if (r1 <= r0) {
                 for (int q = lane; q < 3 * 64 * 16; q += 32) {   // this warp's 16 output channels
                     const int j = q / (64 * 16), rem = q - j * 64 * 16;
