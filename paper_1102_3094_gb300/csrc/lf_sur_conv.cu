@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
     unsigned char* sB = smem + S::B_OFF;
     unsigned char* sR = smem + S::R_OFF;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);   // ring slot loaded
-    uint64_t* empty = full + S::NSLOT;                                   // ring slot read by its last MMA
+    uint64_t* empty = full + S::NSLOT;                                   // ring slot read (MMAs, ring residual)
     uint64_t* accf = empty + S::NSLOT;                                   // accumulator complete
     uint64_t* acce = accf + S::NACC;                                     // accumulator read by the epilogue
     uint64_t* done = acce + S::NACC;                                     // every MMA of the CTA complete
@@ -170,8 +170,9 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
     const bool start = *abort_flag == 0;
 
     if (warp == EW) {
-        // TMA producer: padded rows ya .. yb + 1 of each segment into the ring,
-        // one box (130 pixels x 8 channels) per k core
+        // TMA producer: the weights, then padded rows ya .. yb + 1 of each
+        // segment into the ring, one box per row (64 channels, swizzled) or per
+        // k core (8 channels)
         if (lane == 0 && start) {
             if (S::SW) {   // the 9 weight taps, one swizzled box of COUT rows x 64 channels each
                 tc::mbar_arrive_expect_tx(wbar, 9 * S::B_TAP);
@@ -196,7 +197,9 @@ __global__ void __launch_bounds__(conv_threads<COUT>(), 1)
                 }
                 q += g.yb - g.ya;
             }
-            // leave no copy in flight: the newest load of every slot has landed
+            // leave no copy in flight: the weights and the newest load of every
+            // slot have landed (after an abort the MMA warp may not have waited)
+            if (S::SW) tc::mbar_wait(wbar, 0);
             for (uint32_t k = ld > (uint32_t)S::NSLOT ? ld - S::NSLOT : 0u; k < ld; ++k)
                 tc::mbar_wait(&full[k % S::NSLOT], (k / S::NSLOT) & 1);
         }
