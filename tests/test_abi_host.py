@@ -153,3 +153,42 @@ def test_checked_mode_adds_guard_bands(L, monkeypatch):
     plain = L.lf_workspace_bytes(g, w, p)
     monkeypatch.setenv("LF_CHECKED", "1")
     assert L.lf_workspace_bytes(g, w, p) == plain + 10 * 64 * 1024
+
+
+def test_convolution_calls_refuse_bad_arguments(L):
+    """The surrogate's convolution entry points check their arguments before
+    any CUDA call (shapes the tensor-core kernels take, 16-byte alignment of
+    every buffer that TMA or vector accesses read, required outputs, scratch
+    size); the pointers below are never dereferenced."""
+    lib = L._sur2_lib()
+    EINVAL = L.LF_EINVAL
+    p = C.c_void_p(0x10000)             # 16-byte aligned, never dereferenced
+    q = C.c_void_p(0x10008)             # 8-byte aligned only
+    conv = lib.lf_sur_conv3x3
+
+    def c(B=2, NY=8, NX=256, cin=64, cout=64, inp=p, w=p, out=p, resid=None, mask=None, out2=None, zout=None,
+          x4=None, y4=None, err=p):
+        return conv(B, NY, NX, cin, cout, inp, w, None, 1, resid, mask, out, out2, zout, x4, y4, err, None)
+
+    assert c(NX=200) == EINVAL            # NX not a multiple of the 128-pixel tile
+    assert c(NX=0) == EINVAL
+    assert c(B=0) == EINVAL
+    assert c(cin=32) == EINVAL            # (cin, cout) outside the three layer shapes
+    assert c(cin=16, cout=16) == EINVAL
+    assert c(inp=q) == EINVAL             # TMA and vector accesses need 16-byte alignment
+    assert c(resid=q) == EINVAL
+    assert c(out=None) == EINVAL          # nothing to write
+    assert c(mask=p) == EINVAL            # a mask needs out2
+    assert c(cout=16, cin=64, out=None, y4=p) == EINVAL   # y4 needs x4
+    assert c(err=None) == EINVAL
+
+    sc = lib.lf_sur_wgrad_scratch_floats
+    assert sc(64, 64) == 3 * (2 * 152 // 3) * 3 * 64 * 64     # three tap groups by dy
+    assert sc(16, 64) == (2 * 152) * 9 * 64 * 16              # one group of nine taps
+    assert sc(64, 16) == (2 * 152) * 9 * 64 * 16
+    assert sc(32, 64) == 0
+    wg = lib.lf_sur_conv3x3_wgrad
+    assert wg(2, 8, 256, 64, 64, p, p, p, sc(64, 64) - 1, p, p, None) == EINVAL   # scratch too small
+    assert wg(2, 8, 200, 64, 64, p, p, p, sc(64, 64), p, p, None) == EINVAL
+    assert wg(2, 8, 256, 64, 64, q, p, p, sc(64, 64), p, p, None) == EINVAL
+    assert wg(2, 8, 256, 64, 32, p, p, p, 1 << 30, p, p, None) == EINVAL
